@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: Riemannian shading of a 1920x1080 view field through the graph
+metric of 64 Gaussian bumps (FP32 RK4, h = 0.005, at most 2000 steps), with 32
+spheres and a 10k-triangle mesh in a BVH.  One step = one full frame traced by
+the persistent geodesic kernel through the C ABI (every ray of the frame).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2005_05386_gb300 import scenes  # noqa: E402
+
+METRIC = "Mrays/s at 1080p/64 bumps (FP32 RK4 h=0.005, <=2000 steps); RK4 steps/s alongside"
+UNIT = "Mrays/s"
+SM_MAX_MHZ_FALLBACK = 2070.0
+FLOPS_PER_BUMP = 27        # per bump per right-hand side: 9 FFMA (x2) + 6 FMUL + 3 FADD
+FLOPS_PER_RHS_EXTRA = 20   # per right-hand side outside the bump loop
+FLOPS_PER_STEP_EXTRA = 70  # RK4 stage combination and compensated update
+CPU_SAMPLE_FRACTION = 0.002
+
+
+def workload(name: str, resolution: str | None = None) -> scenes.Workload:
+    if name == "1080p_64":
+        w = scenes.config_1080p_64()
+    elif name == "1080p_twist":
+        w = scenes.config_1080p_twist()
+    elif name == "parity_64":
+        w = scenes.config_parity_64()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if resolution:
+        W, H = (int(v) for v in resolution.lower().split("x"))
+        w = scenes.scaled(w, W, H)
+    return w
+
+
+def flops_per_rk4_step(K: int) -> int:
+    return 4 * (K * FLOPS_PER_BUMP + FLOPS_PER_RHS_EXTRA) + FLOPS_PER_STEP_EXTRA
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_05386_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}.traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("RGEO_BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(w: scenes.Workload):
+    px = scenes.pixel_sample(w.n_pixels, w.seed + 1000, CPU_SAMPLE_FRACTION)
+    return px
+
+
+def run_oracle(w, px, threads):
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.trace(w, px, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return dt, o
+
+
+def cpu_baseline(w, threads=None):
+    import oracle
+    threads = threads or oracle.default_threads()
+    px = oracle_sample(w)
+    dt, o = run_oracle(w, px, threads)
+    steps = int(o["steps"].astype(np.int64).sum())
+    return {"value": len(px) / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(px)} seeded pixels of the {w.width}x{w.height} frame "
+                      f"(SplitMix64 1-in-{int(1 / CPU_SAMPLE_FRACTION)} sample), FP64, {dt:.2f} s wall",
+            "rk4_steps_per_s": steps / dt}
+
+
+def bench_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    import oracle
+    w = workload(args.workload, args.resolution)
+    threads = oracle.default_threads()
+    px = oracle_sample(w)
+    for _ in range(args.warmup):
+        run_oracle(w, px, threads)
+    times, steps = [], 0
+    for _ in range(args.steps):
+        dt, o = run_oracle(w, px, threads)
+        times.append(dt)
+        steps = int(o["steps"].astype(np.int64).sum())
+    total = sum(times)
+    value = len(px) * args.steps / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 scene)",
+            "config": {"workload": w.name, "width": w.width, "height": w.height, "bumps": w.metric.n_bumps,
+                       "h": w.h, "max_steps": w.max_steps, "integrator": "rk4", "sample_pixels": len(px)},
+            "rk4_steps_per_s": steps * args.steps / total,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{len(px)} seeded pixels per step of the {w.width}x{w.height} frame"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def bench_gpu(args):
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+    import paper_2005_05386_gb300 as rg
+    torch.cuda.set_device(local)
+    w = workload(args.workload, args.resolution)
+    K = w.metric.n_bumps
+    N = w.n_pixels
+    metric, scene = rg.Metric(w.metric), rg.Scene(w.scene)
+    out = rg.alloc_outputs(N)
+    cam = rg.camera_struct(w.camera)
+    ostruct = rg.outputs_struct(out)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def frame():
+        rg.rgeo_trace(metric.handle, scene.handle, cam, w.width, w.height, w.h, w.max_steps, w.integrator,
+                      w.shading, 0, ostruct, stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            frame()
+        rg.rgeo_sync(stream.cuda_stream)
+        steps_total = int(out["steps"].to(torch.int64).sum().item())
+        ids = out["id"].cpu().numpy()
+
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()                      # L2 flushed between timed frames (256 MiB write)
+            ev[i][0].record(stream)
+            frame()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        rg.rgeo_sync(stream.cuda_stream)
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = reduce_max(sum(kernel_ms) / 1e3, world)
+    rays = N * args.steps * world
+    value = rays / total_s / 1e6
+    mean_ms = sum(kernel_ms) / len(kernel_ms)
+    flops = steps_total * flops_per_rk4_step(K)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
+    except Exception:
+        sm_max = SM_MAX_MHZ_FALLBACK
+    peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (mean_ms * 1e-3) / 1e12
+    ffma_tflops, _ = rg.rgeo_ffma_probe()
+
+    # end to end through the public C API with host buffers: per frame, upload the bump
+    # centres from host memory, trace, copy every output back (rgeo_trace_host synchronises)
+    e2e = None
+    if not args.no_e2e:
+        host = rg.alloc_outputs(N, pin=True)
+        hstruct = rg.outputs_struct(host)
+        centers = np.ascontiguousarray(w.metric.center, np.float32)
+
+        def e2e_frame():
+            rg.rgeo_metric_set_centers(metric.handle, centers, stream.cuda_stream)
+            rg.rgeo_trace_host(metric.handle, scene.handle, cam, w.width, w.height, w.h, w.max_steps,
+                               w.integrator, w.shading, 0, hstruct, stream.cuda_stream)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_frame()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_frame()
+        e2e_s = reduce_max(time.perf_counter() - t0, world)
+        assert np.array_equal(host["id"].numpy(), ids), "e2e outputs differ from the device-timed frame"
+        e2e = {"value": rays / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(centers.nbytes),
+               "d2h_bytes_per_step": int(N * (4 + 12 + 4 + 4)), "gpu_launches_per_step": 2}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank != 0:
+        return 0
+    traffic = dram_traffic("k_trace_1080p_64")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded SplitMix64 bumps, spheres and displaced-sphere mesh)",
+        "config": {"workload": w.name, "width": w.width, "height": w.height, "bumps": K,
+                   "spheres": w.scene.n_spheres, "triangles": w.scene.n_tris, "h": w.h,
+                   "max_steps": w.max_steps, "integrator": "rk4", "camera": "(0,0,-6) +z, 60 deg",
+                   "l2": "flushed between timed frames (256 MiB write)",
+                   "per_rank": "one full frame per rank per step"},
+        "rk4_steps_per_s": steps_total * args.steps * world / total_s,
+        "rays_hit_miss_budget": [float(np.mean(ids >= 0)), float(np.mean(ids == -1)), float(np.mean(ids == -2))],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                     "ffma_probe_tflops": ffma_tflops, "frac_of_ffma_probe": achieved / ffma_tflops,
+                     "flops_per_launch": flops, "flops_per_rk4_step": flops_per_rk4_step(K),
+                     "rk4_steps_per_launch": steps_total, "kernel_ms": mean_ms},
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["rgeo", "reference"], default="rgeo")
+    ap.add_argument("--workload", default="1080p_64", choices=["1080p_64", "1080p_twist", "parity_64"])
+    ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * rgeo.h -- C ABI of librgeo, a geodesic ray tracer for (R^3, g) on sm_103a.
+ *
+ * The library traces one geodesic per pixel through R^3 endowed with a
+ * designed Riemannian metric and intersects every step's segment with a scene
+ * of spheres and triangles ("Design and visualization of Riemannian metrics",
+ * Novello, da Silva, Velho 2020):
+ *   - metric: the graph metric g = I + grad f grad f^T of a sum of Gaussian
+ *     bumps (Eq. 5.2, Eq. 6.1, Section 6 "Summing functions"), or the
+ *     pull-back metric g = J^T J of the twist diffeomorphism (Eq. 5.6,
+ *     Section 5.2);
+ *   - geodesics: the geodesic flow of Eq. 3.3 with the Christoffel symbols of
+ *     Eq. 5.3 (graph) or Theorem 5.1 (diffeomorphism), i.e. the accelerations
+ *     of Eq. 5.4 and Eq. 5.8, integrated by classical RK4 (Section 4.1 names it)
+ *     or by Euler marching (Eq. 4.1);
+ *   - shading: Riemannian shading (Section 4): each direction of the observer's
+ *     view field gets the colour of the first object its geodesic meets; the
+ *     polygon's segments are tested in order (Section 4.1).
+ *
+ * Conventions (apply to every entry point):
+ *   - All entry points return an rgeo_status.  On a non-OK status a message
+ *     describing the failure is available from rgeo_last_error() on the same
+ *     host thread.  No C++ exception crosses this boundary.
+ *   - Pointers documented as HOST are read during the call only.  Pointers
+ *     documented as DEVICE must be device-accessible allocations on the
+ *     current CUDA device; they are used asynchronously on the given stream.
+ *   - A NULL stream means the legacy default stream.  Every launch is
+ *     asynchronous with respect to the host unless stated otherwise.
+ *   - Device-side errors (an exhausted traversal stack, a wait that timed
+ *     out) are recorded in a per-device sticky error word; rgeo_sync() waits
+ *     for the stream, reads and clears it, and maps it to a status.
+ *   - float is IEEE binary32; all arithmetic on the device path is FP32 except
+ *     the optional energy-drift diagnostic, which is FP64.
+ */
+#ifndef RGEO_H
+#define RGEO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RGEO_ABI_VERSION 1
+
+typedef enum {
+  RGEO_OK = 0,
+  RGEO_EINVAL = 1,       /* an argument failed validation */
+  RGEO_ENOMEM = 2,       /* a device or host allocation failed */
+  RGEO_ECUDA = 3,        /* a CUDA runtime call failed */
+  RGEO_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  RGEO_EUNSUPPORTED = 5, /* valid request this build does not implement */
+  RGEO_EDEVICE = 6       /* a kernel recorded a device-side error */
+} rgeo_status;
+
+typedef enum {
+  RGEO_METRIC_GRAPH_BUMPS = 0, /* graph of f (Eq. 5.2), f a sum of Gaussian bumps (Eq. 6.1) */
+  RGEO_METRIC_DIFFEO_TWIST = 1 /* pull-back through the twist of Section 5.2 (Eq. 5.6) */
+} rgeo_metric_kind;
+
+typedef enum { RGEO_RK4 = 0, RGEO_EULER = 1 } rgeo_integrator;
+typedef enum { RGEO_SHADE_LAMBERT = 0, RGEO_SHADE_PSEUDO = 1 } rgeo_shading;
+
+/* rgeo_trace flags */
+#define RGEO_FLAG_ENERGY_DIAG 1u /* write drift[p] = g(v_end, v_end) / g(v_0, v_0) - 1 (FP64) */
+#define RGEO_FLAG_NO_SAFE_SKIP 2u /* test every segment (disables the exact safe-distance skip) */
+
+/* Object ids written to rgeo_outputs.id */
+#define RGEO_ID_MISS (-1)   /* the geodesic left every bump support and met nothing */
+#define RGEO_ID_BUDGET (-2) /* max_steps integration steps without a hit */
+
+typedef struct rgeo_metric rgeo_metric; /* opaque, owns device memory */
+typedef struct rgeo_scene rgeo_scene;   /* opaque, owns device memory */
+
+/* Metric description.  For the graph metric
+ *   f(x) = b.x + 1/2 x^T A x + sum_k a_k exp(-sum_i (x_i - c_ki)^2 / (2 sigma_ki^2))
+ * (Eq. 6.1 summed).  Each bump is truncated to ||(x - c_k) / sigma_k|| < cutoff_sigmas;
+ * cutoff_sigmas <= 0 keeps every bump untruncated.  Where no truncated support
+ * contains the ray and A = 0, Hess f = 0 and the geodesic is a straight line
+ * (Eq. 5.4); the tracer then advances in closed form to the next support.
+ * Bumps with a_k = 0 are inert.  For the twist, twist_rate k gives
+ * Phi(x, y, z) = (cos(kz) x - sin(kz) y, sin(kz) x + cos(kz) y, z) (k = 1 in the paper). */
+typedef struct {
+  int32_t kind;            /* rgeo_metric_kind */
+  int32_t n_bumps;         /* K >= 0 (graph only); at most RGEO_MAX_BUMPS */
+  const float *center;     /* HOST [K*3] bump centres c_k */
+  const float *amplitude;  /* HOST [K] amplitudes a_k, finite */
+  const float *sigma;      /* HOST [K*3] spreads sigma_k per axis, > 0; equal triple = isotropic */
+  float affine_b[3];       /* b */
+  float quad_A[9];         /* A, row-major, must be symmetric */
+  float cutoff_sigmas;     /* c; 4 is the default used by the workloads */
+  float twist_rate;        /* k (twist only) */
+  int32_t reserved[4];     /* must be zero */
+} rgeo_metric_desc;
+
+#define RGEO_MAX_BUMPS 4096
+
+/* Pinhole observer: position p, forward and up vectors (need not be unit or
+ * orthogonal; up must not be parallel to forward), vertical field of view in
+ * degrees (0, 180).  Pixel (i, j), row 0 at the top, looks along
+ * normalize(F + u R + w U) with R = normalize(up x F), U = F x R,
+ * u = (2 (i + 1/2) / W - 1) tan(fov/2) W / H and w = (1 - 2 (j + 1/2) / H) tan(fov/2);
+ * its initial tangent is that direction scaled to g-unit length, a point of
+ * the unit sphere S^2_p of Section 4. */
+typedef struct {
+  float pos[3];
+  float forward[3];
+  float up[3];
+  float vfov_deg;
+} rgeo_camera;
+
+/* Per-pixel outputs, caller-owned DEVICE buffers, pixel p = j * W + i.
+ *   id    [W*H] int32: sphere index in [0, S), S + t for triangle t, or RGEO_ID_*
+ *   hit   [3*W*H] float, planar: hit[p], hit[N + p], hit[2N + p] = x, y, z of the hit
+ *         point on the polygon segment (for MISS / BUDGET: the last position)
+ *   steps [W*H] int32: integration steps taken (closed-form flat advances not counted)
+ *   rgba  [4*W*H] uint8: shaded colour, alpha 255 on a hit, all zero otherwise
+ *   drift [W*H] double, may be NULL: energy drift when RGEO_FLAG_ENERGY_DIAG is set */
+typedef struct {
+  int32_t *id;
+  float *hit;
+  int32_t *steps;
+  uint8_t *rgba;
+  double *drift;
+} rgeo_outputs;
+
+/* Library version and device capability check.  Returns RGEO_ABI_VERSION. */
+int32_t rgeo_abi_version(void);
+
+/* Message for the last non-OK status returned on this host thread ("" if none).
+ * The string stays valid until the next rgeo_* call on this thread. */
+const char *rgeo_last_error(void);
+
+/* Build a metric on the current device (Eq. 5.2 / Eq. 6.1 or Eq. 5.6).  The
+ * HOST arrays of desc are copied; the handle owns its device copies.  Packing
+ * of the bump table runs on the device; the call synchronises before returning.
+ * Errors: RGEO_EINVAL (NULL out/desc, unknown kind, K < 0 or > RGEO_MAX_BUMPS,
+ * NULL arrays with K > 0, sigma <= 0, non-finite value, asymmetric A, twist
+ * with bumps), RGEO_ENOMEM, RGEO_ECUDA.  On error *out is set to NULL. */
+rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out);
+
+/* Replace the bump centres of a graph metric in place (HOST [K*3], same K),
+ * enqueued on the stream (no synchronisation).  Used for animated metrics.
+ * Errors: RGEO_EINVAL (NULL, not a graph metric, non-finite), RGEO_ECUDA. */
+rgeo_status rgeo_metric_set_centers(rgeo_metric *metric, const float *center, void *cuda_stream);
+
+void rgeo_metric_destroy(rgeo_metric *metric);
+
+/* Build a scene on the current device: S spheres (HOST [S*4]: cx, cy, cz, r > 0),
+ * a triangle mesh (HOST verts [V*3], HOST tris [T*3] vertex indices in [0, V)),
+ * and albedo (HOST [(S+1)*3], one RGB per sphere then one for the whole mesh,
+ * each in [0, 1]).  Builds a binned-SAH BVH over the triangles and a grid of
+ * lower bounds of the distance to the scene on the host, then uploads them.
+ * S and T may be zero.  Synchronises before returning.
+ * Errors: RGEO_EINVAL, RGEO_ENOMEM, RGEO_ECUDA.  On error *out is set to NULL. */
+rgeo_status rgeo_scene_create(const float *spheres, int32_t n_spheres, const float *verts,
+                              int32_t n_verts, const int32_t *tris, int32_t n_tris,
+                              const float *albedo, rgeo_scene **out);
+
+void rgeo_scene_destroy(rgeo_scene *scene);
+
+/* Riemannian shading of a W x H view field (Section 4): for each pixel, march
+ * its geodesic with step h (Section 4.1; RK4 or Euler per `integrator`) for at
+ * most max_steps steps, test each segment against the scene, shade the first
+ * hit.  Enqueued on `cuda_stream`; returns after enqueueing (asynchronous).
+ * Allocates a 4-byte work counter with cudaMallocAsync on the stream per call.
+ * Errors (synchronous): RGEO_EINVAL (NULL handles/outputs, W or H < 1,
+ * W*H >= 2^31, h not finite or <= 0, max_steps < 1, bad enum, drift NULL with
+ * RGEO_FLAG_ENERGY_DIAG), RGEO_ECUDA.  Device-side errors surface at rgeo_sync. */
+rgeo_status rgeo_trace(const rgeo_metric *metric, const rgeo_scene *scene,
+                       const rgeo_camera *camera, int32_t width, int32_t height, float h,
+                       int32_t max_steps, int32_t integrator, int32_t shading, uint32_t flags,
+                       const rgeo_outputs *out, void *cuda_stream);
+
+/* rgeo_trace with HOST output buffers (same layout as rgeo_outputs; drift may be
+ * NULL).  Stages the outputs in device memory, traces on the stream, copies the
+ * results back and synchronises the stream before returning.  Host buffers
+ * that are page-locked give asynchronous copies. */
+rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
+                            const rgeo_camera *camera, int32_t width, int32_t height, float h,
+                            int32_t max_steps, int32_t integrator, int32_t shading,
+                            uint32_t flags, const rgeo_outputs *host_out, void *cuda_stream);
+
+/* Wait for the stream, then read and clear the device error word of the
+ * current device.  Returns RGEO_OK, RGEO_EDEVICE or RGEO_ETIMEOUT (message in
+ * rgeo_last_error), or RGEO_ECUDA if the stream itself failed. */
+rgeo_status rgeo_sync(void *cuda_stream);
+
+/* Measurement helper: time an FP32 FFMA loop on the current device and write
+ * the achieved rate in TFLOP/s (2 flops per FFMA) to *tflops.  Synchronous. */
+rgeo_status rgeo_ffma_probe(float *tflops, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGEO_H */

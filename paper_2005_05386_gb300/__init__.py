@@ -1,0 +1,269 @@
+"""Python binding of librgeo, a geodesic ray tracer for designed Riemannian metrics on GB300.
+
+The functions ``rgeo_*`` below carry the names of the C entry points declared in
+``include/rgeo.h`` and only marshal arguments: every step of the traced path
+runs in the library's CUDA kernels.  PyTorch provides device memory and streams.
+There is no CPU fallback: when the library is missing or cannot be loaded, the
+first call raises.
+
+Convenience wrappers (``Metric``, ``Scene``, ``trace``) build the C structs from
+the seeded workloads of :mod:`paper_2005_05386_gb300.scenes` and allocate the
+output buffers as torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librgeo.so")
+
+RGEO_OK, RGEO_EINVAL, RGEO_ENOMEM, RGEO_ECUDA, RGEO_ETIMEOUT, RGEO_EUNSUPPORTED, RGEO_EDEVICE = range(7)
+RGEO_METRIC_GRAPH_BUMPS, RGEO_METRIC_DIFFEO_TWIST = 0, 1
+RGEO_RK4, RGEO_EULER = 0, 1
+RGEO_SHADE_LAMBERT, RGEO_SHADE_PSEUDO = 0, 1
+RGEO_FLAG_ENERGY_DIAG = 1
+RGEO_FLAG_NO_SAFE_SKIP = 2
+RGEO_ID_MISS, RGEO_ID_BUDGET = -1, -2
+RGEO_MAX_BUMPS = 4096
+
+# Every symbol include/rgeo.h declares (checked by the tests).
+EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_metric_set_centers",
+           "rgeo_metric_destroy", "rgeo_scene_create", "rgeo_scene_destroy", "rgeo_trace",
+           "rgeo_trace_host", "rgeo_sync", "rgeo_ffma_probe")
+
+
+class RgeoError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where} failed with status {status}: {message}")
+        self.status = status
+
+
+class rgeo_metric_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_bumps", ctypes.c_int32),
+                ("center", ctypes.POINTER(ctypes.c_float)), ("amplitude", ctypes.POINTER(ctypes.c_float)),
+                ("sigma", ctypes.POINTER(ctypes.c_float)), ("affine_b", ctypes.c_float * 3),
+                ("quad_A", ctypes.c_float * 9), ("cutoff_sigmas", ctypes.c_float),
+                ("twist_rate", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+
+
+class rgeo_camera(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("forward", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("vfov_deg", ctypes.c_float)]
+
+
+class rgeo_outputs(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_void_p), ("hit", ctypes.c_void_p), ("steps", ctypes.c_void_p),
+                ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Load librgeo.so (built in-tree by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librgeo.so not found at {LIB_PATH}; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_float
+    fp = ctypes.POINTER(ctypes.c_float)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    L.rgeo_abi_version.restype = i32
+    L.rgeo_abi_version.argtypes = []
+    L.rgeo_last_error.restype = ctypes.c_char_p
+    L.rgeo_last_error.argtypes = []
+    L.rgeo_metric_create.restype = i32
+    L.rgeo_metric_create.argtypes = [ctypes.POINTER(rgeo_metric_desc), ctypes.POINTER(vp)]
+    L.rgeo_metric_set_centers.restype = i32
+    L.rgeo_metric_set_centers.argtypes = [vp, fp, vp]
+    L.rgeo_metric_destroy.restype = None
+    L.rgeo_metric_destroy.argtypes = [vp]
+    L.rgeo_scene_create.restype = i32
+    L.rgeo_scene_create.argtypes = [fp, i32, fp, i32, ip, i32, fp, ctypes.POINTER(vp)]
+    L.rgeo_scene_destroy.restype = None
+    L.rgeo_scene_destroy.argtypes = [vp]
+    trace_args = [vp, vp, ctypes.POINTER(rgeo_camera), i32, i32, f32, i32, i32, i32, u32,
+                  ctypes.POINTER(rgeo_outputs), vp]
+    L.rgeo_trace.restype = i32
+    L.rgeo_trace.argtypes = trace_args
+    L.rgeo_trace_host.restype = i32
+    L.rgeo_trace_host.argtypes = trace_args
+    L.rgeo_sync.restype = i32
+    L.rgeo_sync.argtypes = [vp]
+    L.rgeo_ffma_probe.restype = i32
+    L.rgeo_ffma_probe.argtypes = [fp, fp]
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != RGEO_OK:
+        raise RgeoError(status, where, rgeo_last_error())
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if a is not None else None
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------- raw C entry points
+def rgeo_abi_version() -> int:
+    return library().rgeo_abi_version()
+
+
+def rgeo_last_error() -> str:
+    return library().rgeo_last_error().decode()
+
+
+def rgeo_metric_create(desc: rgeo_metric_desc) -> int:
+    out = ctypes.c_void_p()
+    _check(library().rgeo_metric_create(ctypes.byref(desc), ctypes.byref(out)), "rgeo_metric_create")
+    return out.value
+
+
+def rgeo_metric_set_centers(metric: int, center, stream=None):
+    import numpy as np
+    c = np.ascontiguousarray(center, dtype=np.float32)
+    _check(library().rgeo_metric_set_centers(metric, _fptr(c), _stream_handle(stream)), "rgeo_metric_set_centers")
+
+
+def rgeo_metric_destroy(metric: int):
+    library().rgeo_metric_destroy(metric)
+
+
+def rgeo_scene_create(spheres, verts, tris, albedo) -> int:
+    import numpy as np
+    s = np.ascontiguousarray(spheres, dtype=np.float32).reshape(-1, 4)
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    a = np.ascontiguousarray(albedo, dtype=np.float32).reshape(-1, 3)
+    out = ctypes.c_void_p()
+    _check(library().rgeo_scene_create(_fptr(s), s.shape[0], _fptr(v), v.shape[0],
+                                       t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), t.shape[0],
+                                       _fptr(a), ctypes.byref(out)), "rgeo_scene_create")
+    return out.value
+
+
+def rgeo_scene_destroy(scene: int):
+    library().rgeo_scene_destroy(scene)
+
+
+def rgeo_trace(metric: int, scene: int, camera: rgeo_camera, width: int, height: int, h: float,
+               max_steps: int, integrator: int, shading: int, flags: int, out: rgeo_outputs, stream=None):
+    _check(library().rgeo_trace(metric, scene, ctypes.byref(camera), width, height, h, max_steps, integrator,
+                                shading, flags, ctypes.byref(out), _stream_handle(stream)), "rgeo_trace")
+
+
+def rgeo_trace_host(metric: int, scene: int, camera: rgeo_camera, width: int, height: int, h: float,
+                    max_steps: int, integrator: int, shading: int, flags: int, out: rgeo_outputs, stream=None):
+    _check(library().rgeo_trace_host(metric, scene, ctypes.byref(camera), width, height, h, max_steps,
+                                     integrator, shading, flags, ctypes.byref(out), _stream_handle(stream)),
+           "rgeo_trace_host")
+
+
+def rgeo_sync(stream=None):
+    _check(library().rgeo_sync(_stream_handle(stream)), "rgeo_sync")
+
+
+def rgeo_ffma_probe():
+    t, ms = ctypes.c_float(), ctypes.c_float()
+    _check(library().rgeo_ffma_probe(ctypes.byref(t), ctypes.byref(ms)), "rgeo_ffma_probe")
+    return t.value, ms.value
+
+
+# ------------------------------------------------------------------ conveniences
+def metric_desc(m: scenes.Metric):
+    """C descriptor for a ``scenes.Metric``; returns (desc, keep-alive arrays)."""
+    import numpy as np
+    c = np.ascontiguousarray(m.center, np.float32).reshape(-1)
+    a = np.ascontiguousarray(m.amplitude, np.float32).reshape(-1)
+    s = np.ascontiguousarray(m.sigma, np.float32).reshape(-1)
+    d = rgeo_metric_desc()
+    d.kind = m.kind
+    d.n_bumps = a.shape[0] if m.kind == RGEO_METRIC_GRAPH_BUMPS else 0
+    d.center, d.amplitude, d.sigma = (_fptr(c), _fptr(a), _fptr(s)) if d.n_bumps else (None, None, None)
+    d.affine_b = (ctypes.c_float * 3)(*m.affine_b)
+    d.quad_A = (ctypes.c_float * 9)(*m.quad_A)
+    d.cutoff_sigmas = m.cutoff
+    d.twist_rate = m.twist_rate
+    return d, (c, a, s)
+
+
+def camera_struct(cam: scenes.Camera) -> rgeo_camera:
+    return rgeo_camera((ctypes.c_float * 3)(*cam.pos), (ctypes.c_float * 3)(*cam.forward),
+                       (ctypes.c_float * 3)(*cam.up), cam.vfov_deg)
+
+
+class Metric:
+    """Owning handle of a device metric."""
+
+    def __init__(self, m: scenes.Metric):
+        desc, self._keep = metric_desc(m)
+        self.handle = rgeo_metric_create(desc)
+
+    def close(self):
+        if self.handle:
+            rgeo_metric_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+class Scene:
+    """Owning handle of a device scene (spheres + triangle BVH + safe-distance grid)."""
+
+    def __init__(self, s: scenes.Scene):
+        self.handle = rgeo_scene_create(s.spheres, s.verts, s.tris, s.albedo)
+
+    def close(self):
+        if self.handle:
+            rgeo_scene_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def alloc_outputs(n_pixels: int, device="cuda", drift: bool = False, pin: bool = False):
+    """Output tensors: id, hit (planar [3, N]), steps, rgba ([N, 4]), drift (optional)."""
+    import torch
+    kw = dict(device=device)
+    if pin:
+        kw = dict(device="cpu", pin_memory=True)
+    out = dict(id=torch.empty(n_pixels, dtype=torch.int32, **kw),
+               hit=torch.empty(3, n_pixels, dtype=torch.float32, **kw),
+               steps=torch.empty(n_pixels, dtype=torch.int32, **kw),
+               rgba=torch.empty(n_pixels, 4, dtype=torch.uint8, **kw))
+    out["drift"] = torch.empty(n_pixels, dtype=torch.float64, **kw) if drift else None
+    return out
+
+
+def outputs_struct(out) -> rgeo_outputs:
+    return rgeo_outputs(out["id"].data_ptr(), out["hit"].data_ptr(), out["steps"].data_ptr(),
+                        out["rgba"].data_ptr(), out["drift"].data_ptr() if out["drift"] is not None else None)
+
+
+def trace(work: scenes.Workload, metric: Metric = None, scene: Scene = None, out=None, stream=None,
+          flags: int = 0):
+    """Trace a workload on the current CUDA device into torch tensors (asynchronous on ``stream``)."""
+    metric = metric or Metric(work.metric)
+    scene = scene or Scene(work.scene)
+    if out is None:
+        out = alloc_outputs(work.n_pixels, drift=bool(flags & RGEO_FLAG_ENERGY_DIAG))
+    rgeo_trace(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height, work.h,
+               work.max_steps, work.integrator, work.shading, flags, outputs_struct(out), stream)
+    out["_handles"] = (metric, scene)
+    return out

@@ -1,0 +1,390 @@
+// rgeo_api.cu -- the C ABI of librgeo: argument validation, handle ownership,
+// scene construction and kernel launches.  See include/rgeo.h for the contract.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "rgeo.h"
+#include "rgeo_internal.h"
+
+struct rgeo_metric {
+  rgeo::MetricDev d;
+  int device;
+};
+
+struct rgeo_scene {
+  rgeo::SceneDev d;
+  int device;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rgeo_status fail(rgeo_status s, const std::string &msg) {
+  g_last_error = msg;
+  return s;
+}
+
+rgeo_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? RGEO_ENOMEM : RGEO_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RGEO_CUDA(call, what)                 \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool finite_all(const float *p, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t n) {
+  *dst = nullptr;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_metric(rgeo_metric *m) {
+  if (!m) return;
+  cudaFree(m->d.bumps);
+  cudaFree(m->d.raw);
+  delete m;
+}
+
+void free_scene(rgeo_scene *s) {
+  if (!s) return;
+  cudaFree(s->d.spheres);
+  cudaFree(s->d.albedo);
+  cudaFree(s->d.nodes);
+  cudaFree(s->d.tris);
+  cudaFree(s->d.grid);
+  delete s;
+}
+
+rgeo_status validate_trace(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *cam,
+                           int32_t W, int32_t H, float h, int32_t max_steps, int32_t integrator,
+                           int32_t shading, uint32_t flags, const rgeo_outputs *out) {
+  if (!metric || !scene || !cam || !out) return fail(RGEO_EINVAL, "rgeo_trace: NULL handle, camera or outputs");
+  if (W < 1 || H < 1 || (int64_t)W * H >= (int64_t(1) << 31))
+    return fail(RGEO_EINVAL, "rgeo_trace: width and height must be >= 1 with W*H < 2^31");
+  if (!std::isfinite(h) || h <= 0.f) return fail(RGEO_EINVAL, "rgeo_trace: step h must be finite and > 0");
+  if (max_steps < 1) return fail(RGEO_EINVAL, "rgeo_trace: max_steps must be >= 1");
+  if (integrator != RGEO_RK4 && integrator != RGEO_EULER)
+    return fail(RGEO_EINVAL, "rgeo_trace: unknown integrator");
+  if (shading != RGEO_SHADE_LAMBERT && shading != RGEO_SHADE_PSEUDO)
+    return fail(RGEO_EINVAL, "rgeo_trace: unknown shading mode");
+  if (flags & ~(RGEO_FLAG_ENERGY_DIAG | RGEO_FLAG_NO_SAFE_SKIP))
+    return fail(RGEO_EINVAL, "rgeo_trace: unknown flag bits");
+  if (!out->id || !out->hit || !out->steps || !out->rgba)
+    return fail(RGEO_EINVAL, "rgeo_trace: id, hit, steps and rgba outputs are required");
+  if ((flags & RGEO_FLAG_ENERGY_DIAG) && !out->drift)
+    return fail(RGEO_EINVAL, "rgeo_trace: RGEO_FLAG_ENERGY_DIAG needs a drift buffer");
+  if (!finite_all(cam->pos, 3) || !finite_all(cam->forward, 3) || !finite_all(cam->up, 3) ||
+      !std::isfinite(cam->vfov_deg) || cam->vfov_deg <= 0.f || cam->vfov_deg >= 180.f)
+    return fail(RGEO_EINVAL, "rgeo_trace: camera values must be finite, 0 < vfov < 180");
+  const float *f = cam->forward, *u = cam->up;
+  const float cx = u[1] * f[2] - u[2] * f[1], cy = u[2] * f[0] - u[0] * f[2], cz = u[0] * f[1] - u[1] * f[0];
+  if (f[0] * f[0] + f[1] * f[1] + f[2] * f[2] == 0.f || cx * cx + cy * cy + cz * cz == 0.f)
+    return fail(RGEO_EINVAL, "rgeo_trace: forward must be nonzero and not parallel to up");
+  return RGEO_OK;
+}
+
+rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *cam,
+                              int32_t W, int32_t H, float h, int32_t max_steps, int32_t integrator,
+                              int32_t shading, uint32_t flags, const rgeo_outputs *out) {
+  rgeo::TraceParams p;
+  std::memset(&p, 0, sizeof(p));
+  const rgeo::MetricDev &m = metric->d;
+  p.bumps = m.bumps;
+  p.K = m.kind == RGEO_METRIC_GRAPH_BUMPS ? m.K : 0;
+  p.kind = m.kind;
+  p.aniso = m.aniso;
+  p.skippable = m.skippable;
+  std::memcpy(p.b, m.b, sizeof(p.b));
+  std::memcpy(p.A, m.A, sizeof(p.A));
+  p.has_affine = m.has_affine;
+  p.has_quad = m.has_quad;
+  p.twist_k = m.twist_k;
+  const rgeo::SceneDev &s = scene->d;
+  p.spheres = s.spheres;
+  p.S = s.S;
+  p.albedo = s.albedo;
+  p.nodes = s.nodes;
+  p.tris = s.tris;
+  p.T = s.T;
+  p.grid = s.grid;
+  std::memcpy(p.gdim, s.gdim, sizeof(p.gdim));
+  std::memcpy(p.gmin, s.gmin, sizeof(p.gmin));
+  p.ginv = s.ginv;
+  std::memcpy(p.smin, s.smin, sizeof(p.smin));
+  std::memcpy(p.smax, s.smax, sizeof(p.smax));
+  p.has_grid = s.has_grid;
+  p.safe_skip = s.has_grid && !(flags & RGEO_FLAG_NO_SAFE_SKIP);
+  std::memcpy(p.cam_pos, cam->pos, sizeof(p.cam_pos));
+  std::memcpy(p.cam_fwd, cam->forward, sizeof(p.cam_fwd));
+  std::memcpy(p.cam_up, cam->up, sizeof(p.cam_up));
+  p.vfov_deg = cam->vfov_deg;
+  p.W = W;
+  p.H = H;
+  p.tiles_x = (W + 7) / 8;
+  const int tiles_y = (H + 3) / 4;
+  p.n_items = (uint32_t)p.tiles_x * (uint32_t)tiles_y * 32u;
+  p.h = h;
+  p.max_steps = max_steps;
+  p.integrator = integrator;
+  p.shading = shading;
+  p.energy = (flags & RGEO_FLAG_ENERGY_DIAG) ? 1 : 0;
+  p.id = out->id;
+  p.hit = out->hit;
+  p.steps = out->steps;
+  p.rgba = reinterpret_cast<uchar4 *>(out->rgba);
+  p.drift = out->drift;
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t rgeo_abi_version(void) { return RGEO_ABI_VERSION; }
+
+const char *rgeo_last_error(void) { return g_last_error.c_str(); }
+
+rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) {
+  g_last_error.clear();
+  if (!out) return fail(RGEO_EINVAL, "rgeo_metric_create: out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(RGEO_EINVAL, "rgeo_metric_create: desc is NULL");
+  const int K = desc->n_bumps;
+  if (desc->kind != RGEO_METRIC_GRAPH_BUMPS && desc->kind != RGEO_METRIC_DIFFEO_TWIST)
+    return fail(RGEO_EINVAL, "rgeo_metric_create: unknown metric kind");
+  if (K < 0 || K > RGEO_MAX_BUMPS) return fail(RGEO_EINVAL, "rgeo_metric_create: n_bumps out of range");
+  for (int i = 0; i < 4; i++)
+    if (desc->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_metric_create: reserved fields must be zero");
+  if (desc->kind == RGEO_METRIC_DIFFEO_TWIST && K != 0)
+    return fail(RGEO_EINVAL, "rgeo_metric_create: the twist metric takes no bumps");
+  if (!finite_all(desc->affine_b, 3) || !finite_all(desc->quad_A, 9) || !std::isfinite(desc->cutoff_sigmas) ||
+      !std::isfinite(desc->twist_rate))
+    return fail(RGEO_EINVAL, "rgeo_metric_create: non-finite parameter");
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < i; j++)
+      if (desc->quad_A[3 * i + j] != desc->quad_A[3 * j + i])
+        return fail(RGEO_EINVAL, "rgeo_metric_create: quad_A must be symmetric");
+  if (K > 0) {
+    if (!desc->center || !desc->amplitude || !desc->sigma)
+      return fail(RGEO_EINVAL, "rgeo_metric_create: NULL bump arrays");
+    if (!finite_all(desc->center, 3 * (size_t)K) || !finite_all(desc->amplitude, K) ||
+        !finite_all(desc->sigma, 3 * (size_t)K))
+      return fail(RGEO_EINVAL, "rgeo_metric_create: non-finite bump value");
+    for (int i = 0; i < 3 * K; i++)
+      if (!(desc->sigma[i] > 0.f)) return fail(RGEO_EINVAL, "rgeo_metric_create: sigma must be > 0");
+  }
+  rgeo_metric *m = new rgeo_metric();
+  std::memset(&m->d, 0, sizeof(m->d));
+  cudaGetDevice(&m->device);
+  m->d.kind = desc->kind;
+  m->d.K = K;
+  int aniso = 0;
+  for (int k = 0; k < K; k++)
+    if (desc->sigma[3 * k] != desc->sigma[3 * k + 1] || desc->sigma[3 * k] != desc->sigma[3 * k + 2]) aniso = 1;
+  m->d.aniso = aniso;
+  bool quad = false, affine = false;
+  for (int i = 0; i < 9; i++) {
+    m->d.A[i] = desc->quad_A[i];
+    quad |= desc->quad_A[i] != 0.f;
+  }
+  for (int i = 0; i < 3; i++) {
+    m->d.b[i] = desc->affine_b[i];
+    affine |= desc->affine_b[i] != 0.f;
+  }
+  m->d.has_quad = quad;
+  m->d.has_affine = affine;
+  m->d.cutoff = desc->cutoff_sigmas;
+  m->d.twist_k = desc->twist_rate;
+  m->d.skippable = desc->kind == RGEO_METRIC_GRAPH_BUMPS && desc->cutoff_sigmas > 0.f && !quad;
+  if (K > 0) {
+    std::vector<float> raw(7 * (size_t)K);
+    std::memcpy(raw.data(), desc->center, sizeof(float) * 3 * K);
+    std::memcpy(raw.data() + 3 * K, desc->amplitude, sizeof(float) * K);
+    std::memcpy(raw.data() + 4 * K, desc->sigma, sizeof(float) * 3 * K);
+    cudaError_t e = upload(&m->d.raw, raw.data(), raw.size());
+    const int stride = aniso ? rgeo::kAnisoStride : rgeo::kIsoStride;
+    if (e == cudaSuccess) e = cudaMalloc(&m->d.bumps, sizeof(float4) * stride * (size_t)K);
+    if (e == cudaSuccess) e = rgeo::launch_pack_bumps(m->d.raw, K, desc->cutoff_sigmas, aniso, m->d.bumps, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+      free_metric(m);
+      return cuda_fail(e, "rgeo_metric_create");
+    }
+  }
+  *out = m;
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_metric_set_centers(rgeo_metric *metric, const float *center, void *cuda_stream) {
+  g_last_error.clear();
+  if (!metric || !center) return fail(RGEO_EINVAL, "rgeo_metric_set_centers: NULL argument");
+  if (metric->d.kind != RGEO_METRIC_GRAPH_BUMPS)
+    return fail(RGEO_EINVAL, "rgeo_metric_set_centers: not a graph metric");
+  const int K = metric->d.K;
+  if (K == 0) return RGEO_OK;
+  if (!finite_all(center, 3 * (size_t)K)) return fail(RGEO_EINVAL, "rgeo_metric_set_centers: non-finite centre");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  RGEO_CUDA(cudaMemcpyAsync(metric->d.raw, center, sizeof(float) * 3 * K, cudaMemcpyHostToDevice, st),
+            "rgeo_metric_set_centers: copy");
+  RGEO_CUDA(rgeo::launch_set_centers(metric->d.raw, K, metric->d.aniso, metric->d.bumps, st),
+            "rgeo_metric_set_centers: launch");
+  return RGEO_OK;
+}
+
+void rgeo_metric_destroy(rgeo_metric *metric) { free_metric(metric); }
+
+rgeo_status rgeo_scene_create(const float *spheres, int32_t S, const float *verts, int32_t V,
+                              const int32_t *tris, int32_t T, const float *albedo, rgeo_scene **out) {
+  g_last_error.clear();
+  if (!out) return fail(RGEO_EINVAL, "rgeo_scene_create: out is NULL");
+  *out = nullptr;
+  if (S < 0 || V < 0 || T < 0) return fail(RGEO_EINVAL, "rgeo_scene_create: negative count");
+  if ((S > 0 && !spheres) || (T > 0 && (!verts || !tris)) || !albedo)
+    return fail(RGEO_EINVAL, "rgeo_scene_create: NULL array");
+  if (T > (1 << 26) || S > (1 << 20)) return fail(RGEO_EINVAL, "rgeo_scene_create: scene too large");
+  if (S > 0 && !finite_all(spheres, 4 * (size_t)S)) return fail(RGEO_EINVAL, "rgeo_scene_create: non-finite sphere");
+  for (int s = 0; s < S; s++)
+    if (!(spheres[4 * s + 3] > 0.f)) return fail(RGEO_EINVAL, "rgeo_scene_create: sphere radius must be > 0");
+  if (V > 0 && !finite_all(verts, 3 * (size_t)V)) return fail(RGEO_EINVAL, "rgeo_scene_create: non-finite vertex");
+  for (int t = 0; t < 3 * T; t++)
+    if (tris[t] < 0 || tris[t] >= V) return fail(RGEO_EINVAL, "rgeo_scene_create: vertex index out of range");
+  for (int i = 0; i < 3 * (S + 1); i++)
+    if (!(albedo[i] >= 0.f && albedo[i] <= 1.f)) return fail(RGEO_EINVAL, "rgeo_scene_create: albedo outside [0, 1]");
+
+  rgeo::HostBVH bvh;
+  if (!rgeo::build_bvh(verts, V, tris, T, bvh, rgeo::kMaxBvhDepth))
+    return fail(RGEO_EINVAL, "rgeo_scene_create: BVH build failed");
+  rgeo::HostGrid grid;
+  rgeo::build_safe_grid(spheres, S, verts, tris, T, 64, grid);
+
+  rgeo_scene *sc = new rgeo_scene();
+  std::memset(&sc->d, 0, sizeof(sc->d));
+  cudaGetDevice(&sc->device);
+  sc->d.S = S;
+  sc->d.T = T;
+  sc->d.n_nodes = (int)bvh.nodes.size() / 2;
+  std::vector<float4> sph(S);
+  for (int s = 0; s < S; s++)
+    sph[s] = make_float4(spheres[4 * s], spheres[4 * s + 1], spheres[4 * s + 2], spheres[4 * s + 3]);
+  cudaError_t e = upload(&sc->d.spheres, sph.data(), sph.size());
+  if (e == cudaSuccess) e = upload(&sc->d.albedo, albedo, 3 * (size_t)(S + 1));
+  if (e == cudaSuccess) e = upload(&sc->d.nodes, bvh.nodes.data(), bvh.nodes.size());
+  if (e == cudaSuccess) e = upload(&sc->d.tris, bvh.tris.data(), bvh.tris.size());
+  if (e == cudaSuccess && !grid.dist.empty()) {
+    e = upload(&sc->d.grid, grid.dist.data(), grid.dist.size());
+    sc->d.has_grid = 1;
+    for (int i = 0; i < 3; i++) {
+      sc->d.gdim[i] = grid.dim[i];
+      sc->d.gmin[i] = grid.gmin[i];
+      sc->d.smin[i] = grid.smin[i];
+      sc->d.smax[i] = grid.smax[i];
+    }
+    sc->d.ginv = 1.0f / grid.cell;
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_scene(sc);
+    return cuda_fail(e, "rgeo_scene_create");
+  }
+  *out = sc;
+  return RGEO_OK;
+}
+
+void rgeo_scene_destroy(rgeo_scene *scene) { free_scene(scene); }
+
+rgeo_status rgeo_trace(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                       int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
+                       int32_t shading, uint32_t flags, const rgeo_outputs *out, void *cuda_stream) {
+  g_last_error.clear();
+  rgeo_status s = validate_trace(metric, scene, camera, width, height, h, max_steps, integrator, shading,
+                                 flags, out);
+  if (s != RGEO_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  rgeo::TraceParams p = make_params(metric, scene, camera, width, height, h, max_steps, integrator, shading,
+                                    flags, out);
+  uint32_t *counter = nullptr;
+  RGEO_CUDA(cudaMallocAsync((void **)&counter, sizeof(uint32_t), st), "rgeo_trace: work counter");
+  p.counter = counter;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = rgeo::launch_trace(p, st);
+  cudaError_t e2 = cudaFreeAsync(counter, st);
+  if (e != cudaSuccess) return cuda_fail(e, "rgeo_trace: launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rgeo_trace: free");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                            int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
+                            int32_t shading, uint32_t flags, const rgeo_outputs *host_out,
+                            void *cuda_stream) {
+  g_last_error.clear();
+  rgeo_status s = validate_trace(metric, scene, camera, width, height, h, max_steps, integrator, shading,
+                                 flags, host_out);
+  if (s != RGEO_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t N = (size_t)width * height;
+  const bool drift = host_out->drift != nullptr;
+  const size_t bytes = N * (4 + 12 + 4 + 4) + (drift ? N * 8 : 0);
+  char *buf = nullptr;
+  RGEO_CUDA(cudaMallocAsync((void **)&buf, bytes, st), "rgeo_trace_host: staging");
+  rgeo_outputs d;
+  d.drift = drift ? (double *)buf : nullptr;
+  char *q = buf + (drift ? N * 8 : 0);
+  d.hit = (float *)q;
+  q += N * 12;
+  d.id = (int32_t *)q;
+  q += N * 4;
+  d.steps = (int32_t *)q;
+  q += N * 4;
+  d.rgba = (uint8_t *)q;
+  s = rgeo_trace(metric, scene, camera, width, height, h, max_steps, integrator, shading, flags, &d, st);
+  cudaError_t e = cudaSuccess;
+  if (s == RGEO_OK) {
+    e = cudaMemcpyAsync(host_out->id, d.id, N * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->hit, d.hit, N * 12, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->steps, d.steps, N * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->rgba, d.rgba, N * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && drift) e = cudaMemcpyAsync(host_out->drift, d.drift, N * 8, cudaMemcpyDeviceToHost, st);
+  }
+  cudaFreeAsync(buf, st);
+  if (s != RGEO_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "rgeo_trace_host: copy back");
+  RGEO_CUDA(cudaStreamSynchronize(st), "rgeo_trace_host: synchronise");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_sync(void *cuda_stream) {
+  g_last_error.clear();
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  RGEO_CUDA(cudaStreamSynchronize(st), "rgeo_sync: stream");
+  unsigned word = 0;
+  RGEO_CUDA(rgeo::read_and_clear_device_error(&word, st), "rgeo_sync: error word");
+  if (word & rgeo::kErrTimeout) return fail(RGEO_ETIMEOUT, "a bounded device-side wait timed out");
+  if (word & rgeo::kErrStackOverflow)
+    return fail(RGEO_EDEVICE, "BVH traversal stack exhausted (the affected segment tests were cut short)");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_ffma_probe(float *tflops, float *ms) {
+  g_last_error.clear();
+  if (!tflops || !ms) return fail(RGEO_EINVAL, "rgeo_ffma_probe: NULL output");
+  RGEO_CUDA(rgeo::run_ffma_probe(tflops, ms), "rgeo_ffma_probe");
+  return RGEO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// rgeo_internal.h -- device data layouts and launch interfaces shared by the
+// translation units of librgeo (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rgeo.h"
+
+namespace rgeo {
+
+// Bump table, packed per bump as two float4 (isotropic fast form):
+//   b0 = (cx, cy, cz, R2)   R2 = (cutoff * sigma)^2, +inf when untruncated, -1 when inert (a = 0)
+//   b1 = (qn2, la, qs, q)   q = 1 / sigma^2, qn2 = -q log2(e) / 2, la = log2 |a|, qs = -q sign(a)
+// so that with d = x - c, r2 = |d|^2 and w = 2^(r2 qn2 + la) = |a| exp(-q r2 / 2):
+//   grad f  += (w qs) d
+//   -v^T Hess f v += (w qs) (q (d.v)^2 - |v|^2)
+// Anisotropic bumps use three float4:
+//   b0 = (cx, cy, cz, Rball2)  Rball2 = (cutoff * max_i sigma_i)^2 (support ball for the flat skip)
+//   b1 = (qx, qy, qz, sgn)     q_i = 1 / sigma_i^2, sgn = sign(a)
+//   b2 = (la, c2, 0, 0)        c2 = cutoff^2 (+inf when untruncated, -1 when inert)
+constexpr int kIsoStride = 2;
+constexpr int kAnisoStride = 3;
+
+struct MetricDev {
+  int kind;            // 0 graph, 1 twist
+  int K;               // bumps (inert ones included)
+  int aniso;           // 1: anisotropic layout
+  int skippable;       // graph, truncated, A == 0: flat space outside the supports
+  float4 *bumps;       // packed table (device)
+  float *raw;          // raw centres/amplitudes/sigmas (device) [K*7]
+  float b[3];
+  float A[9];
+  int has_affine, has_quad;
+  float cutoff;
+  float twist_k;
+};
+
+// BVH node: two float4.  n0 = (lo.xyz, int first_or_left), n1 = (hi.xyz, int count);
+// count > 0: leaf over triangles [first, first + count); count == 0: children at left, left + 1.
+// Triangles in BVH order: three float4 (v0.xyz, int original index), (v1.xyz, 0), (v2.xyz, 0).
+struct SceneDev {
+  int S, T, n_nodes;
+  float4 *spheres;   // [S]
+  float *albedo;     // [(S+1)*3]
+  float4 *nodes;     // [2 * n_nodes]
+  float4 *tris;      // [3 * T]
+  float *grid;       // [gx * gy * gz] lower bounds of the distance to the scene
+  int gdim[3];
+  float gmin[3];
+  float ginv;        // 1 / cell size
+  float smin[3], smax[3];  // scene bounding box
+  int has_grid;
+};
+
+struct TraceParams {
+  // metric
+  const float4 *bumps;
+  int K, kind, aniso, skippable;
+  float b[3];
+  float A[9];
+  int has_affine, has_quad;
+  float twist_k;
+  // scene
+  const float4 *spheres;
+  int S;
+  const float *albedo;
+  const float4 *nodes;
+  const float4 *tris;
+  int T;
+  const float *grid;
+  int gdim[3];
+  float gmin[3];
+  float ginv;
+  float smin[3], smax[3];
+  int has_grid, safe_skip;
+  // camera
+  float cam_pos[3], cam_fwd[3], cam_up[3];
+  float vfov_deg;
+  int W, H, tiles_x;
+  uint32_t n_items;
+  // integration
+  float h;
+  int max_steps, integrator, shading, energy;
+  // outputs
+  int32_t *id;
+  float *hit;
+  int32_t *steps;
+  uchar4 *rgba;
+  double *drift;
+  uint32_t *counter;
+};
+
+// Host-side scene acceleration structures (rgeo_scene_build.cpp).
+struct HostBVH {
+  std::vector<float4> nodes;  // 2 per node
+  std::vector<float4> tris;   // 3 per triangle, BVH order
+  int depth = 0;
+};
+bool build_bvh(const float *verts, int n_verts, const int32_t *tris, int n_tris, HostBVH &out,
+               int max_depth);
+
+struct HostGrid {
+  std::vector<float> dist;
+  int dim[3] = {0, 0, 0};
+  float gmin[3] = {0, 0, 0};
+  float cell = 1.0f;
+  float smin[3] = {0, 0, 0}, smax[3] = {0, 0, 0};
+};
+void build_safe_grid(const float *spheres, int S, const float *verts, const int32_t *tris, int T,
+                     int res, HostGrid &out);
+
+constexpr int kMaxBvhDepth = 48;
+constexpr int kTraversalStack = 64;
+
+// Device error word bits (sticky, per device).
+constexpr unsigned kErrStackOverflow = 1u;
+constexpr unsigned kErrTimeout = 2u;
+
+// Kernel launchers (rgeo_trace.cu).
+cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
+                              cudaStream_t st);
+cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
+cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
+cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
+cudaError_t run_ffma_probe(float *tflops, float *ms);
+
+}  // namespace rgeo

@@ -1,0 +1,107 @@
+"""The C-ABI library: loads, exports every declared symbol, and rejects invalid
+arguments before touching the device.  CPU only (no compute calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rg():
+    from paper_2005_05386_gb300 import _build
+    _build.build()
+    import paper_2005_05386_gb300 as rg
+    rg.library()
+    return rg
+
+
+def _declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", hdr)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(rgeo_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(rg):
+    declared = _declared_functions()
+    assert len(declared) >= 10
+    assert set(declared) == set(rg.EXPORTS)
+    lib = ctypes.CDLL(rg.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_abi_version(rg):
+    assert rg.rgeo_abi_version() == 1
+
+
+def _desc(rg, **kw):
+    from paper_2005_05386_gb300 import scenes
+    m = scenes.Metric(center=np.zeros((1, 3), np.float32), amplitude=np.ones(1, np.float32),
+                      sigma=np.full((1, 3), 0.5, np.float32))
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return rg.metric_desc(m)
+
+
+@pytest.mark.parametrize("bad", ["sigma", "amplitude", "kind", "quad", "reserved", "count"])
+def test_metric_validation(rg, bad):
+    d, keep = _desc(rg)
+    if bad == "sigma":
+        keep[2][0] = 0.0
+    elif bad == "amplitude":
+        keep[1][0] = np.nan
+    elif bad == "kind":
+        d.kind = 7
+    elif bad == "quad":
+        d.quad_A[1] = 0.5
+    elif bad == "reserved":
+        d.reserved[0] = 1
+    elif bad == "count":
+        d.n_bumps = rg.RGEO_MAX_BUMPS + 1
+    with pytest.raises(rg.RgeoError) as e:
+        rg.rgeo_metric_create(d)
+    assert e.value.status == rg.RGEO_EINVAL
+    assert rg.rgeo_last_error()
+
+
+def test_scene_validation(rg):
+    alb = np.ones((2, 3), np.float32)
+    with pytest.raises(rg.RgeoError) as e:
+        rg.rgeo_scene_create(np.array([[0, 0, 0, -1.0]]), np.zeros((0, 3)), np.zeros((0, 3)), alb)
+    assert e.value.status == rg.RGEO_EINVAL
+    with pytest.raises(rg.RgeoError) as e:
+        rg.rgeo_scene_create(np.zeros((0, 4)), np.zeros((3, 3)), np.array([[0, 1, 3]]), np.ones((1, 3)))
+    assert "index" in str(e.value)
+    with pytest.raises(rg.RgeoError):
+        rg.rgeo_scene_create(np.zeros((0, 4)), np.zeros((0, 3)), np.zeros((0, 3)), np.full((1, 3), 2.0))
+
+
+def test_trace_validation(rg):
+    cam = rg.camera_struct(__import__("paper_2005_05386_gb300").scenes.Camera())
+    out = rg.rgeo_outputs(1, 1, 1, 1, None)
+    for args in [(None, None, cam, 4, 4, 0.01, 10, 0, 0, 0, out),]:
+        with pytest.raises(rg.RgeoError) as e:
+            rg.rgeo_trace(*args, stream=0)
+        assert e.value.status == rg.RGEO_EINVAL
+    # all remaining checks fail before the handles are dereferenced
+    fake = 1
+    for W, H, h, steps, integ, shade, flags, o in [
+            (0, 4, 0.01, 10, 0, 0, 0, out), (4, 4, -1.0, 10, 0, 0, 0, out), (4, 4, float("nan"), 10, 0, 0, 0, out),
+            (4, 4, 0.01, 0, 0, 0, 0, out), (4, 4, 0.01, 10, 5, 0, 0, out), (4, 4, 0.01, 10, 0, 9, 0, out),
+            (4, 4, 0.01, 10, 0, 0, 64, out), (4, 4, 0.01, 10, 0, 0, 1, out),
+            (65536, 65536, 0.01, 10, 0, 0, 0, out)]:
+        with pytest.raises(rg.RgeoError) as e:
+            rg.rgeo_trace(fake, fake, cam, W, H, h, steps, integ, shade, flags, o, stream=0)
+        assert e.value.status == rg.RGEO_EINVAL
+    bad_cam = rg.camera_struct(__import__("paper_2005_05386_gb300").scenes.Camera(up=(0.0, 0.0, 2.0)))
+    with pytest.raises(rg.RgeoError) as e:
+        rg.rgeo_trace(fake, fake, bad_cam, 4, 4, 0.01, 10, 0, 0, 0, out, stream=0)
+    assert "parallel" in str(e.value)
