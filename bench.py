@@ -275,7 +275,8 @@ def bench_gpu(args):
         sm_max = SM_MAX_MHZ_FALLBACK
     peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (mean_ms * 1e-3) / 1e12
-    ffma_tflops, _ = rg.rgeo_ffma_probe()
+    ffma_tflops, _ = rg.rgeo_ffma_probe(0)
+    ffma2_tflops, _ = rg.rgeo_ffma_probe(1)
 
     # end to end through the public C API with host buffers: per frame, upload the bump
     # centres from host memory, trace, copy every output back (rgeo_trace_host synchronises)
@@ -324,6 +325,7 @@ def bench_gpu(args):
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                      "ffma_probe_tflops": ffma_tflops, "frac_of_ffma_probe": achieved / ffma_tflops,
+                     "ffma2_probe_tflops": ffma2_tflops,
                      "flops_per_launch": flops, "flops_per_rk4_step": flops_per_rk4_step(K),
                      "rk4_steps_per_launch": steps_total, "kernel_ms": mean_ms},
         "clocks": clk,

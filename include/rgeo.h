@@ -186,9 +186,25 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
  * rgeo_last_error), or RGEO_ECUDA if the stream itself failed. */
 rgeo_status rgeo_sync(void *cuda_stream);
 
-/* Measurement helper: time an FP32 FFMA loop on the current device and write
- * the achieved rate in TFLOP/s (2 flops per FFMA) to *tflops.  Synchronous. */
-rgeo_status rgeo_ffma_probe(float *tflops, float *ms);
+/* Process-wide launch tuning of rgeo_trace (no effect on results beyond the
+ * order of float32 summation).  rays_per_thread: 1 or 2 rays advanced together
+ * by each thread (2 applies to isotropic graph metrics only; 0 restores the
+ * default).  The setting is read when a trace is enqueued; it is not
+ * synchronised between host threads.  Errors: RGEO_EINVAL (NULL, bad value,
+ * nonzero reserved fields). */
+typedef struct {
+  int32_t rays_per_thread;
+  int32_t reserved[7]; /* must be zero */
+} rgeo_tuning;
+
+rgeo_status rgeo_set_tuning(const rgeo_tuning *tuning);
+rgeo_status rgeo_get_tuning(rgeo_tuning *tuning);
+
+/* Measurement helper: time an FP32 fused multiply-add loop on the current
+ * device (mode 0: scalar FFMA; mode 1: paired f32x2 FMA) and write the achieved
+ * rate in TFLOP/s (2 flops per multiply-add) to *tflops and the loop time to
+ * *ms.  Synchronous.  Errors: RGEO_EINVAL (NULL output, unknown mode), RGEO_ECUDA. */
+rgeo_status rgeo_ffma_probe(int32_t mode, float *tflops, float *ms);
 
 #ifdef __cplusplus
 }

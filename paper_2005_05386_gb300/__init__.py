@@ -32,7 +32,7 @@ RGEO_MAX_BUMPS = 4096
 # Every symbol include/rgeo.h declares (checked by the tests).
 EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_metric_set_centers",
            "rgeo_metric_destroy", "rgeo_scene_create", "rgeo_scene_destroy", "rgeo_trace",
-           "rgeo_trace_host", "rgeo_sync", "rgeo_ffma_probe")
+           "rgeo_trace_host", "rgeo_sync", "rgeo_set_tuning", "rgeo_get_tuning", "rgeo_ffma_probe")
 
 
 class RgeoError(RuntimeError):
@@ -52,6 +52,10 @@ class rgeo_metric_desc(ctypes.Structure):
 class rgeo_camera(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_float * 3), ("forward", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
                 ("vfov_deg", ctypes.c_float)]
+
+
+class rgeo_tuning(ctypes.Structure):
+    _fields_ = [("rays_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class rgeo_outputs(ctypes.Structure):
@@ -96,8 +100,12 @@ def library() -> ctypes.CDLL:
     L.rgeo_trace_host.argtypes = trace_args
     L.rgeo_sync.restype = i32
     L.rgeo_sync.argtypes = [vp]
+    L.rgeo_set_tuning.restype = i32
+    L.rgeo_set_tuning.argtypes = [ctypes.POINTER(rgeo_tuning)]
+    L.rgeo_get_tuning.restype = i32
+    L.rgeo_get_tuning.argtypes = [ctypes.POINTER(rgeo_tuning)]
     L.rgeo_ffma_probe.restype = i32
-    L.rgeo_ffma_probe.argtypes = [fp, fp]
+    L.rgeo_ffma_probe.argtypes = [i32, fp, fp]
     _lib = L
     return L
 
@@ -179,9 +187,21 @@ def rgeo_sync(stream=None):
     _check(library().rgeo_sync(_stream_handle(stream)), "rgeo_sync")
 
 
-def rgeo_ffma_probe():
+def rgeo_set_tuning(rays_per_thread: int = 0):
+    t = rgeo_tuning()
+    t.rays_per_thread = rays_per_thread
+    _check(library().rgeo_set_tuning(ctypes.byref(t)), "rgeo_set_tuning")
+
+
+def rgeo_get_tuning() -> dict:
+    t = rgeo_tuning()
+    _check(library().rgeo_get_tuning(ctypes.byref(t)), "rgeo_get_tuning")
+    return {"rays_per_thread": t.rays_per_thread}
+
+
+def rgeo_ffma_probe(mode: int = 0):
     t, ms = ctypes.c_float(), ctypes.c_float()
-    _check(library().rgeo_ffma_probe(ctypes.byref(t), ctypes.byref(ms)), "rgeo_ffma_probe")
+    _check(library().rgeo_ffma_probe(mode, ctypes.byref(t), ctypes.byref(ms)), "rgeo_ffma_probe")
     return t.value, ms.value
 
 

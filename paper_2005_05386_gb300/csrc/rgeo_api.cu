@@ -148,10 +148,18 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   p.steps = out->steps;
   p.rgba = reinterpret_cast<uchar4 *>(out->rgba);
   p.drift = out->drift;
+  p.rays_per_thread = rgeo::tuning().rays_per_thread;
   return p;
 }
 
 }  // namespace
+
+namespace rgeo {
+Tuning &tuning() {
+  static Tuning t;
+  return t;
+}
+}  // namespace rgeo
 
 extern "C" {
 
@@ -217,8 +225,7 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
     std::memcpy(raw.data() + 3 * K, desc->amplitude, sizeof(float) * K);
     std::memcpy(raw.data() + 4 * K, desc->sigma, sizeof(float) * 3 * K);
     cudaError_t e = upload(&m->d.raw, raw.data(), raw.size());
-    const int stride = aniso ? rgeo::kAnisoStride : rgeo::kIsoStride;
-    if (e == cudaSuccess) e = cudaMalloc(&m->d.bumps, sizeof(float4) * stride * (size_t)K);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d.bumps, sizeof(float4) * (size_t)rgeo::packed_float4s(K, aniso));
     if (e == cudaSuccess) e = rgeo::launch_pack_bumps(m->d.raw, K, desc->cutoff_sigmas, aniso, m->d.bumps, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
@@ -380,10 +387,30 @@ rgeo_status rgeo_sync(void *cuda_stream) {
   return RGEO_OK;
 }
 
-rgeo_status rgeo_ffma_probe(float *tflops, float *ms) {
+rgeo_status rgeo_set_tuning(const rgeo_tuning *t) {
+  g_last_error.clear();
+  if (!t) return fail(RGEO_EINVAL, "rgeo_set_tuning: NULL");
+  for (int i = 0; i < 7; i++)
+    if (t->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_set_tuning: reserved fields must be zero");
+  if (t->rays_per_thread != 0 && t->rays_per_thread != 1 && t->rays_per_thread != 2)
+    return fail(RGEO_EINVAL, "rgeo_set_tuning: rays_per_thread must be 0, 1 or 2");
+  rgeo::tuning().rays_per_thread = t->rays_per_thread == 0 ? rgeo::Tuning().rays_per_thread : t->rays_per_thread;
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_get_tuning(rgeo_tuning *t) {
+  g_last_error.clear();
+  if (!t) return fail(RGEO_EINVAL, "rgeo_get_tuning: NULL");
+  std::memset(t, 0, sizeof(*t));
+  t->rays_per_thread = rgeo::tuning().rays_per_thread;
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_ffma_probe(int32_t mode, float *tflops, float *ms) {
   g_last_error.clear();
   if (!tflops || !ms) return fail(RGEO_EINVAL, "rgeo_ffma_probe: NULL output");
-  RGEO_CUDA(rgeo::run_ffma_probe(tflops, ms), "rgeo_ffma_probe");
+  if (mode != 0 && mode != 1) return fail(RGEO_EINVAL, "rgeo_ffma_probe: mode must be 0 or 1");
+  RGEO_CUDA(rgeo::run_ffma_probe(mode, tflops, ms), "rgeo_ffma_probe");
   return RGEO_OK;
 }
 

@@ -11,18 +11,25 @@
 
 namespace rgeo {
 
-// Bump table, packed per bump as two float4 (isotropic fast form):
-//   b0 = (cx, cy, cz, R2)   R2 = (cutoff * sigma)^2, +inf when untruncated, -1 when inert (a = 0)
-//   b1 = (qn2, la, qs, q)   q = 1 / sigma^2, qn2 = -q log2(e) / 2, la = log2 |a|, qs = -q sign(a)
-// so that with d = x - c, r2 = |d|^2 and w = 2^(r2 qn2 + la) = |a| exp(-q r2 / 2):
-//   grad f  += (w qs) d
+// Bump table, isotropic fast form: bumps are packed in pairs (2j, 2j+1) so that
+// the device evaluates both with one paired-FP32 instruction per operation.
+// Pair j occupies four float4 (lo = bump 2j, hi = bump 2j+1):
+//   P0 = (-cx_lo, -cx_hi, -cy_lo, -cy_hi)
+//   P1 = (-cz_lo, -cz_hi, R2_lo, R2_hi)   R2 = (cutoff sigma)^2, +inf untruncated, -1 inert (a = 0)
+//   P2 = (qn2_lo, qn2_hi, la_lo, la_hi)   q = 1 / sigma^2, qn2 = -q log2(e) / 2, la = log2 |a|
+//   P3 = (qs_lo, qs_hi, q_lo, q_hi)       qs = -q sign(a)
+// An odd bump count is padded with one inert bump.  With d = x - c, r2 = |d|^2 and
+// w = 2^(r2 qn2 + la) = |a| exp(-q r2 / 2):
+//   grad f        += (w qs) d
 //   -v^T Hess f v += (w qs) (q (d.v)^2 - |v|^2)
-// Anisotropic bumps use three float4:
+// Anisotropic bumps use three float4 per bump:
 //   b0 = (cx, cy, cz, Rball2)  Rball2 = (cutoff * max_i sigma_i)^2 (support ball for the flat skip)
 //   b1 = (qx, qy, qz, sgn)     q_i = 1 / sigma_i^2, sgn = sign(a)
 //   b2 = (la, c2, 0, 0)        c2 = cutoff^2 (+inf when untruncated, -1 when inert)
-constexpr int kIsoStride = 2;
-constexpr int kAnisoStride = 3;
+constexpr int kIsoPairStride = 4;  // float4 per bump pair
+constexpr int kAnisoStride = 3;    // float4 per bump
+// float4 count of a packed table of K bumps
+__host__ __device__ inline int packed_float4s(int K, int aniso) { return aniso ? kAnisoStride * K : kIsoPairStride * ((K + 1) / 2); }
 
 struct MetricDev {
   int kind;            // 0 graph, 1 twist
@@ -91,7 +98,15 @@ struct TraceParams {
   uchar4 *rgba;
   double *drift;
   uint32_t *counter;
+  // launch shape
+  int rays_per_thread;  // 1, or 2 (isotropic graph metric only)
 };
+
+// Process-wide launch tuning (set by rgeo_set_tuning, read at every trace).
+struct Tuning {
+  int rays_per_thread = 1;  // measured faster on GB300 at 64 bumps (occupancy beats shared traffic)
+};
+Tuning &tuning();
 
 // Host-side scene acceleration structures (rgeo_scene_build.cpp).
 struct HostBVH {
@@ -125,6 +140,6 @@ cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, 
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
 cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
 cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
-cudaError_t run_ffma_probe(float *tflops, float *ms);
+cudaError_t run_ffma_probe(int mode, float *tflops, float *ms);
 
 }  // namespace rgeo

@@ -85,36 +85,68 @@ __device__ __forceinline__ void poly_terms(const TraceParams &P, F3 x, F3 v, flo
   }
 }
 
-// Eq. 5.4 over isotropic bumps in shared memory.  With INSIDE, also reports
-// whether x lies in some truncated support (the flat-skip test).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Eq. 5.4 over isotropic bumps in shared memory, two bumps per paired-FP32
+// instruction (the pair layout is described in rgeo_internal.h).  With INSIDE,
+// also reports whether x lies in some truncated support (the flat-skip test).
 template <bool INSIDE>
 __device__ __forceinline__ F3 accel_graph_iso(const TraceParams &P, const float4 *__restrict__ sb,
-                                              int K, F3 x, F3 v, bool &inside) {
+                                              int npairs, F3 x, F3 v, bool &inside) {
   const float vv = dot(v, v);
-  float gx = 0.f, gy = 0.f, gz = 0.f, sn = 0.f;
+  const float2 X = f2(x.x, x.x), Y = f2(x.y, x.y), Z = f2(x.z, x.z);
+  const float2 VX = f2(v.x, v.x), VY = f2(v.y, v.y), VZ = f2(v.z, v.z), NVV = f2(-vv, -vv);
+  float2 gx = f2(0.f, 0.f), gy = gx, gz = gx, sn = gx;
   bool in = false;
-#pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    const float4 b0 = sb[2 * k];
-    const float4 b1 = sb[2 * k + 1];
-    const float dx = x.x - b0.x, dy = x.y - b0.y, dz = x.z - b0.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    float w = ex2_approx(fmaf(r2, b1.x, b1.y));
-    const bool p = r2 < b0.w;
-    if (INSIDE) in |= p;
-    w = p ? w : 0.f;
-    const float g = w * b1.z;  // -a q e
-    gx = fmaf(g, dx, gx);
-    gy = fmaf(g, dy, gy);
-    gz = fmaf(g, dz, gz);
-    const float dv = fmaf(dz, v.z, fmaf(dy, v.y, dx * v.x));
-    const float t = fmaf(dv * b1.w, dv, -vv);  // q (d.v)^2 - |v|^2
-    sn = fmaf(g, t, sn);                       // accumulates -v^T Hess f v
+#pragma unroll 2
+  for (int j = 0; j < npairs; ++j) {
+    const float4 p0 = sb[4 * j], p1 = sb[4 * j + 1], p2 = sb[4 * j + 2], p3 = sb[4 * j + 3];
+    const float2 dx = __fadd2_rn(X, f2(p0.x, p0.y));
+    const float2 dy = __fadd2_rn(Y, f2(p0.z, p0.w));
+    const float2 dz = __fadd2_rn(Z, f2(p1.x, p1.y));
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float2 arg = __ffma2_rn(r2, f2(p2.x, p2.y), f2(p2.z, p2.w));
+    float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
+    const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
+    if (INSIDE) in |= in0 | in1;
+    w0 = in0 ? w0 : 0.f;
+    w1 = in1 ? w1 : 0.f;
+    const float2 g = __fmul2_rn(f2(w0, w1), f2(p3.x, p3.y));  // -a q e
+    gx = __ffma2_rn(g, dx, gx);
+    gy = __ffma2_rn(g, dy, gy);
+    gz = __ffma2_rn(g, dz, gz);
+    float2 dv = __fmul2_rn(dx, VX);
+    dv = __ffma2_rn(dy, VY, dv);
+    dv = __ffma2_rn(dz, VZ, dv);
+    const float2 t = __ffma2_rn(__fmul2_rn(dv, f2(p3.z, p3.w)), dv, NVV);  // q (d.v)^2 - |v|^2
+    sn = __ffma2_rn(g, t, sn);                                             // -v^T Hess f v
   }
-  poly_terms(P, x, v, gx, gy, gz, sn);
-  const float coef = sn / fmaf(gz, gz, fmaf(gy, gy, fmaf(gx, gx, 1.f)));
+  float sgx = gx.x + gx.y, sgy = gy.x + gy.y, sgz = gz.x + gz.y, ssn = sn.x + sn.y;
+  poly_terms(P, x, v, sgx, sgy, sgz, ssn);
+  const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
   if (INSIDE) inside = in;
-  return f3(coef * gx, coef * gy, coef * gz);
+  return f3(coef * sgx, coef * sgy, coef * sgz);
+}
+
+// One bump of a packed isotropic pair: centre, R2 and the exponent/scale constants.
+struct IsoBump {
+  F3 c;
+  float R2, qn2, la, qs, q;
+};
+__device__ __forceinline__ IsoBump iso_bump(const float4 *sb, int k) {
+  const float4 p0 = sb[4 * (k >> 1)], p1 = sb[4 * (k >> 1) + 1], p2 = sb[4 * (k >> 1) + 2],
+               p3 = sb[4 * (k >> 1) + 3];
+  IsoBump b;
+  if ((k & 1) == 0) {
+    b.c = f3(-p0.x, -p0.z, -p1.x);
+    b.R2 = p1.z; b.qn2 = p2.x; b.la = p2.z; b.qs = p3.x; b.q = p3.z;
+  } else {
+    b.c = f3(-p0.y, -p0.w, -p1.y);
+    b.R2 = p1.w; b.qn2 = p2.y; b.la = p2.w; b.qs = p3.y; b.q = p3.w;
+  }
+  return b;
 }
 
 template <bool INSIDE>
@@ -157,7 +189,7 @@ __device__ __forceinline__ F3 accel_twist(float k, F3 x, F3 v) {
 
 template <int MK, bool INSIDE>
 __device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside) {
-  if (MK == MK_GRAPH_ISO) return accel_graph_iso<INSIDE>(P, sb, P.K, x, v, inside);
+  if (MK == MK_GRAPH_ISO) return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
   if (MK == MK_GRAPH_ANISO) return accel_graph_aniso<INSIDE>(P, sb, P.K, x, v, inside);
   return accel_twist(P.twist_k, x, v);
 }
@@ -170,14 +202,13 @@ __device__ F3 grad_f(const TraceParams &P, const float4 *sb, F3 x) {
     float4 b0, b1, b2;
     float dx, dy, dz, u;
     if (MK == MK_GRAPH_ISO) {
-      b0 = sb[2 * k];
-      b1 = sb[2 * k + 1];
-      dx = x.x - b0.x; dy = x.y - b0.y; dz = x.z - b0.z;
+      const IsoBump b = iso_bump(sb, k);
+      dx = x.x - b.c.x; dy = x.y - b.c.y; dz = x.z - b.c.z;
       u = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      const float w = u < b0.w ? ex2_approx(fmaf(u, b1.x, b1.y)) : 0.f;
-      gx = fmaf(w * b1.z, dx, gx);
-      gy = fmaf(w * b1.z, dy, gy);
-      gz = fmaf(w * b1.z, dz, gz);
+      const float w = u < b.R2 ? ex2_approx(fmaf(u, b.qn2, b.la)) : 0.f;
+      gx = fmaf(w * b.qs, dx, gx);
+      gy = fmaf(w * b.qs, dy, gy);
+      gz = fmaf(w * b.qs, dz, gz);
     } else {
       b0 = sb[3 * k];
       b1 = sb[3 * k + 1];
@@ -373,16 +404,27 @@ __device__ __forceinline__ float safe_distance(const TraceParams &P, F3 x) {
 }
 
 // Smallest t >= 0 at which x + t v enters a support ball (flat skip), +inf if none.
-__device__ float support_entry(const float4 *sb, int stride, int K, F3 x, F3 v) {
+template <int MK>
+__device__ float support_entry(const float4 *sb, int K, F3 x, F3 v) {
   const float A = dot(v, v);
   float best = __int_as_float(0x7f800000);
   for (int k = 0; k < K; ++k) {
-    const float4 b0 = sb[stride * k];
-    if (b0.w < 0.f) continue;
-    const F3 o = f3(x.x - b0.x, x.y - b0.y, x.z - b0.z);
+    F3 c;
+    float R2;
+    if (MK == MK_GRAPH_ISO) {
+      const IsoBump b = iso_bump(sb, k);
+      c = b.c;
+      R2 = b.R2;
+    } else {
+      const float4 b0 = sb[kAnisoStride * k];
+      c = f3(b0.x, b0.y, b0.z);
+      R2 = b0.w;
+    }
+    if (R2 < 0.f) continue;
+    const F3 o = f3(x.x - c.x, x.y - c.y, x.z - c.z);
     const float B = dot(o, v);
     if (B >= 0.f) continue;
-    const float C = dot(o, o) - b0.w;
+    const float C = dot(o, o) - R2;
     const float disc = B * B - A * C;
     if (disc < 0.f) continue;
     const float t = fmaxf((-B - sqrtf(disc)) / A, 0.f);
@@ -496,142 +538,316 @@ __device__ void finish_ray(const TraceParams &P, const float4 *sb, const float4 
   }
 }
 
-template <int MK, int INTEG>
-__global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
-  extern __shared__ float4 smem[];
-  const int stride = MK == MK_GRAPH_ANISO ? kAnisoStride : kIsoStride;
-  const int nb4 = MK == MK_TWIST ? 0 : stride * P.K;
+// Stage the bump table and the spheres in shared memory; returns the bump part size.
+template <int MK>
+__device__ __forceinline__ int stage_shared(const TraceParams &P, float4 *smem) {
+  const int nb4 = MK == MK_TWIST ? 0 : packed_float4s(P.K, MK == MK_GRAPH_ANISO);
   for (int i = threadIdx.x; i < nb4; i += blockDim.x) smem[i] = P.bumps[i];
   for (int i = threadIdx.x; i < P.S; i += blockDim.x) smem[nb4 + i] = P.spheres[i];
   __syncthreads();
-  const float4 *sb = smem;
-  const float4 *ss = smem + nb4;
+  return nb4;
+}
 
+// Warp-synchronous refill: every lane calls this; lanes whose slot is empty take
+// the next queue items (one atomic per warp).  Items walk 8 x 4 pixel tiles so that
+// a warp's rays start close together.
+template <int MK>
+__device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, bool &active,
+                                       bool &drained, Ray &r) {
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  bool active = false, drained = false;
-  Ray r;
-  const float h = P.h;
-
-  for (;;) {
-    // ---- refill: lanes without a ray take the next items of the queue
-    const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      unsigned base = 0;
-      if ((int)lane == leader) base = atomicAdd(P.counter, (unsigned)__popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (base + (unsigned)__popc(need) >= P.n_items) drained = true;
-      if (!active && ((need >> lane) & 1u)) {
-        const unsigned item = base + (unsigned)__popc(need & lt_mask);
-        if (item < P.n_items) {
-          // items walk 8 x 4 pixel tiles so that a warp's rays start close together
-          const unsigned tile = item >> 5, sub = item & 31u;
-          const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
-          const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
-          if (px < P.W && py < P.H) {
-            init_ray<MK>(P, sb, py * P.W + px, r);
-            active = true;
-          }
-        }
-      }
-    }
-    if (!__any_sync(0xffffffffu, active)) {
-      if (drained) break;
-      continue;
-    }
-    if (!active) continue;
-
-    // ---- stage 1 at (x, v), with the flat-skip test
-    bool inside = true;
-    F3 x = xhi(r), v = vhi(r);
-    F3 a1 = accel<MK, true>(P, sb, x, v, inside);
-    if (MK != MK_TWIST && P.skippable && !inside) {
-      // straight line to the next support ball (exact: Hess f = 0 out here, Eq. 5.4)
-      const float t = support_entry(sb, stride, P.K, x, v);
-      HitRec hr;
-      if (scene_hit(P, ss, x, v, t, hr)) {
-        finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v);
-        active = false;
-        continue;
-      }
-      if (isinf(t)) {
-        finish_ray<MK>(P, sb, ss, r, RGEO_ID_MISS, hr, x, v);
-        active = false;
-        continue;
-      }
-      for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], t * comp(v, c));
-      r.dleft = 0.f;
-      x = xhi(r);
-      a1 = accel<MK, false>(P, sb, x, v, inside);
-    }
-    if (r.steps >= P.max_steps) {
-      HitRec hr;
-      hr.id = -1;
-      finish_ray<MK>(P, sb, ss, r, RGEO_ID_BUDGET, hr, x, v);
-      active = false;
-      continue;
-    }
-
-    // ---- one integration step
-    F3 dx, dvel;
-    if (INTEG == 0) {  // classical RK4
-      const float h2 = 0.5f * h;
-      const F3 v2 = axpy(h2, a1, v);
-      const F3 a2 = accel<MK, false>(P, sb, axpy(h2, v, x), v2, inside);
-      const F3 v3 = axpy(h2, a2, v);
-      const F3 a3 = accel<MK, false>(P, sb, axpy(h2, v2, x), v3, inside);
-      const F3 v4 = axpy(h, a3, v);
-      const F3 a4 = accel<MK, false>(P, sb, axpy(h, v3, x), v4, inside);
-      const float h6 = h * (1.f / 6.f);
-      dx = h6 * (v + 2.f * (v2 + v3) + v4);
-      dvel = h6 * (a1 + 2.f * (a2 + a3) + a4);
-    } else {  // Euler marching, Eq. 4.1
-      dx = h * v;
-      dvel = h * a1;
-    }
-    for (int c = 0; c < 3; c++) {
-      comp_add(r.xh[c], r.xl[c], comp(dx, c));
-      comp_add(r.vh[c], r.vl[c], comp(dvel, c));
-    }
-    r.steps++;
-
-    // ---- segment [x_i, x_{i+1}] against the scene, skipped exactly while the
-    //      polygon cannot have left a ball that holds no scene point
-    const F3 xn = xhi(r);
-    const F3 D = xn - x;
-    bool test = true;
-    if (P.safe_skip) {
-      const float L = sqrtf(dot(D, D)) * (1.f + 1e-6f);
-      if (L < r.dleft) {
-        r.dleft -= L;
-        test = false;
-      } else {
-        const float d0 = safe_distance(P, x);
-        if (L < d0) {
-          r.dleft = d0 - L;
-          test = false;
-        } else {
-          r.dleft = 0.f;
-        }
-      }
-    }
-    if (test) {
-      HitRec hr;
-      if (scene_hit(P, ss, x, D, 1.f, hr)) {
-        finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, x), D);
-        active = false;
+  const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+  if (!need) return;
+  const int leader = __ffs(need) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(P.counter, (unsigned)__popc(need));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (base + (unsigned)__popc(need) >= P.n_items) drained = true;
+  if (!active && ((need >> lane) & 1u)) {
+    const unsigned item = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+    if (item < P.n_items) {
+      const unsigned tile = item >> 5, sub = item & 31u;
+      const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
+      const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
+      if (px < P.W && py < P.H) {
+        init_ray<MK>(P, sb, py * P.W + px, r);
+        active = true;
       }
     }
   }
 }
 
+// Before a step: closed-form advance through flat space when x lies outside every
+// truncated support (exact: Hess f = 0 there, Eq. 5.4), then the step budget.
+// a1 is the stage-1 acceleration at x; it is recomputed if x moves.  Returns false
+// when the ray finished (its pixel is written).
+template <int MK>
+__device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb, const float4 *ss,
+                                         Ray &r, F3 &a1, bool inside) {
+  F3 x = xhi(r);
+  const F3 v = vhi(r);
+  if (MK != MK_TWIST && P.skippable && !inside) {
+    const float t = support_entry<MK>(sb, P.K, x, v);
+    HitRec hr;
+    if (scene_hit(P, ss, x, v, t, hr)) {
+      finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v);
+      return false;
+    }
+    if (isinf(t)) {
+      finish_ray<MK>(P, sb, ss, r, RGEO_ID_MISS, hr, x, v);
+      return false;
+    }
+    for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], t * comp(v, c));
+    r.dleft = 0.f;
+    x = xhi(r);
+    bool dummy;
+    a1 = accel<MK, false>(P, sb, x, v, dummy);
+  }
+  if (r.steps >= P.max_steps) {
+    HitRec hr;
+    hr.id = -1;
+    finish_ray<MK>(P, sb, ss, r, RGEO_ID_BUDGET, hr, x, v);
+    return false;
+  }
+  return true;
+}
+
+// After a step: compensated update of (x, v), then the new polygon segment
+// [x_i, x_{i+1}] against the scene (Section 4.1), skipped exactly while the polygon
+// cannot have left a ball that holds no scene point.  Returns false on a hit.
+template <int MK>
+__device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb, const float4 *ss,
+                                          Ray &r, F3 dx, F3 dvel) {
+  const F3 x = xhi(r);
+  for (int c = 0; c < 3; c++) {
+    comp_add(r.xh[c], r.xl[c], comp(dx, c));
+    comp_add(r.vh[c], r.vl[c], comp(dvel, c));
+  }
+  r.steps++;
+  const F3 D = xhi(r) - x;
+  if (P.safe_skip) {
+    const float L = sqrtf(dot(D, D)) * (1.f + 1e-6f);
+    if (L < r.dleft) {
+      r.dleft -= L;
+      return true;
+    }
+    const float d0 = safe_distance(P, x);
+    if (L < d0) {
+      r.dleft = d0 - L;
+      return true;
+    }
+    r.dleft = 0.f;
+  }
+  HitRec hr;
+  if (scene_hit(P, ss, x, D, 1.f, hr)) {
+    finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, x), D);
+    return false;
+  }
+  return true;
+}
+
+// RK4 (or Euler, Eq. 4.1) increments of one step from (x, v) with stage-1 value a1.
+template <int MK, int INTEG>
+__device__ __forceinline__ void step_increments(const TraceParams &P, const float4 *sb, F3 x, F3 v,
+                                                F3 a1, F3 &dx, F3 &dvel) {
+  const float h = P.h;
+  if (INTEG == 0) {
+    bool dummy;
+    const float h2 = 0.5f * h;
+    const F3 v2 = axpy(h2, a1, v);
+    const F3 a2 = accel<MK, false>(P, sb, axpy(h2, v, x), v2, dummy);
+    const F3 v3 = axpy(h2, a2, v);
+    const F3 a3 = accel<MK, false>(P, sb, axpy(h2, v2, x), v3, dummy);
+    const F3 v4 = axpy(h, a3, v);
+    const F3 a4 = accel<MK, false>(P, sb, axpy(h, v3, x), v4, dummy);
+    const float h6 = h * (1.f / 6.f);
+    dx = h6 * (v + 2.f * (v2 + v3) + v4);
+    dvel = h6 * (a1 + 2.f * (a2 + a3) + a4);
+  } else {
+    dx = h * v;
+    dvel = h * a1;
+  }
+}
+
+// One ray per thread (every metric kind).
+template <int MK, int INTEG>
+__global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
+  extern __shared__ float4 smem[];
+  const int nb4 = stage_shared<MK>(P, smem);
+  const float4 *sb = smem;
+  const float4 *ss = smem + nb4;
+  bool active = false, drained = false;
+  Ray r;
+  for (;;) {
+    refill<MK>(P, sb, active, drained, r);
+    if (!__any_sync(0xffffffffu, active)) {
+      if (drained) break;
+      continue;
+    }
+    if (!active) continue;
+    bool inside = true;
+    F3 a1 = accel<MK, true>(P, sb, xhi(r), vhi(r), inside);
+    if (!pre_step<MK>(P, sb, ss, r, a1, inside)) {
+      active = false;
+      continue;
+    }
+    F3 dx, dvel;
+    step_increments<MK, INTEG>(P, sb, xhi(r), vhi(r), a1, dx, dvel);
+    active = post_step<MK>(P, sb, ss, r, dx, dvel);
+  }
+}
+
+// Eq. 5.4 for two rays against the same isotropic bump pairs: each loaded pair
+// of bumps serves both rays, halving shared-memory traffic per ray.
+template <bool INSIDE>
+__device__ __forceinline__ void accel_graph_iso_x2(const TraceParams &P, const float4 *__restrict__ sb,
+                                                   int npairs, F3 xa, F3 va, F3 xb, F3 vb, F3 &aa,
+                                                   F3 &ab, bool &ina, bool &inb) {
+  const float vva = dot(va, va), vvb = dot(vb, vb);
+  const float2 XA = f2(xa.x, xa.x), YA = f2(xa.y, xa.y), ZA = f2(xa.z, xa.z);
+  const float2 VXA = f2(va.x, va.x), VYA = f2(va.y, va.y), VZA = f2(va.z, va.z), NVVA = f2(-vva, -vva);
+  const float2 XB = f2(xb.x, xb.x), YB = f2(xb.y, xb.y), ZB = f2(xb.z, xb.z);
+  const float2 VXB = f2(vb.x, vb.x), VYB = f2(vb.y, vb.y), VZB = f2(vb.z, vb.z), NVVB = f2(-vvb, -vvb);
+  float2 gxa = f2(0.f, 0.f), gya = gxa, gza = gxa, sna = gxa;
+  float2 gxb = gxa, gyb = gxa, gzb = gxa, snb = gxa;
+  bool ia = false, ib = false;
+#pragma unroll 1
+  for (int j = 0; j < npairs; ++j) {
+    const float4 p0 = sb[4 * j], p1 = sb[4 * j + 1], p2 = sb[4 * j + 2], p3 = sb[4 * j + 3];
+    const float2 ncx = f2(p0.x, p0.y), ncy = f2(p0.z, p0.w), ncz = f2(p1.x, p1.y);
+    const float2 qn2 = f2(p2.x, p2.y), la = f2(p2.z, p2.w), qs = f2(p3.x, p3.y), q = f2(p3.z, p3.w);
+    {
+      const float2 dx = __fadd2_rn(XA, ncx), dy = __fadd2_rn(YA, ncy), dz = __fadd2_rn(ZA, ncz);
+      float2 r2 = __fmul2_rn(dx, dx);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dz, dz, r2);
+      const float2 arg = __ffma2_rn(r2, qn2, la);
+      float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
+      const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
+      if (INSIDE) ia |= in0 | in1;
+      w0 = in0 ? w0 : 0.f;
+      w1 = in1 ? w1 : 0.f;
+      const float2 g = __fmul2_rn(f2(w0, w1), qs);
+      gxa = __ffma2_rn(g, dx, gxa);
+      gya = __ffma2_rn(g, dy, gya);
+      gza = __ffma2_rn(g, dz, gza);
+      float2 dv = __fmul2_rn(dx, VXA);
+      dv = __ffma2_rn(dy, VYA, dv);
+      dv = __ffma2_rn(dz, VZA, dv);
+      sna = __ffma2_rn(g, __ffma2_rn(__fmul2_rn(dv, q), dv, NVVA), sna);
+    }
+    {
+      const float2 dx = __fadd2_rn(XB, ncx), dy = __fadd2_rn(YB, ncy), dz = __fadd2_rn(ZB, ncz);
+      float2 r2 = __fmul2_rn(dx, dx);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dz, dz, r2);
+      const float2 arg = __ffma2_rn(r2, qn2, la);
+      float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
+      const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
+      if (INSIDE) ib |= in0 | in1;
+      w0 = in0 ? w0 : 0.f;
+      w1 = in1 ? w1 : 0.f;
+      const float2 g = __fmul2_rn(f2(w0, w1), qs);
+      gxb = __ffma2_rn(g, dx, gxb);
+      gyb = __ffma2_rn(g, dy, gyb);
+      gzb = __ffma2_rn(g, dz, gzb);
+      float2 dv = __fmul2_rn(dx, VXB);
+      dv = __ffma2_rn(dy, VYB, dv);
+      dv = __ffma2_rn(dz, VZB, dv);
+      snb = __ffma2_rn(g, __ffma2_rn(__fmul2_rn(dv, q), dv, NVVB), snb);
+    }
+  }
+  {
+    float sgx = gxa.x + gxa.y, sgy = gya.x + gya.y, sgz = gza.x + gza.y, ssn = sna.x + sna.y;
+    poly_terms(P, xa, va, sgx, sgy, sgz, ssn);
+    const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
+    aa = f3(coef * sgx, coef * sgy, coef * sgz);
+  }
+  {
+    float sgx = gxb.x + gxb.y, sgy = gyb.x + gyb.y, sgz = gzb.x + gzb.y, ssn = snb.x + snb.y;
+    poly_terms(P, xb, vb, sgx, sgy, sgz, ssn);
+    const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
+    ab = f3(coef * sgx, coef * sgy, coef * sgz);
+  }
+  if (INSIDE) {
+    ina = ia;
+    inb = ib;
+  }
+}
+
+// Two rays per thread (isotropic graph metric): both rays step together and share
+// every bump pair read from shared memory; each has its own refill, skip and
+// termination.  An empty slot keeps evaluating its last state (results unused).
+template <int INTEG>
+__global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
+  extern __shared__ float4 smem[];
+  const int nb4 = stage_shared<MK_GRAPH_ISO>(P, smem);
+  const float4 *sb = smem;
+  const float4 *ss = smem + nb4;
+  const int np = (P.K + 1) >> 1;
+  bool act0 = false, act1 = false, drained = false;
+  Ray r0, r1;
+  for (int c = 0; c < 3; c++) {
+    r0.xh[c] = r0.vh[c] = r1.xh[c] = r1.vh[c] = 0.f;
+    r0.xl[c] = r0.vl[c] = r1.xl[c] = r1.vl[c] = 0.f;
+  }
+  const float h = P.h;
+  for (;;) {
+    refill<MK_GRAPH_ISO>(P, sb, act0, drained, r0);
+    refill<MK_GRAPH_ISO>(P, sb, act1, drained, r1);
+    if (!__any_sync(0xffffffffu, act0 || act1)) {
+      if (drained) break;
+      continue;
+    }
+    if (!act0 && !act1) continue;
+    bool in0 = true, in1 = true;
+    F3 a10, a11;
+    accel_graph_iso_x2<true>(P, sb, np, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
+    if (act0) act0 = pre_step<MK_GRAPH_ISO>(P, sb, ss, r0, a10, in0);
+    if (act1) act1 = pre_step<MK_GRAPH_ISO>(P, sb, ss, r1, a11, in1);
+    if (!act0 && !act1) continue;
+    const F3 x0 = xhi(r0), v0 = vhi(r0), x1 = xhi(r1), v1 = vhi(r1);
+    F3 dx0, dv0, dx1, dv1;
+    if (INTEG == 0) {
+      bool dummy0, dummy1;
+      const float h2 = 0.5f * h;
+      const F3 v20 = axpy(h2, a10, v0), v21 = axpy(h2, a11, v1);
+      F3 a20, a21;
+      accel_graph_iso_x2<false>(P, sb, np, axpy(h2, v0, x0), v20, axpy(h2, v1, x1), v21, a20, a21, dummy0,
+                                dummy1);
+      const F3 v30 = axpy(h2, a20, v0), v31 = axpy(h2, a21, v1);
+      F3 a30, a31;
+      accel_graph_iso_x2<false>(P, sb, np, axpy(h2, v20, x0), v30, axpy(h2, v21, x1), v31, a30, a31, dummy0,
+                                dummy1);
+      const F3 v40 = axpy(h, a30, v0), v41 = axpy(h, a31, v1);
+      F3 a40, a41;
+      accel_graph_iso_x2<false>(P, sb, np, axpy(h, v30, x0), v40, axpy(h, v31, x1), v41, a40, a41, dummy0,
+                                dummy1);
+      const float h6 = h * (1.f / 6.f);
+      dx0 = h6 * (v0 + 2.f * (v20 + v30) + v40);
+      dv0 = h6 * (a10 + 2.f * (a20 + a30) + a40);
+      dx1 = h6 * (v1 + 2.f * (v21 + v31) + v41);
+      dv1 = h6 * (a11 + 2.f * (a21 + a31) + a41);
+    } else {
+      dx0 = h * v0;
+      dv0 = h * a10;
+      dx1 = h * v1;
+      dv1 = h * a11;
+    }
+    if (act0) act0 = post_step<MK_GRAPH_ISO>(P, sb, ss, r0, dx0, dv0);
+    if (act1) act1 = post_step<MK_GRAPH_ISO>(P, sb, ss, r1, dx1, dv1);
+  }
+}
+
+// Packs bump k (isotropic: into its half of pair k / 2; one thread per half, so the
+// padding half of an odd count is written too).
 __global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const float *c = raw + 3 * k;
-  const float a = raw[3 * K + k];
-  const float *sg = raw + 4 * K + 3 * k;
+  const int limit = aniso ? K : 2 * ((K + 1) / 2);
+  if (k >= limit) return;
+  const bool pad = k >= K;
+  const float *c = raw + 3 * (pad ? 0 : k);
+  const float a = pad ? 0.f : raw[3 * K + k];
+  const float *sg = raw + 4 * K + 3 * (pad ? 0 : k);
   const bool inert = a == 0.f;
   const float la = inert ? -__int_as_float(0x7f800000) : log2f(fabsf(a));
   const float sgn = a > 0.f ? 1.f : (a < 0.f ? -1.f : 0.f);
@@ -641,8 +857,16 @@ __global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, f
     const float q = 1.f / (s * s);
     float R2 = cutoff > 0.f ? (cutoff * s) * (cutoff * s) : inf;
     if (inert) R2 = -1.f;
-    out[2 * k] = make_float4(c[0], c[1], c[2], R2);
-    out[2 * k + 1] = make_float4(-0.5f * q * kLog2e, la, -q * sgn, q);
+    float *p = reinterpret_cast<float *>(out + 4 * (k >> 1));
+    const int h = k & 1;
+    p[0 + h] = -c[0];
+    p[2 + h] = -c[1];
+    p[4 + h] = -c[2];
+    p[6 + h] = R2;
+    p[8 + h] = -0.5f * q * kLog2e;
+    p[10 + h] = la;
+    p[12 + h] = -q * sgn;
+    p[14 + h] = q;
   } else {
     const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
     float Rb = cutoff > 0.f ? (cutoff * smax) * (cutoff * smax) : inf;
@@ -657,26 +881,51 @@ __global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, f
   }
 }
 
-__global__ void k_set_centers(const float *c, int K, int stride, float4 *bumps) {
+__global__ void k_set_centers(const float *c, int K, int aniso, float4 *bumps) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
-  float4 b = bumps[stride * k];
-  b.x = c[3 * k];
-  b.y = c[3 * k + 1];
-  b.z = c[3 * k + 2];
-  bumps[stride * k] = b;
+  if (aniso) {
+    float4 b = bumps[kAnisoStride * k];
+    b.x = c[3 * k];
+    b.y = c[3 * k + 1];
+    b.z = c[3 * k + 2];
+    bumps[kAnisoStride * k] = b;
+  } else {
+    float *p = reinterpret_cast<float *>(bumps + 4 * (k >> 1));
+    const int h = k & 1;
+    p[0 + h] = -c[3 * k];
+    p[2 + h] = -c[3 * k + 1];
+    p[4 + h] = -c[3 * k + 2];
+  }
 }
 
-__global__ void k_ffma(float *out, int iters) {
+// FP32 throughput probe: 8 independent FMA chains per thread, scalar (mode 0) or
+// paired f32x2 (mode 1, 16 chains' worth of flops per loop), 2 flops per FMA.
+__global__ void k_ffma(float *out, int iters, int mode) {
   float a0 = threadIdx.x * 1e-3f, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f;
   float a4 = a0 + 4.f, a5 = a0 + 5.f, a6 = a0 + 6.f, a7 = a0 + 7.f;
   const float b = 0.999999f, c = 1e-7f;
-  for (int i = 0; i < iters; ++i) {
+  if (mode == 0) {
+    for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      a0 = fmaf(a0, b, c); a1 = fmaf(a1, b, c); a2 = fmaf(a2, b, c); a3 = fmaf(a3, b, c);
-      a4 = fmaf(a4, b, c); a5 = fmaf(a5, b, c); a6 = fmaf(a6, b, c); a7 = fmaf(a7, b, c);
+      for (int u = 0; u < 16; ++u) {
+        a0 = fmaf(a0, b, c); a1 = fmaf(a1, b, c); a2 = fmaf(a2, b, c); a3 = fmaf(a3, b, c);
+        a4 = fmaf(a4, b, c); a5 = fmaf(a5, b, c); a6 = fmaf(a6, b, c); a7 = fmaf(a7, b, c);
+      }
     }
+  } else {
+    float2 p0 = make_float2(a0, a1), p1 = make_float2(a2, a3), p2 = make_float2(a4, a5),
+           p3 = make_float2(a6, a7);
+    const float2 B = make_float2(b, b), C = make_float2(c, c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        p0 = __ffma2_rn(p0, B, C); p1 = __ffma2_rn(p1, B, C);
+        p2 = __ffma2_rn(p2, B, C); p3 = __ffma2_rn(p3, B, C);
+      }
+    }
+    a0 = p0.x + p0.y; a1 = p1.x + p1.y; a2 = p2.x + p2.y; a3 = p3.x + p3.y;
+    a4 = a5 = a6 = a7 = 0.f;
   }
   const float s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
   if (s == 12345.f) out[threadIdx.x] = s;  // keeps the loop alive
@@ -684,10 +933,12 @@ __global__ void k_ffma(float *out, int iters) {
 
 template <int MK, int INTEG>
 cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
-  const int stride = MK == MK_GRAPH_ANISO ? kAnisoStride : kIsoStride;
-  const size_t smem = (size_t)((MK == MK_TWIST ? 0 : stride * p.K) + p.S) * sizeof(float4);
+  const size_t smem =
+      (size_t)((MK == MK_TWIST ? 0 : packed_float4s(p.K, MK == MK_GRAPH_ANISO)) + p.S) * sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
-  auto kern = k_trace<MK, INTEG>;
+  const bool x2 = MK == MK_GRAPH_ISO && p.rays_per_thread == 2;
+  void (*kern)(const TraceParams) = k_trace<MK, INTEG>;
+  if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -697,7 +948,8 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)sms * per_sm;
-  const long long need = ((long long)p.n_items + 127) / 128;
+  const long long rays_per_block = x2 ? 256 : 128;
+  const long long need = ((long long)p.n_items + rays_per_block - 1) / rays_per_block;
   if (blocks > need) blocks = need > 0 ? need : 1;
   kern<<<(unsigned)blocks, 128, smem, st>>>(p);
   return cudaGetLastError();
@@ -715,13 +967,13 @@ cudaError_t launch_trace(const TraceParams &p, cudaStream_t st) {
 cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
                               cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_pack_bumps<<<(K + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, out);
+  k_pack_bumps<<<(K + 1 + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_set_centers<<<(K + 127) / 128, 128, 0, st>>>(c, K, aniso ? kAnisoStride : kIsoStride, bumps);
+  k_set_centers<<<(K + 127) / 128, 128, 0, st>>>(c, K, aniso, bumps);
   return cudaGetLastError();
 }
 
@@ -736,7 +988,7 @@ cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st) {
   return cudaStreamSynchronize(st);
 }
 
-cudaError_t run_ffma_probe(float *tflops, float *ms) {
+cudaError_t run_ffma_probe(int mode, float *tflops, float *ms) {
   int dev = 0, sms = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -747,9 +999,9 @@ cudaError_t run_ffma_probe(float *tflops, float *ms) {
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  k_ffma<<<blocks, threads>>>(out, 64);  // warm-up
+  k_ffma<<<blocks, threads>>>(out, 64, mode);  // warm-up
   cudaEventRecord(a);
-  k_ffma<<<blocks, threads>>>(out, iters);
+  k_ffma<<<blocks, threads>>>(out, iters, mode);
   cudaEventRecord(b);
   e = cudaEventSynchronize(b);
   float t = 0.f;

@@ -135,6 +135,21 @@ def test_safe_distance_skip_is_exact(rg):
     assert (a["hit"] == b["hit"]).all()
 
 
+def test_one_and_two_rays_per_thread_agree(rg):
+    """The launch shape changes only the float32 summation order of the bump sums."""
+    w = scenes.config_1080p_64(width=320, height=180)
+    try:
+        rg.rgeo_set_tuning(1)
+        a = _run(rg, w)
+        rg.rgeo_set_tuning(2)
+        assert rg.rgeo_get_tuning()["rays_per_thread"] == 2
+        b = _run(rg, w)
+    finally:
+        rg.rgeo_set_tuning(0)
+    st = compare(a, dict(b, hit=b["hit"].astype(np.float64)), w.scene.n_spheres)
+    assert st["agree"] >= 0.999, st
+
+
 def test_host_buffers_match_device_buffers(rg):
     import torch
     w = scenes.config_parity_64()
