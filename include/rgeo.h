@@ -186,6 +186,47 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
  * rgeo_last_error), or RGEO_ECUDA if the stream itself failed. */
 rgeo_status rgeo_sync(void *cuda_stream);
 
+/* Allocation-free tracing (the paper has no counterpart; this serves callers).
+ *
+ * Some callers cannot allocate device memory: a plugin whose host application
+ * owns the whole device memory budget, a real-time frame loop in which
+ * cudaMalloc (which may synchronise the device) is not allowed, or code that
+ * hands out memory only from its own fixed arena.  They also cannot create the
+ * metric and scene handles, which allocate.  rgeo_trace_noalloc takes the
+ * inputs as DEVICE arrays the caller owns and allocates nothing: it calls no
+ * cudaMalloc, cudaMallocAsync, cudaFree or other allocating routine.  Its
+ * scratch (the packed bump table and the work counter) is a file-scope device
+ * array of 33,024 bytes that every GPU loading the library holds until the
+ * process exits.
+ *
+ * Scope: the graph metric of up to RGEO_NOALLOC_MAX_BUMPS isotropic Gaussian
+ * bumps (no affine or quadratic part), up to RGEO_NOALLOC_MAX_SPHERES spheres,
+ * no triangle mesh, no energy diagnostic; results equal those of rgeo_trace on
+ * the same inputs.
+ *   center    DEVICE [K*3] bump centres       amplitude DEVICE [K]
+ *   sigma     DEVICE [K] isotropic spreads (> 0)
+ *   spheres   DEVICE [S*4] cx, cy, cz, r (16-byte aligned)
+ *   albedo    DEVICE [(S+1)*3]
+ * Other arguments as for rgeo_trace (out->drift is ignored).  A bump whose
+ * device values are non-finite or whose spread is <= 0 is treated as inert.
+ *
+ * The first call on a device looks up the scratch address with that device
+ * current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the one scratch array per device and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (different streams
+ * without ordering between them) race and must not be issued.  Asynchronous on
+ * the stream.  Errors: RGEO_EINVAL (counts beyond the maxima, NULL pointers,
+ * bad camera, size, step or enum), RGEO_ECUDA. */
+#define RGEO_NOALLOC_MAX_BUMPS 1024
+#define RGEO_NOALLOC_MAX_SPHERES 1024
+
+rgeo_status rgeo_trace_noalloc(const float *center, const float *amplitude, const float *sigma,
+                               int32_t n_bumps, float cutoff_sigmas, const float *spheres,
+                               int32_t n_spheres, const float *albedo, const rgeo_camera *camera,
+                               int32_t width, int32_t height, float h, int32_t max_steps,
+                               int32_t integrator, int32_t shading, const rgeo_outputs *out,
+                               void *cuda_stream);
+
 /* Process-wide launch tuning of rgeo_trace (no effect on results beyond the
  * order of float32 summation).  rays_per_thread: 1 or 2 rays advanced together
  * by each thread (2 applies to isotropic graph metrics only; 0 restores the

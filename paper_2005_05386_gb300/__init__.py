@@ -32,7 +32,10 @@ RGEO_MAX_BUMPS = 4096
 # Every symbol include/rgeo.h declares (checked by the tests).
 EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_metric_set_centers",
            "rgeo_metric_destroy", "rgeo_scene_create", "rgeo_scene_destroy", "rgeo_trace",
-           "rgeo_trace_host", "rgeo_sync", "rgeo_set_tuning", "rgeo_get_tuning", "rgeo_ffma_probe")
+           "rgeo_trace_host", "rgeo_sync", "rgeo_set_tuning", "rgeo_get_tuning", "rgeo_ffma_probe",
+           "rgeo_trace_noalloc")
+RGEO_NOALLOC_MAX_BUMPS = 1024
+RGEO_NOALLOC_MAX_SPHERES = 1024
 
 
 class RgeoError(RuntimeError):
@@ -100,6 +103,9 @@ def library() -> ctypes.CDLL:
     L.rgeo_trace_host.argtypes = trace_args
     L.rgeo_sync.restype = i32
     L.rgeo_sync.argtypes = [vp]
+    L.rgeo_trace_noalloc.restype = i32
+    L.rgeo_trace_noalloc.argtypes = [vp, vp, vp, i32, f32, vp, i32, vp, ctypes.POINTER(rgeo_camera), i32, i32,
+                                     f32, i32, i32, i32, ctypes.POINTER(rgeo_outputs), vp]
     L.rgeo_set_tuning.restype = i32
     L.rgeo_set_tuning.argtypes = [ctypes.POINTER(rgeo_tuning)]
     L.rgeo_get_tuning.restype = i32
@@ -181,6 +187,16 @@ def rgeo_trace_host(metric: int, scene: int, camera: rgeo_camera, width: int, he
     _check(library().rgeo_trace_host(metric, scene, ctypes.byref(camera), width, height, h, max_steps,
                                      integrator, shading, flags, ctypes.byref(out), _stream_handle(stream)),
            "rgeo_trace_host")
+
+
+def rgeo_trace_noalloc(center: int, amplitude: int, sigma: int, n_bumps: int, cutoff: float, spheres: int,
+                       n_spheres: int, albedo: int, camera: rgeo_camera, width: int, height: int, h: float,
+                       max_steps: int, integrator: int, shading: int, out: rgeo_outputs, stream=None):
+    """Allocation-free trace: every array argument is a device pointer the caller owns
+    (isotropic spreads, spheres only); see include/rgeo.h."""
+    _check(library().rgeo_trace_noalloc(center, amplitude, sigma, n_bumps, cutoff, spheres, n_spheres, albedo,
+                                        ctypes.byref(camera), width, height, h, max_steps, integrator, shading,
+                                        ctypes.byref(out), _stream_handle(stream)), "rgeo_trace_noalloc")
 
 
 def rgeo_sync(stream=None):

@@ -159,6 +159,8 @@ Tuning &tuning() {
   static Tuning t;
   return t;
 }
+
+void set_last_error(const char *msg) { g_last_error = msg; }
 }  // namespace rgeo
 
 extern "C" {

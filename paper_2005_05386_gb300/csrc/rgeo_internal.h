@@ -108,6 +108,9 @@ struct Tuning {
 };
 Tuning &tuning();
 
+// Sets the message rgeo_last_error() returns on this host thread.
+void set_last_error(const char *msg);
+
 // Host-side scene acceleration structures (rgeo_scene_build.cpp).
 struct HostBVH {
   std::vector<float4> nodes;  // 2 per node
