@@ -64,6 +64,7 @@ typedef enum { RGEO_SHADE_LAMBERT = 0, RGEO_SHADE_PSEUDO = 1 } rgeo_shading;
 /* rgeo_trace flags */
 #define RGEO_FLAG_ENERGY_DIAG 1u /* write drift[p] = g(v_end, v_end) / g(v_0, v_0) - 1 (FP64) */
 #define RGEO_FLAG_NO_SAFE_SKIP 2u /* test every segment (disables the exact safe-distance skip) */
+#define RGEO_FLAG_DENSE 4u        /* sum over every bump even when the metric has a cull grid */
 
 /* Object ids written to rgeo_outputs.id */
 #define RGEO_ID_MISS (-1)   /* the geodesic left every bump support and met nothing */
@@ -78,7 +79,10 @@ typedef struct rgeo_scene rgeo_scene;   /* opaque, owns device memory */
  * cutoff_sigmas <= 0 keeps every bump untruncated.  Where no truncated support
  * contains the ray and A = 0, Hess f = 0 and the geodesic is a straight line
  * (Eq. 5.4); the tracer then advances in closed form to the next support.
- * Bumps with a_k = 0 are inert.  For the twist, twist_rate k gives
+ * Bumps with a_k = 0 are inert.  With a cull grid (isotropic truncated bumps),
+ * each cell records which bumps' supports meet it, and a point's sums run over
+ * its cell's bumps only; excluded bumps are exactly zero there, so the result is
+ * the same sum up to float32 summation order.  For the twist, twist_rate k gives
  * Phi(x, y, z) = (cos(kz) x - sin(kz) y, sin(kz) x + cos(kz) y, z) (k = 1 in the paper). */
 typedef struct {
   int32_t kind;            /* rgeo_metric_kind */
@@ -90,7 +94,9 @@ typedef struct {
   float quad_A[9];         /* A, row-major, must be symmetric */
   float cutoff_sigmas;     /* c; 4 is the default used by the workloads */
   float twist_rate;        /* k (twist only) */
-  int32_t reserved[4];     /* must be zero */
+  int32_t cull_grid;       /* bump-support cull grid of G^3 cells: 0 = automatic (G = 32 for
+                              >= 16 isotropic truncated bumps), -1 = none, 4..128 = that G */
+  int32_t reserved[3];     /* must be zero */
 } rgeo_metric_desc;
 
 #define RGEO_MAX_BUMPS 4096

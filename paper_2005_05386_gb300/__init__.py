@@ -26,6 +26,7 @@ RGEO_RK4, RGEO_EULER = 0, 1
 RGEO_SHADE_LAMBERT, RGEO_SHADE_PSEUDO = 0, 1
 RGEO_FLAG_ENERGY_DIAG = 1
 RGEO_FLAG_NO_SAFE_SKIP = 2
+RGEO_FLAG_DENSE = 4
 RGEO_ID_MISS, RGEO_ID_BUDGET = -1, -2
 RGEO_MAX_BUMPS = 4096
 
@@ -49,7 +50,7 @@ class rgeo_metric_desc(ctypes.Structure):
                 ("center", ctypes.POINTER(ctypes.c_float)), ("amplitude", ctypes.POINTER(ctypes.c_float)),
                 ("sigma", ctypes.POINTER(ctypes.c_float)), ("affine_b", ctypes.c_float * 3),
                 ("quad_A", ctypes.c_float * 9), ("cutoff_sigmas", ctypes.c_float),
-                ("twist_rate", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+                ("twist_rate", ctypes.c_float), ("cull_grid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class rgeo_camera(ctypes.Structure):
@@ -236,6 +237,7 @@ def metric_desc(m: scenes.Metric):
     d.quad_A = (ctypes.c_float * 9)(*m.quad_A)
     d.cutoff_sigmas = m.cutoff
     d.twist_rate = m.twist_rate
+    d.cull_grid = getattr(m, "cull_grid", 0)
     return d, (c, a, s)
 
 

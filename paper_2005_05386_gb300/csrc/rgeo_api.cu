@@ -57,6 +57,8 @@ void free_metric(rgeo_metric *m) {
   if (!m) return;
   cudaFree(m->d.bumps);
   cudaFree(m->d.raw);
+  cudaFree(m->d.cull_masks);
+  cudaFree(m->d.cull_hdr);
   delete m;
 }
 
@@ -82,7 +84,7 @@ rgeo_status validate_trace(const rgeo_metric *metric, const rgeo_scene *scene, c
     return fail(RGEO_EINVAL, "rgeo_trace: unknown integrator");
   if (shading != RGEO_SHADE_LAMBERT && shading != RGEO_SHADE_PSEUDO)
     return fail(RGEO_EINVAL, "rgeo_trace: unknown shading mode");
-  if (flags & ~(RGEO_FLAG_ENERGY_DIAG | RGEO_FLAG_NO_SAFE_SKIP))
+  if (flags & ~(RGEO_FLAG_ENERGY_DIAG | RGEO_FLAG_NO_SAFE_SKIP | RGEO_FLAG_DENSE))
     return fail(RGEO_EINVAL, "rgeo_trace: unknown flag bits");
   if (!out->id || !out->hit || !out->steps || !out->rgba)
     return fail(RGEO_EINVAL, "rgeo_trace: id, hit, steps and rgba outputs are required");
@@ -105,6 +107,12 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   std::memset(&p, 0, sizeof(p));
   const rgeo::MetricDev &m = metric->d;
   p.bumps = m.bumps;
+  if (m.cull_G > 0 && !(flags & RGEO_FLAG_DENSE)) {
+    p.cull_masks = m.cull_masks;
+    p.cull_hdr = m.cull_hdr;
+    p.cull_G = m.cull_G;
+    p.cull_words = m.cull_words;
+  }
   p.K = m.kind == RGEO_METRIC_GRAPH_BUMPS ? m.K : 0;
   p.kind = m.kind;
   p.aniso = m.aniso;
@@ -178,8 +186,10 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
   if (desc->kind != RGEO_METRIC_GRAPH_BUMPS && desc->kind != RGEO_METRIC_DIFFEO_TWIST)
     return fail(RGEO_EINVAL, "rgeo_metric_create: unknown metric kind");
   if (K < 0 || K > RGEO_MAX_BUMPS) return fail(RGEO_EINVAL, "rgeo_metric_create: n_bumps out of range");
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < 3; i++)
     if (desc->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_metric_create: reserved fields must be zero");
+  if (desc->cull_grid != 0 && desc->cull_grid != -1 && (desc->cull_grid < 4 || desc->cull_grid > 128))
+    return fail(RGEO_EINVAL, "rgeo_metric_create: cull_grid must be 0, -1 or in [4, 128]");
   if (desc->kind == RGEO_METRIC_DIFFEO_TWIST && K != 0)
     return fail(RGEO_EINVAL, "rgeo_metric_create: the twist metric takes no bumps");
   if (!finite_all(desc->affine_b, 3) || !finite_all(desc->quad_A, 9) || !std::isfinite(desc->cutoff_sigmas) ||
@@ -229,6 +239,18 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
     cudaError_t e = upload(&m->d.raw, raw.data(), raw.size());
     if (e == cudaSuccess) e = cudaMalloc(&m->d.bumps, sizeof(float4) * (size_t)rgeo::packed_float4s(K, aniso));
     if (e == cudaSuccess) e = rgeo::launch_pack_bumps(m->d.raw, K, desc->cutoff_sigmas, aniso, m->d.bumps, 0);
+    // bump-support cull grid: isotropic truncated bumps only
+    int G = 0;
+    if (desc->kind == RGEO_METRIC_GRAPH_BUMPS && !aniso && desc->cutoff_sigmas > 0.f)
+      G = desc->cull_grid == 0 ? (K >= 16 ? 32 : 0) : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
+    if (e == cudaSuccess && G > 0) {
+      const int words = ((K + 1) / 2 + 31) / 32;
+      m->d.cull_G = G;
+      m->d.cull_words = words;
+      e = cudaMalloc(&m->d.cull_masks, sizeof(uint32_t) * (size_t)G * G * G * words);
+      if (e == cudaSuccess) e = cudaMalloc(&m->d.cull_hdr, sizeof(float4) * 2);
+      if (e == cudaSuccess) e = rgeo::launch_build_cull(m->d.bumps, K, G, words, m->d.cull_hdr, m->d.cull_masks, 0);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
       free_metric(m);
@@ -252,6 +274,10 @@ rgeo_status rgeo_metric_set_centers(rgeo_metric *metric, const float *center, vo
             "rgeo_metric_set_centers: copy");
   RGEO_CUDA(rgeo::launch_set_centers(metric->d.raw, K, metric->d.aniso, metric->d.bumps, st),
             "rgeo_metric_set_centers: launch");
+  if (metric->d.cull_G > 0)
+    RGEO_CUDA(rgeo::launch_build_cull(metric->d.bumps, K, metric->d.cull_G, metric->d.cull_words, metric->d.cull_hdr,
+                                      metric->d.cull_masks, st),
+              "rgeo_metric_set_centers: cull grid");
   return RGEO_OK;
 }
 

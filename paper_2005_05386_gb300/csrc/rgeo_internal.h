@@ -43,7 +43,15 @@ struct MetricDev {
   int has_affine, has_quad;
   float cutoff;
   float twist_k;
+  // bump-support cull grid (isotropic, truncated): G^3 cells, `words` uint32 of pair bits per cell
+  int cull_G, cull_words;
+  uint32_t *cull_masks;  // [G^3 * words]
+  float4 *cull_hdr;      // (gmin.xyz, 1 / cell)
 };
+
+// Cull grid: inflation of every support radius (absolute), covering float32 rounding
+// of the cell look-up.
+constexpr float kCullInflate = 1e-3f;
 
 // BVH node: two float4.  n0 = (lo.xyz, int first_or_left), n1 = (hi.xyz, int count);
 // count > 0: leaf over triangles [first, first + count); count == 0: children at left, left + 1.
@@ -66,6 +74,9 @@ struct TraceParams {
   // metric
   const float4 *bumps;
   int K, kind, aniso, skippable;
+  const uint32_t *cull_masks;  // null: dense sums over all bumps
+  const float4 *cull_hdr;
+  int cull_G, cull_words;
   float b[3];
   float A[9];
   int has_affine, has_quad;
@@ -142,6 +153,8 @@ cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, 
                               cudaStream_t st);
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
 cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
+cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
+                              cudaStream_t st);
 cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
 cudaError_t run_ffma_probe(int mode, float *tflops, float *ms);
 

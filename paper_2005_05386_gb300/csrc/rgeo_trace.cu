@@ -87,47 +87,95 @@ __device__ __forceinline__ void poly_terms(const TraceParams &P, F3 x, F3 v, flo
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Broadcast position and velocity of one ray, and its paired accumulators.
+struct PairAcc {
+  float2 X, Y, Z, VX, VY, VZ, NVV;
+  float2 gx, gy, gz, sn;
+  bool in;
+};
+
+__device__ __forceinline__ void pair_acc_init(PairAcc &a, F3 x, F3 v) {
+  const float vv = dot(v, v);
+  a.X = f2(x.x, x.x); a.Y = f2(x.y, x.y); a.Z = f2(x.z, x.z);
+  a.VX = f2(v.x, v.x); a.VY = f2(v.y, v.y); a.VZ = f2(v.z, v.z); a.NVV = f2(-vv, -vv);
+  a.gx = a.gy = a.gz = a.sn = f2(0.f, 0.f);
+  a.in = false;
+}
+
+// Adds bump pair j (both halves at once): grad f and -v^T Hess f v of Eq. 6.1.
+template <bool INSIDE>
+__device__ __forceinline__ void pair_eval(PairAcc &a, const float4 *__restrict__ sb, int j) {
+  const float4 p0 = sb[4 * j], p1 = sb[4 * j + 1], p2 = sb[4 * j + 2], p3 = sb[4 * j + 3];
+  const float2 dx = __fadd2_rn(a.X, f2(p0.x, p0.y));
+  const float2 dy = __fadd2_rn(a.Y, f2(p0.z, p0.w));
+  const float2 dz = __fadd2_rn(a.Z, f2(p1.x, p1.y));
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dz, dz, r2);
+  const float2 arg = __ffma2_rn(r2, f2(p2.x, p2.y), f2(p2.z, p2.w));
+  float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
+  const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
+  if (INSIDE) a.in |= in0 | in1;
+  w0 = in0 ? w0 : 0.f;
+  w1 = in1 ? w1 : 0.f;
+  const float2 g = __fmul2_rn(f2(w0, w1), f2(p3.x, p3.y));  // -a q e
+  a.gx = __ffma2_rn(g, dx, a.gx);
+  a.gy = __ffma2_rn(g, dy, a.gy);
+  a.gz = __ffma2_rn(g, dz, a.gz);
+  float2 dv = __fmul2_rn(dx, a.VX);
+  dv = __ffma2_rn(dy, a.VY, dv);
+  dv = __ffma2_rn(dz, a.VZ, dv);
+  const float2 t = __ffma2_rn(__fmul2_rn(dv, f2(p3.z, p3.w)), dv, a.NVV);  // q (d.v)^2 - |v|^2
+  a.sn = __ffma2_rn(g, t, a.sn);                                           // -v^T Hess f v
+}
+
+// Eq. 5.4 from the accumulated sums (plus the affine and quadratic part of f).
+__device__ __forceinline__ F3 pair_acc_finish(const TraceParams &P, const PairAcc &a, F3 x, F3 v) {
+  float sgx = a.gx.x + a.gx.y, sgy = a.gy.x + a.gy.y, sgz = a.gz.x + a.gz.y, ssn = a.sn.x + a.sn.y;
+  poly_terms(P, x, v, sgx, sgy, sgz, ssn);
+  const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
+  return f3(coef * sgx, coef * sgy, coef * sgz);
+}
+
 // Eq. 5.4 over isotropic bumps in shared memory, two bumps per paired-FP32
 // instruction (the pair layout is described in rgeo_internal.h).  With INSIDE,
 // also reports whether x lies in some truncated support (the flat-skip test).
 template <bool INSIDE>
 __device__ __forceinline__ F3 accel_graph_iso(const TraceParams &P, const float4 *__restrict__ sb,
                                               int npairs, F3 x, F3 v, bool &inside) {
-  const float vv = dot(v, v);
-  const float2 X = f2(x.x, x.x), Y = f2(x.y, x.y), Z = f2(x.z, x.z);
-  const float2 VX = f2(v.x, v.x), VY = f2(v.y, v.y), VZ = f2(v.z, v.z), NVV = f2(-vv, -vv);
-  float2 gx = f2(0.f, 0.f), gy = gx, gz = gx, sn = gx;
-  bool in = false;
+  PairAcc a;
+  pair_acc_init(a, x, v);
 #pragma unroll 2
-  for (int j = 0; j < npairs; ++j) {
-    const float4 p0 = sb[4 * j], p1 = sb[4 * j + 1], p2 = sb[4 * j + 2], p3 = sb[4 * j + 3];
-    const float2 dx = __fadd2_rn(X, f2(p0.x, p0.y));
-    const float2 dy = __fadd2_rn(Y, f2(p0.z, p0.w));
-    const float2 dz = __fadd2_rn(Z, f2(p1.x, p1.y));
-    float2 r2 = __fmul2_rn(dx, dx);
-    r2 = __ffma2_rn(dy, dy, r2);
-    r2 = __ffma2_rn(dz, dz, r2);
-    const float2 arg = __ffma2_rn(r2, f2(p2.x, p2.y), f2(p2.z, p2.w));
-    float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
-    const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
-    if (INSIDE) in |= in0 | in1;
-    w0 = in0 ? w0 : 0.f;
-    w1 = in1 ? w1 : 0.f;
-    const float2 g = __fmul2_rn(f2(w0, w1), f2(p3.x, p3.y));  // -a q e
-    gx = __ffma2_rn(g, dx, gx);
-    gy = __ffma2_rn(g, dy, gy);
-    gz = __ffma2_rn(g, dz, gz);
-    float2 dv = __fmul2_rn(dx, VX);
-    dv = __ffma2_rn(dy, VY, dv);
-    dv = __ffma2_rn(dz, VZ, dv);
-    const float2 t = __ffma2_rn(__fmul2_rn(dv, f2(p3.z, p3.w)), dv, NVV);  // q (d.v)^2 - |v|^2
-    sn = __ffma2_rn(g, t, sn);                                             // -v^T Hess f v
+  for (int j = 0; j < npairs; ++j) pair_eval<INSIDE>(a, sb, j);
+  if (INSIDE) inside = a.in;
+  return pair_acc_finish(P, a, x, v);
+}
+
+// Culled form: the lane looks up the cull-grid cell of x; the participating lanes
+// (pmask) OR their cells' pair masks and evaluate the union in lockstep.  Bumps
+// outside the union have supports that miss every participating lane's cell, so
+// they add exactly zero there.
+template <bool INSIDE>
+__device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const float4 *__restrict__ sb,
+                                                     float4 ghdr, unsigned pmask, F3 x, F3 v, bool &inside) {
+  PairAcc a;
+  pair_acc_init(a, x, v);
+  const int G = P.cull_G;
+  const float fx = (x.x - ghdr.x) * ghdr.w, fy = (x.y - ghdr.y) * ghdr.w, fz = (x.z - ghdr.z) * ghdr.w;
+  const bool ing = fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G;
+  const uint32_t *cm =
+      P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
+  for (int wi = 0; wi < P.cull_words; ++wi) {
+    unsigned m = ing ? __ldg(cm + wi) : 0u;
+    m = __reduce_or_sync(pmask, m);
+    while (m) {
+      const int j = (wi << 5) + __ffs(m) - 1;
+      m &= m - 1u;
+      pair_eval<INSIDE>(a, sb, j);
+    }
   }
-  float sgx = gx.x + gx.y, sgy = gy.x + gy.y, sgz = gz.x + gz.y, ssn = sn.x + sn.y;
-  poly_terms(P, x, v, sgx, sgy, sgz, ssn);
-  const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
-  if (INSIDE) inside = in;
-  return f3(coef * sgx, coef * sgy, coef * sgz);
+  if (INSIDE) inside = a.in;
+  return pair_acc_finish(P, a, x, v);
 }
 
 // One bump of a packed isotropic pair: centre, R2 and the exponent/scale constants.
@@ -187,9 +235,20 @@ __device__ __forceinline__ F3 accel_twist(float k, F3 x, F3 v) {
   return f3(-(c * q1 + s * q2), -(c * q2 - s * q1), 0.f);
 }
 
+// Per-launch context of the bump sums: the cull-grid header and the lanes that
+// take part in the current call (for the warp-wide mask reduction).
+struct SumCtx {
+  float4 ghdr;
+  unsigned pmask;
+};
+
 template <int MK, bool INSIDE>
-__device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside) {
-  if (MK == MK_GRAPH_ISO) return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
+__device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, const SumCtx &cx, F3 x, F3 v,
+                                    bool &inside) {
+  if (MK == MK_GRAPH_ISO) {
+    if (P.cull_masks) return accel_graph_iso_culled<INSIDE>(P, sb, cx.ghdr, cx.pmask, x, v, inside);
+    return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
+  }
   if (MK == MK_GRAPH_ANISO) return accel_graph_aniso<INSIDE>(P, sb, P.K, x, v, inside);
   return accel_twist(P.twist_k, x, v);
 }
@@ -580,28 +639,35 @@ __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, b
 // truncated support (exact: Hess f = 0 there, Eq. 5.4), then the step budget.
 // a1 is the stage-1 acceleration at x; it is recomputed if x moves.  Returns false
 // when the ray finished (its pixel is written).
+// Every lane of cx.pmask must call this (it holds a warp vote).
 template <int MK>
 __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb, const float4 *ss,
-                                         Ray &r, F3 &a1, bool inside) {
+                                         const SumCtx &cx, Ray &r, F3 &a1, bool inside) {
   F3 x = xhi(r);
   const F3 v = vhi(r);
+  bool moved = false, finished = false;
   if (MK != MK_TWIST && P.skippable && !inside) {
     const float t = support_entry<MK>(sb, P.K, x, v);
     HitRec hr;
     if (scene_hit(P, ss, x, v, t, hr)) {
       finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v);
-      return false;
-    }
-    if (isinf(t)) {
+      finished = true;
+    } else if (isinf(t)) {
       finish_ray<MK>(P, sb, ss, r, RGEO_ID_MISS, hr, x, v);
-      return false;
+      finished = true;
+    } else {
+      for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], t * comp(v, c));
+      r.dleft = 0.f;
+      x = xhi(r);
+      moved = true;
     }
-    for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], t * comp(v, c));
-    r.dleft = 0.f;
-    x = xhi(r);
-    bool dummy;
-    a1 = accel<MK, false>(P, sb, x, v, dummy);
   }
+  const unsigned mmask = __ballot_sync(cx.pmask, moved);
+  if (moved) {
+    bool dummy;
+    a1 = accel<MK, false>(P, sb, SumCtx{cx.ghdr, mmask}, x, v, dummy);
+  }
+  if (finished) return false;
   if (r.steps >= P.max_steps) {
     HitRec hr;
     hr.id = -1;
@@ -647,18 +713,18 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
 
 // RK4 (or Euler, Eq. 4.1) increments of one step from (x, v) with stage-1 value a1.
 template <int MK, int INTEG>
-__device__ __forceinline__ void step_increments(const TraceParams &P, const float4 *sb, F3 x, F3 v,
-                                                F3 a1, F3 &dx, F3 &dvel) {
+__device__ __forceinline__ void step_increments(const TraceParams &P, const float4 *sb, const SumCtx &cx, F3 x,
+                                                F3 v, F3 a1, F3 &dx, F3 &dvel) {
   const float h = P.h;
   if (INTEG == 0) {
     bool dummy;
     const float h2 = 0.5f * h;
     const F3 v2 = axpy(h2, a1, v);
-    const F3 a2 = accel<MK, false>(P, sb, axpy(h2, v, x), v2, dummy);
+    const F3 a2 = accel<MK, false>(P, sb, cx, axpy(h2, v, x), v2, dummy);
     const F3 v3 = axpy(h2, a2, v);
-    const F3 a3 = accel<MK, false>(P, sb, axpy(h2, v2, x), v3, dummy);
+    const F3 a3 = accel<MK, false>(P, sb, cx, axpy(h2, v2, x), v3, dummy);
     const F3 v4 = axpy(h, a3, v);
-    const F3 a4 = accel<MK, false>(P, sb, axpy(h, v3, x), v4, dummy);
+    const F3 a4 = accel<MK, false>(P, sb, cx, axpy(h, v3, x), v4, dummy);
     const float h6 = h * (1.f / 6.f);
     dx = h6 * (v + 2.f * (v2 + v3) + v4);
     dvel = h6 * (a1 + 2.f * (a2 + a3) + a4);
@@ -675,23 +741,27 @@ __global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
+  const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
   bool active = false, drained = false;
   Ray r;
   for (;;) {
     refill<MK>(P, sb, active, drained, r);
-    if (!__any_sync(0xffffffffu, active)) {
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
+    if (!amask) {
       if (drained) break;
       continue;
     }
     if (!active) continue;
     bool inside = true;
-    F3 a1 = accel<MK, true>(P, sb, xhi(r), vhi(r), inside);
-    if (!pre_step<MK>(P, sb, ss, r, a1, inside)) {
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask}, xhi(r), vhi(r), inside);
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, amask}, r, a1, inside);
+    const unsigned smask = __ballot_sync(amask, go);
+    if (!go) {
       active = false;
       continue;
     }
     F3 dx, dvel;
-    step_increments<MK, INTEG>(P, sb, xhi(r), vhi(r), a1, dx, dvel);
+    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask}, xhi(r), vhi(r), a1, dx, dvel);
     active = post_step<MK>(P, sb, ss, r, dx, dvel);
   }
 }
@@ -794,7 +864,8 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
   for (;;) {
     refill<MK_GRAPH_ISO>(P, sb, act0, drained, r0);
     refill<MK_GRAPH_ISO>(P, sb, act1, drained, r1);
-    if (!__any_sync(0xffffffffu, act0 || act1)) {
+    const unsigned m0 = __ballot_sync(0xffffffffu, act0), m1 = __ballot_sync(0xffffffffu, act1);
+    if (!(m0 | m1)) {
       if (drained) break;
       continue;
     }
@@ -802,8 +873,9 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     bool in0 = true, in1 = true;
     F3 a10, a11;
     accel_graph_iso_x2<true>(P, sb, np, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
-    if (act0) act0 = pre_step<MK_GRAPH_ISO>(P, sb, ss, r0, a10, in0);
-    if (act1) act1 = pre_step<MK_GRAPH_ISO>(P, sb, ss, r1, a11, in1);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);  // this kernel sums densely (no cull grid)
+    if (act0) act0 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m0}, r0, a10, in0);
+    if (act1) act1 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m1}, r1, a11, in1);
     if (!act0 && !act1) continue;
     const F3 x0 = xhi(r0), v0 = vhi(r0), x1 = xhi(r1), v1 = vhi(r1);
     F3 dx0, dv0, dx1, dv1;
@@ -899,6 +971,87 @@ __global__ void k_set_centers(const float *c, int K, int aniso, float4 *bumps) {
   }
 }
 
+// Cull grid, step 1 (one block): bounding box of every live support ball, inflated
+// by kCullInflate; hdr[0] = (min corner, 1 / cell), hdr[1].x = cell (cubic cells, G
+// along the longest axis).  With no live bump, hdr[0].w = 0 and every mask is empty.
+__global__ void k_cull_bounds(const float4 *bumps, int K, int G, float4 *hdr) {
+  __shared__ float red[6][256];
+  float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const IsoBump b = iso_bump(bumps, k);
+    if (!(b.R2 >= 0.f) || isinf(b.R2)) continue;
+    const float R = sqrtf(b.R2) + kCullInflate;
+    for (int c = 0; c < 3; c++) {
+      lo[c] = fminf(lo[c], comp(b.c, c) - R);
+      hi[c] = fmaxf(hi[c], comp(b.c, c) + R);
+    }
+  }
+  for (int c = 0; c < 3; c++) {
+    red[c][threadIdx.x] = lo[c];
+    red[3 + c][threadIdx.x] = hi[c];
+  }
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int c = 0; c < 3; c++) {
+        red[c][threadIdx.x] = fminf(red[c][threadIdx.x], red[c][threadIdx.x + s]);
+        red[3 + c][threadIdx.x] = fmaxf(red[3 + c][threadIdx.x], red[3 + c][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    float ext = 0.f;
+    for (int c = 0; c < 3; c++) ext = fmaxf(ext, red[3 + c][0] - red[c][0]);
+    if (!(ext > 0.f) || !(red[0][0] < FLT_MAX)) {
+      hdr[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      hdr[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      const float cell = ext / (float)G;
+      hdr[0] = make_float4(red[0][0], red[1][0], red[2][0], 1.f / cell);
+      hdr[1] = make_float4(cell, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// Cull grid, step 2 (one thread per cell): bit j of the cell's words is set when a
+// live support ball of pair j (radius + kCullInflate) meets the cell box.
+__global__ void k_cull_masks(const float4 *bumps, int K, int G, int words, const float4 *hdr, uint32_t *masks) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= (long long)G * G * G) return;
+  uint32_t *out = masks + cell * words;
+  const float4 h0 = hdr[0];
+  if (h0.w == 0.f) {
+    for (int w = 0; w < words; ++w) out[w] = 0u;
+    return;
+  }
+  const float cs = hdr[1].x;
+  const int ix = (int)(cell % G), iy = (int)((cell / G) % G), iz = (int)(cell / ((long long)G * G));
+  const float lo[3] = {h0.x + ix * cs, h0.y + iy * cs, h0.z + iz * cs};
+  const int npairs = (K + 1) >> 1;
+  for (int w = 0; w < words; ++w) {
+    uint32_t bits = 0u;
+    for (int b = 0; b < 32; ++b) {
+      const int j = w * 32 + b;
+      if (j >= npairs) break;
+      for (int hh = 0; hh < 2; ++hh) {
+        const int k = 2 * j + hh;
+        if (k >= K) continue;
+        const IsoBump bb = iso_bump(bumps, k);
+        if (!(bb.R2 >= 0.f) || isinf(bb.R2)) continue;
+        const float R = sqrtf(bb.R2) + kCullInflate;
+        float d2 = 0.f;
+        for (int c = 0; c < 3; c++) {
+          const float cc = comp(bb.c, c);
+          const float e = fmaxf(fmaxf(lo[c] - cc, cc - (lo[c] + cs)), 0.f);
+          d2 = fmaf(e, e, d2);
+        }
+        if (d2 <= R * R) bits |= 1u << b;
+      }
+    }
+    out[w] = bits;
+  }
+}
+
 // FP32 throughput probe: 8 independent FMA chains per thread, scalar (mode 0) or
 // paired f32x2 (mode 1, 16 chains' worth of flops per loop), 2 flops per FMA.
 __global__ void k_ffma(float *out, int iters, int mode) {
@@ -936,7 +1089,7 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   const size_t smem =
       (size_t)((MK == MK_TWIST ? 0 : packed_float4s(p.K, MK == MK_GRAPH_ANISO)) + p.S) * sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
-  const bool x2 = MK == MK_GRAPH_ISO && p.rays_per_thread == 2;
+  const bool x2 = MK == MK_GRAPH_ISO && p.rays_per_thread == 2 && p.cull_masks == nullptr;
   void (*kern)(const TraceParams) = k_trace<MK, INTEG>;
   if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -968,6 +1121,17 @@ cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, 
                               cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
   k_pack_bumps<<<(K + 1 + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
+                              cudaStream_t st) {
+  if (K <= 0 || G <= 0) return cudaSuccess;
+  k_cull_bounds<<<1, 256, 0, st>>>(bumps, K, G, hdr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long cells = (long long)G * G * G;
+  k_cull_masks<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(bumps, K, G, words, hdr, masks);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,7 @@ class Metric:
     quad_A: tuple = (0.0,) * 9
     cutoff: float = 4.0
     twist_rate: float = 1.0
+    cull_grid: int = 0          # bump-support cull grid: 0 automatic, -1 none, G in [4, 128]
 
     @property
     def n_bumps(self) -> int:

@@ -135,6 +135,29 @@ def test_safe_distance_skip_is_exact(rg):
     assert (a["hit"] == b["hit"]).all()
 
 
+@pytest.mark.parametrize("G", [0, 8, 64])
+def test_cull_grid_matches_dense_sums(rg, G):
+    """Bumps outside a cell's list contribute exactly zero there: culled and dense sums agree."""
+    w = scenes.config_1080p_64(width=320, height=180)
+    w.metric.cull_grid = G
+    culled = _run(rg, w)
+    dense = _run(rg, w, rg.RGEO_FLAG_DENSE)
+    st = compare(culled, dict(dense, hit=dense["hit"].astype(np.float64)), w.scene.n_spheres)
+    assert st["agree"] >= 0.999 and st["hits"] > 5000, st
+
+
+def test_cull_grid_with_many_bumps_matches_oracle(rg):
+    """1024 bumps (several mask words per cell) against the oracle on a sample."""
+    w = scenes.config_4k_1024()
+    w = scenes.scaled(w, 480, 270)
+    w.max_steps = 600
+    px = scenes.pixel_sample(w.n_pixels, 7, 0.02)
+    g = _run(rg, w, 0, px)
+    ref = oracle.trace(w, px)
+    st = compare(g, ref, w.scene.n_spheres)
+    assert_parity(st, min_hits=200)
+
+
 def test_one_and_two_rays_per_thread_agree(rg):
     """The launch shape changes only the float32 summation order of the bump sums."""
     w = scenes.config_1080p_64(width=320, height=180)
