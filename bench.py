@@ -55,6 +55,12 @@ def flops_per_rk4_step(K: int) -> int:
     return 4 * (K * FLOPS_PER_BUMP + FLOPS_PER_RHS_EXTRA) + FLOPS_PER_STEP_EXTRA
 
 
+def algorithmic_flops(rk4_steps: int, bump_terms: int) -> int:
+    """27 flops per bump term summed (K per RHS dense; the ray's cell list culled), plus the
+    per-RHS and per-step work outside the bump sums."""
+    return bump_terms * FLOPS_PER_BUMP + rk4_steps * (4 * FLOPS_PER_RHS_EXTRA + FLOPS_PER_STEP_EXTRA)
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_05386_gb300", "csrc")
@@ -235,16 +241,25 @@ def bench_gpu(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def frame():
+    flags = rg.RGEO_FLAG_DENSE if args.dense else 0
+
+    def frame(fl=flags, st=ostruct):
         rg.rgeo_trace(metric.handle, scene.handle, cam, w.width, w.height, w.h, w.max_steps, w.integrator,
-                      w.shading, 0, ostruct, stream.cuda_stream)
+                      w.shading, fl, st, stream.cuda_stream)
+
+    def counted(fl):
+        # one untimed frame with the work counter: RK4 steps and bump terms summed
+        cout = rg.alloc_outputs(N, count=True)
+        frame(fl, rg.outputs_struct(cout))
+        rg.rgeo_sync(stream.cuda_stream)
+        return (int(cout["steps"].to(torch.int64).sum().item()), int(cout["bump_evals"].item()),
+                cout["id"].cpu().numpy())
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             frame()
         rg.rgeo_sync(stream.cuda_stream)
-        steps_total = int(out["steps"].to(torch.int64).sum().item())
-        ids = out["id"].cpu().numpy()
+        steps_total, evals_total, ids = counted(flags)
 
         clocks = ClockSampler(local)
         barrier(world)
@@ -266,7 +281,7 @@ def bench_gpu(args):
     rays = N * args.steps * world
     value = rays / total_s / 1e6
     mean_ms = sum(kernel_ms) / len(kernel_ms)
-    flops = steps_total * flops_per_rk4_step(K)
+    flops = algorithmic_flops(steps_total, evals_total)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -277,6 +292,23 @@ def bench_gpu(args):
     achieved = flops / (mean_ms * 1e-3) / 1e12
     ffma_tflops, _ = rg.rgeo_ffma_probe(0)
     ffma2_tflops, _ = rg.rgeo_ffma_probe(1)
+
+    # the dense kernel (every bump summed at every stage), timed alongside for its FP32 fraction
+    dense = None
+    if not args.dense and K > 0 and not args.no_dense_reference:
+        with torch.cuda.stream(stream):
+            frame(rg.RGEO_FLAG_DENSE)
+            d_steps, d_evals, _ = counted(rg.RGEO_FLAG_DENSE)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            frame(rg.RGEO_FLAG_DENSE)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        d_ms = e0.elapsed_time(e1)
+        d_ach = algorithmic_flops(d_steps, d_evals) / (d_ms * 1e-3) / 1e12
+        dense = {"kernel_ms": d_ms, "mrays_per_s": N / d_ms / 1e3, "achieved": d_ach, "frac": d_ach / peak_tflops,
+                 "unit": "TFLOP/s", "bump_terms_per_launch": d_evals}
 
     # end to end through the public C API with host buffers: per frame, upload the bump
     # centres from host memory, trace, copy every output back (rgeo_trace_host synchronises)
@@ -326,8 +358,11 @@ def bench_gpu(args):
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                      "ffma_probe_tflops": ffma_tflops, "frac_of_ffma_probe": achieved / ffma_tflops,
                      "ffma2_probe_tflops": ffma2_tflops,
-                     "flops_per_launch": flops, "flops_per_rk4_step": flops_per_rk4_step(K),
-                     "rk4_steps_per_launch": steps_total, "kernel_ms": mean_ms},
+                     "flops_per_launch": flops, "bump_terms_per_launch": evals_total,
+                     "bump_terms_per_rhs": evals_total / max(1, 4 * steps_total),
+                     "rk4_steps_per_launch": steps_total, "kernel_ms": mean_ms,
+                     "sums": "dense" if args.dense else "cull grid"},
+        "dense_kernel": dense,
         "clocks": clk,
         "gpu_launches": args.steps,
         "e2e": e2e,
@@ -346,6 +381,8 @@ def main():
     ap.add_argument("--workload", default="1080p_64", choices=["1080p_64", "1080p_twist", "parity_64"])
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dense", action="store_true", help="time the dense sums (no cull grid) as the step")
+    ap.add_argument("--no-dense-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -94,7 +94,7 @@ typedef struct {
   float quad_A[9];         /* A, row-major, must be symmetric */
   float cutoff_sigmas;     /* c; 4 is the default used by the workloads */
   float twist_rate;        /* k (twist only) */
-  int32_t cull_grid;       /* bump-support cull grid of G^3 cells: 0 = automatic (G = 32 for
+  int32_t cull_grid;       /* bump-support cull grid of G^3 cells: 0 = automatic (G = 64 for
                               >= 16 isotropic truncated bumps), -1 = none, 4..128 = that G */
   int32_t reserved[3];     /* must be zero */
 } rgeo_metric_desc;
@@ -121,13 +121,18 @@ typedef struct {
  *         point on the polygon segment (for MISS / BUDGET: the last position)
  *   steps [W*H] int32: integration steps taken (closed-form flat advances not counted)
  *   rgba  [4*W*H] uint8: shaded colour, alpha 255 on a hit, all zero otherwise
- *   drift [W*H] double, may be NULL: energy drift when RGEO_FLAG_ENERGY_DIAG is set */
+ *   drift [W*H] double, may be NULL: energy drift when RGEO_FLAG_ENERGY_DIAG is set
+ *   bump_evals: optional work counter (below) */
 typedef struct {
   int32_t *id;
   float *hit;
   int32_t *steps;
   uint8_t *rgba;
   double *drift;
+  unsigned long long *bump_evals; /* DEVICE, may be NULL: one counter that receives (added to
+                                     its current value) the number of bump terms summed, over
+                                     all rays and RHS stages: K per stage for dense sums, the
+                                     bumps of the ray's cull-grid cell otherwise */
 } rgeo_outputs;
 
 /* Library version and device capability check.  Returns RGEO_ABI_VERSION. */

@@ -64,7 +64,7 @@ class rgeo_tuning(ctypes.Structure):
 
 class rgeo_outputs(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("hit", ctypes.c_void_p), ("steps", ctypes.c_void_p),
-                ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p)]
+                ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p), ("bump_evals", ctypes.c_void_p)]
 
 
 _lib = None
@@ -275,8 +275,9 @@ class Scene:
     __del__ = close
 
 
-def alloc_outputs(n_pixels: int, device="cuda", drift: bool = False, pin: bool = False):
-    """Output tensors: id, hit (planar [3, N]), steps, rgba ([N, 4]), drift (optional)."""
+def alloc_outputs(n_pixels: int, device="cuda", drift: bool = False, pin: bool = False, count: bool = False):
+    """Output tensors: id, hit (planar [3, N]), steps, rgba ([N, 4]), drift (optional) and
+    bump_evals (optional device work counter, zeroed)."""
     import torch
     kw = dict(device=device)
     if pin:
@@ -286,12 +287,16 @@ def alloc_outputs(n_pixels: int, device="cuda", drift: bool = False, pin: bool =
                steps=torch.empty(n_pixels, dtype=torch.int32, **kw),
                rgba=torch.empty(n_pixels, 4, dtype=torch.uint8, **kw))
     out["drift"] = torch.empty(n_pixels, dtype=torch.float64, **kw) if drift else None
+    out["bump_evals"] = torch.zeros(1, dtype=torch.int64, device=device) if count and not pin else None
     return out
 
 
 def outputs_struct(out) -> rgeo_outputs:
+    def ptr(k):
+        t = out.get(k)
+        return t.data_ptr() if t is not None else None
     return rgeo_outputs(out["id"].data_ptr(), out["hit"].data_ptr(), out["steps"].data_ptr(),
-                        out["rgba"].data_ptr(), out["drift"].data_ptr() if out["drift"] is not None else None)
+                        out["rgba"].data_ptr(), ptr("drift"), ptr("bump_evals"))
 
 
 def trace(work: scenes.Workload, metric: Metric = None, scene: Scene = None, out=None, stream=None,

@@ -67,7 +67,7 @@ void free_scene(rgeo_scene *s) {
   cudaFree(s->d.spheres);
   cudaFree(s->d.albedo);
   cudaFree(s->d.nodes);
-  cudaFree(s->d.tris);
+  cudaFree(s->d.prims);
   cudaFree(s->d.grid);
   delete s;
 }
@@ -127,7 +127,7 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   p.S = s.S;
   p.albedo = s.albedo;
   p.nodes = s.nodes;
-  p.tris = s.tris;
+  p.prims = s.prims;
   p.T = s.T;
   p.grid = s.grid;
   std::memcpy(p.gdim, s.gdim, sizeof(p.gdim));
@@ -156,6 +156,7 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   p.steps = out->steps;
   p.rgba = reinterpret_cast<uchar4 *>(out->rgba);
   p.drift = out->drift;
+  p.bump_evals = out->bump_evals;
   p.rays_per_thread = rgeo::tuning().rays_per_thread;
   return p;
 }
@@ -242,7 +243,7 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
     // bump-support cull grid: isotropic truncated bumps only
     int G = 0;
     if (desc->kind == RGEO_METRIC_GRAPH_BUMPS && !aniso && desc->cutoff_sigmas > 0.f)
-      G = desc->cull_grid == 0 ? (K >= 16 ? 32 : 0) : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
+      G = desc->cull_grid == 0 ? (K >= 16 ? 64 : 0) : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
     if (e == cudaSuccess && G > 0) {
       const int words = ((K + 1) / 2 + 31) / 32;
       m->d.cull_G = G;
@@ -302,7 +303,7 @@ rgeo_status rgeo_scene_create(const float *spheres, int32_t S, const float *vert
     if (!(albedo[i] >= 0.f && albedo[i] <= 1.f)) return fail(RGEO_EINVAL, "rgeo_scene_create: albedo outside [0, 1]");
 
   rgeo::HostBVH bvh;
-  if (!rgeo::build_bvh(verts, V, tris, T, bvh, rgeo::kMaxBvhDepth))
+  if (!rgeo::build_bvh(spheres, S, verts, V, tris, T, bvh, rgeo::kMaxBvhDepth))
     return fail(RGEO_EINVAL, "rgeo_scene_create: BVH build failed");
   rgeo::HostGrid grid;
   rgeo::build_safe_grid(spheres, S, verts, tris, T, 64, grid);
@@ -319,7 +320,7 @@ rgeo_status rgeo_scene_create(const float *spheres, int32_t S, const float *vert
   cudaError_t e = upload(&sc->d.spheres, sph.data(), sph.size());
   if (e == cudaSuccess) e = upload(&sc->d.albedo, albedo, 3 * (size_t)(S + 1));
   if (e == cudaSuccess) e = upload(&sc->d.nodes, bvh.nodes.data(), bvh.nodes.size());
-  if (e == cudaSuccess) e = upload(&sc->d.tris, bvh.tris.data(), bvh.tris.size());
+  if (e == cudaSuccess) e = upload(&sc->d.prims, bvh.prims.data(), bvh.prims.size());
   if (e == cudaSuccess && !grid.dist.empty()) {
     e = upload(&sc->d.grid, grid.dist.data(), grid.dist.size());
     sc->d.has_grid = 1;
@@ -378,6 +379,7 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene, 
   char *buf = nullptr;
   RGEO_CUDA(cudaMallocAsync((void **)&buf, bytes, st), "rgeo_trace_host: staging");
   rgeo_outputs d;
+  d.bump_evals = nullptr;
   d.drift = drift ? (double *)buf : nullptr;
   char *q = buf + (drift ? N * 8 : 0);
   d.hit = (float *)q;

@@ -54,14 +54,16 @@ struct MetricDev {
 constexpr float kCullInflate = 1e-3f;
 
 // BVH node: two float4.  n0 = (lo.xyz, int first_or_left), n1 = (hi.xyz, int count);
-// count > 0: leaf over triangles [first, first + count); count == 0: children at left, left + 1.
-// Triangles in BVH order: three float4 (v0.xyz, int original index), (v1.xyz, 0), (v2.xyz, 0).
+// count > 0: leaf over primitives [first, first + count); count == 0: children at
+// left, left + 1.  Primitives in BVH order, three float4 each, the first carrying
+// the object id in .w: id < S is sphere id, (c.xyz, id), (r, 0, 0, 0), unused;
+// otherwise triangle id - S, (v0.xyz, id), (v1.xyz, 0), (v2.xyz, 0).
 struct SceneDev {
   int S, T, n_nodes;
   float4 *spheres;   // [S]
   float *albedo;     // [(S+1)*3]
   float4 *nodes;     // [2 * n_nodes]
-  float4 *tris;      // [3 * T]
+  float4 *prims;     // [3 * (S + T)]
   float *grid;       // [gx * gy * gz] lower bounds of the distance to the scene
   int gdim[3];
   float gmin[3];
@@ -85,8 +87,8 @@ struct TraceParams {
   const float4 *spheres;
   int S;
   const float *albedo;
-  const float4 *nodes;
-  const float4 *tris;
+  const float4 *nodes;  // null: no BVH, spheres tested one by one from shared memory
+  const float4 *prims;
   int T;
   const float *grid;
   int gdim[3];
@@ -108,6 +110,7 @@ struct TraceParams {
   int32_t *steps;
   uchar4 *rgba;
   double *drift;
+  unsigned long long *bump_evals;  // optional work counter
   uint32_t *counter;
   // launch shape
   int rays_per_thread;  // 1, or 2 (isotropic graph metric only)
@@ -125,11 +128,11 @@ void set_last_error(const char *msg);
 // Host-side scene acceleration structures (rgeo_scene_build.cpp).
 struct HostBVH {
   std::vector<float4> nodes;  // 2 per node
-  std::vector<float4> tris;   // 3 per triangle, BVH order
+  std::vector<float4> prims;  // 3 per primitive (spheres, then triangles), BVH order
   int depth = 0;
 };
-bool build_bvh(const float *verts, int n_verts, const int32_t *tris, int n_tris, HostBVH &out,
-               int max_depth);
+bool build_bvh(const float *spheres, int n_spheres, const float *verts, int n_verts, const int32_t *tris,
+               int n_tris, HostBVH &out, int max_depth);
 
 struct HostGrid {
   std::vector<float> dist;

@@ -1,10 +1,11 @@
 // rgeo_scene_build.cpp -- host construction of the scene acceleration structures.
 //
-// * A BVH over the triangles, built top-down with binned surface-area-heuristic
-//   splits (12 bins on the longest centroid axis).  Children of a node are stored
-//   next to each other so a node needs one child index.  Node boxes are padded
-//   by a few float32 ulps so that the single-precision slab test on the device
-//   never rejects a box that the segment touches.
+// * One BVH over every primitive of the scene, spheres and triangles, built
+//   top-down with binned surface-area-heuristic splits (12 bins on the longest
+//   centroid axis).  Children of a node are stored next to each other so a node
+//   needs one child index.  Node boxes are padded by a few float32 ulps so that
+//   the single-precision slab test on the device never rejects a box that the
+//   segment touches.
 // * A uniform grid of lower bounds on the Euclidean distance from any point of a
 //   cell to the scene.  Cells overlapped by the bounding box of a primitive are
 //   marked; the exact box-to-box distance from a cell to the nearest marked cell
@@ -163,17 +164,27 @@ inline float int_bits(int v) {
 
 }  // namespace
 
-bool build_bvh(const float *verts, int n_verts, const int32_t *tris, int n_tris, HostBVH &out,
-               int max_depth) {
+bool build_bvh(const float *spheres, int n_spheres, const float *verts, int n_verts, const int32_t *tris,
+               int n_tris, HostBVH &out, int max_depth) {
   out.nodes.clear();
-  out.tris.clear();
+  out.prims.clear();
   out.depth = 0;
-  if (n_tris <= 0) return true;
+  const int n = n_spheres + n_tris;
+  if (n <= 0) return true;
   Builder B;
   B.max_depth = max_depth;
-  B.prims.resize(n_tris);
+  B.prims.resize(n);
+  for (int s = 0; s < n_spheres; s++) {
+    Prim &p = B.prims[s];
+    for (int i = 0; i < 3; i++) {
+      p.box.lo[i] = spheres[4 * s + i] - spheres[4 * s + 3];
+      p.box.hi[i] = spheres[4 * s + i] + spheres[4 * s + 3];
+      p.c[i] = spheres[4 * s + i];
+    }
+    p.idx = s;  // object id: sphere index
+  }
   for (int t = 0; t < n_tris; t++) {
-    Prim &p = B.prims[t];
+    Prim &p = B.prims[n_spheres + t];
     p.box.reset();
     for (int v = 0; v < 3; v++) {
       int vi = tris[3 * t + v];
@@ -181,33 +192,41 @@ bool build_bvh(const float *verts, int n_verts, const int32_t *tris, int n_tris,
       p.box.grow(verts + 3 * vi);
     }
     for (int i = 0; i < 3; i++) p.c[i] = 0.5f * (p.box.lo[i] + p.box.hi[i]);
-    p.idx = t;
+    p.idx = n_spheres + t;  // object id: S + triangle index
   }
   int root = B.alloc_node();
-  B.build(root, 0, n_tris, 0);
+  B.build(root, 0, n, 0);
   out.depth = B.depth_seen;
   const int nn = (int)B.node_box.size();
   out.nodes.resize(2 * nn);
-  for (int n = 0; n < nn; n++) {
-    const Box &b = B.node_box[n];
+  for (int k = 0; k < nn; k++) {
+    const Box &b = B.node_box[k];
     float lo[3], hi[3];
     for (int i = 0; i < 3; i++) {
       float pad = 4e-6f * std::max(1.0f, std::max(std::fabs(b.lo[i]), std::fabs(b.hi[i])));
       lo[i] = b.lo[i] - pad;
       hi[i] = b.hi[i] + pad;
     }
-    out.nodes[2 * n] = make_float4(lo[0], lo[1], lo[2], int_bits(B.node_first[n]));
-    out.nodes[2 * n + 1] = make_float4(hi[0], hi[1], hi[2], int_bits(B.node_count[n]));
+    out.nodes[2 * k] = make_float4(lo[0], lo[1], lo[2], int_bits(B.node_first[k]));
+    out.nodes[2 * k + 1] = make_float4(hi[0], hi[1], hi[2], int_bits(B.node_count[k]));
   }
-  out.tris.resize(3 * n_tris);
-  for (int q = 0; q < n_tris; q++) {
-    int t = B.prims[q].idx;
-    const float *a = verts + 3 * tris[3 * t];
-    const float *b = verts + 3 * tris[3 * t + 1];
-    const float *c = verts + 3 * tris[3 * t + 2];
-    out.tris[3 * q] = make_float4(a[0], a[1], a[2], int_bits(t));
-    out.tris[3 * q + 1] = make_float4(b[0], b[1], b[2], 0.0f);
-    out.tris[3 * q + 2] = make_float4(c[0], c[1], c[2], 0.0f);
+  out.prims.resize(3 * n);
+  for (int q = 0; q < n; q++) {
+    const int id = B.prims[q].idx;
+    if (id < n_spheres) {
+      const float *sp = spheres + 4 * id;
+      out.prims[3 * q] = make_float4(sp[0], sp[1], sp[2], int_bits(id));
+      out.prims[3 * q + 1] = make_float4(sp[3], 0.0f, 0.0f, 0.0f);
+      out.prims[3 * q + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+      const int t = id - n_spheres;
+      const float *a = verts + 3 * tris[3 * t];
+      const float *b = verts + 3 * tris[3 * t + 1];
+      const float *c = verts + 3 * tris[3 * t + 2];
+      out.prims[3 * q] = make_float4(a[0], a[1], a[2], int_bits(id));
+      out.prims[3 * q + 1] = make_float4(b[0], b[1], b[2], 0.0f);
+      out.prims[3 * q + 2] = make_float4(c[0], c[1], c[2], 0.0f);
+    }
   }
   return true;
 }

@@ -133,7 +133,8 @@ __device__ __forceinline__ void pair_eval(PairAcc &a, const float4 *__restrict__
 __device__ __forceinline__ F3 pair_acc_finish(const TraceParams &P, const PairAcc &a, F3 x, F3 v) {
   float sgx = a.gx.x + a.gx.y, sgy = a.gy.x + a.gy.y, sgz = a.gz.x + a.gz.y, ssn = a.sn.x + a.sn.y;
   poly_terms(P, x, v, sgx, sgy, sgz, ssn);
-  const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
+  // the denominator 1 + |grad f|^2 is >= 1, so the fast division is accurate to 2 ulp
+  const float coef = __fdividef(ssn, fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f))));
   return f3(coef * sgx, coef * sgy, coef * sgz);
 }
 
@@ -157,7 +158,8 @@ __device__ __forceinline__ F3 accel_graph_iso(const TraceParams &P, const float4
 // they add exactly zero there.
 template <bool INSIDE>
 __device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const float4 *__restrict__ sb,
-                                                     float4 ghdr, unsigned pmask, F3 x, F3 v, bool &inside) {
+                                                     float4 ghdr, unsigned pmask, F3 x, F3 v, bool &inside,
+                                                     unsigned long long &evals) {
   PairAcc a;
   pair_acc_init(a, x, v);
   const int G = P.cull_G;
@@ -167,6 +169,7 @@ __device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const
       P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
   for (int wi = 0; wi < P.cull_words; ++wi) {
     unsigned m = ing ? __ldg(cm + wi) : 0u;
+    evals += 2u * (unsigned)__popc(m);  // the bumps of this lane's own cell
     m = __reduce_or_sync(pmask, m);
     while (m) {
       const int j = (wi << 5) + __ffs(m) - 1;
@@ -240,16 +243,21 @@ __device__ __forceinline__ F3 accel_twist(float k, F3 x, F3 v) {
 struct SumCtx {
   float4 ghdr;
   unsigned pmask;
+  unsigned long long *evals;  // per-lane count of bump terms summed
 };
 
 template <int MK, bool INSIDE>
 __device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, const SumCtx &cx, F3 x, F3 v,
                                     bool &inside) {
   if (MK == MK_GRAPH_ISO) {
-    if (P.cull_masks) return accel_graph_iso_culled<INSIDE>(P, sb, cx.ghdr, cx.pmask, x, v, inside);
+    if (P.cull_masks) return accel_graph_iso_culled<INSIDE>(P, sb, cx.ghdr, cx.pmask, x, v, inside, *cx.evals);
+    *cx.evals += (unsigned)P.K;
     return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
   }
-  if (MK == MK_GRAPH_ANISO) return accel_graph_aniso<INSIDE>(P, sb, P.K, x, v, inside);
+  if (MK == MK_GRAPH_ANISO) {
+    *cx.evals += (unsigned)P.K;
+    return accel_graph_aniso<INSIDE>(P, sb, P.K, x, v, inside);
+  }
   return accel_twist(P.twist_k, x, v);
 }
 
@@ -382,22 +390,26 @@ __device__ __forceinline__ float hit_triangle(const WFrame &f, F3 O, float smax,
   return (s >= 0.f && s < smax) ? s : -1.f;
 }
 
-// Earliest hit of O + s D, s in [0, smax): spheres (shared memory), then the BVH.
-// Ties: smaller s, then lower id (spheres come before triangles).
+// Earliest hit of O + s D, s in [0, smax), against the scene.  With a BVH, spheres
+// and triangles are found through it; without one (scenes passed as bare sphere
+// arrays), every sphere in shared memory is tested.  Ties: smaller s, then lower
+// id (spheres come before triangles).
 __device__ bool scene_hit(const TraceParams &P, const float4 *ss, F3 O, F3 D, float smax,
                           HitRec &hr) {
   hr.id = -1;
   hr.tq = -1;
   hr.s = smax;
   const float dd = dot(D, D);
-  for (int k = 0; k < P.S; ++k) {
-    float s;
-    if (hit_sphere(O, D, dd, ss[k], s) && s < smax && (hr.id < 0 || s < hr.s)) {
-      hr.s = s;
-      hr.id = k;
+  if (P.nodes == nullptr) {
+    for (int k = 0; k < P.S; ++k) {
+      float s;
+      if (hit_sphere(O, D, dd, ss[k], s) && s < smax && (hr.id < 0 || s < hr.s)) {
+        hr.s = s;
+        hr.id = k;
+      }
     }
+    return hr.id >= 0;
   }
-  if (P.T == 0) return hr.id >= 0;
   const WFrame fr = make_frame(D);
   const F3 inv = f3(1.f / (D.x != 0.f ? D.x : 1e-30f), 1.f / (D.y != 0.f ? D.y : 1e-30f),
                     1.f / (D.z != 0.f ? D.z : 1e-30f));
@@ -418,17 +430,22 @@ __device__ bool scene_hit(const TraceParams &P, const float4 *ss, F3 O, F3 D, fl
       const int cnt = __float_as_int(n1.w);
       if (cnt > 0) {
         for (int q = first; q < first + cnt; ++q) {
-          const float4 a4 = __ldg(&P.tris[3 * q]);
-          const float4 b4 = __ldg(&P.tris[3 * q + 1]);
-          const float4 c4 = __ldg(&P.tris[3 * q + 2]);
-          const float s = hit_triangle(fr, O, smax, a4, b4, c4);
-          if (s >= 0.f) {
-            const int id = P.S + __float_as_int(a4.w);
-            if (hr.id < 0 || s < hr.s || (s == hr.s && id < hr.id)) {
-              hr.s = s;
-              hr.id = id;
-              hr.tq = q;
-            }
+          const float4 a4 = __ldg(&P.prims[3 * q]);
+          const float4 b4 = __ldg(&P.prims[3 * q + 1]);
+          const int id = __float_as_int(a4.w);
+          float s;
+          bool got;
+          if (id < P.S) {
+            got = hit_sphere(O, D, dd, make_float4(a4.x, a4.y, a4.z, b4.x), s) && s < smax;
+          } else {
+            const float4 c4 = __ldg(&P.prims[3 * q + 2]);
+            s = hit_triangle(fr, O, smax, a4, b4, c4);
+            got = s >= 0.f;
+          }
+          if (got && (hr.id < 0 || s < hr.s || (s == hr.s && id < hr.id))) {
+            hr.s = s;
+            hr.id = id;
+            hr.tq = id < P.S ? -1 : q;
           }
         }
       } else {
@@ -509,11 +526,11 @@ __device__ uchar4 shade(const TraceParams &P, const float4 *ss, const HitRec &hr
     F3 n;
     int obj;
     if (hr.id < P.S) {
-      const float4 sp = ss[hr.id];
+      const float4 sp = P.nodes ? __ldg(&P.spheres[hr.id]) : ss[hr.id];
       n = f3(Ph.x - sp.x, Ph.y - sp.y, Ph.z - sp.z);
       obj = hr.id;
     } else {
-      const float4 a4 = P.tris[3 * hr.tq], b4 = P.tris[3 * hr.tq + 1], c4 = P.tris[3 * hr.tq + 2];
+      const float4 a4 = P.prims[3 * hr.tq], b4 = P.prims[3 * hr.tq + 1], c4 = P.prims[3 * hr.tq + 2];
       n = cross(f3(b4.x - a4.x, b4.y - a4.y, b4.z - a4.z), f3(c4.x - a4.x, c4.y - a4.y, c4.z - a4.z));
       if (dot(n, D) > 0.f) n = -1.f * n;
       obj = P.S;
@@ -602,7 +619,8 @@ template <int MK>
 __device__ __forceinline__ int stage_shared(const TraceParams &P, float4 *smem) {
   const int nb4 = MK == MK_TWIST ? 0 : packed_float4s(P.K, MK == MK_GRAPH_ANISO);
   for (int i = threadIdx.x; i < nb4; i += blockDim.x) smem[i] = P.bumps[i];
-  for (int i = threadIdx.x; i < P.S; i += blockDim.x) smem[nb4 + i] = P.spheres[i];
+  if (P.nodes == nullptr)  // spheres are tested one by one only when there is no BVH
+    for (int i = threadIdx.x; i < P.S; i += blockDim.x) smem[nb4 + i] = P.spheres[i];
   __syncthreads();
   return nb4;
 }
@@ -665,7 +683,7 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
   const unsigned mmask = __ballot_sync(cx.pmask, moved);
   if (moved) {
     bool dummy;
-    a1 = accel<MK, false>(P, sb, SumCtx{cx.ghdr, mmask}, x, v, dummy);
+    a1 = accel<MK, false>(P, sb, SumCtx{cx.ghdr, mmask, cx.evals}, x, v, dummy);
   }
   if (finished) return false;
   if (r.steps >= P.max_steps) {
@@ -742,6 +760,7 @@ __global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned long long evals = 0;
   bool active = false, drained = false;
   Ray r;
   for (;;) {
@@ -753,16 +772,20 @@ __global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
     }
     if (!active) continue;
     bool inside = true;
-    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask}, xhi(r), vhi(r), inside);
-    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, amask}, r, a1, inside);
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask, &evals}, xhi(r), vhi(r), inside);
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, amask, &evals}, r, a1, inside);
     const unsigned smask = __ballot_sync(amask, go);
     if (!go) {
       active = false;
       continue;
     }
     F3 dx, dvel;
-    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask}, xhi(r), vhi(r), a1, dx, dvel);
+    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
     active = post_step<MK>(P, sb, ss, r, dx, dvel);
+  }
+  if (P.bump_evals) {
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
+    if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
   }
 }
 
@@ -855,6 +878,7 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
   const float4 *ss = smem + nb4;
   const int np = (P.K + 1) >> 1;
   bool act0 = false, act1 = false, drained = false;
+  unsigned long long evals = 0;
   Ray r0, r1;
   for (int c = 0; c < 3; c++) {
     r0.xh[c] = r0.vh[c] = r1.xh[c] = r1.vh[c] = 0.f;
@@ -874,8 +898,9 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     F3 a10, a11;
     accel_graph_iso_x2<true>(P, sb, np, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);  // this kernel sums densely (no cull grid)
-    if (act0) act0 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m0}, r0, a10, in0);
-    if (act1) act1 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m1}, r1, a11, in1);
+    evals += 2ull * (unsigned)P.K;
+    if (act0) act0 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m0, &evals}, r0, a10, in0);
+    if (act1) act1 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m1, &evals}, r1, a11, in1);
     if (!act0 && !act1) continue;
     const F3 x0 = xhi(r0), v0 = vhi(r0), x1 = xhi(r1), v1 = vhi(r1);
     F3 dx0, dv0, dx1, dv1;
@@ -894,6 +919,7 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
       F3 a40, a41;
       accel_graph_iso_x2<false>(P, sb, np, axpy(h, v30, x0), v40, axpy(h, v31, x1), v41, a40, a41, dummy0,
                                 dummy1);
+      evals += 6ull * (unsigned)P.K;
       const float h6 = h * (1.f / 6.f);
       dx0 = h6 * (v0 + 2.f * (v20 + v30) + v40);
       dv0 = h6 * (a10 + 2.f * (a20 + a30) + a40);
@@ -907,6 +933,10 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     }
     if (act0) act0 = post_step<MK_GRAPH_ISO>(P, sb, ss, r0, dx0, dv0);
     if (act1) act1 = post_step<MK_GRAPH_ISO>(P, sb, ss, r1, dx1, dv1);
+  }
+  if (P.bump_evals) {
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
+    if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
   }
 }
 
@@ -1087,7 +1117,8 @@ __global__ void k_ffma(float *out, int iters, int mode) {
 template <int MK, int INTEG>
 cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   const size_t smem =
-      (size_t)((MK == MK_TWIST ? 0 : packed_float4s(p.K, MK == MK_GRAPH_ANISO)) + p.S) * sizeof(float4);
+      (size_t)((MK == MK_TWIST ? 0 : packed_float4s(p.K, MK == MK_GRAPH_ANISO)) + (p.nodes ? 0 : p.S)) *
+      sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
   const bool x2 = MK == MK_GRAPH_ISO && p.rays_per_thread == 2 && p.cull_masks == nullptr;
   void (*kern)(const TraceParams) = k_trace<MK, INTEG>;

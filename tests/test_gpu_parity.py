@@ -146,6 +146,24 @@ def test_cull_grid_matches_dense_sums(rg, G):
     assert st["agree"] >= 0.999 and st["hits"] > 5000, st
 
 
+def test_bump_term_counter(rg):
+    """The optional work counter: dense sums count K terms per RHS evaluation (4 per RK4 step
+    plus one stage-1 evaluation per finished ray and per flat advance); culled sums count fewer."""
+    import torch
+    w = scenes.config_1080p_64(width=160, height=90)
+    counts = {}
+    for name, flags in (("dense", rg.RGEO_FLAG_DENSE), ("culled", 0)):
+        out = rg.alloc_outputs(w.n_pixels, count=True)
+        rg.trace(w, out=out, flags=flags)
+        rg.rgeo_sync()
+        counts[name] = int(out["bump_evals"].item())
+        steps = int(out["steps"].to(torch.int64).sum().item())
+    K = w.metric.n_bumps
+    assert 4 * K * steps <= counts["dense"] <= 4 * K * steps + 3 * K * w.n_pixels
+    assert counts["dense"] % K == 0
+    assert 0 < counts["culled"] < counts["dense"] / 2
+
+
 def test_cull_grid_with_many_bumps_matches_oracle(rg):
     """1024 bumps (several mask words per cell) against the oracle on a sample."""
     w = scenes.config_4k_1024()
