@@ -192,6 +192,61 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
                             int32_t max_steps, int32_t integrator, int32_t shading,
                             uint32_t flags, const rgeo_outputs *host_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------- batches
+ * Time- or user-dependent metrics (Introduction) and many views at once: a batch
+ * traces several instances -- each its own metric, scene, camera, resolution,
+ * step and outputs -- in one persistent launch whose warps move between
+ * instances as their queues drain, so uneven sizes keep the GPU full.  Every
+ * instance of a batch must share the metric kind, the bump layout (isotropic or
+ * not) and the integrator.  Instances read their metric and scene at launch
+ * time, so metrics animated with rgeo_metric_advance between launches are
+ * traced at their new state.  rgeo_batch_launch enqueues only device work (a
+ * memset of the per-instance counters and one kernel), so a stream capture of
+ * [rgeo_metric_advance..., rgeo_batch_launch] replays as a CUDA graph. */
+typedef struct rgeo_batch rgeo_batch; /* opaque, owns device memory */
+
+typedef struct {
+  const rgeo_metric *metric;
+  const rgeo_scene *scene;
+  rgeo_camera camera;
+  int32_t width, height;
+  float h;
+  int32_t max_steps;
+  int32_t integrator; /* rgeo_integrator */
+  int32_t shading;    /* rgeo_shading */
+  uint32_t flags;     /* RGEO_FLAG_* as for rgeo_trace */
+  rgeo_outputs out;   /* DEVICE buffers of this instance */
+} rgeo_instance;
+
+/* Validate n >= 1 instances (each as rgeo_trace would), upload the instance
+ * table and allocate per-instance work counters.  Synchronises.  The handles and
+ * output buffers must outlive the batch.  Errors: RGEO_EINVAL (n < 1, NULL,
+ * invalid instance, mixed metric kinds / layouts / integrators), RGEO_ENOMEM,
+ * RGEO_ECUDA. */
+rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *instances, rgeo_batch **out);
+
+/* Trace every instance of the batch in one launch on the stream (asynchronous). */
+rgeo_status rgeo_batch_launch(rgeo_batch *batch, void *cuda_stream);
+
+void rgeo_batch_destroy(rgeo_batch *batch);
+
+/* Sinusoidal motion of the bump centres of a graph metric:
+ *   c_k(t) = c_k(0) + A_k sin(2 pi f_k t + phi_k), per axis of A_k,
+ * with c_k(0) the centres the metric holds when this is called.  HOST arrays
+ * amplitude [K*3], frequency [K], phase [K].  Sets t = 0.  Synchronises.
+ * Errors: RGEO_EINVAL (NULL, not a graph metric, non-finite), RGEO_ENOMEM, RGEO_ECUDA. */
+rgeo_status rgeo_metric_set_motion(rgeo_metric *metric, const float *amplitude, const float *frequency,
+                                   const float *phase);
+
+/* Set the motion time t (stream-ordered). */
+rgeo_status rgeo_metric_set_time(rgeo_metric *metric, float t, void *cuda_stream);
+
+/* Move the centres to c_k(t), rebuild the cull grid, then advance t by dt; t
+ * lives in device memory, so a captured graph of this call animates frame after
+ * frame without host input.  Asynchronous.  Errors: RGEO_EINVAL (no motion set,
+ * non-finite dt), RGEO_ECUDA. */
+rgeo_status rgeo_metric_advance(rgeo_metric *metric, float dt, void *cuda_stream);
+
 /* Wait for the stream, then read and clear the device error word of the
  * current device.  Returns RGEO_OK, RGEO_EDEVICE or RGEO_ETIMEOUT (message in
  * rgeo_last_error), or RGEO_ECUDA if the stream itself failed. */

@@ -34,7 +34,8 @@ RGEO_MAX_BUMPS = 4096
 EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_metric_set_centers",
            "rgeo_metric_destroy", "rgeo_scene_create", "rgeo_scene_destroy", "rgeo_trace",
            "rgeo_trace_host", "rgeo_sync", "rgeo_set_tuning", "rgeo_get_tuning", "rgeo_ffma_probe",
-           "rgeo_trace_noalloc")
+           "rgeo_trace_noalloc", "rgeo_batch_create", "rgeo_batch_launch", "rgeo_batch_destroy",
+           "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -65,6 +66,13 @@ class rgeo_tuning(ctypes.Structure):
 class rgeo_outputs(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("hit", ctypes.c_void_p), ("steps", ctypes.c_void_p),
                 ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p), ("bump_evals", ctypes.c_void_p)]
+
+
+class rgeo_instance(ctypes.Structure):
+    _fields_ = [("metric", ctypes.c_void_p), ("scene", ctypes.c_void_p), ("camera", rgeo_camera),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("h", ctypes.c_float),
+                ("max_steps", ctypes.c_int32), ("integrator", ctypes.c_int32), ("shading", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("out", rgeo_outputs)]
 
 
 _lib = None
@@ -104,6 +112,18 @@ def library() -> ctypes.CDLL:
     L.rgeo_trace_host.argtypes = trace_args
     L.rgeo_sync.restype = i32
     L.rgeo_sync.argtypes = [vp]
+    L.rgeo_batch_create.restype = i32
+    L.rgeo_batch_create.argtypes = [i32, ctypes.POINTER(rgeo_instance), ctypes.POINTER(vp)]
+    L.rgeo_batch_launch.restype = i32
+    L.rgeo_batch_launch.argtypes = [vp, vp]
+    L.rgeo_batch_destroy.restype = None
+    L.rgeo_batch_destroy.argtypes = [vp]
+    L.rgeo_metric_set_motion.restype = i32
+    L.rgeo_metric_set_motion.argtypes = [vp, fp, fp, fp]
+    L.rgeo_metric_set_time.restype = i32
+    L.rgeo_metric_set_time.argtypes = [vp, f32, vp]
+    L.rgeo_metric_advance.restype = i32
+    L.rgeo_metric_advance.argtypes = [vp, f32, vp]
     L.rgeo_trace_noalloc.restype = i32
     L.rgeo_trace_noalloc.argtypes = [vp, vp, vp, i32, f32, vp, i32, vp, ctypes.POINTER(rgeo_camera), i32, i32,
                                      f32, i32, i32, i32, ctypes.POINTER(rgeo_outputs), vp]
@@ -198,6 +218,37 @@ def rgeo_trace_noalloc(center: int, amplitude: int, sigma: int, n_bumps: int, cu
     _check(library().rgeo_trace_noalloc(center, amplitude, sigma, n_bumps, cutoff, spheres, n_spheres, albedo,
                                         ctypes.byref(camera), width, height, h, max_steps, integrator, shading,
                                         ctypes.byref(out), _stream_handle(stream)), "rgeo_trace_noalloc")
+
+
+def rgeo_batch_create(instances) -> int:
+    arr = (rgeo_instance * len(instances))(*instances)
+    out = ctypes.c_void_p()
+    _check(library().rgeo_batch_create(len(instances), arr, ctypes.byref(out)), "rgeo_batch_create")
+    return out.value
+
+
+def rgeo_batch_launch(batch: int, stream=None):
+    _check(library().rgeo_batch_launch(batch, _stream_handle(stream)), "rgeo_batch_launch")
+
+
+def rgeo_batch_destroy(batch: int):
+    library().rgeo_batch_destroy(batch)
+
+
+def rgeo_metric_set_motion(metric: int, amplitude, frequency, phase):
+    import numpy as np
+    a = np.ascontiguousarray(amplitude, np.float32).reshape(-1)
+    f = np.ascontiguousarray(frequency, np.float32).reshape(-1)
+    p = np.ascontiguousarray(phase, np.float32).reshape(-1)
+    _check(library().rgeo_metric_set_motion(metric, _fptr(a), _fptr(f), _fptr(p)), "rgeo_metric_set_motion")
+
+
+def rgeo_metric_set_time(metric: int, t: float, stream=None):
+    _check(library().rgeo_metric_set_time(metric, t, _stream_handle(stream)), "rgeo_metric_set_time")
+
+
+def rgeo_metric_advance(metric: int, dt: float, stream=None):
+    _check(library().rgeo_metric_advance(metric, dt, _stream_handle(stream)), "rgeo_metric_advance")
 
 
 def rgeo_sync(stream=None):
@@ -297,6 +348,30 @@ def outputs_struct(out) -> rgeo_outputs:
         return t.data_ptr() if t is not None else None
     return rgeo_outputs(out["id"].data_ptr(), out["hit"].data_ptr(), out["steps"].data_ptr(),
                         out["rgba"].data_ptr(), ptr("drift"), ptr("bump_evals"))
+
+
+def instance(work: scenes.Workload, metric: Metric, scene: Scene, out, flags: int = 0) -> rgeo_instance:
+    """One batch instance: a workload's camera and stepping with its own handles and outputs."""
+    return rgeo_instance(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height,
+                         work.h, work.max_steps, work.integrator, work.shading, flags, outputs_struct(out))
+
+
+class Batch:
+    """Owning handle of a batch of instances traced in one launch."""
+
+    def __init__(self, instances):
+        self._instances = list(instances)
+        self.handle = rgeo_batch_create(self._instances)
+
+    def launch(self, stream=None):
+        rgeo_batch_launch(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            rgeo_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
 
 
 def trace(work: scenes.Workload, metric: Metric = None, scene: Scene = None, out=None, stream=None,

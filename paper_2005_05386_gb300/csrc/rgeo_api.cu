@@ -1,5 +1,6 @@
 // rgeo_api.cu -- the C ABI of librgeo: argument validation, handle ownership,
 // scene construction and kernel launches.  See include/rgeo.h for the contract.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,14 @@ struct rgeo_metric {
 struct rgeo_scene {
   rgeo::SceneDev d;
   int device;
+};
+
+struct rgeo_batch {
+  rgeo::TraceParams *table;  // device instance table
+  uint32_t *counters;        // device, one work counter per instance
+  int n, kind, aniso, integrator;
+  int max_table_f4;  // largest packed bump table of the instances, in float4
+  long long total_items;
 };
 
 namespace {
@@ -59,6 +68,8 @@ void free_metric(rgeo_metric *m) {
   cudaFree(m->d.raw);
   cudaFree(m->d.cull_masks);
   cudaFree(m->d.cull_hdr);
+  cudaFree(m->d.motion);
+  cudaFree(m->d.time);
   delete m;
 }
 
@@ -441,6 +452,113 @@ rgeo_status rgeo_ffma_probe(int32_t mode, float *tflops, float *ms) {
   if (!tflops || !ms) return fail(RGEO_EINVAL, "rgeo_ffma_probe: NULL output");
   if (mode != 0 && mode != 1) return fail(RGEO_EINVAL, "rgeo_ffma_probe: mode must be 0 or 1");
   RGEO_CUDA(rgeo::run_ffma_probe(mode, tflops, ms), "rgeo_ffma_probe");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *inst, rgeo_batch **out) {
+  g_last_error.clear();
+  if (!out) return fail(RGEO_EINVAL, "rgeo_batch_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || !inst) return fail(RGEO_EINVAL, "rgeo_batch_create: need n >= 1 instances");
+  std::vector<rgeo::TraceParams> table(n);
+  long long total = 0;
+  int max_f4 = 0;
+  for (int i = 0; i < n; i++) {
+    const rgeo_instance &q = inst[i];
+    rgeo_status s = validate_trace(q.metric, q.scene, &q.camera, q.width, q.height, q.h, q.max_steps, q.integrator,
+                                   q.shading, q.flags, &q.out);
+    if (s != RGEO_OK) return fail(s, "rgeo_batch_create: instance " + std::to_string(i) + ": " + g_last_error);
+    if (q.metric->d.kind != inst[0].metric->d.kind || q.metric->d.aniso != inst[0].metric->d.aniso ||
+        q.integrator != inst[0].integrator)
+      return fail(RGEO_EINVAL, "rgeo_batch_create: instances must share metric kind, bump layout and integrator");
+    table[i] = make_params(q.metric, q.scene, &q.camera, q.width, q.height, q.h, q.max_steps, q.integrator,
+                           q.shading, q.flags, &q.out);
+    table[i].rays_per_thread = 1;
+    total += table[i].n_items;
+    if (q.metric->d.kind == RGEO_METRIC_GRAPH_BUMPS)
+      max_f4 = std::max(max_f4, rgeo::packed_float4s(q.metric->d.K, q.metric->d.aniso));
+  }
+  rgeo_batch *b = new rgeo_batch();
+  b->n = n;
+  b->kind = inst[0].metric->d.kind;
+  b->aniso = inst[0].metric->d.aniso;
+  b->integrator = inst[0].integrator;
+  b->total_items = total;
+  b->max_table_f4 = max_f4;
+  cudaError_t e = cudaMalloc(&b->counters, sizeof(uint32_t) * n);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < n; i++) table[i].counter = b->counters + i;
+    e = upload(&b->table, table.data(), table.size());
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(b->counters);
+    cudaFree(b->table);
+    delete b;
+    return cuda_fail(e, "rgeo_batch_create");
+  }
+  *out = b;
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_batch_launch(rgeo_batch *b, void *cuda_stream) {
+  g_last_error.clear();
+  if (!b) return fail(RGEO_EINVAL, "rgeo_batch_launch: NULL batch");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  RGEO_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(uint32_t) * b->n, st), "rgeo_batch_launch: counters");
+  RGEO_CUDA(rgeo::launch_batch(b->table, b->n, b->kind, b->aniso, b->integrator, b->max_table_f4, b->total_items,
+                               st),
+            "rgeo_batch_launch: launch");
+  return RGEO_OK;
+}
+
+void rgeo_batch_destroy(rgeo_batch *b) {
+  if (!b) return;
+  cudaFree(b->counters);
+  cudaFree(b->table);
+  delete b;
+}
+
+rgeo_status rgeo_metric_set_motion(rgeo_metric *m, const float *amplitude, const float *frequency,
+                                   const float *phase) {
+  g_last_error.clear();
+  if (!m || !amplitude || !frequency || !phase) return fail(RGEO_EINVAL, "rgeo_metric_set_motion: NULL argument");
+  if (m->d.kind != RGEO_METRIC_GRAPH_BUMPS) return fail(RGEO_EINVAL, "rgeo_metric_set_motion: not a graph metric");
+  const int K = m->d.K;
+  if (!finite_all(amplitude, 3 * (size_t)K) || !finite_all(frequency, K) || !finite_all(phase, K))
+    return fail(RGEO_EINVAL, "rgeo_metric_set_motion: non-finite value");
+  if (!m->d.motion && K > 0) RGEO_CUDA(cudaMalloc(&m->d.motion, sizeof(float) * 8 * (size_t)K), "rgeo_metric_set_motion");
+  if (!m->d.time) RGEO_CUDA(cudaMalloc(&m->d.time, sizeof(float)), "rgeo_metric_set_motion");
+  if (K > 0) {
+    RGEO_CUDA(cudaMemcpy(m->d.motion, m->d.raw, sizeof(float) * 3 * K, cudaMemcpyDeviceToDevice), "set_motion: c0");
+    RGEO_CUDA(cudaMemcpy(m->d.motion + 3 * K, amplitude, sizeof(float) * 3 * K, cudaMemcpyHostToDevice), "set_motion: A");
+    RGEO_CUDA(cudaMemcpy(m->d.motion + 6 * K, frequency, sizeof(float) * K, cudaMemcpyHostToDevice), "set_motion: f");
+    RGEO_CUDA(cudaMemcpy(m->d.motion + 7 * K, phase, sizeof(float) * K, cudaMemcpyHostToDevice), "set_motion: phi");
+  }
+  RGEO_CUDA(cudaMemset(m->d.time, 0, sizeof(float)), "rgeo_metric_set_motion: t");
+  RGEO_CUDA(cudaDeviceSynchronize(), "rgeo_metric_set_motion");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_metric_set_time(rgeo_metric *m, float t, void *cuda_stream) {
+  g_last_error.clear();
+  if (!m || !m->d.time) return fail(RGEO_EINVAL, "rgeo_metric_set_time: no motion set");
+  if (!std::isfinite(t)) return fail(RGEO_EINVAL, "rgeo_metric_set_time: non-finite t");
+  RGEO_CUDA(rgeo::launch_set_time(m->d.time, t, (cudaStream_t)cuda_stream), "rgeo_metric_set_time");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_metric_advance(rgeo_metric *m, float dt, void *cuda_stream) {
+  g_last_error.clear();
+  if (!m || !m->d.time) return fail(RGEO_EINVAL, "rgeo_metric_advance: no motion set");
+  if (!std::isfinite(dt)) return fail(RGEO_EINVAL, "rgeo_metric_advance: non-finite dt");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  RGEO_CUDA(rgeo::launch_advance_motion(m->d.motion, m->d.K, m->d.aniso, m->d.raw, m->d.bumps, m->d.time, dt, st),
+            "rgeo_metric_advance: motion");
+  if (m->d.cull_G > 0)
+    RGEO_CUDA(rgeo::launch_build_cull(m->d.bumps, m->d.K, m->d.cull_G, m->d.cull_words, m->d.cull_hdr,
+                                      m->d.cull_masks, st),
+              "rgeo_metric_advance: cull grid");
   return RGEO_OK;
 }
 

@@ -47,6 +47,9 @@ struct MetricDev {
   int cull_G, cull_words;
   uint32_t *cull_masks;  // [G^3 * words]
   float4 *cull_hdr;      // (gmin.xyz, 1 / cell)
+  // sinusoidal motion of the centres: [K*3 c0 | K*3 A | K f | K phi] and the time t
+  float *motion;
+  float *time;
 };
 
 // Cull grid: inflation of every support radius (absolute), covering float32 rounding
@@ -158,6 +161,11 @@ cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
 cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
 cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
                               cudaStream_t st);
+cudaError_t launch_batch(const TraceParams *dev_inst, int n, int kind, int aniso, int integrator,
+                         int max_table_f4, long long total_items, cudaStream_t st);
+cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
+                                  float dt, cudaStream_t st);
+cudaError_t launch_set_time(float *t, float value, cudaStream_t st);
 cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
 cudaError_t run_ffma_probe(int mode, float *tflops, float *ms);
 

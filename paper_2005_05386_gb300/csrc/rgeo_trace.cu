@@ -940,6 +940,115 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
   }
 }
 
+// Many instances (frames, views or metrics of uneven size) in one persistent launch.
+// Each warp serves one instance at a time: its lanes refill from that instance's
+// queue (the instance's own counter), and once the instance is drained and the
+// warp's lanes are idle it moves to the next instance.  Bump tables, cull masks
+// and spheres are read through L1 because warps of one block may be on
+// different instances.  All instances share the metric kind and integrator.
+// Shared-memory slot of one warp in the batch kernel: a copy of the current
+// instance's parameters, then (when it fits) its packed bump table.
+constexpr int kParamWords = (int)((sizeof(TraceParams) + 15) / 16) * 4;
+
+__device__ __forceinline__ void warp_load_instance(const TraceParams *inst, int i, uint32_t *slot, int table_f4,
+                                                   const float4 *&sb) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(inst + i);
+  for (int k = (int)lane; k < (int)(sizeof(TraceParams) / 4); k += 32) slot[k] = __ldg(src + k);
+  __syncwarp();
+  const TraceParams &P = *reinterpret_cast<const TraceParams *>(slot);
+  const int need = P.kind != 1 ? packed_float4s(P.K, P.aniso) : 0;
+  float4 *tab = reinterpret_cast<float4 *>(slot + kParamWords);
+  if (need <= table_f4) {
+    for (int k = (int)lane; k < need; k += 32) tab[k] = __ldg(P.bumps + k);
+    sb = tab;
+  } else {
+    sb = P.bumps;  // too large for the slot: read through L1
+  }
+  __syncwarp();
+}
+
+template <int MK, int INTEG>
+__global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
+  extern __shared__ float4 bsmem[];
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) + (threadIdx.x >> 5) * (kParamWords + 4 * table_f4);
+  const int warp_global = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int i = warp_global % n;
+  int visited = 0;
+  unsigned long long evals = 0;
+  bool active = false, drained = false;
+  Ray r;
+  const float4 *sb = nullptr;
+  warp_load_instance(inst, i, slot, table_f4, sb);
+  for (;;) {
+    const TraceParams &P = *reinterpret_cast<const TraceParams *>(slot);
+    const float4 *ss = P.spheres;
+    refill<MK>(P, sb, active, drained, r);
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
+    if (!amask) {
+      if (drained) {
+        if (P.bump_evals) {
+          for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
+          if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
+        }
+        evals = 0;
+        if (++visited >= n) break;
+        i = (i + 1) % n;
+        drained = false;
+        warp_load_instance(inst, i, slot, table_f4, sb);
+      }
+      continue;
+    }
+    if (!active) continue;
+    const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
+    bool inside = true;
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask, &evals}, xhi(r), vhi(r), inside);
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, amask, &evals}, r, a1, inside);
+    const unsigned smask = __ballot_sync(amask, go);
+    if (!go) {
+      active = false;
+      continue;
+    }
+    F3 dx, dvel;
+    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
+    active = post_step<MK>(P, sb, ss, r, dx, dvel);
+  }
+}
+
+// Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
+// table; t is read from and advanced in device memory so that a captured graph
+// animates without host input.  motion = [K*3 c0 | K*3 A | K f | K phi].
+__global__ void k_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
+                                 float dt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const float tt = *t;
+  if (k < K) {
+    const float f = motion[6 * K + k], ph = motion[7 * K + k];
+    const float s = sinf(6.283185307179586f * f * tt + ph);
+    float c[3];
+    for (int a = 0; a < 3; a++) {
+      c[a] = motion[3 * k + a] + motion[3 * K + 3 * k + a] * s;
+      raw[3 * k + a] = c[a];
+    }
+    if (aniso) {
+      float4 b = bumps[kAnisoStride * k];
+      b.x = c[0];
+      b.y = c[1];
+      b.z = c[2];
+      bumps[kAnisoStride * k] = b;
+    } else {
+      float *p = reinterpret_cast<float *>(bumps + 4 * (k >> 1));
+      const int h = k & 1;
+      p[0 + h] = -c[0];
+      p[2 + h] = -c[1];
+      p[4 + h] = -c[2];
+    }
+  }
+}
+
+__global__ void k_tick(float *t, float dt) { *t += dt; }
+__global__ void k_set_time(float *t, float value) { *t = value; }
+
 // Packs bump k (isotropic: into its half of pair k / 2; one thread per half, so the
 // padding half of an odd count is written too).
 __global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out) {
@@ -1139,7 +1248,58 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int MK, int INTEG>
+cudaError_t launch_batch_t(const TraceParams *dev_inst, int n, int table_f4, long long total_items,
+                           cudaStream_t st) {
+  auto kern = k_trace_batch<MK, INTEG>;
+  const size_t smem = (size_t)4 * (kParamWords * 4 + (size_t)table_f4 * 16);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)sms * per_sm;
+  const long long need = (total_items + 127) / 128;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  kern<<<(unsigned)blocks, 128, smem, st>>>(dev_inst, n, table_f4);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_batch(const TraceParams *dev_inst, int n, int kind, int aniso, int integrator,
+                         int max_table_f4, long long total_items, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  // per-warp bump tables up to 1024 float4 (512 pairs); larger tables are read through L1
+  const int table_f4 = max_table_f4 <= 1024 ? max_table_f4 : 0;
+  const int mk = kind == 1 ? MK_TWIST : (aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO);
+  if (mk == MK_GRAPH_ISO)
+    return integrator == 0 ? launch_batch_t<MK_GRAPH_ISO, 0>(dev_inst, n, table_f4, total_items, st)
+                           : launch_batch_t<MK_GRAPH_ISO, 1>(dev_inst, n, table_f4, total_items, st);
+  if (mk == MK_GRAPH_ANISO)
+    return integrator == 0 ? launch_batch_t<MK_GRAPH_ANISO, 0>(dev_inst, n, table_f4, total_items, st)
+                           : launch_batch_t<MK_GRAPH_ANISO, 1>(dev_inst, n, table_f4, total_items, st);
+  return integrator == 0 ? launch_batch_t<MK_TWIST, 0>(dev_inst, n, table_f4, total_items, st)
+                         : launch_batch_t<MK_TWIST, 1>(dev_inst, n, table_f4, total_items, st);
+}
+
+cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
+                                  float dt, cudaStream_t st) {
+  if (K > 0) {
+    k_advance_motion<<<(K + 127) / 128, 128, 0, st>>>(motion, K, aniso, raw, bumps, t, dt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_tick<<<1, 1, 0, st>>>(t, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(float *t, float value, cudaStream_t st) {
+  k_set_time<<<1, 1, 0, st>>>(t, value);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st) {
   const int mk = p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO);

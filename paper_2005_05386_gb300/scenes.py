@@ -288,6 +288,34 @@ def config_4k_1024(seed: int = 4) -> Workload:
                     seed=seed)
 
 
+BATCH_RESOLUTIONS = ((256, 256), (512, 512), (1280, 720), (1920, 1080))
+
+
+def config_batch16(seed: int = 3, n: int = 16):
+    """n instances over the 1080p scene: resolution uniform from BATCH_RESOLUTIONS, bump count
+    floor(exp(U[ln 8, ln 257))) with the 1080p bump distributions, each instance its own bumps."""
+    base = config_1080p_64()
+    rng = SplitMix64(sub_seed(seed, STREAM_BUMPS))
+    out = []
+    for i in range(n):
+        W, H = BATCH_RESOLUTIONS[min(int(rng.uniform(0, 4)), 3)]
+        K = int(math.floor(math.exp(rng.uniform(math.log(8.0), math.log(257.0)))))
+        c, a, s = random_bumps(seed * 1000 + i, K)
+        w = dataclasses.replace(base, width=W, height=H, metric=Metric(center=c, amplitude=a, sigma=s),
+                                name=f"batch{i}_{W}x{H}_{K}bumps", seed=seed * 1000 + i)
+        out.append(w)
+    return out
+
+
+def motion(seed: int, K: int):
+    """Seeded sinusoidal motion of K centres: A ~ U[0, 0.5]^3, f ~ U[0.1, 0.5] Hz, phi ~ U[0, 2 pi)."""
+    rng = SplitMix64(sub_seed(seed, STREAM_ANIM))
+    A = np.array([[rng.uniform(0.0, 0.5) for _ in range(3)] for _ in range(K)], np.float32).reshape(K, 3)
+    f = np.array([rng.uniform(0.1, 0.5) for _ in range(K)], np.float32)
+    ph = np.array([rng.uniform(0.0, 2.0 * math.pi) for _ in range(K)], np.float32)
+    return A, f, ph
+
+
 def scaled(w: Workload, width: int, height: int) -> Workload:
     """Same metric and scene at another resolution."""
     return dataclasses.replace(w, width=width, height=height)

@@ -1,0 +1,140 @@
+"""Batched launches, animated metrics, CUDA-graph replay and the autotuner (GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2005_05386_gb300 import scenes
+from parity import assert_parity, compare, gpu_arrays
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import torch
+    import paper_2005_05386_gb300 as rg
+    torch.cuda.set_device(0)
+    return rg
+
+
+def _small_instances():
+    a = scenes.config_parity_64()
+    b = scenes.config_1080p_64(width=160, height=90)
+    c, amp, s = scenes.random_bumps(77, 13)
+    d = scenes.config_1080p_64(width=96, height=54)
+    d.metric = scenes.Metric(center=c, amplitude=amp, sigma=s)
+    return [a, b, d]
+
+
+def _same(x, y):
+    for k in ("id", "steps", "rgba", "hit"):
+        assert np.array_equal(x[k], y[k]), k
+
+
+def _close(x, y, S):
+    """Different kernels may contract multiply-adds differently: parity tolerance."""
+    st = compare(x, dict(y, hit=y["hit"].astype(np.float64)), S)
+    assert st["agree"] >= 0.999, st
+
+
+def test_batch_equals_separate_traces(rg):
+    """A batch traces each instance as rgeo_trace does (launch shape aside)."""
+    ws = _small_instances()
+    handles = [(rg.Metric(w.metric), rg.Scene(w.scene)) for w in ws]
+    outs = [rg.alloc_outputs(w.n_pixels) for w in ws]
+    batch = rg.Batch([rg.instance(w, m, s, o) for w, (m, s), o in zip(ws, handles, outs)])
+    for _ in range(2):   # the second launch reuses the counters
+        batch.launch()
+        rg.rgeo_sync()
+        for w, (m, s), o in zip(ws, handles, outs):
+            ref = rg.trace(w, m, s)
+            rg.rgeo_sync()
+            _close(gpu_arrays(o), gpu_arrays(ref), w.scene.n_spheres)
+
+
+def test_batch_rejects_mixed_integrators(rg):
+    a, b = scenes.config_parity_64(), scenes.config_parity_64()
+    b.integrator = scenes.INTEGRATOR_EULER
+    ha, hb = (rg.Metric(a.metric), rg.Scene(a.scene)), (rg.Metric(b.metric), rg.Scene(b.scene))
+    oa, ob = rg.alloc_outputs(a.n_pixels), rg.alloc_outputs(b.n_pixels)
+    with pytest.raises(rg.RgeoError) as e:
+        rg.Batch([rg.instance(a, *ha, oa), rg.instance(b, *hb, ob)])
+    assert e.value.status == rg.RGEO_EINVAL
+
+
+def test_motion_matches_centres_set_on_the_host(rg):
+    w = scenes.config_1080p_64(width=160, height=90)
+    A, f, ph = scenes.motion(5, w.metric.n_bumps)
+    m = rg.Metric(w.metric)
+    rg.rgeo_metric_set_motion(m.handle, A, f, ph)
+    t0 = 1.7
+    rg.rgeo_metric_set_time(m.handle, t0)
+    rg.rgeo_metric_advance(m.handle, 1.0 / 30.0)   # moves the centres to c(t0), then t += dt
+    got = rg.trace(w, metric=m)
+    rg.rgeo_sync()
+    c = w.metric.center.astype(np.float64) + A * np.sin(2 * math.pi * f * t0 + ph)[:, None]
+    w.metric.center = c.astype(np.float32)
+    ref = rg.trace(w)
+    rg.rgeo_sync()
+    st = compare(gpu_arrays(got), dict(gpu_arrays(ref)), w.scene.n_spheres)
+    assert st["agree"] >= 0.999 and st["hits"] > 1000, st
+
+
+def test_graph_replay_of_animation_and_batch(rg):
+    """A captured graph of [advance, batch launch] replays frame after frame with no host input
+    and gives the same frames as direct calls."""
+    import torch
+    ws = _small_instances()[1:]
+    handles = [(rg.Metric(w.metric), rg.Scene(w.scene)) for w in ws]
+    for w, (m, _) in zip(ws, handles):
+        A, f, ph = scenes.motion(9, w.metric.n_bumps)
+        rg.rgeo_metric_set_motion(m.handle, A, f, ph)
+    outs = [rg.alloc_outputs(w.n_pixels) for w in ws]
+    batch = rg.Batch([rg.instance(w, m, s, o) for w, (m, s), o in zip(ws, handles, outs)])
+    dt = 1.0 / 30.0
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for m, _ in handles:
+            rg.rgeo_metric_advance(m.handle, dt, stream.cuda_stream)
+        batch.launch(stream.cuda_stream)
+    frames = []
+    for m, _ in handles:
+        rg.rgeo_metric_set_time(m.handle, 0.0)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        frames.append([gpu_arrays(o) for o in outs])
+    rg.rgeo_sync()
+    # direct calls from the same start time
+    for m, _ in handles:
+        rg.rgeo_metric_set_time(m.handle, 0.0)
+    for k in range(3):
+        for m, _ in handles:
+            rg.rgeo_metric_advance(m.handle, dt)
+        batch.launch()
+        rg.rgeo_sync()
+        for o, ref in zip(outs, frames[k]):
+            _same(gpu_arrays(o), ref)
+    # the frames really move
+    assert not np.array_equal(frames[0][0]["hit"], frames[2][0]["hit"])
+
+
+def test_autotuner_returns_a_candidate_and_caches(rg, tmp_path, monkeypatch):
+    from paper_2005_05386_gb300 import autotune
+    monkeypatch.setenv("RGEO_TUNING_CACHE", str(tmp_path / "tuning.json"))
+    w = scenes.config_1080p_64(width=256, height=144)
+    first = autotune.tune(w, repeats=1)
+    assert not first["cached"] and first["ms"] > 0
+    assert {k: first[k] for k in ("cull_grid", "rays_per_thread")} in autotune.candidates(w)
+    second = autotune.tune(w, repeats=1)
+    assert second["cached"] and second["cull_grid"] == first["cull_grid"]
+    tuned = autotune.apply(w, second)
+    out = rg.trace(tuned)
+    rg.rgeo_sync()
+    rg.rgeo_set_tuning(0)
+    ref = rg.trace(w)
+    rg.rgeo_sync()
+    _close(gpu_arrays(out), gpu_arrays(ref), w.scene.n_spheres)
