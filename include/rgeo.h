@@ -247,6 +247,67 @@ rgeo_status rgeo_metric_set_time(rgeo_metric *metric, float t, void *cuda_stream
  * non-finite dt), RGEO_ECUDA. */
 rgeo_status rgeo_metric_advance(rgeo_metric *metric, float dt, void *cuda_stream);
 
+/* -------------------------------------------------- learned exponential map
+ * A surrogate of exp_p (Eq. 3.5) over short arcs: an MLP 7 -> 256 -> 256 -> 256 -> 7
+ * (ReLU) maps a segment's start (x / box, unit direction d, s / s_max) to the
+ * scaled residuals of its endpoint and tangent with respect to the straight line,
+ *   r_x = (x_s - x - s v) / s^2,   r_v = (v_s - v) / s   (v the g-unit tangent along d),
+ * plus a seventh output estimating log of its own squared error.  The two
+ * 256 x 256 layers, forward and backward, run as BF16 tcgen05 tensor-core GEMMs
+ * with FP32 accumulation; the 7-wide layers run in FP32.  Parameters are kept in
+ * FP32 (Adam moments too): W1 [256 x 7], b1 [256], W2 [256 x 256], b2, W3, b3,
+ * W4 [7 x 256], b4 [7], each W row-major (out x in), in this order.
+ * Loss: mean squared error of outputs 0..5 against the targets, plus 0.1 x the
+ * squared error of output 6 against log(sum of the six squared errors + 1e-6). */
+typedef struct rgeo_expmap rgeo_expmap; /* opaque, owns device memory */
+
+int64_t rgeo_expmap_param_count(void);
+
+/* Allocate the network for batches of up to max_batch rows (a multiple of 128)
+ * and initialise it (He-uniform weights from the seed, zero biases). Synchronises. */
+rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **out);
+void rgeo_expmap_destroy(rgeo_expmap *expmap);
+
+/* Training segments generated by the integrator: n samples with x ~ U[-box, box]^3,
+ * d uniform on S^2, s = k h with k uniform in 1..round(s_max / h), integrated by
+ * RK4 at step h under the metric (graph metrics).  DEVICE inputs [n*7] =
+ * (x / box, d, s / s_max), DEVICE targets [n*6] = (r_x, r_v).  Asynchronous. */
+rgeo_status rgeo_expmap_generate(const rgeo_metric *metric, int64_t n, uint64_t seed, float box, float s_max,
+                                 float h, float *inputs, float *targets, void *cuda_stream);
+
+/* outputs [n*7] (DEVICE) for inputs [n*7] (DEVICE); any n >= 0.  Asynchronous. */
+rgeo_status rgeo_expmap_forward(const rgeo_expmap *expmap, const float *inputs, int64_t n, float *outputs,
+                                void *cuda_stream);
+
+/* Loss and its gradient w.r.t. every parameter for one batch (a multiple of 128,
+ * at most max_batch): grads (DEVICE [param_count], may be NULL) and loss (DEVICE
+ * [1], may be NULL).  Asynchronous. */
+rgeo_status rgeo_expmap_gradients(rgeo_expmap *expmap, const float *inputs, const float *targets, int32_t batch,
+                                  float *grads, float *loss, void *cuda_stream);
+
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) at learning rate lr. Asynchronous. */
+rgeo_status rgeo_expmap_train_step(rgeo_expmap *expmap, const float *inputs, const float *targets,
+                                   int32_t batch, float lr, float *loss, void *cuda_stream);
+
+/* HOST copies of the FP32 parameters (n must equal rgeo_expmap_param_count()). */
+rgeo_status rgeo_expmap_get_params(const rgeo_expmap *expmap, float *params, int64_t n);
+rgeo_status rgeo_expmap_set_params(rgeo_expmap *expmap, const float *params, int64_t n);
+
+/* Checkpoint: parameters, Adam moments and step count to / from a file. */
+rgeo_status rgeo_expmap_save(const rgeo_expmap *expmap, const char *path);
+rgeo_status rgeo_expmap_load(rgeo_expmap *expmap, const char *path);
+
+/* The tensor-core GEMM of the surrogate, C = A B^T (+ bias), for testing and
+ * measurement: A DEVICE bf16 [M x K] row-major, B DEVICE bf16 [N x K] row-major,
+ * 16 <= N <= 256 with N % 16 == 0, K % 64 == 0, A and B 16-byte aligned.  mode 0: C float [M x ldc] with
+ * bias; mode 1: relu(C + bias) as bf16 [M x ldc] and, if ct != NULL, transposed
+ * bf16 [N x ldt]; mode 2: C added atomically to float [M x ldc], K split over
+ * `splits` CTAs.  Asynchronous; a tensor-core wait that gives up is reported by
+ * rgeo_sync as RGEO_ETIMEOUT. */
+rgeo_status rgeo_gemm_bf16(const void *A, const void *B, int32_t M, int32_t N, int32_t K, int32_t splits,
+                           const float *bias, int32_t mode, void *C, int32_t ldc, void *ct, int32_t ldt,
+                           void *cuda_stream);
+
 /* Wait for the stream, then read and clear the device error word of the
  * current device.  Returns RGEO_OK, RGEO_EDEVICE or RGEO_ETIMEOUT (message in
  * rgeo_last_error), or RGEO_ECUDA if the stream itself failed. */

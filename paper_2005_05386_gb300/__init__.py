@@ -35,7 +35,10 @@ EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_me
            "rgeo_metric_destroy", "rgeo_scene_create", "rgeo_scene_destroy", "rgeo_trace",
            "rgeo_trace_host", "rgeo_sync", "rgeo_set_tuning", "rgeo_get_tuning", "rgeo_ffma_probe",
            "rgeo_trace_noalloc", "rgeo_batch_create", "rgeo_batch_launch", "rgeo_batch_destroy",
-           "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance")
+           "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance", "rgeo_expmap_param_count",
+           "rgeo_expmap_create", "rgeo_expmap_destroy", "rgeo_expmap_generate", "rgeo_expmap_forward",
+           "rgeo_expmap_gradients", "rgeo_expmap_train_step", "rgeo_expmap_get_params", "rgeo_expmap_set_params",
+           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -112,6 +115,31 @@ def library() -> ctypes.CDLL:
     L.rgeo_trace_host.argtypes = trace_args
     L.rgeo_sync.restype = i32
     L.rgeo_sync.argtypes = [vp]
+    i64, u64 = ctypes.c_int64, ctypes.c_uint64
+    L.rgeo_expmap_param_count.restype = i64
+    L.rgeo_expmap_param_count.argtypes = []
+    L.rgeo_expmap_create.restype = i32
+    L.rgeo_expmap_create.argtypes = [i32, u64, ctypes.POINTER(vp)]
+    L.rgeo_expmap_destroy.restype = None
+    L.rgeo_expmap_destroy.argtypes = [vp]
+    L.rgeo_expmap_generate.restype = i32
+    L.rgeo_expmap_generate.argtypes = [vp, i64, u64, f32, f32, f32, vp, vp, vp]
+    L.rgeo_expmap_forward.restype = i32
+    L.rgeo_expmap_forward.argtypes = [vp, vp, i64, vp, vp]
+    L.rgeo_expmap_gradients.restype = i32
+    L.rgeo_expmap_gradients.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.rgeo_expmap_train_step.restype = i32
+    L.rgeo_expmap_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp]
+    L.rgeo_expmap_get_params.restype = i32
+    L.rgeo_expmap_get_params.argtypes = [vp, fp, i64]
+    L.rgeo_expmap_set_params.restype = i32
+    L.rgeo_expmap_set_params.argtypes = [vp, fp, i64]
+    L.rgeo_expmap_save.restype = i32
+    L.rgeo_expmap_save.argtypes = [vp, ctypes.c_char_p]
+    L.rgeo_expmap_load.restype = i32
+    L.rgeo_expmap_load.argtypes = [vp, ctypes.c_char_p]
+    L.rgeo_gemm_bf16.restype = i32
+    L.rgeo_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp]
     L.rgeo_batch_create.restype = i32
     L.rgeo_batch_create.argtypes = [i32, ctypes.POINTER(rgeo_instance), ctypes.POINTER(vp)]
     L.rgeo_batch_launch.restype = i32
@@ -249,6 +277,82 @@ def rgeo_metric_set_time(metric: int, t: float, stream=None):
 
 def rgeo_metric_advance(metric: int, dt: float, stream=None):
     _check(library().rgeo_metric_advance(metric, dt, _stream_handle(stream)), "rgeo_metric_advance")
+
+
+def rgeo_gemm_bf16(A, B, M, N, K, splits, bias, mode, C, ldc, ct, ldt, stream=None):
+    """Pointers are device addresses (ints) or None."""
+    _check(library().rgeo_gemm_bf16(A, B, M, N, K, splits, bias, mode, C, ldc, ct, ldt, _stream_handle(stream)),
+           "rgeo_gemm_bf16")
+
+
+def rgeo_expmap_param_count() -> int:
+    return library().rgeo_expmap_param_count()
+
+
+class Expmap:
+    """The learned exponential map (device weights, Adam state and scratch)."""
+
+    IN, OUT, WIDTH = 7, 7, 256
+
+    def __init__(self, max_batch: int = 8192, seed: int = 1):
+        out = ctypes.c_void_p()
+        _check(library().rgeo_expmap_create(max_batch, seed, ctypes.byref(out)), "rgeo_expmap_create")
+        self.handle, self.max_batch = out.value, max_batch
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().rgeo_expmap_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    @staticmethod
+    def generate(metric: "Metric", n: int, seed: int, box: float = 4.0, s_max: float = 0.5, h: float = 0.005,
+                 stream=None):
+        """(inputs [n, 7], targets [n, 6]) device tensors of integrator-generated segments."""
+        import torch
+        X = torch.empty(n, 7, dtype=torch.float32, device="cuda")
+        T = torch.empty(n, 6, dtype=torch.float32, device="cuda")
+        _check(library().rgeo_expmap_generate(metric.handle, n, seed, box, s_max, h, X.data_ptr(), T.data_ptr(),
+                                              _stream_handle(stream)), "rgeo_expmap_generate")
+        return X, T
+
+    def forward(self, X, out=None, stream=None):
+        import torch
+        Y = out if out is not None else torch.empty(X.shape[0], 7, dtype=torch.float32, device="cuda")
+        _check(library().rgeo_expmap_forward(self.handle, X.data_ptr(), X.shape[0], Y.data_ptr(),
+                                             _stream_handle(stream)), "rgeo_expmap_forward")
+        return Y
+
+    def gradients(self, X, T, stream=None):
+        import torch
+        G = torch.empty(rgeo_expmap_param_count(), dtype=torch.float32, device="cuda")
+        L = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(library().rgeo_expmap_gradients(self.handle, X.data_ptr(), T.data_ptr(), X.shape[0], G.data_ptr(),
+                                               L.data_ptr(), _stream_handle(stream)), "rgeo_expmap_gradients")
+        return G, L
+
+    def train_step(self, X, T, lr: float, loss=None, stream=None):
+        _check(library().rgeo_expmap_train_step(self.handle, X.data_ptr(), T.data_ptr(), X.shape[0], lr,
+                                                loss.data_ptr() if loss is not None else None,
+                                                _stream_handle(stream)), "rgeo_expmap_train_step")
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(rgeo_expmap_param_count(), np.float32)
+        _check(library().rgeo_expmap_get_params(self.handle, _fptr(p), p.size), "rgeo_expmap_get_params")
+        return p
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, np.float32)
+        _check(library().rgeo_expmap_set_params(self.handle, _fptr(p), p.size), "rgeo_expmap_set_params")
+
+    def save(self, path: str):
+        _check(library().rgeo_expmap_save(self.handle, os.fsencode(path)), "rgeo_expmap_save")
+
+    def load(self, path: str):
+        _check(library().rgeo_expmap_load(self.handle, os.fsencode(path)), "rgeo_expmap_load")
 
 
 def rgeo_sync(stream=None):

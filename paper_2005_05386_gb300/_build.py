@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "librgeo")
 LIB = os.path.join(HERE, "librgeo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["rgeo_api.cu", "rgeo_trace.cu", "rgeo_noalloc.cu", "rgeo_scene_build.cpp"]
+SOURCES = ["rgeo_api.cu", "rgeo_trace.cu", "rgeo_noalloc.cu", "rgeo_mlp.cu", "rgeo_scene_build.cpp"]
 
 
 def nvcc() -> str:

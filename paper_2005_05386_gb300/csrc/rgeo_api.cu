@@ -420,8 +420,10 @@ rgeo_status rgeo_sync(void *cuda_stream) {
   g_last_error.clear();
   cudaStream_t st = (cudaStream_t)cuda_stream;
   RGEO_CUDA(cudaStreamSynchronize(st), "rgeo_sync: stream");
-  unsigned word = 0;
+  unsigned word = 0, mlp_word = 0;
   RGEO_CUDA(rgeo::read_and_clear_device_error(&word, st), "rgeo_sync: error word");
+  RGEO_CUDA(rgeo::read_and_clear_mlp_error(&mlp_word), "rgeo_sync: error word");
+  word |= mlp_word;
   if (word & rgeo::kErrTimeout) return fail(RGEO_ETIMEOUT, "a bounded device-side wait timed out");
   if (word & rgeo::kErrStackOverflow)
     return fail(RGEO_EDEVICE, "BVH traversal stack exhausted (the affected segment tests were cut short)");
@@ -559,6 +561,32 @@ rgeo_status rgeo_metric_advance(rgeo_metric *m, float dt, void *cuda_stream) {
     RGEO_CUDA(rgeo::launch_build_cull(m->d.bumps, m->d.K, m->d.cull_G, m->d.cull_words, m->d.cull_hdr,
                                       m->d.cull_masks, st),
               "rgeo_metric_advance: cull grid");
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_expmap_generate(const rgeo_metric *metric, int64_t n, uint64_t seed, float box, float s_max,
+                                 float h, float *inputs, float *targets, void *cuda_stream) {
+  g_last_error.clear();
+  if (!metric || n < 0 || (n > 0 && (!inputs || !targets)))
+    return fail(RGEO_EINVAL, "rgeo_expmap_generate: bad argument");
+  if (metric->d.kind != RGEO_METRIC_GRAPH_BUMPS) return fail(RGEO_EINVAL, "rgeo_expmap_generate: graph metrics only");
+  if (!(box > 0.f) || !(s_max > 0.f) || !(h > 0.f) || !std::isfinite(box) || !std::isfinite(s_max) ||
+      !std::isfinite(h) || s_max < h)
+    return fail(RGEO_EINVAL, "rgeo_expmap_generate: need finite box > 0, h > 0, s_max >= h");
+  rgeo::TraceParams p;
+  std::memset(&p, 0, sizeof(p));
+  const rgeo::MetricDev &m = metric->d;
+  p.bumps = m.bumps;
+  p.K = m.K;
+  p.kind = m.kind;
+  p.aniso = m.aniso;
+  std::memcpy(p.b, m.b, sizeof(p.b));
+  std::memcpy(p.A, m.A, sizeof(p.A));
+  p.has_affine = m.has_affine;
+  p.has_quad = m.has_quad;
+  p.h = h;
+  RGEO_CUDA(rgeo::launch_segments(p, n, seed, box, s_max, inputs, targets, (cudaStream_t)cuda_stream),
+            "rgeo_expmap_generate");
   return RGEO_OK;
 }
 

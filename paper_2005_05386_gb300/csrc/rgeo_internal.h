@@ -166,6 +166,12 @@ cudaError_t launch_batch(const TraceParams *dev_inst, int n, int kind, int aniso
 cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
                                   float dt, cudaStream_t st);
 cudaError_t launch_set_time(float *t, float value, cudaStream_t st);
+cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long long seed, float box, float s_max,
+                            float *X, float *T, cudaStream_t st);
+// rgeo_mlp.cu
+cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits, const float *bias,
+                             int mode, void *C, int ldc, void *ct, int ldt, cudaStream_t st);
+cudaError_t read_and_clear_mlp_error(unsigned *word);
 cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
 cudaError_t run_ffma_probe(int mode, float *tflops, float *ms);
 

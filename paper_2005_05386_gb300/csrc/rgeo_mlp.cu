@@ -1,0 +1,722 @@
+// rgeo_mlp.cu -- tensor-core kernels of the learned exponential map (sm_103a).
+//
+// The surrogate maps (position, unit direction, arc length) to the endpoint and
+// tangent residuals of a geodesic segment (Eq. 3.5: exp_p(s v)); it is a
+// 7 -> 256 -> 256 -> 256 -> 7 MLP with ReLU.  Its 256 x 256 layers -- forward and
+// both backward products -- run on the 5th-generation tensor cores:
+//   * tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulation) issued by one thread,
+//   * accumulators in tensor memory (TMEM), read back with tcgen05.ld,
+//   * operands staged in shared memory in the canonical K-major layout without
+//     swizzle (8-row x 16-byte core matrices), double-buffered with cp.async,
+//   * completion signalled through mbarriers by tcgen05.commit.
+// Every wait is bounded: a wait that runs out records kErrTimeout in the error
+// word and the kernel returns after releasing its tensor memory.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "rgeo.h"
+#include "rgeo_internal.h"
+
+namespace rgeo {
+namespace {
+
+constexpr int kTileM = 128;     // rows of A (and of C) per CTA
+constexpr int kTileK = 64;      // K elements per shared-memory stage (4 MMAs of K = 16)
+constexpr int kMaxTileN = 256;  // columns of C per CTA (TMEM columns)
+constexpr long long kSpinLimit = 1ll << 22;
+
+__device__ unsigned int g_mlp_error;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (K-major, no swizzle): start address, leading
+// byte offset (between the two core matrices of one K = 16 step), stride byte
+// offset (between 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  return d;  // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copy rows [row0, row0 + rows) x K columns [k0, k0 + 64) of a row-major bf16
+// matrix (leading dimension ld elements) into the canonical layout: core matrix
+// (row group g, K chunk c) of 8 rows x 8 elements at byte offset (g * 8 + c) * 128;
+// within it, row r at r * 16.  Hence LBO = 128 (next K chunk), SBO = 1024 (next
+// row group).  Rows at or beyond nrows are filled with zeros.
+__device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *src, int ld, int row0, int rows,
+                                           int nrows, int k0) {
+  const int chunks = rows * (kTileK / 8);  // 16-byte chunks
+  for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+    const int r = q >> 3, c = q & 7;
+    uint8_t *d = dst + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16;
+    if (row0 + r < nrows) {
+      cp_async16(d, src + (size_t)(row0 + r) * ld + k0 + c * 8);
+    } else {
+      *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
+// C[M x N] = A[M x K] B[N x K]^T (+ bias), with an epilogue:
+//   mode 0: C fp32 row-major (ldc), plus bias
+//   mode 1: relu(C + bias) as bf16 row-major (ldc) and, when ct != null, its transpose
+//           (N x M, leading dimension ldt) as bf16
+//   mode 2: atomicAdd of C into fp32 row-major (split-K: blockIdx.y picks a K range)
+// Requirements (checked by the launcher): K % 64 == 0, N % 16 == 0, 16 <= N <= 256.
+__global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restrict__ A,
+                                                   const __nv_bfloat16 *__restrict__ B, int M, int N, int K,
+                                                   int k_per_split, const float *__restrict__ bias, int mode,
+                                                   void *C, int ldc, __nv_bfloat16 *ct, int ldt) {
+  extern __shared__ __align__(1024) uint8_t gsm[];
+  uint8_t *sA[2] = {gsm, gsm + kTileM * kTileK * 2};
+  uint8_t *sB[2] = {gsm + 2 * kTileM * kTileK * 2, gsm + 2 * kTileM * kTileK * 2 + kMaxTileN * kTileK * 2};
+  __shared__ uint64_t bar_stage[2];
+  __shared__ uint64_t bar_done;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5;
+  const int m0 = blockIdx.x * kTileM;
+  const int kbeg = blockIdx.y * k_per_split;
+  const int kend = min(K, kbeg + k_per_split);
+  const int nstages = (kend - kbeg) / kTileK;
+  const int ncols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_stage[0], 1);
+    mbar_init(&bar_stage[1], 1);
+    mbar_init(&bar_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_slot;
+  const uint32_t idesc = idesc_bf16(kTileM, N);
+
+  // prologue: stage 0
+  if (nstages > 0) {
+    stage_tile(sA[0], A, K, m0, kTileM, M, kbeg);
+    stage_tile(sB[0], B, K, 0, N, N, kbeg);
+    cp_async_commit();
+  }
+  uint32_t phase[2] = {0u, 0u};
+  for (int s = 0; s < nstages; ++s) {
+    const int buf = s & 1;
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make the staged data visible to the tensor core
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA[buf]), b0 = smem_u32(sB[buf]);
+      for (int kk = 0; kk < kTileK / 16; ++kk) {
+        const uint64_t ad = smem_desc(a0 + kk * 256, 128, 1024);
+        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+        const uint32_t acc = (s > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar_stage[buf]))
+                   : "memory");
+    }
+    // stage s + 1 into the other buffer once the MMAs that read it (stage s - 1) are done
+    if (s + 1 < nstages) {
+      const int nb = buf ^ 1;
+      if (s >= 1) {
+        if (!mbar_wait(&bar_stage[nb], phase[nb])) abort_flag = 1;
+        phase[nb] ^= 1u;
+      }
+      __syncthreads();
+      if (abort_flag) break;
+      stage_tile(sA[nb], A, K, m0, kTileM, M, kbeg + (s + 1) * kTileK);
+      stage_tile(sB[nb], B, K, 0, N, N, kbeg + (s + 1) * kTileK);
+      cp_async_commit();
+    }
+  }
+  cp_async_wait_all();
+  // All MMAs issued (also after an abort): one more commit tracks every one of them,
+  // so the tensor memory is released only once none is in flight.
+  if (threadIdx.x == 0 && nstages > 0) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&bar_done))
+                 : "memory");
+  }
+  __syncthreads();
+  bool ok = !abort_flag;
+  if (nstages > 0 && !mbar_wait(&bar_done, 0u)) ok = false;
+  if (!ok) atomicOr(&g_mlp_error, kErrTimeout);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  // epilogue: warp w owns rows 32 w .. 32 w + 31 (TMEM lanes); 32 columns per load
+  const int row = m0 + warp * 32 + (threadIdx.x & 31);
+  if (ok && nstages > 0) {
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        const int nn = min(32, N - c0);
+        if (mode == 0) {
+          float *crow = reinterpret_cast<float *>(C) + (size_t)row * ldc + c0;
+          for (int j = 0; j < nn; ++j) crow[j] = __uint_as_float(v[j]) + (bias ? bias[c0 + j] : 0.f);
+        } else if (mode == 1) {
+          __nv_bfloat16 *crow = reinterpret_cast<__nv_bfloat16 *>(C) + (size_t)row * ldc + c0;
+          for (int j = 0; j < nn; ++j) {
+            const float y = fmaxf(__uint_as_float(v[j]) + (bias ? bias[c0 + j] : 0.f), 0.f);
+            const __nv_bfloat16 yb = __float2bfloat16_rn(y);
+            crow[j] = yb;
+            if (ct) ct[(size_t)(c0 + j) * ldt + row] = yb;
+          }
+        } else {
+          float *crow = reinterpret_cast<float *>(C) + (size_t)row * ldc + c0;
+          for (int j = 0; j < nn; ++j) atomicAdd(crow + j, __uint_as_float(v[j]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+
+// ------------------------------------------------------------------ the MLP
+// Parameters (FP32 master copy, flat): W1 [256 x 7], b1 [256], W2 [256 x 256], b2,
+// W3 [256 x 256], b3, W4 [7 x 256], b4 [7]; every W is row-major out x in.
+constexpr int kIn = 7, kOut = 7, kWid = 256;
+constexpr int oW1 = 0, ob1 = oW1 + kWid * kIn, oW2 = ob1 + kWid, ob2 = oW2 + kWid * kWid, oW3 = ob2 + kWid,
+              ob3 = oW3 + kWid * kWid, oW4 = ob3 + kWid, ob4 = oW4 + kOut * kWid, kParams = ob4 + kOut;
+
+// Layer 1 in FP32 (K = 7 is too small for the tensor cores): H1 = relu(X W1^T + b1),
+// written as bf16 rows and as the transposed bf16 copy used by the weight gradient.
+__global__ void k_layer_in(const float *__restrict__ X, int B, const float *__restrict__ P,
+                           __nv_bfloat16 *H1, __nv_bfloat16 *H1t) {
+  const int b = blockIdx.x;
+  const int j = threadIdx.x;  // 256 threads: one output unit each
+  __shared__ float xs[kIn];
+  if (j < kIn) xs[j] = X[(size_t)b * kIn + j];
+  __syncthreads();
+  float z = P[ob1 + j];
+  for (int k = 0; k < kIn; ++k) z = fmaf(P[oW1 + j * kIn + k], xs[k], z);
+  const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(z, 0.f));
+  H1[(size_t)b * kWid + j] = h;
+  H1t[(size_t)j * B + b] = h;
+}
+
+// Layer 4 in FP32 (N = 7): Y = H3 W4^T + b4.  One warp per row.
+__global__ void k_layer_out(const __nv_bfloat16 *__restrict__ H3, int B, const float *__restrict__ P, float *Y) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;
+  float acc[kOut];
+  for (int o = 0; o < kOut; ++o) acc[o] = 0.f;
+  for (int k = lane; k < kWid; k += 32) {
+    const float h = __bfloat162float(H3[(size_t)b * kWid + k]);
+    for (int o = 0; o < kOut; ++o) acc[o] = fmaf(P[oW4 + o * kWid + k], h, acc[o]);
+  }
+  for (int o = 0; o < kOut; ++o)
+    for (int off = 16; off > 0; off >>= 1) acc[o] += __shfl_down_sync(0xffffffffu, acc[o], off);
+  if (lane == 0)
+    for (int o = 0; o < kOut; ++o) Y[(size_t)b * kOut + o] = acc[o] + P[ob4 + o];
+}
+
+// Loss and its gradient.  Outputs 0..5 regress the scaled residuals T (mean squared
+// error); output 6 regresses e = log(sum_i (Y_i - T_i)^2 + 1e-6), the log squared
+// error of the same sample (a target that is not differentiated), weighted by lam.
+__global__ void k_loss_grad(const float *__restrict__ Y, const float *__restrict__ T, int B, float lam, float *dY,
+                            float *loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (b < B) {
+    float se = 0.f;
+    for (int o = 0; o < 6; ++o) {
+      const float d = Y[(size_t)b * kOut + o] - T[(size_t)b * 6 + o];
+      se = fmaf(d, d, se);
+      dY[(size_t)b * kOut + o] = 2.f * d / (6.f * B);
+    }
+    const float e = logf(se + 1e-6f);
+    const float d6 = Y[(size_t)b * kOut + 6] - e;
+    dY[(size_t)b * kOut + 6] = 2.f * lam * d6 / B;
+    l = se / (6.f * B) + lam * d6 * d6 / B;
+  }
+  for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+// Gradient of layer 4 and the error into layer 3:
+//   dW4[o, k] += sum_b dY[b, o] H3[b, k], db4[o] += sum_b dY[b, o]  (atomics per block)
+//   dZ3[b, k] = (sum_o dY[b, o] W4[o, k]) [H3[b, k] > 0], as bf16 rows and transposed.
+__global__ void k_back_out(const float *__restrict__ dY, const __nv_bfloat16 *__restrict__ H3, int B,
+                           const float *__restrict__ P, float *G, __nv_bfloat16 *dZ3, __nv_bfloat16 *dZ3t) {
+  const int k = threadIdx.x;  // 256 threads: one hidden unit each
+  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
+  float gw[kOut];
+  for (int o = 0; o < kOut; ++o) gw[o] = 0.f;
+  float w4[kOut];
+  for (int o = 0; o < kOut; ++o) w4[o] = P[oW4 + o * kWid + k];
+  for (int b = b0; b < b1; ++b) {
+    const float h = __bfloat162float(H3[(size_t)b * kWid + k]);
+    float dh = 0.f;
+    for (int o = 0; o < kOut; ++o) {
+      const float dy = dY[(size_t)b * kOut + o];
+      gw[o] = fmaf(dy, h, gw[o]);
+      dh = fmaf(dy, w4[o], dh);
+    }
+    const __nv_bfloat16 dz = __float2bfloat16_rn(h > 0.f ? dh : 0.f);
+    dZ3[(size_t)b * kWid + k] = dz;
+    dZ3t[(size_t)k * B + b] = dz;
+  }
+  for (int o = 0; o < kOut; ++o) atomicAdd(&G[oW4 + o * kWid + k], gw[o]);
+  if (k < kOut) {
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b) s += dY[(size_t)b * kOut + k];
+    atomicAdd(&G[ob4 + k], s);
+  }
+}
+
+// dZ = dH [H > 0] for a hidden layer: bf16 rows + transposed copy (layers 2, 3), or
+// FP32 rows (layer 1).  Also the bias gradient db[k] += sum_b dZ[b, k].
+__global__ void k_relu_back(const float *__restrict__ dH, const __nv_bfloat16 *__restrict__ H, int B, float *db,
+                            __nv_bfloat16 *dZ, __nv_bfloat16 *dZt, float *dZf) {
+  const int k = threadIdx.x;
+  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
+  float s = 0.f;
+  for (int b = b0; b < b1; ++b) {
+    const float g = __bfloat162float(H[(size_t)b * kWid + k]) > 0.f ? dH[(size_t)b * kWid + k] : 0.f;
+    s += g;
+    if (dZ) {
+      const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+      dZ[(size_t)b * kWid + k] = gb;
+      dZt[(size_t)k * B + b] = gb;
+    }
+    if (dZf) dZf[(size_t)b * kWid + k] = g;
+  }
+  atomicAdd(&db[k], s);
+}
+
+// Bias gradient of a layer whose dZ exists only in bf16 (layer 3): db[k] += sum_b dZ[b, k].
+__global__ void k_bias_back(const __nv_bfloat16 *__restrict__ dZ, int B, float *db) {
+  const int k = threadIdx.x;
+  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
+  float s = 0.f;
+  for (int b = b0; b < b1; ++b) s += __bfloat162float(dZ[(size_t)b * kWid + k]);
+  atomicAdd(&db[k], s);
+}
+
+// Layer-1 weight gradient: dW1[j, i] += sum_b dZ1[b, j] X[b, i].
+__global__ void k_back_in(const float *__restrict__ dZ1, const float *__restrict__ X, int B, float *G) {
+  const int j = threadIdx.x;
+  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
+  float g[kIn];
+  for (int i = 0; i < kIn; ++i) g[i] = 0.f;
+  for (int b = b0; b < b1; ++b) {
+    const float dz = dZ1[(size_t)b * kWid + j];
+    for (int i = 0; i < kIn; ++i) g[i] = fmaf(dz, X[(size_t)b * kIn + i], g[i]);
+  }
+  for (int i = 0; i < kIn; ++i) atomicAdd(&G[oW1 + j * kIn + i], g[i]);
+}
+
+// Adam (Kingma and Ba 2015) on the FP32 master parameters; then the bf16 copies of
+// W2 and W3 (row-major, and transposed for the backward products).
+__global__ void k_adam(float *P, const float *G, float *m, float *v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float mi = b1 * m[i] + (1.f - b1) * g;
+  const float vi = b2 * v[i] + (1.f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_refresh_bf16(const float *P, __nv_bfloat16 *W2b, __nv_bfloat16 *W3b, __nv_bfloat16 *W2t,
+                               __nv_bfloat16 *W3t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kWid * kWid) return;
+  const int r = i / kWid, c = i % kWid;
+  const __nv_bfloat16 a = __float2bfloat16_rn(P[oW2 + i]), b = __float2bfloat16_rn(P[oW3 + i]);
+  W2b[i] = a;
+  W3b[i] = b;
+  W2t[c * kWid + r] = a;
+  W3t[c * kWid + r] = b;
+}
+
+// Counter-based uniform in [0, 1) from (seed, i): SplitMix64 (Steele, Lea, Flood 2014) output of
+// the state seed + (i + 1) * golden, top 24 bits.
+__device__ __forceinline__ float u01(unsigned long long seed, unsigned long long i) {
+  unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)(z >> 40) * (1.f / 16777216.f);
+}
+
+// He-uniform initialisation of the weights, zero biases.
+__global__ void k_init(float *P, unsigned long long seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kParams) return;
+  float fan = 0.f;
+  if (i < ob1) fan = kIn;
+  else if (i >= oW2 && i < ob2) fan = kWid;
+  else if (i >= oW3 && i < ob3) fan = kWid;
+  else if (i >= oW4 && i < ob4) fan = kWid;
+  P[i] = fan > 0.f ? (2.f * u01(seed, i) - 1.f) * sqrtf(6.f / fan) : 0.f;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits, const float *bias,
+                             int mode, void *C, int ldc, void *ct, int ldt, cudaStream_t st) {
+  if (M <= 0 || N < 16 || N > kMaxTileN || N % 16 != 0 || K <= 0 || K % kTileK != 0 || splits < 1)
+    return cudaErrorInvalidValue;
+  if (splits > 1 && mode != 2) return cudaErrorInvalidValue;
+  // cp.async moves 16-byte chunks: both operands must start on a 16-byte boundary
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) return cudaErrorInvalidValue;
+  if (reinterpret_cast<uintptr_t>(C) & (mode == 1 ? 1u : 3u)) return cudaErrorInvalidValue;
+  if (mode == 1 && ct && (reinterpret_cast<uintptr_t>(ct) & 1u)) return cudaErrorInvalidValue;
+  const int kchunk = ((K / kTileK + splits - 1) / splits) * kTileK;
+  const size_t smem = (size_t)2 * (kTileM + kMaxTileN) * kTileK * 2;  // 96 KB
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)((K + kchunk - 1) / kchunk));
+  k_gemm_bf16<<<grid, 128, smem, st>>>(reinterpret_cast<const __nv_bfloat16 *>(A),
+                                        reinterpret_cast<const __nv_bfloat16 *>(B), M, N, K, kchunk, bias, mode, C,
+                                        ldc, reinterpret_cast<__nv_bfloat16 *>(ct), ldt);
+  return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_mlp_error(unsigned *word) {
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_mlp_error, sizeof(unsigned));
+  if (e != cudaSuccess) return e;
+  const unsigned zero = 0;
+  return cudaMemcpyToSymbol(g_mlp_error, &zero, sizeof(unsigned));
+}
+
+}  // namespace rgeo
+
+namespace rgeo {
+namespace {
+
+struct ExpmapDev {
+  int bmax;
+  long long step;
+  float *P, *G, *m, *v;
+  __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
+  __nv_bfloat16 *H1, *H2, *H3, *H1t, *H2t, *H3t, *dZ, *dZt;
+  float *Y, *dY, *dH, *dZ1, *loss;
+};
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+  return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+void free_all(ExpmapDev &d) {
+  void *ptrs[] = {d.P, d.G, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.H1, d.H2, d.H3, d.H1t, d.H2t, d.H3t,
+                  d.dZ, d.dZt, d.Y, d.dY, d.dH, d.dZ1, d.loss};
+  for (void *q : ptrs) cudaFree(q);
+}
+
+cudaError_t forward(const ExpmapDev &d, const float *X, int B, float *Y, cudaStream_t st) {
+  k_layer_in<<<B, kWid, 0, st>>>(X, B, d.P, d.H1, d.H1t);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_gemm_bf16(d.H1, d.W2b, B, kWid, kWid, 1, d.P + ob2, 1, d.H2, kWid, d.H2t, B, st);
+  if (e != cudaSuccess) return e;
+  e = launch_gemm_bf16(d.H2, d.W3b, B, kWid, kWid, 1, d.P + ob3, 1, d.H3, kWid, d.H3t, B, st);
+  if (e != cudaSuccess) return e;
+  k_layer_out<<<(B + 7) / 8, 256, 0, st>>>(d.H3, B, d.P, Y);
+  return cudaGetLastError();
+}
+
+// Gradients of the loss w.r.t. every parameter into d.G (zeroed first); loss into d.loss.
+cudaError_t gradients(ExpmapDev &d, const float *X, const float *T, int B, float lam, cudaStream_t st) {
+  cudaError_t e = forward(d, X, B, d.Y, st);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(d.G, 0, sizeof(float) * kParams, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(d.loss, 0, sizeof(float), st)) != cudaSuccess) return e;
+  k_loss_grad<<<(B + 255) / 256, 256, 0, st>>>(d.Y, T, B, lam, d.dY, d.loss);
+  const unsigned rb = (unsigned)((B + 31) / 32);
+  k_back_out<<<rb, kWid, 0, st>>>(d.dY, d.H3, B, d.P, d.G, d.dZ, d.dZt);
+  k_bias_back<<<rb, kWid, 0, st>>>(d.dZ, B, d.G + ob3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int splits = B >= 2048 ? 16 : 1;
+  // dW3 = dZ3^T H2, dH2 = dZ3 W3
+  e = launch_gemm_bf16(d.dZt, d.H2t, kWid, kWid, B, splits, nullptr, 2, d.G + oW3, kWid, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_gemm_bf16(d.dZ, d.W3t, B, kWid, kWid, 1, nullptr, 0, d.dH, kWid, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  k_relu_back<<<rb, kWid, 0, st>>>(d.dH, d.H2, B, d.G + ob2, d.dZ, d.dZt, nullptr);
+  // dW2 = dZ2^T H1, dH1 = dZ2 W2
+  e = launch_gemm_bf16(d.dZt, d.H1t, kWid, kWid, B, splits, nullptr, 2, d.G + oW2, kWid, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_gemm_bf16(d.dZ, d.W2t, B, kWid, kWid, 1, nullptr, 0, d.dH, kWid, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  k_relu_back<<<rb, kWid, 0, st>>>(d.dH, d.H1, B, d.G + ob1, nullptr, nullptr, d.dZ1);
+  k_back_in<<<rb, kWid, 0, st>>>(d.dZ1, X, B, d.G);
+  return cudaGetLastError();
+}
+
+cudaError_t refresh(ExpmapDev &d, cudaStream_t st) {
+  k_refresh_bf16<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.W2t, d.W3t);
+  return cudaGetLastError();
+}
+
+constexpr float kErrWeight = 0.1f;
+constexpr char kMagic[8] = {'R', 'G', 'E', 'O', 'X', 'M', 'P', '1'};
+
+rgeo_status mlp_fail(rgeo_status s, const char *msg) {
+  set_last_error(msg);
+  return s;
+}
+
+rgeo_status mlp_cuda(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return RGEO_OK;
+  static thread_local char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return mlp_fail(e == cudaErrorMemoryAllocation ? RGEO_ENOMEM : RGEO_ECUDA, buf);
+}
+
+}  // namespace
+}  // namespace rgeo
+
+struct rgeo_expmap {
+  rgeo::ExpmapDev d;
+};
+
+extern "C" {
+
+int64_t rgeo_expmap_param_count(void) { return rgeo::kParams; }
+
+rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **out) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!out) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_create: out is NULL");
+  *out = nullptr;
+  if (max_batch < 128 || max_batch % 128 != 0 || max_batch > (1 << 20))
+    return mlp_fail(RGEO_EINVAL, "rgeo_expmap_create: max_batch must be a multiple of 128 in [128, 2^20]");
+  rgeo_expmap *x = new rgeo_expmap();
+  std::memset(&x->d, 0, sizeof(x->d));
+  ExpmapDev &d = x->d;
+  d.bmax = max_batch;
+  const size_t B = (size_t)max_batch, HW = B * kWid;
+  cudaError_t e = dalloc(&d.P, kParams);
+  if (e == cudaSuccess) e = dalloc(&d.G, kParams);
+  if (e == cudaSuccess) e = dalloc(&d.m, kParams);
+  if (e == cudaSuccess) e = dalloc(&d.v, kParams);
+  if (e == cudaSuccess) e = dalloc(&d.W2b, (size_t)kWid * kWid);
+  if (e == cudaSuccess) e = dalloc(&d.W3b, (size_t)kWid * kWid);
+  if (e == cudaSuccess) e = dalloc(&d.W2t, (size_t)kWid * kWid);
+  if (e == cudaSuccess) e = dalloc(&d.W3t, (size_t)kWid * kWid);
+  __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H3, &d.H1t, &d.H2t, &d.H3t, &d.dZ, &d.dZt};
+  for (auto b : bufs)
+    if (e == cudaSuccess) e = dalloc(b, HW);
+  if (e == cudaSuccess) e = dalloc(&d.Y, B * kOut);
+  if (e == cudaSuccess) e = dalloc(&d.dY, B * kOut);
+  if (e == cudaSuccess) e = dalloc(&d.dH, HW);
+  if (e == cudaSuccess) e = dalloc(&d.dZ1, HW);
+  if (e == cudaSuccess) e = dalloc(&d.loss, 1);
+  if (e == cudaSuccess) {
+    k_init<<<(kParams + 255) / 256, 256>>>(d.P, (unsigned long long)seed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemset(d.m, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(d.v, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = refresh(d, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(d);
+    delete x;
+    return mlp_cuda(e, "rgeo_expmap_create");
+  }
+  *out = x;
+  return RGEO_OK;
+}
+
+void rgeo_expmap_destroy(rgeo_expmap *x) {
+  if (!x) return;
+  rgeo::free_all(x->d);
+  delete x;
+}
+
+rgeo_status rgeo_expmap_forward(const rgeo_expmap *x, const float *inputs, int64_t n, float *outputs,
+                                void *cuda_stream) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!x || (n > 0 && (!inputs || !outputs)) || n < 0) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_forward: bad argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (int64_t off = 0; off < n; off += x->d.bmax) {
+    const int B = (int)std::min<int64_t>(x->d.bmax, n - off);
+    rgeo_status s = mlp_cuda(forward(x->d, inputs + off * kIn, B, outputs + off * kOut, st), "rgeo_expmap_forward");
+    if (s != RGEO_OK) return s;
+  }
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_expmap_gradients(rgeo_expmap *x, const float *inputs, const float *targets, int32_t batch,
+                                  float *grads, float *loss, void *cuda_stream) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!x || !inputs || !targets) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_gradients: NULL argument");
+  if (batch < 128 || batch % 128 != 0 || batch > x->d.bmax)
+    return mlp_fail(RGEO_EINVAL, "rgeo_expmap_gradients: batch must be a multiple of 128, at most max_batch");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  rgeo_status s = mlp_cuda(gradients(x->d, inputs, targets, batch, kErrWeight, st), "rgeo_expmap_gradients");
+  if (s != RGEO_OK) return s;
+  if (grads) s = mlp_cuda(cudaMemcpyAsync(grads, x->d.G, sizeof(float) * kParams, cudaMemcpyDeviceToDevice, st),
+                          "rgeo_expmap_gradients: copy");
+  if (s == RGEO_OK && loss)
+    s = mlp_cuda(cudaMemcpyAsync(loss, x->d.loss, sizeof(float), cudaMemcpyDeviceToDevice, st), "rgeo_expmap_gradients");
+  return s;
+}
+
+rgeo_status rgeo_expmap_train_step(rgeo_expmap *x, const float *inputs, const float *targets, int32_t batch,
+                                   float lr, float *loss, void *cuda_stream) {
+  using namespace rgeo;
+  rgeo_status s = rgeo_expmap_gradients(x, inputs, targets, batch, nullptr, loss, cuda_stream);
+  if (s != RGEO_OK) return s;
+  if (!(lr > 0.f)) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_train_step: lr must be > 0");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  x->d.step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)x->d.step), c2 = 1.f - powf(b2, (float)x->d.step);
+  k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(x->d.P, x->d.G, x->d.m, x->d.v, kParams, lr, b1, b2, 1e-8f, c1, c2);
+  s = mlp_cuda(cudaGetLastError(), "rgeo_expmap_train_step: adam");
+  if (s == RGEO_OK) s = mlp_cuda(refresh(x->d, st), "rgeo_expmap_train_step: refresh");
+  return s;
+}
+
+rgeo_status rgeo_expmap_get_params(const rgeo_expmap *x, float *host, int64_t n) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!x || !host || n != kParams) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_get_params: bad argument");
+  return mlp_cuda(cudaMemcpy(host, x->d.P, sizeof(float) * kParams, cudaMemcpyDeviceToHost), "rgeo_expmap_get_params");
+}
+
+rgeo_status rgeo_expmap_set_params(rgeo_expmap *x, const float *host, int64_t n) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!x || !host || n != kParams) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_set_params: bad argument");
+  rgeo_status s = mlp_cuda(cudaMemcpy(x->d.P, host, sizeof(float) * kParams, cudaMemcpyHostToDevice), "set_params");
+  if (s == RGEO_OK) s = mlp_cuda(refresh(x->d, 0), "rgeo_expmap_set_params: refresh");
+  if (s == RGEO_OK) s = mlp_cuda(cudaDeviceSynchronize(), "rgeo_expmap_set_params");
+  return s;
+}
+
+// Checkpoint: magic, parameter count, step, then parameters and both Adam moments.
+rgeo_status rgeo_expmap_save(const rgeo_expmap *x, const char *path) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!x || !path) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_save: NULL argument");
+  std::vector<float> buf(3 * (size_t)kParams);
+  rgeo_status s = mlp_cuda(cudaMemcpy(buf.data(), x->d.P, sizeof(float) * kParams, cudaMemcpyDeviceToHost), "save");
+  if (s == RGEO_OK) s = mlp_cuda(cudaMemcpy(buf.data() + kParams, x->d.m, sizeof(float) * kParams, cudaMemcpyDeviceToHost), "save");
+  if (s == RGEO_OK) s = mlp_cuda(cudaMemcpy(buf.data() + 2 * kParams, x->d.v, sizeof(float) * kParams, cudaMemcpyDeviceToHost), "save");
+  if (s != RGEO_OK) return s;
+  FILE *f = fopen(path, "wb");
+  if (!f) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_save: cannot open file");
+  const int64_t hdr[2] = {(int64_t)kParams, (int64_t)x->d.step};
+  bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? RGEO_OK : mlp_fail(RGEO_EINVAL, "rgeo_expmap_save: write failed");
+}
+
+rgeo_status rgeo_expmap_load(rgeo_expmap *x, const char *path) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!x || !path) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_load: NULL argument");
+  FILE *f = fopen(path, "rb");
+  if (!f) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_load: cannot open file");
+  char magic[8];
+  int64_t hdr[2];
+  std::vector<float> buf(3 * (size_t)kParams);
+  bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+            hdr[0] == kParams && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_load: not a checkpoint of this network");
+  x->d.step = hdr[1];
+  rgeo_status s = mlp_cuda(cudaMemcpy(x->d.P, buf.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice), "load");
+  if (s == RGEO_OK) s = mlp_cuda(cudaMemcpy(x->d.m, buf.data() + kParams, sizeof(float) * kParams, cudaMemcpyHostToDevice), "load");
+  if (s == RGEO_OK) s = mlp_cuda(cudaMemcpy(x->d.v, buf.data() + 2 * kParams, sizeof(float) * kParams, cudaMemcpyHostToDevice), "load");
+  if (s == RGEO_OK) s = mlp_cuda(refresh(x->d, 0), "load");
+  if (s == RGEO_OK) s = mlp_cuda(cudaDeviceSynchronize(), "rgeo_expmap_load");
+  return s;
+}
+
+rgeo_status rgeo_gemm_bf16(const void *A, const void *B, int32_t M, int32_t N, int32_t K, int32_t splits,
+                           const float *bias, int32_t mode, void *C, int32_t ldc, void *ct, int32_t ldt,
+                           void *cuda_stream) {
+  using namespace rgeo;
+  set_last_error("");
+  if (!A || !B || !C || mode < 0 || mode > 2) return mlp_fail(RGEO_EINVAL, "rgeo_gemm_bf16: bad argument");
+  cudaError_t e = launch_gemm_bf16(A, B, M, N, K, splits, bias, mode, C, ldc, ct, ldt, (cudaStream_t)cuda_stream);
+  if (e == cudaErrorInvalidValue)
+    return mlp_fail(RGEO_EINVAL,
+                    "rgeo_gemm_bf16: need M >= 1, 16 <= N <= 256, N % 16 == 0, K % 64 == 0, A and B 16-byte aligned");
+  return mlp_cuda(e, "rgeo_gemm_bf16");
+}
+
+}  // extern "C"

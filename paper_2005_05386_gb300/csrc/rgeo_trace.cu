@@ -1046,6 +1046,80 @@ __global__ void k_advance_motion(const float *motion, int K, int aniso, float *r
   }
 }
 
+// Counter-based uniform in [0, 1): SplitMix64 (Steele, Lea, Flood 2014) output for the
+// state seed + (i + 1) golden, top 24 bits.
+__device__ __forceinline__ float u01(unsigned long long seed, unsigned long long i) {
+  unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)(z >> 40) * (1.f / 16777216.f);
+}
+
+// Training segments of the learned exponential map (Eq. 3.5): sample i draws a
+// position x ~ U[-box, box]^3, a direction d uniform on S^2 and an arc length
+// s = n h with n uniform in 1..round(s_max / h); its g-unit tangent v then follows the
+// geodesic flow for n RK4 steps (dense sums) to (x_s, v_s).  Written per sample:
+//   X = (x / box, d, s / s_max)                    (the network input)
+//   T = ((x_s - x - s v) / s^2, (v_s - v) / s)     (scaled residuals of the straight line)
+template <int MK>
+__global__ void k_segments(const TraceParams P, long long n, unsigned long long seed, float box, float s_max,
+                           float *X, float *T) {
+  const int nmax = max(1, (int)roundf(s_max / P.h));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long base = (unsigned long long)i * 8ull;
+    const F3 x0 = f3(box * (2.f * u01(seed, base) - 1.f), box * (2.f * u01(seed, base + 1) - 1.f),
+                     box * (2.f * u01(seed, base + 2) - 1.f));
+    const float z = 2.f * u01(seed, base + 3) - 1.f, ph = 6.283185307179586f * u01(seed, base + 4);
+    const float rxy = sqrtf(fmaxf(0.f, 1.f - z * z));
+    const F3 d = f3(rxy * cosf(ph), rxy * sinf(ph), z);
+    const int steps = min(nmax, 1 + (int)(u01(seed, base + 5) * nmax));
+    const float s = steps * P.h;
+    F3 g = grad_f<MK>(P, P.bumps, x0);
+    const float gd = dot(g, d);
+    const F3 v0 = rsqrtf(fmaf(gd, gd, dot(d, d))) * d;
+    float xh[3] = {x0.x, x0.y, x0.z}, xl[3] = {0.f, 0.f, 0.f}, vh[3] = {v0.x, v0.y, v0.z}, vl[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < steps; ++k) {
+      const F3 x = f3(xh[0], xh[1], xh[2]), v = f3(vh[0], vh[1], vh[2]);
+      bool dummy;
+      const F3 a1 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, x, v, dummy)
+                                       : accel_graph_aniso<false>(P, P.bumps, P.K, x, v, dummy);
+      const float h = P.h, h2 = 0.5f * h;
+      const F3 v2 = axpy(h2, a1, v);
+      const F3 a2 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, axpy(h2, v, x), v2, dummy)
+                                       : accel_graph_aniso<false>(P, P.bumps, P.K, axpy(h2, v, x), v2, dummy);
+      const F3 v3 = axpy(h2, a2, v);
+      const F3 a3 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, axpy(h2, v2, x), v3, dummy)
+                                       : accel_graph_aniso<false>(P, P.bumps, P.K, axpy(h2, v2, x), v3, dummy);
+      const F3 v4 = axpy(h, a3, v);
+      const F3 a4 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, axpy(h, v3, x), v4, dummy)
+                                       : accel_graph_aniso<false>(P, P.bumps, P.K, axpy(h, v3, x), v4, dummy);
+      const float h6 = h * (1.f / 6.f);
+      const F3 dx = h6 * (v + 2.f * (v2 + v3) + v4), dv = h6 * (a1 + 2.f * (a2 + a3) + a4);
+      for (int c = 0; c < 3; c++) {
+        comp_add(xh[c], xl[c], comp(dx, c));
+        comp_add(vh[c], vl[c], comp(dv, c));
+      }
+    }
+    float *xo = X + i * 7, *to = T + i * 6;
+    xo[0] = x0.x / box;
+    xo[1] = x0.y / box;
+    xo[2] = x0.z / box;
+    xo[3] = d.x;
+    xo[4] = d.y;
+    xo[5] = d.z;
+    xo[6] = s / s_max;
+    const float is2 = 1.f / (s * s), is = 1.f / s;
+    for (int c = 0; c < 3; c++) {
+      // (x_s - x - s v) from the compensated pair: (hi - x) + lo - s v
+      const float dxs = (xh[c] - comp(x0, c)) + xl[c] - s * comp(v0, c);
+      to[c] = dxs * is2;
+      to[3 + c] = ((vh[c] - comp(v0, c)) + vl[c]) * is;
+    }
+  }
+}
+
 __global__ void k_tick(float *t, float dt) { *t += dt; }
 __global__ void k_set_time(float *t, float value) { *t = value; }
 
@@ -1293,6 +1367,20 @@ cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *
     if (e != cudaSuccess) return e;
   }
   k_tick<<<1, 1, 0, st>>>(t, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long long seed, float box, float s_max,
+                            float *X, float *T, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const long long want = (n + 127) / 128;
+  const unsigned blocks = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+  if (p.aniso) k_segments<MK_GRAPH_ANISO><<<blocks, 128, 0, st>>>(p, n, seed, box, s_max, X, T);
+  else k_segments<MK_GRAPH_ISO><<<blocks, 128, 0, st>>>(p, n, seed, box, s_max, X, T);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,215 @@
+"""The learned exponential map on the GPU: its tcgen05 GEMM, its gradients against the
+FP64 oracle's back-propagation, the integrator-generated training segments against the
+oracle's RK4, training, and checkpoints.
+
+Tolerances.  The two 256 x 256 layers take BF16 operands (unit roundoff 2^-8, so a
+rounding is off by at most 2^-9 ~ 0.2 %) with FP32 accumulation.  Five roundings stand
+between the FP32 master weights and any gradient (two weight copies, three activation
+or error tensors), so each output and gradient block is expected within about 1 % of
+the FP64 result; the tests allow 3 % normwise per block.  The GEMM itself is compared
+with an FP32 product of the same BF16 operands, where only the summation order differs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2005_05386_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rg():
+    import torch
+    import paper_2005_05386_gb300 as rg
+    torch.cuda.set_device(0)
+    return rg
+
+
+def _bf16(shape, gen, scale=1.0):
+    import torch
+    return (torch.rand(shape, generator=gen, device="cuda") * 2 - 1).mul_(scale).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 256), (300, 48, 64), (1000, 16, 1024), (129, 256, 512),
+                                   (4096, 256, 256)])
+def test_gemm_mode0_matches_fp32_product(rg, M, N, K):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
+    A, B = _bf16((M, K), g), _bf16((N, K), g)
+    bias = torch.rand(N, generator=g, device="cuda")
+    C = torch.full((M, N), float("nan"), device="cuda")
+    rg.rgeo_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, 1, bias.data_ptr(), 0, C.data_ptr(), N, None, 0)
+    rg.rgeo_sync()
+    ref = A.float() @ B.float().T + bias
+    torch.testing.assert_close(C, ref, rtol=1e-5, atol=1e-4 * K ** 0.5)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (200, 64, 128)])
+def test_gemm_mode1_relu_bf16_and_transpose(rg, M, N, K):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(11 + M)
+    A, B = _bf16((M, K), g), _bf16((N, K), g)
+    bias = torch.rand(N, generator=g, device="cuda") - 0.5
+    C = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+    Ct = torch.zeros((N, M), dtype=torch.bfloat16, device="cuda")
+    rg.rgeo_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, 1, bias.data_ptr(), 1, C.data_ptr(), N, Ct.data_ptr(), M)
+    rg.rgeo_sync()
+    ref = torch.relu(A.float() @ B.float().T + bias)
+    torch.testing.assert_close(C.float(), ref, rtol=2 ** -8, atol=1e-5)
+    assert torch.equal(Ct, C.T.contiguous())
+    assert (C.float() >= 0).all()
+
+
+@pytest.mark.parametrize("splits", [1, 4, 16])
+def test_gemm_mode2_split_k_accumulates(rg, splits):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(5 + splits)
+    M, N, K = 256, 256, 2048
+    A, B = _bf16((M, K), g), _bf16((N, K), g)
+    C0 = torch.rand((M, N), generator=g, device="cuda")
+    C = C0.clone()
+    rg.rgeo_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, splits, None, 2, C.data_ptr(), N, None, 0)
+    rg.rgeo_sync()
+    torch.testing.assert_close(C, C0 + A.float() @ B.float().T, rtol=1e-5, atol=2e-3)
+
+
+def test_gemm_rejects_bad_shapes(rg):
+    import torch
+    A = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(128, 256, device="cuda")
+    for M, N, K in [(128, 8, 64), (128, 24, 64), (128, 272, 64), (128, 16, 48), (0, 16, 64)]:
+        with pytest.raises(rg.RgeoError):
+            rg.rgeo_gemm_bf16(A.data_ptr(), A.data_ptr(), M, N, K, 1, None, 0, C.data_ptr(), 256, None, 0)
+    with pytest.raises(rg.RgeoError):  # operand not 16-byte aligned
+        rg.rgeo_gemm_bf16(A.data_ptr() + 2, A.data_ptr(), 64, 16, 64, 1, None, 0, C.data_ptr(), 256, None, 0)
+    with pytest.raises(rg.RgeoError):  # split-K needs the accumulate epilogue
+        rg.rgeo_gemm_bf16(A.data_ptr(), A.data_ptr(), 128, 16, 64, 2, None, 0, C.data_ptr(), 256, None, 0)
+
+
+def _field_metric(seed=1):
+    c, a, s = scenes.random_bumps(seed, 64)
+    return scenes.Metric(center=c, amplitude=a, sigma=s)
+
+
+def _blocks(v):
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in mlp.SHAPES])
+    return [(name, v[offs[i]:offs[i + 1]]) for i, (name, _) in enumerate(mlp.SHAPES)]
+
+
+def test_generator_matches_oracle_rk4(rg):
+    """Targets from the device integrator against the oracle's FP64 RK4 of the same segments."""
+    m = _field_metric()
+    dm = rg.Metric(m)
+    box, s_max, h = 4.0, 0.5, 0.005
+    X, T = rg.Expmap.generate(dm, 256, seed=17, box=box, s_max=s_max, h=h)
+    rg.rgeo_sync()
+    X, T = X.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64)
+    # inputs: positions in [-1, 1], unit directions, arc lengths k h / s_max with k in 1..100
+    assert np.abs(X[:, :3]).max() <= 1.0
+    np.testing.assert_allclose(np.linalg.norm(X[:, 3:6], axis=1), 1.0, atol=1e-6)
+    kf = X[:, 6] * s_max / h
+    k = np.round(kf)
+    np.testing.assert_allclose(kf, k, atol=1e-3)
+    assert k.min() >= 1 and k.max() <= 100 and len(np.unique(k)) > 50
+    R = mlp.segment_residuals(oracle.Metric.from_desc(m), X, box, s_max, h)
+    s = k * h
+    # compare unscaled residuals (x_s - x - s v, v_s - v): FP32 integration error lives there
+    Ug = np.concatenate([T[:, :3] * s[:, None] ** 2, T[:, 3:] * s[:, None]], axis=1)
+    Ur = np.concatenate([R[:, :3] * s[:, None] ** 2, R[:, 3:] * s[:, None]], axis=1)
+    err = np.abs(Ug - Ur)
+    ok = (err <= 2e-6 + 1e-4 * np.abs(Ur)).all(axis=1)
+    assert ok.mean() >= 0.99, (ok.mean(), err.max())
+    assert err.max() < 1e-3
+    assert np.abs(Ur).max() > 1e-3
+
+
+def test_forward_matches_oracle(rg):
+    import torch
+    x = rg.Expmap(max_batch=128, seed=3)
+    params = x.get_params().astype(np.float64)
+    r = np.random.default_rng(0)
+    Xh = np.concatenate([r.uniform(-1, 1, (300, 3)), r.normal(size=(300, 3)), r.uniform(0, 1, (300, 1))], axis=1)
+    Xh[:, 3:6] /= np.linalg.norm(Xh[:, 3:6], axis=1, keepdims=True)
+    Y = x.forward(torch.tensor(Xh, dtype=torch.float32, device="cuda"))  # 300 rows: three chunks, ragged tail
+    rg.rgeo_sync()
+    Y = Y.cpu().numpy()
+    Yr, _ = mlp.forward(params, Xh.astype(np.float32).astype(np.float64))
+    for o in range(7):
+        rel = np.linalg.norm(Y[:, o] - Yr[:, o]) / np.linalg.norm(Yr[:, o])
+        assert rel < 3e-2, (o, rel)
+    assert x.forward(torch.empty(0, 7, device="cuda")).shape == (0, 7)
+
+
+@pytest.mark.parametrize("batch", [256, 2048])
+def test_gradients_match_oracle(rg, batch):
+    """Back-propagation on the tensor cores against the oracle's FP64 back-propagation
+    (batch 2048 takes the split-K weight-gradient products)."""
+    dm = rg.Metric(_field_metric())
+    X, T = rg.Expmap.generate(dm, batch, seed=23)
+    x = rg.Expmap(max_batch=2048, seed=9)
+    G, L = x.gradients(X, T)
+    rg.rgeo_sync()
+    params = x.get_params().astype(np.float64)
+    Lr, Gr = mlp.loss_and_grads(params, X.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64))
+    assert abs(L.item() - Lr) <= 1e-2 * abs(Lr), (L.item(), Lr)
+    G = G.cpu().numpy().astype(np.float64)
+    for (name, gb), (_, rb) in zip(_blocks(G), _blocks(Gr)):
+        rel = np.linalg.norm(gb - rb) / np.linalg.norm(rb)
+        cos = gb @ rb / (np.linalg.norm(gb) * np.linalg.norm(rb))
+        assert rel < 3e-2 and cos > 0.999, (name, rel, cos)
+
+
+def test_gradients_reject_bad_batches(rg):
+    import torch
+    x = rg.Expmap(max_batch=256, seed=1)
+    X = torch.zeros(512, 7, device="cuda")
+    T = torch.zeros(512, 6, device="cuda")
+    for b in (0, 100, 512):
+        with pytest.raises(rg.RgeoError):
+            x.gradients(X[:b], T[:b])
+
+
+def test_training_reduces_loss_and_checkpoint_roundtrip(rg, tmp_path):
+    import torch
+    dm = rg.Metric(_field_metric())
+    X, T = rg.Expmap.generate(dm, 1 << 17, seed=31)
+    Xv, Tv = rg.Expmap.generate(dm, 4096, seed=32)
+    x = rg.Expmap(max_batch=4096, seed=2)
+
+    def holdout():
+        _, L = x.gradients(Xv, Tv)
+        return L.item()
+
+    l0 = holdout()
+    loss = torch.zeros(1, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for it in range(400):
+        idx = torch.randint(0, X.shape[0], (4096,), generator=g, device="cuda")
+        x.train_step(X[idx].contiguous(), T[idx].contiguous(), 1e-3, loss)
+    rg.rgeo_sync()
+    l1 = holdout()
+    assert np.isfinite(l1) and l1 < 0.5 * l0, (l0, l1)
+    path = str(tmp_path / "expmap.ckpt")
+    x.save(path)
+    y = rg.Expmap(max_batch=4096, seed=99)
+    assert not np.array_equal(y.get_params(), x.get_params())
+    y.load(path)
+    assert np.array_equal(y.get_params(), x.get_params())
+    Yx, Yy = x.forward(Xv), y.forward(Xv)
+    rg.rgeo_sync()
+    assert torch.equal(Yx, Yy)
+    # The Adam moments and step count travel too: one more step on the same batch moves
+    # both copies alike.  (Gradient sums use atomics, so the two steps differ in rounding
+    # only; with fresh moments every coordinate would instead move by about lr.)
+    p0 = x.get_params().astype(np.float64)
+    x.train_step(X[:4096], T[:4096], 1e-3)
+    y.train_step(X[:4096], T[:4096], 1e-3)
+    rg.rgeo_sync()
+    dx, dy = x.get_params() - p0, y.get_params() - p0
+    assert np.linalg.norm(dx - dy) <= 1e-2 * np.linalg.norm(dx), (np.linalg.norm(dx - dy), np.linalg.norm(dx))
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint")
+    with pytest.raises(rg.RgeoError):
+        y.load(str(bad))
