@@ -271,9 +271,16 @@ void rgeo_expmap_destroy(rgeo_expmap *expmap);
 /* Training segments generated by the integrator: n samples with x ~ U[-box, box]^3,
  * d uniform on S^2, s = k h with k uniform in 1..round(s_max / h), integrated by
  * RK4 at step h under the metric (graph metrics).  DEVICE inputs [n*7] =
- * (x / box, d, s / s_max), DEVICE targets [n*6] = (r_x, r_v).  Asynchronous. */
+ * (x / box, d, s / s_max), DEVICE targets [n*6] = (r_x, r_v).
+ * accel_bound > 0 restricts the samples to the far field: a candidate is kept when
+ * an upper bound on |x''| along every path of Euclidean length s from x (summed
+ * per-bump bounds on |grad f| and ||Hess f|| of Eq. 6.1 at the nearest reachable
+ * distance) is at most accel_bound, and the targets are divided by accel_bound, so
+ * |r_x| <= 1/2 and |r_v| <= 1.  Up to 4096 candidates are drawn per sample (the last
+ * is kept if none passes).  It needs isotropic bumps without affine or quadratic
+ * part.  Asynchronous. */
 rgeo_status rgeo_expmap_generate(const rgeo_metric *metric, int64_t n, uint64_t seed, float box, float s_max,
-                                 float h, float *inputs, float *targets, void *cuda_stream);
+                                 float h, float accel_bound, float *inputs, float *targets, void *cuda_stream);
 
 /* outputs [n*7] (DEVICE) for inputs [n*7] (DEVICE); any n >= 0.  Asynchronous. */
 rgeo_status rgeo_expmap_forward(const rgeo_expmap *expmap, const float *inputs, int64_t n, float *outputs,
@@ -296,6 +303,50 @@ rgeo_status rgeo_expmap_set_params(rgeo_expmap *expmap, const float *params, int
 /* Checkpoint: parameters, Adam moments and step count to / from a file. */
 rgeo_status rgeo_expmap_save(const rgeo_expmap *expmap, const char *path);
 rgeo_status rgeo_expmap_load(rgeo_expmap *expmap, const char *path);
+
+/* Tracing with surrogate jumps (Section 3, Eq. 3.5; graph metrics, RK4).
+ * As rgeo_trace, except that a ray inside the bumps' supports may replace k RK4
+ * steps (k_min <= k, k h <= s_max) by one evaluation of the trained network:
+ *   x <- x + s v + s^2 r_x,   v <- v + s r_v,   s = k h.
+ * A jump is attempted only where it cannot reach the scene: g = I + grad f grad f^T
+ * >= I (Eq. 5.2) bounds the Euclidean length of a geodesic arc by its g-length s,
+ * so the jump is queued when the scene's safe distance at x exceeds 1.01 s + 1e-4,
+ * |x_i| <= box, and the step budget allows k steps.  The network evaluates the
+ * queue in batches on the tensor cores; a jump is taken when its predicted error
+ * satisfies exp(output 6) <= tau^2 (tau = 0 takes none), otherwise the ray
+ * integrates those k steps by RK4 before it may try again.  With accel_bound > 0
+ * the jump must also lie in the far field of rgeo_expmap_generate (k is halved up
+ * to twice to find such a jump) and the network's outputs are multiplied by
+ * accel_bound; tau is then in units of accel_bound.  Rays that found no
+ * certified jump retry after cool_check steps.  steps[p] counts a jump as its k
+ * steps.  Rays advance in rounds; each round ends with a host wait on the stream,
+ * so this call returns when the image is complete (it is not graph-capturable).
+ * The last round (max_rounds, or 0 for max_steps / k_min + 2) takes no jumps.
+ * stats may be NULL.  Errors: as rgeo_trace, plus RGEO_EINVAL for a metric that
+ * is not a graph metric, an integrator other than RK4, or bad surrogate values. */
+typedef struct {
+  const rgeo_expmap *expmap; /* trained network (its max_batch is the inference chunk) */
+  float box;                 /* input scale of positions; jumps only where |x_i| <= box */
+  float s_max;               /* input scale of arc length; longest jump */
+  float tau;                 /* threshold on the predicted root-sum-square error of (r_x, r_v) */
+  int32_t k_min;             /* shortest jump in steps, >= 1 */
+  int32_t cool_check;        /* steps between attempts where no jump is certified, >= 1 */
+  int32_t max_rounds;        /* 0: max_steps / k_min + 2 */
+  float accel_bound;         /* > 0: far-field domain, as in rgeo_expmap_generate; 0: none */
+  int32_t reserved;          /* must be zero */
+} rgeo_surrogate;
+
+typedef struct {
+  int64_t jumps_accepted;
+  int64_t jumps_rejected;
+  int32_t rounds;
+  int32_t reserved;
+} rgeo_surrogate_stats;
+
+rgeo_status rgeo_trace_surrogate(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                                 int32_t width, int32_t height, float h, int32_t max_steps, int32_t shading,
+                                 uint32_t flags, const rgeo_surrogate *surrogate, const rgeo_outputs *out,
+                                 rgeo_surrogate_stats *stats, void *cuda_stream);
 
 /* The tensor-core GEMM of the surrogate, C = A B^T (+ bias), for testing and
  * measurement: A DEVICE bf16 [M x K] row-major, B DEVICE bf16 [N x K] row-major,

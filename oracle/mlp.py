@@ -11,7 +11,9 @@ Loss: mean over the batch and the six residual outputs of the squared error, plu
 lam times the mean squared error of output 6 against log(sum of the six squared
 errors + 1e-6), that target being held fixed (not differentiated).
 
-Pinned by central finite differences of the loss (tests/test_oracle_mlp.py).
+Pinned by central finite differences of the loss, straight-line and Dormand-Prince
+cases of the residuals, and the far-field bound against accelerations sampled along
+integrated geodesics (tests/test_oracle_mlp.py).
 """
 from __future__ import annotations
 
@@ -95,6 +97,31 @@ def loss_and_grads(params, X, T, lam=0.1):
     g["W1"] = dZ1.T @ X
     g["b1"] = dZ1.sum(axis=0)
     return L, pack(g)
+
+
+def far_field_bound(center, amplitude, sigma, cutoff, x, s):
+    """Upper bound on |x''| (Eq. 5.4) along every path of Euclidean length <= s from x,
+    for a g-unit tangent, over isotropic bumps (Eq. 6.1) truncated at cutoff sigma.
+
+    |x''| = |v^T Hess f v| t / (1 + t^2), t = |grad f|, |v| <= 1 (g >= I), and
+    t / (1 + t^2) <= min(t, 1/2).  For one bump at distance r, with u = r^2 / sigma^2:
+    |grad f_k| = |a| q r e^{-u/2}, ||Hess f_k|| <= |a| q (1 + u) e^{-u/2}; both decrease
+    in r for u >= 1, so each is taken at u = max(rho^2 q, 1), rho = max(0, |x - c| - s).
+    Bumps whose support the path cannot reach (rho >= cutoff sigma) are left out.
+    """
+    c = np.asarray(center, np.float64).reshape(-1, 3)
+    a = np.abs(np.asarray(amplitude, np.float64).reshape(-1))
+    sg = np.asarray(sigma, np.float64).reshape(-1, 3)[:, 0]
+    q = 1.0 / sg ** 2
+    rho = np.maximum(np.linalg.norm(np.asarray(x, np.float64) - c, axis=1) - s, 0.0)
+    reach = a > 0
+    if cutoff > 0:
+        reach &= rho < cutoff * sg
+    u = np.maximum(q * rho ** 2, 1.0)
+    e = a * q * np.exp(-u / 2)
+    Gb = (e * np.sqrt(u / q))[reach].sum()
+    Hb = (e * (1 + u))[reach].sum()
+    return float(Hb * min(Gb, 0.5))
 
 
 def segment_residuals(metric, X, box, s_max, h):

@@ -38,7 +38,7 @@ EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_me
            "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance", "rgeo_expmap_param_count",
            "rgeo_expmap_create", "rgeo_expmap_destroy", "rgeo_expmap_generate", "rgeo_expmap_forward",
            "rgeo_expmap_gradients", "rgeo_expmap_train_step", "rgeo_expmap_get_params", "rgeo_expmap_set_params",
-           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16")
+           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -69,6 +69,17 @@ class rgeo_tuning(ctypes.Structure):
 class rgeo_outputs(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("hit", ctypes.c_void_p), ("steps", ctypes.c_void_p),
                 ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p), ("bump_evals", ctypes.c_void_p)]
+
+
+class rgeo_surrogate(ctypes.Structure):
+    _fields_ = [("expmap", ctypes.c_void_p), ("box", ctypes.c_float), ("s_max", ctypes.c_float),
+                ("tau", ctypes.c_float), ("k_min", ctypes.c_int32), ("cool_check", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("accel_bound", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+class rgeo_surrogate_stats(ctypes.Structure):
+    _fields_ = [("jumps_accepted", ctypes.c_int64), ("jumps_rejected", ctypes.c_int64), ("rounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class rgeo_instance(ctypes.Structure):
@@ -123,7 +134,7 @@ def library() -> ctypes.CDLL:
     L.rgeo_expmap_destroy.restype = None
     L.rgeo_expmap_destroy.argtypes = [vp]
     L.rgeo_expmap_generate.restype = i32
-    L.rgeo_expmap_generate.argtypes = [vp, i64, u64, f32, f32, f32, vp, vp, vp]
+    L.rgeo_expmap_generate.argtypes = [vp, i64, u64, f32, f32, f32, f32, vp, vp, vp]
     L.rgeo_expmap_forward.restype = i32
     L.rgeo_expmap_forward.argtypes = [vp, vp, i64, vp, vp]
     L.rgeo_expmap_gradients.restype = i32
@@ -138,6 +149,10 @@ def library() -> ctypes.CDLL:
     L.rgeo_expmap_save.argtypes = [vp, ctypes.c_char_p]
     L.rgeo_expmap_load.restype = i32
     L.rgeo_expmap_load.argtypes = [vp, ctypes.c_char_p]
+    L.rgeo_trace_surrogate.restype = i32
+    L.rgeo_trace_surrogate.argtypes = [vp, vp, ctypes.POINTER(rgeo_camera), i32, i32, f32, i32, i32, ctypes.c_uint32,
+                                       ctypes.POINTER(rgeo_surrogate), ctypes.POINTER(rgeo_outputs),
+                                       ctypes.POINTER(rgeo_surrogate_stats), vp]
     L.rgeo_gemm_bf16.restype = i32
     L.rgeo_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp]
     L.rgeo_batch_create.restype = i32
@@ -279,6 +294,25 @@ def rgeo_metric_advance(metric: int, dt: float, stream=None):
     _check(library().rgeo_metric_advance(metric, dt, _stream_handle(stream)), "rgeo_metric_advance")
 
 
+def trace_surrogate(work: scenes.Workload, expmap: "Expmap", tau: float, box: float = 4.0, s_max: float = 0.5,
+                    k_min: int = 20, cool_check: int = 16, max_rounds: int = 0, accel_bound: float = 0.0,
+                    metric: "Metric" = None, scene: "Scene" = None, out=None, stream=None, flags: int = 0):
+    """Trace a workload with surrogate jumps (RK4 only; returns when the image is done).
+    Returns (outputs, stats dict)."""
+    metric = metric or Metric(work.metric)
+    scene = scene or Scene(work.scene)
+    if out is None:
+        out = alloc_outputs(work.n_pixels, drift=bool(flags & RGEO_FLAG_ENERGY_DIAG))
+    sur = rgeo_surrogate(expmap.handle, box, s_max, tau, k_min, cool_check, max_rounds, accel_bound)
+    st = rgeo_surrogate_stats()
+    _check(library().rgeo_trace_surrogate(metric.handle, scene.handle, ctypes.byref(camera_struct(work.camera)),
+                                          work.width, work.height, work.h, work.max_steps, work.shading, flags,
+                                          ctypes.byref(sur), ctypes.byref(outputs_struct(out)), ctypes.byref(st),
+                                          _stream_handle(stream)), "rgeo_trace_surrogate")
+    out["_handles"] = (metric, scene)
+    return out, dict(accepted=st.jumps_accepted, rejected=st.jumps_rejected, rounds=st.rounds)
+
+
 def rgeo_gemm_bf16(A, B, M, N, K, splits, bias, mode, C, ldc, ct, ldt, stream=None):
     """Pointers are device addresses (ints) or None."""
     _check(library().rgeo_gemm_bf16(A, B, M, N, K, splits, bias, mode, C, ldc, ct, ldt, _stream_handle(stream)),
@@ -308,13 +342,14 @@ class Expmap:
 
     @staticmethod
     def generate(metric: "Metric", n: int, seed: int, box: float = 4.0, s_max: float = 0.5, h: float = 0.005,
-                 stream=None):
-        """(inputs [n, 7], targets [n, 6]) device tensors of integrator-generated segments."""
+                 accel_bound: float = 0.0, stream=None):
+        """(inputs [n, 7], targets [n, 6]) device tensors of integrator-generated segments
+        (far-field segments with targets divided by accel_bound when it is > 0)."""
         import torch
         X = torch.empty(n, 7, dtype=torch.float32, device="cuda")
         T = torch.empty(n, 6, dtype=torch.float32, device="cuda")
-        _check(library().rgeo_expmap_generate(metric.handle, n, seed, box, s_max, h, X.data_ptr(), T.data_ptr(),
-                                              _stream_handle(stream)), "rgeo_expmap_generate")
+        _check(library().rgeo_expmap_generate(metric.handle, n, seed, box, s_max, h, accel_bound, X.data_ptr(),
+                                              T.data_ptr(), _stream_handle(stream)), "rgeo_expmap_generate")
         return X, T
 
     def forward(self, X, out=None, stream=None):
@@ -409,7 +444,7 @@ class Metric:
         self.handle = rgeo_metric_create(desc)
 
     def close(self):
-        if self.handle:
+        if getattr(self, "handle", None):
             rgeo_metric_destroy(self.handle)
             self.handle = None
 
@@ -423,7 +458,7 @@ class Scene:
         self.handle = rgeo_scene_create(s.spheres, s.verts, s.tris, s.albedo)
 
     def close(self):
-        if self.handle:
+        if getattr(self, "handle", None):
             rgeo_scene_destroy(self.handle)
             self.handle = None
 
@@ -471,7 +506,7 @@ class Batch:
         rgeo_batch_launch(self.handle, stream)
 
     def close(self):
-        if self.handle:
+        if getattr(self, "handle", None):
             rgeo_batch_destroy(self.handle)
             self.handle = None
 

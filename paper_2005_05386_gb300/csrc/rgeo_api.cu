@@ -565,11 +565,15 @@ rgeo_status rgeo_metric_advance(rgeo_metric *m, float dt, void *cuda_stream) {
 }
 
 rgeo_status rgeo_expmap_generate(const rgeo_metric *metric, int64_t n, uint64_t seed, float box, float s_max,
-                                 float h, float *inputs, float *targets, void *cuda_stream) {
+                                 float h, float accel_bound, float *inputs, float *targets, void *cuda_stream) {
   g_last_error.clear();
   if (!metric || n < 0 || (n > 0 && (!inputs || !targets)))
     return fail(RGEO_EINVAL, "rgeo_expmap_generate: bad argument");
   if (metric->d.kind != RGEO_METRIC_GRAPH_BUMPS) return fail(RGEO_EINVAL, "rgeo_expmap_generate: graph metrics only");
+  if (!std::isfinite(accel_bound) || accel_bound < 0.f)
+    return fail(RGEO_EINVAL, "rgeo_expmap_generate: accel_bound must be finite and >= 0");
+  if (accel_bound > 0.f && (metric->d.aniso || metric->d.has_affine || metric->d.has_quad))
+    return fail(RGEO_EINVAL, "rgeo_expmap_generate: a far-field bound needs isotropic bumps without polynomial part");
   if (!(box > 0.f) || !(s_max > 0.f) || !(h > 0.f) || !std::isfinite(box) || !std::isfinite(s_max) ||
       !std::isfinite(h) || s_max < h)
     return fail(RGEO_EINVAL, "rgeo_expmap_generate: need finite box > 0, h > 0, s_max >= h");
@@ -585,8 +589,95 @@ rgeo_status rgeo_expmap_generate(const rgeo_metric *metric, int64_t n, uint64_t 
   p.has_affine = m.has_affine;
   p.has_quad = m.has_quad;
   p.h = h;
-  RGEO_CUDA(rgeo::launch_segments(p, n, seed, box, s_max, inputs, targets, (cudaStream_t)cuda_stream),
+  RGEO_CUDA(rgeo::launch_segments(p, n, seed, box, s_max, accel_bound, inputs, targets, (cudaStream_t)cuda_stream),
             "rgeo_expmap_generate");
+  return RGEO_OK;
+}
+
+
+rgeo_status rgeo_trace_surrogate(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                                 int32_t width, int32_t height, float h, int32_t max_steps, int32_t shading,
+                                 uint32_t flags, const rgeo_surrogate *sur, const rgeo_outputs *out,
+                                 rgeo_surrogate_stats *stats, void *cuda_stream) {
+  g_last_error.clear();
+  rgeo_status s = validate_trace(metric, scene, camera, width, height, h, max_steps, RGEO_RK4, shading, flags, out);
+  if (s != RGEO_OK) return s;
+  if (metric->d.kind != RGEO_METRIC_GRAPH_BUMPS)
+    return fail(RGEO_EINVAL, "rgeo_trace_surrogate: graph metrics only");
+  if (sur && (!std::isfinite(sur->accel_bound) || sur->accel_bound < 0.f))
+    return fail(RGEO_EINVAL, "rgeo_trace_surrogate: accel_bound must be finite and >= 0");
+  if (sur && sur->accel_bound > 0.f && (metric->d.aniso || metric->d.has_affine || metric->d.has_quad))
+    return fail(RGEO_EINVAL, "rgeo_trace_surrogate: a far-field bound needs isotropic bumps without polynomial part");
+  if (!sur || !sur->expmap) return fail(RGEO_EINVAL, "rgeo_trace_surrogate: NULL surrogate or network");
+  if (!(sur->box > 0.f) || !std::isfinite(sur->box) || !(sur->s_max >= h) || !std::isfinite(sur->s_max) ||
+      !(sur->tau >= 0.f) || !std::isfinite(sur->tau) || sur->k_min < 1 || sur->cool_check < 1 || sur->max_rounds < 0 ||
+      sur->reserved != 0)
+    return fail(RGEO_EINVAL,
+                "rgeo_trace_surrogate: need finite box > 0, s_max >= h, tau >= 0, k_min >= 1, cool_check >= 1, "
+                "max_rounds >= 0, zero reserved fields");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  rgeo::TraceParams p = make_params(metric, scene, camera, width, height, h, max_steps, RGEO_RK4, shading, flags, out);
+  const size_t N = (size_t)width * height;
+  // one device block: state 14 N floats, steps, cool, two queues, jump_k (N ints each),
+  // X and Y (7 N floats each), the work counter, the queue length and two statistics
+  const size_t words = 14 * N + 5 * N + 14 * N;
+  char *buf = nullptr;
+  RGEO_CUDA(cudaMallocAsync((void **)&buf, words * 4 + 64, st), "rgeo_trace_surrogate: state");
+  float *fw = (float *)buf;
+  rgeo::WaveArgs w;
+  std::memset(&w, 0, sizeof(w));
+  w.st = fw;
+  w.steps = (int32_t *)(fw + 14 * N);
+  w.cool = w.steps + N;
+  int32_t *qa = w.cool + N, *qb = qa + N;
+  w.jump_k = qb + N;
+  w.X = (float *)(w.jump_k + N);
+  float *Y = w.X + 7 * N;
+  w.Y = Y;
+  uint32_t *counter = (uint32_t *)(Y + 7 * N);
+  w.n_queue = counter + 1;
+  w.stats = (unsigned long long *)(buf + words * 4 + 16);
+  w.box = sur->box;
+  w.s_max = sur->s_max;
+  w.log_tau2 = sur->tau > 0.f ? 2.f * std::log(sur->tau) : -INFINITY;
+  w.cool_check = sur->cool_check;
+  w.accel_bound = sur->accel_bound;
+  w.N = (long long)N;
+  const long long natural = (long long)max_steps / sur->k_min + 2;
+  const long long max_rounds = sur->max_rounds > 0 ? sur->max_rounds : natural;
+  p.counter = counter;
+  cudaError_t e = cudaMemsetAsync(w.stats, 0, 16, st);
+  uint32_t n_in = p.n_items, nq = 0;
+  int rounds = 0;
+  for (long long round = 0; e == cudaSuccess; ++round) {
+    w.first = round == 0;
+    w.list_in = qa;
+    w.queue = qb;
+    w.k_min = round + 1 >= max_rounds ? 0x7fffffff : sur->k_min;
+    p.n_items = n_in;
+    if ((e = cudaMemsetAsync(counter, 0, 8, st)) != cudaSuccess) break;
+    if ((e = rgeo::launch_wave_trace(p, w, st)) != cudaSuccess) break;
+    ++rounds;
+    if ((e = cudaMemcpyAsync(&nq, w.n_queue, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    if (nq == 0) break;
+    if ((e = rgeo::expmap_infer(sur->expmap, w.X, nq, Y, st)) != cudaSuccess) break;
+    if ((e = rgeo::launch_wave_apply(w, nq, h, st)) != cudaSuccess) break;
+    std::swap(qa, qb);
+    n_in = nq;
+  }
+  unsigned long long hs[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs, w.stats, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaError_t e2 = cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "rgeo_trace_surrogate");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rgeo_trace_surrogate: free");
+  if (stats) {
+    stats->jumps_accepted = (int64_t)hs[0];
+    stats->jumps_rejected = (int64_t)hs[1];
+    stats->rounds = rounds;
+    stats->reserved = 0;
+  }
   return RGEO_OK;
 }
 

@@ -119,6 +119,26 @@ struct TraceParams {
   int rays_per_thread;  // 1, or 2 (isotropic graph metric only)
 };
 
+// State of the surrogate tracer: per-ray SoA over the N = W * H pixels, the queue of
+// rays waiting for a surrogate jump, and the network's inputs and outputs per slot.
+struct WaveArgs {
+  float *st;            // [14][N]: xh[3], xl[3], vh[3], vl[3], dleft, e0m1
+  int32_t *steps;       // [N] equivalent RK4 steps taken
+  int32_t *cool;        // [N] RK4 steps to take before the next jump attempt
+  const int32_t *list_in;  // rays advanced this round (round > 0)
+  int first;            // round 0: rays start at the camera
+  int32_t *queue;       // [N] pixels queued for a jump, by slot
+  uint32_t *n_queue;    // queue length
+  int32_t *jump_k;      // [N] jump length in steps, by slot
+  float *X;             // [N][7] network inputs, by slot
+  const float *Y;       // [N][7] network outputs, by slot
+  unsigned long long *stats;  // [2]: accepted, rejected jumps
+  float box, s_max, log_tau2;
+  float accel_bound;    // > 0: jumps only where the far-field bound holds; outputs scaled by it
+  int k_min, cool_check;
+  long long N;
+};
+
 // Process-wide launch tuning (set by rgeo_set_tuning, read at every trace).
 struct Tuning {
   int rays_per_thread = 1;  // measured faster on GB300 at 64 bumps (occupancy beats shared traffic)
@@ -167,11 +187,17 @@ cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *
                                   float dt, cudaStream_t st);
 cudaError_t launch_set_time(float *t, float value, cudaStream_t st);
 cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long long seed, float box, float s_max,
-                            float *X, float *T, cudaStream_t st);
+                            float accel_bound, float *X, float *T, cudaStream_t st);
+// Surrogate tracer: one round of RK4 until each ray finishes or queues a jump, and
+// the application of the network's jumps to the queued rays.
+cudaError_t launch_wave_trace(const TraceParams &p, const WaveArgs &w, cudaStream_t st);
+cudaError_t launch_wave_apply(const WaveArgs &w, unsigned n, float h, cudaStream_t st);
 // rgeo_mlp.cu
 cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits, const float *bias,
                              int mode, void *C, int ldc, void *ct, int ldt, cudaStream_t st);
 cudaError_t read_and_clear_mlp_error(unsigned *word);
+// Surrogate forward pass over n rows of 7 inputs into n rows of 7 outputs (stream-ordered).
+cudaError_t expmap_infer(const rgeo_expmap *x, const float *X, long long n, float *Y, cudaStream_t st);
 cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
 cudaError_t run_ffma_probe(int mode, float *tflops, float *ms);
 

@@ -249,7 +249,8 @@ constexpr int oW1 = 0, ob1 = oW1 + kWid * kIn, oW2 = ob1 + kWid, ob2 = oW2 + kWi
               ob3 = oW3 + kWid * kWid, oW4 = ob3 + kWid, ob4 = oW4 + kOut * kWid, kParams = ob4 + kOut;
 
 // Layer 1 in FP32 (K = 7 is too small for the tensor cores): H1 = relu(X W1^T + b1),
-// written as bf16 rows and as the transposed bf16 copy used by the weight gradient.
+// written as bf16 rows and (when H1t is set) as the transposed bf16 copy used by the
+// weight gradient.
 __global__ void k_layer_in(const float *__restrict__ X, int B, const float *__restrict__ P,
                            __nv_bfloat16 *H1, __nv_bfloat16 *H1t) {
   const int b = blockIdx.x;
@@ -261,7 +262,7 @@ __global__ void k_layer_in(const float *__restrict__ X, int B, const float *__re
   for (int k = 0; k < kIn; ++k) z = fmaf(P[oW1 + j * kIn + k], xs[k], z);
   const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(z, 0.f));
   H1[(size_t)b * kWid + j] = h;
-  H1t[(size_t)j * B + b] = h;
+  if (H1t) H1t[(size_t)j * B + b] = h;
 }
 
 // Layer 4 in FP32 (N = 7): Y = H3 W4^T + b4.  One warp per row.
@@ -479,13 +480,16 @@ void free_all(ExpmapDev &d) {
   for (void *q : ptrs) cudaFree(q);
 }
 
-cudaError_t forward(const ExpmapDev &d, const float *X, int B, float *Y, cudaStream_t st) {
-  k_layer_in<<<B, kWid, 0, st>>>(X, B, d.P, d.H1, d.H1t);
+// Forward pass over B rows.  The transposed activations are written only for training.
+cudaError_t forward(const ExpmapDev &d, const float *X, int B, float *Y, cudaStream_t st, bool transposes = true) {
+  k_layer_in<<<B, kWid, 0, st>>>(X, B, d.P, d.H1, transposes ? d.H1t : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_gemm_bf16(d.H1, d.W2b, B, kWid, kWid, 1, d.P + ob2, 1, d.H2, kWid, d.H2t, B, st);
+  e = launch_gemm_bf16(d.H1, d.W2b, B, kWid, kWid, 1, d.P + ob2, 1, d.H2, kWid, transposes ? d.H2t : nullptr, B,
+                       st);
   if (e != cudaSuccess) return e;
-  e = launch_gemm_bf16(d.H2, d.W3b, B, kWid, kWid, 1, d.P + ob3, 1, d.H3, kWid, d.H3t, B, st);
+  e = launch_gemm_bf16(d.H2, d.W3b, B, kWid, kWid, 1, d.P + ob3, 1, d.H3, kWid, transposes ? d.H3t : nullptr, B,
+                       st);
   if (e != cudaSuccess) return e;
   k_layer_out<<<(B + 7) / 8, 256, 0, st>>>(d.H3, B, d.P, Y);
   return cudaGetLastError();
@@ -545,6 +549,18 @@ rgeo_status mlp_cuda(cudaError_t e, const char *what) {
 struct rgeo_expmap {
   rgeo::ExpmapDev d;
 };
+
+namespace rgeo {
+// Inference over n rows in chunks of max_batch (no transposed copies, no host sync).
+cudaError_t expmap_infer(const rgeo_expmap *x, const float *X, long long n, float *Y, cudaStream_t st) {
+  for (long long off = 0; off < n; off += x->d.bmax) {
+    const int B = (int)std::min<long long>(x->d.bmax, n - off);
+    cudaError_t e = forward(x->d, X + off * kIn, B, Y + off * kOut, st, false);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+}  // namespace rgeo
 
 extern "C" {
 
@@ -609,7 +625,8 @@ rgeo_status rgeo_expmap_forward(const rgeo_expmap *x, const float *inputs, int64
   cudaStream_t st = (cudaStream_t)cuda_stream;
   for (int64_t off = 0; off < n; off += x->d.bmax) {
     const int B = (int)std::min<int64_t>(x->d.bmax, n - off);
-    rgeo_status s = mlp_cuda(forward(x->d, inputs + off * kIn, B, outputs + off * kOut, st), "rgeo_expmap_forward");
+    rgeo_status s =
+        mlp_cuda(forward(x->d, inputs + off * kIn, B, outputs + off * kOut, st, false), "rgeo_expmap_forward");
     if (s != RGEO_OK) return s;
   }
   return RGEO_OK;

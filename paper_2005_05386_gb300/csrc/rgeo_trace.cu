@@ -28,6 +28,7 @@ constexpr int MK_GRAPH_ISO = 0;
 constexpr int MK_GRAPH_ANISO = 1;
 constexpr int MK_TWIST = 2;
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kSegTries = 4096;  // candidates per training segment under a far-field bound
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -198,6 +199,30 @@ __device__ __forceinline__ IsoBump iso_bump(const float4 *sb, int k) {
     b.R2 = p1.w; b.qn2 = p2.y; b.la = p2.w; b.qs = p3.y; b.q = p3.w;
   }
   return b;
+}
+
+// Far-field certificate: an upper bound on |x''| (Eq. 5.4) along every path of
+// Euclidean length <= s from x, for a g-unit tangent (|v| <= 1 because g >= I).
+// |x''| = |v^T Hess f v| t / (1 + t^2) with t = |grad f|, and t / (1 + t^2) <=
+// min(t, 1/2).  Per bump of Eq. 6.1 at distance r, |grad f_k| = |a| q r e^{-q r^2/2}
+// and ||Hess f_k|| <= |a| q (1 + q r^2) e^{-q r^2/2}; both are non-increasing in r
+// once q r^2 >= 1, so they are taken at r^2 = max(rho^2, 1/q) with rho = max(0,
+// |x - c| - s), the nearest the path can come.  A bump whose truncated support the
+// path cannot reach adds nothing.  Isotropic bumps without polynomial part only.
+__device__ float far_field_bound(const float4 *sb, int K, F3 x, float s) {
+  float Hb = 0.f, Gb = 0.f;
+  for (int k = 0; k < K; ++k) {
+    const IsoBump b = iso_bump(sb, k);
+    if (b.R2 < 0.f) continue;  // inert (a = 0)
+    const F3 d = x - b.c;
+    const float rho = fmaxf(sqrtf(dot(d, d)) - s, 0.f);
+    if (rho * rho >= b.R2) continue;
+    const float u = fmaxf(b.q * rho * rho, 1.f);
+    const float e = b.q * exp2f(fmaf(-0.5f * kLog2e, u, b.la));  // |a| q e^{-u/2}
+    Gb = fmaf(e, sqrtf(u / b.q), Gb);
+    Hb = fmaf(e, 1.f + u, Hb);
+  }
+  return Hb * fminf(Gb, 0.5f) * 1.0001f;  // slack for float32 rounding
 }
 
 template <bool INSIDE>
@@ -1018,6 +1043,219 @@ __global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restri
 // Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
 // table; t is read from and advanced in device memory so that a captured graph
 // animates without host input.  motion = [K*3 c0 | K*3 A | K f | K phi].
+// ------------------------------------------------------- surrogate tracer
+// Rays advance in rounds.  In a round each ray runs RK4 steps (as k_trace) until it
+// finishes or reaches a point from which a surrogate jump is allowed; it then saves
+// its state and joins the jump queue.  Between rounds the network evaluates the
+// queue (tensor cores) and k_wave_apply takes each jump whose predicted error is
+// within the threshold; a rejected ray integrates that segment by RK4 instead.
+
+__device__ __forceinline__ void wave_store(const WaveArgs &W, const Ray &r, int cool) {
+  const size_t N = (size_t)W.N, p = (size_t)r.pix;
+  for (int c = 0; c < 3; c++) {
+    W.st[c * N + p] = r.xh[c];
+    W.st[(3 + c) * N + p] = r.xl[c];
+    W.st[(6 + c) * N + p] = r.vh[c];
+    W.st[(9 + c) * N + p] = r.vl[c];
+  }
+  W.st[12 * N + p] = r.dleft;
+  W.st[13 * N + p] = r.e0m1;
+  W.steps[p] = r.steps;
+  W.cool[p] = cool;
+}
+
+__device__ __forceinline__ void wave_load(const WaveArgs &W, int pix, Ray &r, int &cool) {
+  const size_t N = (size_t)W.N, p = (size_t)pix;
+  for (int c = 0; c < 3; c++) {
+    r.xh[c] = W.st[c * N + p];
+    r.xl[c] = W.st[(3 + c) * N + p];
+    r.vh[c] = W.st[(6 + c) * N + p];
+    r.vl[c] = W.st[(9 + c) * N + p];
+  }
+  r.dleft = W.st[12 * N + p];
+  r.e0m1 = W.st[13 * N + p];
+  r.steps = W.steps[p];
+  r.pix = pix;
+  cool = W.cool[p];
+}
+
+// As refill, but a ray of a later round resumes from its saved state.
+template <int MK>
+__device__ __forceinline__ void wave_refill(const TraceParams &P, const WaveArgs &W, const float4 *sb,
+                                            bool &active, bool &drained, Ray &r, int &cool) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+  if (!need) return;
+  const int leader = __ffs(need) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(P.counter, (unsigned)__popc(need));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (base + (unsigned)__popc(need) >= P.n_items) drained = true;
+  if (!active && ((need >> lane) & 1u)) {
+    const unsigned item = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+    if (item < P.n_items) {
+      if (W.first) {
+        const unsigned tile = item >> 5, sub = item & 31u;
+        const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
+        const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
+        if (px < P.W && py < P.H) {
+          init_ray<MK>(P, sb, py * P.W + px, r);
+          cool = 0;
+          active = true;
+        }
+      } else {
+        wave_load(W, W.list_in[item], r, cool);
+        active = true;
+      }
+    }
+  }
+}
+
+// Queue a jump of k steps (arc length s = k h) when it is certified free of the
+// scene: g = I + grad f grad f^T >= I (Eq. 5.2), so a geodesic of g-length s with a
+// g-unit tangent stays within Euclidean distance s of x, and the safe distance at x
+// bounds the distance to every scene point from below.  The network was trained on
+// |x_i| <= box; k is at least k_min and fits the step budget.  Under a far-field
+// bound, k is halved (up to twice) until the bound holds over the jump.
+template <int MK>
+__device__ __forceinline__ bool wave_try_queue(const TraceParams &P, const WaveArgs &W, const float4 *sb, Ray &r,
+                                               int &cool) {
+  const F3 x = xhi(r), v = vhi(r);
+  int k = -1;
+  if (fabsf(x.x) <= W.box && fabsf(x.y) <= W.box && fabsf(x.z) <= W.box) {
+    const float reach = fminf(W.s_max, (safe_distance(P, x) - 1e-4f) * (1.f / 1.01f));
+    if (reach > 0.f) k = min((int)(reach / P.h), P.max_steps - r.steps);
+  }
+  if (MK == MK_GRAPH_ISO && W.accel_bound > 0.f) {
+    bool ok = false;
+    for (int t = 0; t < 3 && k >= W.k_min && !ok; ++t) {
+      ok = far_field_bound(sb, P.K, x, k * P.h) <= W.accel_bound;
+      if (!ok) k >>= 1;
+    }
+    if (!ok) k = -1;
+  }
+  if (k < W.k_min) {
+    cool = W.cool_check;
+    return false;
+  }
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned m = __activemask();
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(W.n_queue, (unsigned)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  const unsigned slot = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+  W.queue[slot] = r.pix;
+  W.jump_k[slot] = k;
+  const float inv = rsqrtf(dot(v, v));
+  float *xi = W.X + (size_t)slot * 7;
+  const float ib = 1.f / W.box;
+  xi[0] = x.x * ib;
+  xi[1] = x.y * ib;
+  xi[2] = x.z * ib;
+  xi[3] = v.x * inv;
+  xi[4] = v.y * inv;
+  xi[5] = v.z * inv;
+  xi[6] = (k * P.h) / W.s_max;
+  wave_store(W, r, 0);
+  return true;
+}
+
+// One round of the surrogate tracer (graph metrics, RK4).
+template <int MK>
+__global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const WaveArgs W) {
+  extern __shared__ float4 smem[];
+  const int nb4 = stage_shared<MK>(P, smem);
+  const float4 *sb = smem;
+  const float4 *ss = smem + nb4;
+  const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned long long evals = 0;
+  bool active = false, drained = false;
+  Ray r;
+  int cool = 0;
+  for (;;) {
+    wave_refill<MK>(P, W, sb, active, drained, r, cool);
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
+    if (!amask) {
+      if (drained) break;
+      continue;
+    }
+    if (!active) continue;
+    bool inside = true;
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask, &evals}, xhi(r), vhi(r), inside);
+    bool queued = false;
+    if (inside && r.steps < P.max_steps) {
+      if (cool <= 0) queued = wave_try_queue<MK>(P, W, sb, r, cool);
+      else --cool;
+    }
+    const unsigned qmask = __ballot_sync(amask, !queued);
+    if (queued) {
+      active = false;
+      continue;
+    }
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, qmask, &evals}, r, a1, inside);
+    const unsigned smask = __ballot_sync(qmask, go);
+    if (!go) {
+      active = false;
+      continue;
+    }
+    F3 dx, dvel;
+    step_increments<MK, 0>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
+    active = post_step<MK>(P, sb, ss, r, dx, dvel);
+  }
+  if (P.bump_evals) {
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
+    if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
+  }
+}
+
+// The network's jump for queue slot i: x_s = x + s v + s^2 r_x, v_s = v + s r_v
+// (scaled residuals of Eq. 3.5's exp map), taken when the predicted log squared
+// error (output 6) is at most log tau^2; otherwise the ray integrates the segment.
+__global__ void k_wave_apply(const WaveArgs W, unsigned n, float h) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  int acc = 0, rej = 0;
+  if (i < n) {
+    const int p = W.queue[i], k = W.jump_k[i];
+    const float *y = W.Y + (size_t)i * 7;
+    float yv[7];
+    bool finite = true;
+    for (int o = 0; o < 7; o++) {
+      yv[o] = y[o];
+      finite = finite && isfinite(yv[o]);
+    }
+    const size_t N = (size_t)W.N;
+    const float sc = W.accel_bound > 0.f ? W.accel_bound : 1.f;  // targets were divided by the bound
+    for (int o = 0; o < 6; o++) yv[o] *= sc;
+    if (finite && yv[6] <= W.log_tau2) {
+      const float s = k * h, s2 = s * s;
+      for (int c = 0; c < 3; c++) {
+        float xh = W.st[c * N + p], xl = W.st[(3 + c) * N + p];
+        float vh = W.st[(6 + c) * N + p], vl = W.st[(9 + c) * N + p];
+        const float v = vh;
+        comp_add(xh, xl, fmaf(s2, yv[c], s * v));
+        comp_add(vh, vl, s * yv[3 + c]);
+        W.st[c * N + p] = xh;
+        W.st[(3 + c) * N + p] = xl;
+        W.st[(6 + c) * N + p] = vh;
+        W.st[(9 + c) * N + p] = vl;
+      }
+      W.st[12 * N + p] = 0.f;  // the next chord queries the safe distance afresh
+      W.steps[p] += k;
+      W.cool[p] = 0;
+      acc = 1;
+    } else {
+      W.cool[p] = k;
+      rej = 1;
+    }
+  }
+  const int na = __syncthreads_count(acc), nr = __syncthreads_count(rej);
+  if (threadIdx.x == 0 && (na | nr)) {
+    atomicAdd(&W.stats[0], (unsigned long long)na);
+    atomicAdd(&W.stats[1], (unsigned long long)nr);
+  }
+}
+
 __global__ void k_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
                                  float dt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1064,17 +1302,25 @@ __device__ __forceinline__ float u01(unsigned long long seed, unsigned long long
 //   T = ((x_s - x - s v) / s^2, (v_s - v) / s)     (scaled residuals of the straight line)
 template <int MK>
 __global__ void k_segments(const TraceParams P, long long n, unsigned long long seed, float box, float s_max,
-                           float *X, float *T) {
+                           float accel_bound, float *X, float *T) {
   const int nmax = max(1, (int)roundf(s_max / P.h));
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long base = (unsigned long long)i * 8ull;
-    const F3 x0 = f3(box * (2.f * u01(seed, base) - 1.f), box * (2.f * u01(seed, base + 1) - 1.f),
-                     box * (2.f * u01(seed, base + 2) - 1.f));
-    const float z = 2.f * u01(seed, base + 3) - 1.f, ph = 6.283185307179586f * u01(seed, base + 4);
-    const float rxy = sqrtf(fmaxf(0.f, 1.f - z * z));
-    const F3 d = f3(rxy * cosf(ph), rxy * sinf(ph), z);
-    const int steps = min(nmax, 1 + (int)(u01(seed, base + 5) * nmax));
+    // candidate j of sample i draws counters 8 (j n + i) .. + 5; with a far-field bound
+    // the first candidate within it is kept (the last one if none of kSegTries is)
+    F3 x0, d;
+    int steps = 1;
+    const int tries = accel_bound > 0.f ? kSegTries : 1;
+    for (int j = 0; j < tries; ++j) {
+      const unsigned long long base = ((unsigned long long)j * (unsigned long long)n + (unsigned long long)i) * 8ull;
+      x0 = f3(box * (2.f * u01(seed, base) - 1.f), box * (2.f * u01(seed, base + 1) - 1.f),
+              box * (2.f * u01(seed, base + 2) - 1.f));
+      const float z = 2.f * u01(seed, base + 3) - 1.f, ph = 6.283185307179586f * u01(seed, base + 4);
+      const float rxy = sqrtf(fmaxf(0.f, 1.f - z * z));
+      d = f3(rxy * cosf(ph), rxy * sinf(ph), z);
+      steps = min(nmax, 1 + (int)(u01(seed, base + 5) * nmax));
+      if (accel_bound <= 0.f || far_field_bound(P.bumps, P.K, x0, steps * P.h) <= accel_bound) break;
+    }
     const float s = steps * P.h;
     F3 g = grad_f<MK>(P, P.bumps, x0);
     const float gd = dot(g, d);
@@ -1110,7 +1356,8 @@ __global__ void k_segments(const TraceParams P, long long n, unsigned long long 
     xo[4] = d.y;
     xo[5] = d.z;
     xo[6] = s / s_max;
-    const float is2 = 1.f / (s * s), is = 1.f / s;
+    const float tsc = accel_bound > 0.f ? 1.f / accel_bound : 1.f;
+    const float is2 = tsc / (s * s), is = tsc / s;
     for (int c = 0; c < 3; c++) {
       // (x_s - x - s v) from the compensated pair: (hi - x) + lo - s v
       const float dxs = (xh[c] - comp(x0, c)) + xl[c] - s * comp(v0, c);
@@ -1371,7 +1618,7 @@ cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *
 }
 
 cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long long seed, float box, float s_max,
-                            float *X, float *T, cudaStream_t st) {
+                            float accel_bound, float *X, float *T, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaError_t e;
@@ -1379,8 +1626,34 @@ cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long lon
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const long long want = (n + 127) / 128;
   const unsigned blocks = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
-  if (p.aniso) k_segments<MK_GRAPH_ANISO><<<blocks, 128, 0, st>>>(p, n, seed, box, s_max, X, T);
-  else k_segments<MK_GRAPH_ISO><<<blocks, 128, 0, st>>>(p, n, seed, box, s_max, X, T);
+  if (p.aniso) k_segments<MK_GRAPH_ANISO><<<blocks, 128, 0, st>>>(p, n, seed, box, s_max, accel_bound, X, T);
+  else k_segments<MK_GRAPH_ISO><<<blocks, 128, 0, st>>>(p, n, seed, box, s_max, accel_bound, X, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wave_trace(const TraceParams &p, const WaveArgs &w, cudaStream_t st) {
+  if (p.kind != 0) return cudaErrorInvalidValue;
+  const bool aniso = p.aniso != 0;
+  const size_t smem = (size_t)(packed_float4s(p.K, aniso) + (p.nodes ? 0 : p.S)) * sizeof(float4);
+  if (smem > 227u * 1024u) return cudaErrorInvalidValue;
+  void (*kern)(const TraceParams, const WaveArgs) = aniso ? k_wave_trace<MK_GRAPH_ANISO> : k_wave_trace<MK_GRAPH_ISO>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)sms * per_sm;
+  const long long need = ((long long)p.n_items + 127) / 128;
+  if (blocks > need) blocks = need > 0 ? need : 1;
+  kern<<<(unsigned)blocks, 128, smem, st>>>(p, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wave_apply(const WaveArgs &w, unsigned n, float h, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_wave_apply<<<(n + 255) / 256, 256, 0, st>>>(w, n, h);
   return cudaGetLastError();
 }
 

@@ -82,3 +82,46 @@ def test_segment_residuals_match_adaptive_reference():
         ref = np.concatenate([(xe - x - sl * v) / sl ** 2, (ve - v) / sl])
         assert np.abs(ref - r).max() < 1e-5 * max(1.0, np.abs(ref).max()), (row, ref, r)
     assert np.abs(R).max() > 1e-3  # the field actually bends these segments
+
+
+def test_far_field_bound_dominates_sampled_accelerations():
+    """Along RK4 geodesics of g-length s from x (g-unit tangent), |x''| at every vertex
+    stays below the bound for (x, s); points whose reach misses every support get 0."""
+    import oracle
+    from paper_2005_05386_gb300 import scenes
+    c, a, s = scenes.random_bumps(1, 64)
+    m = oracle.Metric(oracle.GRAPH, c, a, s, cutoff=4.0)
+    r = np.random.default_rng(5)
+    tight = []
+    for _ in range(60):
+        x = r.uniform(-4, 4, 3)
+        d = r.normal(size=3)
+        d /= np.linalg.norm(d)
+        k = int(r.integers(1, 101))
+        sl = k * 0.005
+        B = mlp.far_field_bound(c, a, s, 4.0, x, sl)
+        v = d / np.sqrt(oracle.inner(m, x, d, d))
+        xs, vs = oracle.integrate(m, oracle.RK4, 0.005, k, x, v)
+        amax = max(np.linalg.norm(oracle.accel(m, xi, vi)) for xi, vi in zip(xs, vs))
+        assert amax <= B * (1 + 1e-9) + 1e-15, (x, d, sl, amax, B)
+        if amax > 0:
+            tight.append(amax / B)
+    assert len(tight) > 30 and max(tight) > 1e-2  # not vacuous
+    far = np.array([40.0, 0.0, 0.0])
+    assert mlp.far_field_bound(c, a, s, 4.0, far, 0.5) == 0.0
+    assert np.linalg.norm(oracle.accel(m, far, np.array([1.0, 0, 0]))) == 0.0
+
+
+def test_far_field_bound_single_bump_is_attained_in_gradient_direction():
+    """One bump, s = 0, at distance r = 2 sigma: the gradient factor is exact and the
+    Hessian factor is attained by v along the gradient, so the bound equals
+    |grad f| ||Hess f|| evaluated there (before the min with 1/2)."""
+    sig, amp = 0.5, 0.3
+    x = np.array([2 * sig, 0.0, 0.0])
+    B = mlp.far_field_bound([[0.0, 0.0, 0.0]], [amp], [[sig] * 3], 0.0, x, 0.0)
+    q, u = 1 / sig ** 2, 4.0
+    grad = amp * q * (2 * sig) * np.exp(-u / 2)           # |df/dr| of a Gaussian
+    hess_rr = amp * q * (u - 1) * np.exp(-u / 2)          # d2f/dr2
+    assert grad < 0.5
+    assert B >= grad * hess_rr
+    assert B <= grad * hess_rr * (1 + u) / (u - 1) + 1e-15
