@@ -568,6 +568,51 @@ def bench_surrogate(args):
     return 0
 
 
+def bench_infer(args):
+    """Throughput of the fused tensor-core inference of the learned map on ``--rows`` rows
+    (inputs and outputs larger than L2), with the roofline of its two 256x256 layers."""
+    import torch
+    import paper_2005_05386_gb300 as rg
+    torch.cuda.set_device(0)
+    rows = args.rows
+    net = rg.Expmap(max_batch=128, seed=7)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    X = torch.rand(rows, 7, generator=g, device="cuda") * 2 - 1
+    X[:, 3:6] /= X[:, 3:6].norm(dim=1, keepdim=True)
+    Y = torch.empty(rows, 7, device="cuda")
+    for _ in range(args.warmup):
+        net.forward(X, out=Y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record()
+        net.forward(X, out=Y)
+        b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rg.rgeo_sync()
+    ms = statistics.median([a.elapsed_time(b) for a, b in ev])
+    flops = rows * 2 * 2 * 256 * 256
+    peak = measured_peaks().get("bf16_tflops")
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "rows/s of the learned exponential map (fused tensor-core inference)", "value": rows / ms / 1e3,
+        "unit": "Mrows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
+        "data": "synthetic (uniform inputs)",
+        "config": {"workload": f"expmap_infer_{rows}_rows", "rows": rows,
+                   "l2": "inputs and outputs (56 B per row) exceed L2 at the default size"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "algorithmic": "2 x 2 x 256 x 256 flops per row (layers 2 and 3)"},
+        "clocks": clk, "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,7 +620,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["rgeo", "reference"], default="rgeo")
     ap.add_argument("--workload", default="1080p_64",
-                    choices=["1080p_64", "1080p_twist", "parity_64", "batch16", "anim120", "surrogate"])
+                    choices=["1080p_64", "1080p_twist", "parity_64", "batch16", "anim120", "surrogate", "infer"])
+    ap.add_argument("--rows", type=int, default=1 << 23, help="rows for --workload infer")
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dense", action="store_true", help="time the dense sums (no cull grid) as the step")
@@ -588,6 +634,8 @@ def main():
         return bench_batch(args)
     if args.workload == "surrogate":
         return bench_surrogate(args)
+    if args.workload == "infer":
+        return bench_infer(args)
     return bench_gpu(args)
 
 
