@@ -405,15 +405,20 @@ rgeo_status rgeo_trace_noalloc(const float *center, const float *amplitude, cons
                                int32_t integrator, int32_t shading, const rgeo_outputs *out,
                                void *cuda_stream);
 
-/* Process-wide launch tuning of rgeo_trace (no effect on results beyond the
- * order of float32 summation).  rays_per_thread: 1 or 2 rays advanced together
- * by each thread (2 applies to isotropic graph metrics only; 0 restores the
- * default).  The setting is read when a trace is enqueued; it is not
+/* Process-wide launch tuning of rgeo_trace and rgeo_batch_launch (no effect on
+ * results beyond the order of float32 summation).  rays_per_thread: 1 or 2 rays
+ * advanced together by each thread (2 applies to isotropic graph metrics only; 0
+ * restores the default).  batch_params: where a batch's warps read their
+ * instance's parameters: 0 (default) from the kernel's parameter space when the
+ * batch has at most 64 instances, else from a per-warp shared-memory copy; 1
+ * always from the shared-memory copy.  A setting is read when a trace or batch is
+ * enqueued (a captured graph keeps the choice made at capture); it is not
  * synchronised between host threads.  Errors: RGEO_EINVAL (NULL, bad value,
  * nonzero reserved fields). */
 typedef struct {
   int32_t rays_per_thread;
-  int32_t reserved[7]; /* must be zero */
+  int32_t batch_params;
+  int32_t reserved[6]; /* must be zero */
 } rgeo_tuning;
 
 rgeo_status rgeo_set_tuning(const rgeo_tuning *tuning);

@@ -63,7 +63,8 @@ class rgeo_camera(ctypes.Structure):
 
 
 class rgeo_tuning(ctypes.Structure):
-    _fields_ = [("rays_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("rays_per_thread", ctypes.c_int32), ("batch_params", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class rgeo_outputs(ctypes.Structure):
@@ -394,16 +395,17 @@ def rgeo_sync(stream=None):
     _check(library().rgeo_sync(_stream_handle(stream)), "rgeo_sync")
 
 
-def rgeo_set_tuning(rays_per_thread: int = 0):
+def rgeo_set_tuning(rays_per_thread: int = 0, batch_params: int = 0):
     t = rgeo_tuning()
     t.rays_per_thread = rays_per_thread
+    t.batch_params = batch_params
     _check(library().rgeo_set_tuning(ctypes.byref(t)), "rgeo_set_tuning")
 
 
 def rgeo_get_tuning() -> dict:
     t = rgeo_tuning()
     _check(library().rgeo_get_tuning(ctypes.byref(t)), "rgeo_get_tuning")
-    return {"rays_per_thread": t.rays_per_thread}
+    return {"rays_per_thread": t.rays_per_thread, "batch_params": t.batch_params}
 
 
 def rgeo_ffma_probe(mode: int = 0):

@@ -82,12 +82,12 @@ def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbos
     pw = proxy(work)
     scene = Scene(pw.scene)
     out = alloc_outputs(pw.n_pixels)
-    saved = rgeo_get_tuning()["rays_per_thread"]
+    saved = rgeo_get_tuning()
     results = []
     try:
         for cand in candidates(pw):
             metric = Metric(dataclasses.replace(pw.metric, cull_grid=cand["cull_grid"]))
-            rgeo_set_tuning(cand["rays_per_thread"])
+            rgeo_set_tuning(cand["rays_per_thread"], saved["batch_params"])
             trace(pw, metric, scene, out)           # warm-up
             rgeo_sync()
             best = float("inf")
@@ -103,7 +103,7 @@ def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbos
             if verbose:
                 print(f"autotune {signature(pw)} {cand} {best:.2f} ms", flush=True)
     finally:
-        rgeo_set_tuning(saved)
+        rgeo_set_tuning(saved["rays_per_thread"], saved["batch_params"])
     win = min(results, key=lambda r: r["ms"])
     if use_cache:
         db[key] = win
@@ -113,6 +113,6 @@ def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbos
 
 def apply(work: scenes.Workload, choice: dict) -> scenes.Workload:
     """The workload with the tuned cull grid; sets the process-wide rays-per-thread."""
-    from . import rgeo_set_tuning
-    rgeo_set_tuning(int(choice["rays_per_thread"]))
+    from . import rgeo_get_tuning, rgeo_set_tuning
+    rgeo_set_tuning(int(choice["rays_per_thread"]), rgeo_get_tuning()["batch_params"])
     return dataclasses.replace(work, metric=dataclasses.replace(work.metric, cull_grid=int(choice["cull_grid"])))

@@ -21,6 +21,7 @@ struct rgeo_scene {
 
 struct rgeo_batch {
   rgeo::TraceParams *table;  // device instance table
+  std::vector<rgeo::TraceParams> host_table;  // the same, passed by value when it fits the parameter space
   uint32_t *counters;        // device, one work counter per instance
   int n, kind, aniso, integrator;
   int max_table_f4;  // largest packed bump table of the instances, in float4
@@ -433,11 +434,14 @@ rgeo_status rgeo_sync(void *cuda_stream) {
 rgeo_status rgeo_set_tuning(const rgeo_tuning *t) {
   g_last_error.clear();
   if (!t) return fail(RGEO_EINVAL, "rgeo_set_tuning: NULL");
-  for (int i = 0; i < 7; i++)
+  for (int i = 0; i < 6; i++)
     if (t->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_set_tuning: reserved fields must be zero");
   if (t->rays_per_thread != 0 && t->rays_per_thread != 1 && t->rays_per_thread != 2)
     return fail(RGEO_EINVAL, "rgeo_set_tuning: rays_per_thread must be 0, 1 or 2");
+  if (t->batch_params != 0 && t->batch_params != 1)
+    return fail(RGEO_EINVAL, "rgeo_set_tuning: batch_params must be 0 or 1");
   rgeo::tuning().rays_per_thread = t->rays_per_thread == 0 ? rgeo::Tuning().rays_per_thread : t->rays_per_thread;
+  rgeo::tuning().batch_params = t->batch_params;
   return RGEO_OK;
 }
 
@@ -446,6 +450,7 @@ rgeo_status rgeo_get_tuning(rgeo_tuning *t) {
   if (!t) return fail(RGEO_EINVAL, "rgeo_get_tuning: NULL");
   std::memset(t, 0, sizeof(*t));
   t->rays_per_thread = rgeo::tuning().rays_per_thread;
+  t->batch_params = rgeo::tuning().batch_params;
   return RGEO_OK;
 }
 
@@ -491,6 +496,7 @@ rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *inst, rgeo_batch *
   if (e == cudaSuccess) {
     for (int i = 0; i < n; i++) table[i].counter = b->counters + i;
     e = upload(&b->table, table.data(), table.size());
+    b->host_table = table;
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -508,8 +514,8 @@ rgeo_status rgeo_batch_launch(rgeo_batch *b, void *cuda_stream) {
   if (!b) return fail(RGEO_EINVAL, "rgeo_batch_launch: NULL batch");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   RGEO_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(uint32_t) * b->n, st), "rgeo_batch_launch: counters");
-  RGEO_CUDA(rgeo::launch_batch(b->table, b->n, b->kind, b->aniso, b->integrator, b->max_table_f4, b->total_items,
-                               st),
+  RGEO_CUDA(rgeo::launch_batch(b->table, b->host_table.data(), b->n, b->kind, b->aniso, b->integrator,
+                               b->max_table_f4, b->total_items, st),
             "rgeo_batch_launch: launch");
   return RGEO_OK;
 }

@@ -139,9 +139,17 @@ struct WaveArgs {
   long long N;
 };
 
+// Instance table of a batch passed by value in the kernel's parameter space (CUDA
+// allows 32 KB of parameters; 64 x 368 B fits).
+constexpr int kMaxParamInstances = 64;
+struct BatchTable {
+  TraceParams inst[kMaxParamInstances];
+};
+
 // Process-wide launch tuning (set by rgeo_set_tuning, read at every trace).
 struct Tuning {
   int rays_per_thread = 1;  // measured faster on GB300 at 64 bumps (occupancy beats shared traffic)
+  int batch_params = 0;     // 0: parameter space when n <= kMaxParamInstances; 1: shared-memory copies
 };
 Tuning &tuning();
 
@@ -181,7 +189,8 @@ cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
 cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
 cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
                               cudaStream_t st);
-cudaError_t launch_batch(const TraceParams *dev_inst, int n, int kind, int aniso, int integrator,
+cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int kind, int aniso,
+                         int integrator,
                          int max_table_f4, long long total_items, cudaStream_t st);
 cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
                                   float dt, cudaStream_t st);

@@ -15,6 +15,7 @@
 // (Eq. 5.8) with J and the Hessians of the twist in closed form.
 #include <cfloat>
 #include <cstdint>
+#include <cstring>
 
 #include "rgeo_internal.h"
 
@@ -975,28 +976,52 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
 // instance's parameters, then (when it fits) its packed bump table.
 constexpr int kParamWords = (int)((sizeof(TraceParams) + 15) / 16) * 4;
 
-__device__ __forceinline__ void warp_load_instance(const TraceParams *inst, int i, uint32_t *slot, int table_f4,
-                                                   const float4 *&sb) {
-  const unsigned lane = threadIdx.x & 31u;
-  const uint32_t *src = reinterpret_cast<const uint32_t *>(inst + i);
-  for (int k = (int)lane; k < (int)(sizeof(TraceParams) / 4); k += 32) slot[k] = __ldg(src + k);
-  __syncwarp();
-  const TraceParams &P = *reinterpret_cast<const TraceParams *>(slot);
-  const int need = P.kind != 1 ? packed_float4s(P.K, P.aniso) : 0;
-  float4 *tab = reinterpret_cast<float4 *>(slot + kParamWords);
-  if (need <= table_f4) {
+// Copies instance i's bump table into the warp's shared-memory table (SMEM: the
+// launcher made it large enough for every instance) or reads it through L1.  Keeping
+// the two cases apart lets the compiler see that sb points to shared memory.
+template <bool SMEM>
+__device__ __forceinline__ void warp_load_table(const TraceParams &P, float4 *tab, const float4 *&sb) {
+  if (SMEM) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int need = P.kind != 1 ? packed_float4s(P.K, P.aniso) : 0;
     for (int k = (int)lane; k < need; k += 32) tab[k] = __ldg(P.bumps + k);
     sb = tab;
   } else {
-    sb = P.bumps;  // too large for the slot: read through L1
+    sb = P.bumps;
   }
   __syncwarp();
 }
 
-template <int MK, int INTEG>
-__global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
-  extern __shared__ float4 bsmem[];
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) + (threadIdx.x >> 5) * (kParamWords + 4 * table_f4);
+// Instance parameters from a per-warp shared-memory copy (any number of instances).
+struct SmemInstances {
+  const TraceParams *inst;
+  uint32_t *slot;
+  __device__ __forceinline__ const TraceParams &get(int) const {
+    return *reinterpret_cast<const TraceParams *>(slot);
+  }
+  __device__ __forceinline__ float4 *table() const { return reinterpret_cast<float4 *>(slot + kParamWords); }
+  __device__ __forceinline__ void load(int i) const {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(inst + i);
+    for (int k = (int)lane; k < (int)(sizeof(TraceParams) / 4); k += 32) slot[k] = __ldg(src + k);
+    __syncwarp();
+  }
+};
+
+// Instance parameters from the kernel's parameter space (up to kMaxParamInstances),
+// where field reads are constant-cache loads shared by the whole warp.
+struct ParamInstances {
+  const BatchTable *T;
+  float4 *tab;
+  __device__ __forceinline__ const TraceParams &get(int i) const { return T->inst[i]; }
+  __device__ __forceinline__ float4 *table() const { return tab; }
+  __device__ __forceinline__ void load(int) const {}
+};
+
+// The batch loop: each warp drains one instance's queue, then moves to the next
+// instance (round robin from its own start), reloading parameters and bump table.
+template <int MK, int INTEG, bool SMEM, class Src>
+__device__ __forceinline__ void batch_loop(const Src &src, int n) {
   const int warp_global = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int i = warp_global % n;
   int visited = 0;
@@ -1004,9 +1029,10 @@ __global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restri
   bool active = false, drained = false;
   Ray r;
   const float4 *sb = nullptr;
-  warp_load_instance(inst, i, slot, table_f4, sb);
+  src.load(i);
+  warp_load_table<SMEM>(src.get(i), src.table(), sb);
   for (;;) {
-    const TraceParams &P = *reinterpret_cast<const TraceParams *>(slot);
+    const TraceParams &P = src.get(i);
     const float4 *ss = P.spheres;
     refill<MK>(P, sb, active, drained, r);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
@@ -1020,7 +1046,8 @@ __global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restri
         if (++visited >= n) break;
         i = (i + 1) % n;
         drained = false;
-        warp_load_instance(inst, i, slot, table_f4, sb);
+        src.load(i);
+        warp_load_table<SMEM>(src.get(i), src.table(), sb);
       }
       continue;
     }
@@ -1038,6 +1065,21 @@ __global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restri
     step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
     active = post_step<MK>(P, sb, ss, r, dx, dvel);
   }
+}
+
+template <int MK, int INTEG, bool SMEM>
+__global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
+  extern __shared__ float4 bsmem[];
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) + (threadIdx.x >> 5) * (kParamWords + 4 * table_f4);
+  batch_loop<MK, INTEG, SMEM>(SmemInstances{inst, slot}, n);
+}
+
+template <int MK, int INTEG, bool SMEM>
+__global__ void __launch_bounds__(128) k_trace_batch_param(const __grid_constant__ BatchTable T, int n,
+                                                           int table_f4) {
+  extern __shared__ float4 bsmem[];
+  float4 *tab = bsmem + (threadIdx.x >> 5) * table_f4;
+  batch_loop<MK, INTEG, SMEM>(ParamInstances{&T, tab}, n);
 }
 
 // Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
@@ -1570,10 +1612,16 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
 }
 
 template <int MK, int INTEG>
-cudaError_t launch_batch_t(const TraceParams *dev_inst, int n, int table_f4, long long total_items,
-                           cudaStream_t st) {
-  auto kern = k_trace_batch<MK, INTEG>;
-  const size_t smem = (size_t)4 * (kParamWords * 4 + (size_t)table_f4 * 16);
+cudaError_t launch_batch_t(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int table_f4,
+                           long long total_items, cudaStream_t st) {
+  const bool param = host_inst != nullptr && n <= kMaxParamInstances && tuning().batch_params == 0;
+  const size_t smem = param ? (size_t)4 * table_f4 * 16 : (size_t)4 * (kParamWords * 4 + (size_t)table_f4 * 16);
+  const bool in_smem = table_f4 > 0 || MK == MK_TWIST;
+  void (*kern_s)(const TraceParams *, int, int) =
+      in_smem ? k_trace_batch<MK, INTEG, true> : k_trace_batch<MK, INTEG, false>;
+  void (*kern_p)(const BatchTable, int, int) =
+      in_smem ? k_trace_batch_param<MK, INTEG, true> : k_trace_batch_param<MK, INTEG, false>;
+  const void *kern = param ? (const void *)kern_p : (const void *)kern_s;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -1584,26 +1632,33 @@ cudaError_t launch_batch_t(const TraceParams *dev_inst, int n, int table_f4, lon
   long long blocks = (long long)sms * per_sm;
   const long long need = (total_items + 127) / 128;
   if (blocks > need) blocks = need > 0 ? need : 1;
-  kern<<<(unsigned)blocks, 128, smem, st>>>(dev_inst, n, table_f4);
+  if (param) {
+    static thread_local BatchTable table;  // 23.5 KB: kept off the stack
+    std::memset(&table, 0, sizeof(table));
+    std::memcpy(table.inst, host_inst, sizeof(TraceParams) * (size_t)n);
+    kern_p<<<(unsigned)blocks, 128, smem, st>>>(table, n, table_f4);
+  } else {
+    kern_s<<<(unsigned)blocks, 128, smem, st>>>(dev_inst, n, table_f4);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_batch(const TraceParams *dev_inst, int n, int kind, int aniso, int integrator,
-                         int max_table_f4, long long total_items, cudaStream_t st) {
+cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int kind, int aniso,
+                         int integrator, int max_table_f4, long long total_items, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   // per-warp bump tables up to 1024 float4 (512 pairs); larger tables are read through L1
   const int table_f4 = max_table_f4 <= 1024 ? max_table_f4 : 0;
   const int mk = kind == 1 ? MK_TWIST : (aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO);
   if (mk == MK_GRAPH_ISO)
-    return integrator == 0 ? launch_batch_t<MK_GRAPH_ISO, 0>(dev_inst, n, table_f4, total_items, st)
-                           : launch_batch_t<MK_GRAPH_ISO, 1>(dev_inst, n, table_f4, total_items, st);
+    return integrator == 0 ? launch_batch_t<MK_GRAPH_ISO, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
+                           : launch_batch_t<MK_GRAPH_ISO, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
   if (mk == MK_GRAPH_ANISO)
-    return integrator == 0 ? launch_batch_t<MK_GRAPH_ANISO, 0>(dev_inst, n, table_f4, total_items, st)
-                           : launch_batch_t<MK_GRAPH_ANISO, 1>(dev_inst, n, table_f4, total_items, st);
-  return integrator == 0 ? launch_batch_t<MK_TWIST, 0>(dev_inst, n, table_f4, total_items, st)
-                         : launch_batch_t<MK_TWIST, 1>(dev_inst, n, table_f4, total_items, st);
+    return integrator == 0 ? launch_batch_t<MK_GRAPH_ANISO, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
+                           : launch_batch_t<MK_GRAPH_ANISO, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
+  return integrator == 0 ? launch_batch_t<MK_TWIST, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
+                         : launch_batch_t<MK_TWIST, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
 }
 
 cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,

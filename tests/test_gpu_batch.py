@@ -38,19 +38,45 @@ def _close(x, y, S):
     assert st["agree"] >= 0.999, st
 
 
-def test_batch_equals_separate_traces(rg):
-    """A batch traces each instance as rgeo_trace does (launch shape aside)."""
+@pytest.mark.parametrize("batch_params", [0, 1])
+def test_batch_equals_separate_traces(rg, batch_params):
+    """A batch traces each instance as rgeo_trace does (launch shape aside), whether its warps
+    read the instance table from the kernel's parameter space (0) or shared-memory copies (1)."""
+    saved = rg.rgeo_get_tuning()
+    rg.rgeo_set_tuning(saved["rays_per_thread"], batch_params)
+    try:
+        ws = _small_instances()
+        handles = [(rg.Metric(w.metric), rg.Scene(w.scene)) for w in ws]
+        outs = [rg.alloc_outputs(w.n_pixels) for w in ws]
+        batch = rg.Batch([rg.instance(w, m, s, o) for w, (m, s), o in zip(ws, handles, outs)])
+        for _ in range(2):   # the second launch reuses the counters
+            batch.launch()
+            rg.rgeo_sync()
+            for w, (m, s), o in zip(ws, handles, outs):
+                ref = rg.trace(w, m, s)
+                rg.rgeo_sync()
+                _close(gpu_arrays(o), gpu_arrays(ref), w.scene.n_spheres)
+    finally:
+        rg.rgeo_set_tuning(saved["rays_per_thread"], saved["batch_params"])
+
+
+def test_batch_parameter_space_equals_shared_copies(rg):
+    """The two instance-table sources run the same arithmetic: identical images."""
     ws = _small_instances()
     handles = [(rg.Metric(w.metric), rg.Scene(w.scene)) for w in ws]
-    outs = [rg.alloc_outputs(w.n_pixels) for w in ws]
-    batch = rg.Batch([rg.instance(w, m, s, o) for w, (m, s), o in zip(ws, handles, outs)])
-    for _ in range(2):   # the second launch reuses the counters
-        batch.launch()
-        rg.rgeo_sync()
-        for w, (m, s), o in zip(ws, handles, outs):
-            ref = rg.trace(w, m, s)
+    res = []
+    saved = rg.rgeo_get_tuning()
+    try:
+        for mode in (0, 1):
+            rg.rgeo_set_tuning(saved["rays_per_thread"], mode)
+            outs = [rg.alloc_outputs(w.n_pixels) for w in ws]
+            rg.Batch([rg.instance(w, m, s, o) for w, (m, s), o in zip(ws, handles, outs)]).launch()
             rg.rgeo_sync()
-            _close(gpu_arrays(o), gpu_arrays(ref), w.scene.n_spheres)
+            res.append([gpu_arrays(o) for o in outs])
+    finally:
+        rg.rgeo_set_tuning(saved["rays_per_thread"], saved["batch_params"])
+    for a, b, w in zip(res[0], res[1], ws):
+        _close(a, b, w.scene.n_spheres)
 
 
 def test_batch_rejects_mixed_integrators(rg):
