@@ -37,7 +37,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 # Tests that plant a mistake in a copy of the oracle point this at the copy.
 _LIB_OVERRIDE = os.environ.get("RGEO_ORACLE_LIB")
 
-GRAPH, TWIST = 0, 1
+GRAPH, TWIST, LOCAL = 0, 1, 2
 RK4, EULER = 0, 1
 LAMBERT, PSEUDO = 0, 1
 MISS, BUDGET = -1, -2
@@ -89,6 +89,10 @@ def lib():
         for name in ("or_twist_phi", "or_twist_phi_inv", "or_twist_jacobian", "or_twist_hessian"):
             getattr(L, name).argtypes = [ctypes.c_double, _dp, _dp]
         L.or_inverse_by_minors.argtypes = [_dp, _dp]
+        L.or_metric_set_local.argtypes = [ctypes.c_void_p, _dp, _dp]
+        L.or_local_map.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.or_local_compose.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+        L.or_local_jinv.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.or_hit_sphere.restype = ctypes.c_int
         L.or_hit_sphere.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_hit_triangle.restype = ctypes.c_int
@@ -112,10 +116,12 @@ def _d(a):
 
 
 class Metric:
-    """FP64 copy of a metric description (graph of summed bumps, or twist)."""
+    """FP64 copy of a metric description: graph of summed bumps, twist, or a composition of
+    local diffeomorphisms p + f_i(p) (v_i + B_i (p - c_i)) (kind LOCAL; direction [K,3], field
+    [K,3,3] or None)."""
 
     def __init__(self, kind=GRAPH, center=None, amplitude=None, sigma=None, affine_b=(0, 0, 0),
-                 quad_A=(0,) * 9, cutoff=4.0, twist_rate=1.0):
+                 quad_A=(0,) * 9, cutoff=4.0, twist_rate=1.0, direction=None, field=None):
         center = np.zeros((0, 3)) if center is None else np.asarray(center, np.float64).reshape(-1, 3)
         amplitude = np.zeros((0,)) if amplitude is None else np.asarray(amplitude, np.float64).reshape(-1)
         sigma = np.zeros((0, 3)) if sigma is None else np.asarray(sigma, np.float64).reshape(-1, 3)
@@ -123,13 +129,19 @@ class Metric:
         self._keep = [_d(center), _d(amplitude), _d(sigma), _d(affine_b), _d(quad_A)]
         (_, pc), (_, pa), (_, ps), (_, pb), (_, pA) = self._keep
         self.kind = kind
+        self.K = K
         self.ptr = lib().or_metric_create(kind, K, pc, pa, ps, pb, pA, float(cutoff), float(twist_rate))
+        if kind == LOCAL:
+            dv = _d(np.zeros((K, 3)) if direction is None else np.asarray(direction, np.float64).reshape(-1, 3))
+            fb = _d(np.asarray(field, np.float64).reshape(-1, 9)) if field is not None else (None, None)
+            self._keep += [dv, fb]
+            lib().or_metric_set_local(self.ptr, dv[1], fb[1])
 
     @classmethod
     def from_desc(cls, m):
         """From a ``scenes.Metric`` (float32 arrays converted exactly to float64)."""
         return cls(m.kind, m.center, m.amplitude, m.sigma, m.affine_b, m.quad_A, m.cutoff,
-                   m.twist_rate)
+                   m.twist_rate, getattr(m, "direction", None), getattr(m, "field", None))
 
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:
@@ -238,6 +250,30 @@ def twist_jacobian(k, p):
 
 def twist_hessian(k, p):
     return _twist_call("or_twist_hessian", k, p, 27).reshape(3, 3, 3)
+
+
+def local_map(m: Metric, i: int, p):
+    """(Phi_i(p), J [3,3], H [3,3,3] with H[s, i, j] = d_i d_j (Phi_i)_s) of one local map."""
+    p, pp = _d(p)
+    out, J, H = np.zeros(3), np.zeros(9), np.zeros(27)
+    lib().or_local_map(m.ptr, int(i), pp, out.ctypes.data_as(_dp), J.ctypes.data_as(_dp), H.ctypes.data_as(_dp))
+    return out, J.reshape(3, 3), H.reshape(3, 3, 3)
+
+
+def local_compose(m: Metric, p):
+    """(Phi(p), J, H) of the composition Phi = Phi_1 o ... o Phi_K."""
+    p, pp = _d(p)
+    out, J, H = np.zeros(3), np.zeros(9), np.zeros(27)
+    lib().or_local_compose(m.ptr, pp, out.ctypes.data_as(_dp), J.ctypes.data_as(_dp), H.ctypes.data_as(_dp))
+    return out, J.reshape(3, 3), H.reshape(3, 3, 3)
+
+
+def local_jinv(m: Metric, p):
+    """J^-1 of the composition as the product of the maps' inverses in reverse order."""
+    p, pp = _d(p)
+    out = np.zeros(9)
+    lib().or_local_jinv(m.ptr, pp, out.ctypes.data_as(_dp))
+    return out.reshape(3, 3)
 
 
 def inverse_by_minors(J):

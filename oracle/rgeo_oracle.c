@@ -48,6 +48,7 @@
 
 #define OR_GRAPH 0
 #define OR_TWIST 1
+#define OR_LOCAL 2
 #define OR_RK4 0
 #define OR_EULER 1
 #define OR_LAMBERT 0
@@ -59,8 +60,8 @@
 /* ------------------------------------------------------------------ metric */
 
 typedef struct {
-  int kind;        /* OR_GRAPH or OR_TWIST */
-  int K;           /* number of Gaussian bumps */
+  int kind;        /* OR_GRAPH, OR_TWIST or OR_LOCAL */
+  int K;           /* number of Gaussian bumps (OR_LOCAL: of composed local maps) */
   double *c;       /* [K*3] centres (x0, y0, z0) of Eq. 6.1 */
   double *a;       /* [K] amplitudes a */
   double *sig;     /* [K*3] spreads sigma_x, sigma_y, sigma_z */
@@ -68,6 +69,8 @@ typedef struct {
   double A[9];     /* quadratic part of f: 1/2 x^T A x (A symmetric, row-major) */
   double cutoff;   /* truncation radius in units of sigma; <= 0 means none */
   double k;        /* twist rate: Phi rotates by k z about the z axis */
+  double *dir;     /* OR_LOCAL: [K*3] directions v_i of Phi_i(p) = p + f_i(p) V_i(p) */
+  double *Bf;      /* OR_LOCAL: [K*9] field matrices, V_i(p) = v_i + B_i (p - c_i) */
 } or_metric;
 
 or_metric *or_metric_create(int kind, int K, const double *c, const double *a,
@@ -91,8 +94,21 @@ or_metric *or_metric_create(int kind, int K, const double *c, const double *a,
   return m;
 }
 
+/* Directions and field matrices of an OR_LOCAL metric (B may be NULL: constant V_i = v_i). */
+void or_metric_set_local(or_metric *m, const double *dir, const double *B) {
+  int K = m->K > 0 ? m->K : 1;
+  m->dir = (double *)calloc(3 * (size_t)K, sizeof(double));
+  m->Bf = (double *)calloc(9 * (size_t)K, sizeof(double));
+  if (m->K > 0) {
+    memcpy(m->dir, dir, sizeof(double) * 3 * m->K);
+    if (B) memcpy(m->Bf, B, sizeof(double) * 9 * m->K);
+  }
+}
+
 void or_metric_destroy(or_metric *m) {
   if (!m) return;
+  free(m->dir);
+  free(m->Bf);
   free(m->c);
   free(m->a);
   free(m->sig);
@@ -204,6 +220,95 @@ void or_inverse_by_minors(const double J[9], double Jinv[9]) {
     }
 }
 
+/* ------------------------------------------------- local diffeomorphisms */
+
+/* One local map Phi_i(p) = p + f_i(p) V_i(p) (the local diffeomorphism of Section 6,
+ * "Using diffeomorphism"), with f_i the Gaussian of Eq. 6.1 (isotropic spread sigma_i,
+ * not truncated) and the vector field V_i(p) = v_i + B_i (p - c_i).
+ * out = Phi_i(p); J[s*3+j] = d_j (Phi_i)_s; H[s*9+i*3+j] = d_i d_j (Phi_i)_s:
+ *   d_j (Phi_i)_s = delta_sj + f_j V_s + f B_sj,
+ *   d_i d_j (Phi_i)_s = f_ij V_s + f_j B_si + f_i B_sj   (V is affine). */
+void or_local_map(const or_metric *m, int idx, const double p[3], double out[3], double J[9], double H[27]) {
+  const double *c = m->c + 3 * idx, *v = m->dir + 3 * idx, *B = m->Bf + 9 * idx;
+  double sg = m->sig[3 * idx], q = 1.0 / (sg * sg);
+  double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+  double f = m->a[idx] * exp(-0.5 * q * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  double gr[3], hs[9], V[3];
+  for (int i = 0; i < 3; i++) gr[i] = -q * d[i] * f;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) hs[3 * i + j] = f * (q * q * d[i] * d[j] - (i == j ? q : 0.0));
+  for (int s = 0; s < 3; s++) V[s] = v[s] + B[3 * s] * d[0] + B[3 * s + 1] * d[1] + B[3 * s + 2] * d[2];
+  for (int s = 0; s < 3; s++) {
+    out[s] = p[s] + f * V[s];
+    for (int j = 0; j < 3; j++) J[3 * s + j] = (s == j ? 1.0 : 0.0) + gr[j] * V[s] + f * B[3 * s + j];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++)
+        H[9 * s + 3 * i + j] = hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i] + gr[i] * B[3 * s + j];
+  }
+}
+
+/* The composition Phi = Phi_1 o Phi_2 o ... o Phi_K (Section 6, "Composing diffeomorphisms";
+ * array index K-1 is applied first).  Built from the inside out with Psi_K = Phi_K and
+ * Psi_j = Phi_j o Psi_{j+1}:
+ *   J(Psi_j)_p = J(Phi_j)_{Psi_{j+1}(p)} J(Psi_{j+1})_p                       (chain rule)
+ *   H(x_s o Psi_{j+1})_p = J(Psi_{j+1})^T_p H(x_s)_{Psi_{j+1}(p)} J(Psi_{j+1})_p
+ *                          + sum_r d_r x_s(Psi_{j+1}(p)) H((Psi_{j+1})_r)_p          (Eq. 6.3)
+ * with x_s the s-th coordinate of Phi_j.  out = Phi(p). */
+void or_local_compose(const or_metric *m, const double p[3], double out[3], double J[9], double H[27]) {
+  double q[3], Jj[9], Hj[27], q2[3], Jn[9], Hn[27];
+  or_local_map(m, m->K - 1, p, q, J, H);
+  for (int j = m->K - 2; j >= 0; j--) {
+    or_local_map(m, j, q, q2, Jj, Hj);
+    for (int s = 0; s < 3; s++)
+      for (int c = 0; c < 3; c++) {
+        double acc = 0.0;
+        for (int r = 0; r < 3; r++) acc += Jj[3 * s + r] * J[3 * r + c];
+        Jn[3 * s + c] = acc;
+      }
+    for (int s = 0; s < 3; s++)
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+          double acc = 0.0;
+          for (int k = 0; k < 3; k++)
+            for (int l = 0; l < 3; l++) acc += J[3 * k + a] * Hj[9 * s + 3 * k + l] * J[3 * l + b];
+          for (int r = 0; r < 3; r++) acc += Jj[3 * s + r] * H[9 * r + 3 * a + b];
+          Hn[9 * s + 3 * a + b] = acc;
+        }
+    memcpy(q, q2, sizeof(q));
+    memcpy(J, Jn, sizeof(Jn));
+    memcpy(H, Hn, sizeof(Hn));
+  }
+  memcpy(out, q, sizeof(q));
+}
+
+/* J^-1 of the composition as the paper writes it: J^-1(Phi) = J^-1(Phi_K) ... J^-1(Phi_1),
+ * each factor inverted by the signed minors at its own point Psi_{j+1}(p). */
+void or_local_jinv(const or_metric *m, const double p[3], double Jinv[9]) {
+  double q[3], Ji[9], Hi[27], inv[9], q2[3], acc[9];
+  /* points: Phi_K acts at p, Phi_j at Psi_{j+1}(p) */
+  double *pts = (double *)malloc(sizeof(double) * 3 * (size_t)m->K);
+  memcpy(q, p, sizeof(q));
+  for (int j = m->K - 1; j >= 0; j--) {
+    memcpy(pts + 3 * j, q, sizeof(q));
+    or_local_map(m, j, q, q2, Ji, Hi);
+    memcpy(q, q2, sizeof(q));
+  }
+  /* product J^-1(Phi_K) ... J^-1(Phi_1): start from the right, J^-1(Phi_1) */
+  for (int i = 0; i < 9; i++) Jinv[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  for (int j = 0; j < m->K; j++) {
+    or_local_map(m, j, pts + 3 * j, q2, Ji, Hi);
+    or_inverse_by_minors(Ji, inv);
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 3; c++) {
+        double t = 0.0;
+        for (int k = 0; k < 3; k++) t += inv[3 * r + k] * Jinv[3 * k + c];
+        acc[3 * r + c] = t;
+      }
+    memcpy(Jinv, acc, sizeof(acc));
+  }
+  free(pts);
+}
+
 /* Metric coefficients g_ij at x: Eq. 5.2 (graph) or Eq. 5.6 (pull-back). */
 void or_metric_tensor(const or_metric *m, const double x[3], double g[9]) {
   if (m->kind == OR_GRAPH) {
@@ -213,7 +318,12 @@ void or_metric_tensor(const or_metric *m, const double x[3], double g[9]) {
       for (int j = 0; j < 3; j++) g[3 * i + j] = (i == j ? 1.0 : 0.0) + gr[i] * gr[j];
   } else {
     double J[9];
-    or_twist_jacobian(m->k, x, J);
+    if (m->kind == OR_LOCAL) {
+      double q[3], H[27];
+      or_local_compose(m, x, q, J, H);
+    } else {
+      or_twist_jacobian(m->k, x, J);
+    }
     for (int i = 0; i < 3; i++)
       for (int j = 0; j < 3; j++) {
         double s = 0.0;
@@ -245,9 +355,15 @@ void or_christoffel(const or_metric *m, const double x[3], double Gam[27]) {
   } else {
     /* Theorem 5.1 (Eq. 5.7) */
     double J[9], Jinv[9], H[27];
-    or_twist_jacobian(m->k, x, J);
-    or_inverse_by_minors(J, Jinv);
-    or_twist_hessian(m->k, x, H);
+    if (m->kind == OR_LOCAL) {
+      double q[3];
+      or_local_compose(m, x, q, J, H);
+      or_local_jinv(m, x, Jinv);
+    } else {
+      or_twist_jacobian(m->k, x, J);
+      or_inverse_by_minors(J, Jinv);
+      or_twist_hessian(m->k, x, H);
+    }
     for (int mm = 0; mm < 3; mm++)
       for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {

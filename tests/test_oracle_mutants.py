@@ -35,6 +35,14 @@ MUTANTS = {
                   "double v[3] = {d[0], d[1], d[2]};", "g_unit"),
     "watertight_edge_sign": ("double V = Ax * Cy - Ay * Cx;", "double V = Ay * Cx - Ax * Cy;",
                              "triangle or watertight or bvh"),
+    "eq63_dropped_term": ("          for (int r = 0; r < 3; r++) acc += Jj[3 * s + r] * H[9 * r + 3 * a + b];\n", "",
+                          "local"),
+    "eq63_transposed_jacobian": ("acc += J[3 * k + a] * Hj[9 * s + 3 * k + l] * J[3 * l + b];",
+                                 "acc += J[3 * a + k] * Hj[9 * s + 3 * k + l] * J[3 * b + l];", "local"),
+    "jinv_product_order": ("t += inv[3 * r + k] * Jinv[3 * k + c];", "t += Jinv[3 * r + k] * inv[3 * k + c];",
+                           "local"),
+    "local_field_term": ("hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i] + gr[i] * B[3 * s + j];",
+                         "hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i];", "local"),
 }
 
 

@@ -461,3 +461,82 @@ def test_miss_when_no_support_ahead():
     o = oracle.trace(w, np.array([0, 63, 64 * 64 - 1]))   # corner rays pass outside the bump
     assert list(o["id"]) == [oracle.MISS] * 3
     assert list(o["steps"]) == [0, 0, 0]
+
+
+def test_quadratic_metric_axis_geodesic_closed_form():
+    """f = x^2 + y^2 - z^2 (A = diag(2, 2, -2), Section 5.1's example).  From the origin along x
+    the geodesic stays on the x-axis (the metric is symmetric under y -> -y and z -> -z), where
+    g_xx = 1 + f_x^2 = 1 + 4 x^2, so its arc length is s(x) = x sqrt(1 + 4x^2) / 2 + asinh(2x) / 4."""
+    m = oracle.Metric(oracle.GRAPH, None, None, None, (0, 0, 0), (2, 0, 0, 0, 2, 0, 0, 0, -2), cutoff=0.0)
+    h, n = 0.005, 400
+    xs, vs = oracle.integrate(m, oracle.RK4, h, n, [0.0, 0.0, 0.0], [1.0, 0.0, 0.0])
+    assert np.abs(xs[:, 1:]).max() == 0.0
+    x = xs[-1, 0]
+    s = x * np.sqrt(1 + 4 * x * x) / 2 + np.arcsinh(2 * x) / 4
+    assert abs(s - n * h) < 1e-9, (s, n * h)
+    # and the tangent stays g-unit: (1 + 4x^2) x'^2 = 1
+    assert abs((1 + 4 * x * x) * vs[-1, 0] ** 2 - 1) < 1e-9
+
+
+def _local_metric(K=3, seed=1, field=True):
+    """K local maps p + f_i(p) (v_i + B_i (p - c_i)) with |a_i| |v_i| e^{-1/2} / sigma_i = 0.6."""
+    r = np.random.default_rng(seed)
+    c = r.uniform(-1, 1, (K, 3))
+    sig = r.uniform(0.4, 0.8, K)
+    d = r.normal(size=(K, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    a = 0.6 * sig / np.exp(-0.5)
+    B = r.normal(size=(K, 3, 3)) * 0.1 if field else None
+    return oracle.Metric(oracle.LOCAL, c, a, np.repeat(sig[:, None], 3, 1), cutoff=0.0, direction=d, field=B)
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_local_composition_derivatives_match_finite_differences(K):
+    """J and H of Phi = Phi_1 o ... o Phi_K (chain rule and Eq. 6.3) against central differences
+    of Phi itself and of J."""
+    m = _local_metric(K)
+    p = np.array([0.2, -0.1, 0.3])
+    q, J, H = oracle.local_compose(m, p)
+    eps = 1e-5
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = eps
+        qp, Jp, _ = oracle.local_compose(m, p + e)
+        qm, Jm, _ = oracle.local_compose(m, p - e)
+        np.testing.assert_allclose(J[:, j], (qp - qm) / (2 * eps), atol=1e-8)
+        np.testing.assert_allclose(H[:, :, j], (Jp - Jm) / (2 * eps), atol=1e-8)
+    assert np.abs(q - p).max() > 1e-3  # the maps actually move p
+
+
+def test_local_jinv_product_inverts_the_jacobian():
+    """The paper's J^-1(Phi) = J^-1(Phi_K) ... J^-1(Phi_1) is the inverse of the composed J."""
+    m = _local_metric(4, seed=2)
+    for p in ([0.0, 0.0, 0.0], [0.5, -0.7, 0.1]):
+        _, J, _ = oracle.local_compose(m, p)
+        np.testing.assert_allclose(oracle.local_jinv(m, p) @ J, np.eye(3), atol=1e-12)
+
+
+@pytest.mark.parametrize("field", [False, True])
+def test_local_geodesics_are_preimages_of_lines(field):
+    """Under the pull-back metric g = J^T J of a diffeomorphism, Phi maps geodesics to straight
+    lines (Section 5.2): Phi(x(s)) = Phi(p) + s J(p) v with |J(p) v| = 1, to O(h^4) for RK4."""
+    m = _local_metric(3, field=field)
+    x0, d0 = np.array([-1.0, 0.2, -0.5]), np.array([0.3, 0.5, -0.8])
+    v0 = d0 / np.sqrt(oracle.inner(m, x0, d0, d0))
+    q0, J0, _ = oracle.local_compose(m, x0)
+    assert abs(np.linalg.norm(J0 @ v0) - 1.0) < 1e-12
+    errs = []
+    for h, n in ((0.01, 200), (0.005, 400)):
+        xs, _ = oracle.integrate(m, oracle.RK4, h, n, x0, v0)
+        errs.append(max(np.linalg.norm(oracle.local_compose(m, xs[i])[0] - (q0 + i * h * J0 @ v0))
+                        for i in range(n + 1)))
+        bend = np.linalg.norm(xs[-1] - (x0 + n * h * v0))
+    assert errs[1] < 1e-9 and errs[0] / errs[1] > 10, errs
+    assert bend > 1e-2  # the geodesic is not itself a straight line
+
+
+def test_local_zero_amplitude_is_flat():
+    m = oracle.Metric(oracle.LOCAL, [[0.0, 0.0, 0.0]], [0.0], [[0.5] * 3], cutoff=0.0,
+                      direction=[[1.0, 0.0, 0.0]])
+    xs, _ = oracle.integrate(m, oracle.RK4, 0.01, 50, [0.1, 0.2, 0.3], [0.0, 0.6, 0.8])
+    np.testing.assert_allclose(xs[-1], [0.1, 0.2 + 0.3, 0.3 + 0.4], atol=1e-14)
