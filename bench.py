@@ -43,6 +43,12 @@ def workload(name: str, resolution: str | None = None) -> scenes.Workload:
         w = scenes.config_1080p_twist()
     elif name == "parity_64":
         w = scenes.config_parity_64()
+    elif name == "quad_lattice":
+        w = scenes.config_quad_lattice()
+    elif name == "paraboloid_lattice":
+        w = scenes.config_paraboloid_lattice()
+    elif name == "local8_lattice":
+        w = scenes.config_local_lattice(K=8)
     else:
         raise SystemExit(f"unknown workload {name}")
     if resolution:
@@ -59,6 +65,19 @@ def algorithmic_flops(rk4_steps: int, bump_terms: int) -> int:
     """27 flops per bump term summed (K per RHS dense; the ray's cell list culled), plus the
     per-RHS and per-step work outside the bump sums."""
     return bump_terms * FLOPS_PER_BUMP + rk4_steps * (4 * FLOPS_PER_RHS_EXTRA + FLOPS_PER_STEP_EXTRA)
+
+
+FLOPS_PER_LOCAL_MAP = 87         # jet push through one local map without a field (FMA = 2 flops)
+FLOPS_PER_LOCAL_MAP_FIELD = 217  # the same with the affine field B_k
+FLOPS_PER_LOCAL_SOLVE = 50       # J a = -w by the adjugate, per RHS
+
+
+def algorithmic_flops_local(rk4_steps: int, metric) -> int:
+    """Per RK4 step: four RHS, each the jet push through every map plus the 3x3 solve."""
+    K = metric.n_bumps
+    n_field = 0 if metric.field is None else int(np.count_nonzero(np.abs(np.asarray(metric.field)).reshape(K, -1).sum(1)))
+    rhs = FLOPS_PER_LOCAL_MAP * (K - n_field) + FLOPS_PER_LOCAL_MAP_FIELD * n_field + FLOPS_PER_LOCAL_SOLVE
+    return rk4_steps * (4 * rhs + FLOPS_PER_STEP_EXTRA)
 
 
 def kernel_source_hash() -> str:
@@ -310,7 +329,8 @@ def bench_gpu(args):
     rays = N * args.steps * world
     value = rays / total_s / 1e6
     mean_ms = sum(kernel_ms) / len(kernel_ms)
-    flops = algorithmic_flops(steps_total, evals_total)
+    flops = (algorithmic_flops_local(steps_total, w.metric) if w.metric.kind == scenes.METRIC_DIFFEO_LOCAL
+             else algorithmic_flops(steps_total, evals_total))
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -370,7 +390,9 @@ def bench_gpu(args):
 
     if rank != 0:
         return 0
-    traffic = dram_traffic("k_trace_1080p_64")
+    # the committed DRAM count belongs to the culled 1080p / 64-bump launch only
+    traffic = (dram_traffic("k_trace_1080p_64")
+               if args.workload == "1080p_64" and not args.resolution and not args.dense else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
@@ -391,7 +413,8 @@ def bench_gpu(args):
                      "flops_per_launch": flops, "bump_terms_per_launch": evals_total,
                      "bump_terms_per_rhs": evals_total / max(1, 4 * steps_total),
                      "rk4_steps_per_launch": steps_total, "kernel_ms": mean_ms,
-                     "sums": "dense" if args.dense else "cull grid"},
+                     "sums": ("jet through the composed local maps" if w.metric.kind == scenes.METRIC_DIFFEO_LOCAL
+                              else ("dense" if args.dense else "cull grid"))},
         "dense_kernel": dense,
         "clocks": clk,
         "gpu_launches": args.steps,
@@ -669,7 +692,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["rgeo", "reference"], default="rgeo")
     ap.add_argument("--workload", default="1080p_64",
-                    choices=["1080p_64", "1080p_twist", "parity_64", "batch16", "anim120", "surrogate", "infer"])
+                    choices=["1080p_64", "1080p_twist", "parity_64", "quad_lattice", "paraboloid_lattice",
+                             "local8_lattice", "batch16",
+                             "anim120", "surrogate", "infer"])
     ap.add_argument("--rows", type=int, default=1 << 23, help="rows for --workload infer")
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define RGEO_ABI_VERSION 1
+#define RGEO_ABI_VERSION 2
 
 typedef enum {
   RGEO_OK = 0,
@@ -55,7 +55,8 @@ typedef enum {
 
 typedef enum {
   RGEO_METRIC_GRAPH_BUMPS = 0, /* graph of f (Eq. 5.2), f a sum of Gaussian bumps (Eq. 6.1) */
-  RGEO_METRIC_DIFFEO_TWIST = 1 /* pull-back through the twist of Section 5.2 (Eq. 5.6) */
+  RGEO_METRIC_DIFFEO_TWIST = 1, /* pull-back through the twist of Section 5.2 (Eq. 5.6) */
+  RGEO_METRIC_DIFFEO_LOCAL = 2  /* pull-back through a composition of local maps (Section 6) */
 } rgeo_metric_kind;
 
 typedef enum { RGEO_RK4 = 0, RGEO_EULER = 1 } rgeo_integrator;
@@ -83,7 +84,20 @@ typedef struct rgeo_scene rgeo_scene;   /* opaque, owns device memory */
  * each cell records which bumps' supports meet it, and a point's sums run over
  * its cell's bumps only; excluded bumps are exactly zero there, so the result is
  * the same sum up to float32 summation order.  For the twist, twist_rate k gives
- * Phi(x, y, z) = (cos(kz) x - sin(kz) y, sin(kz) x + cos(kz) y, z) (k = 1 in the paper). */
+ * Phi(x, y, z) = (cos(kz) x - sin(kz) y, sin(kz) x + cos(kz) y, z) (k = 1 in the paper).
+ *
+ * For RGEO_METRIC_DIFFEO_LOCAL, n_bumps = K (1..RGEO_MAX_LOCAL_MAPS) local maps
+ *   Phi_k(p) = p + f_k(p) V_k(p),  f_k(p) = a_k exp(-|p - c_k|^2 / (2 sigma_k^2)),
+ *   V_k(p) = v_k + B_k (p - c_k)
+ * (Section 6, "Using diffeomorphism", with the vector field V affine) are composed as
+ * Phi = Phi_0 o Phi_1 o ... o Phi_{K-1} (map K - 1 acts first; Section 6, "Composing
+ * diffeomorphisms") and the metric is g = J(Phi)^T J(Phi) (Eq. 5.6).  center, amplitude
+ * and sigma (isotropic: equal triple) describe f_k, untruncated (cutoff_sigmas, affine_b
+ * and quad_A unused; the last two must be zero); direction [K*3] holds v_k and field
+ * [K*9] (row-major B_k, may be NULL for B_k = 0) the linear part of V_k.  With no field,
+ * each map must satisfy |a_k| |v_k| e^{-1/2} / sigma_k < 1 (then p -> p + f_k(p) v_k is a
+ * diffeomorphism of R^3); with a field, keeping each map a diffeomorphism is up to the
+ * caller. */
 typedef struct {
   int32_t kind;            /* rgeo_metric_kind */
   int32_t n_bumps;         /* K >= 0 (graph only); at most RGEO_MAX_BUMPS */
@@ -97,9 +111,12 @@ typedef struct {
   int32_t cull_grid;       /* bump-support cull grid of G^3 cells: 0 = automatic (G = 64 for
                               >= 16 isotropic truncated bumps), -1 = none, 4..128 = that G */
   int32_t reserved[3];     /* must be zero */
+  const float *direction;  /* HOST [K*3] v_k (local maps only; else ignored) */
+  const float *field;      /* HOST [K*9] B_k or NULL (local maps only; else ignored) */
 } rgeo_metric_desc;
 
 #define RGEO_MAX_BUMPS 4096
+#define RGEO_MAX_LOCAL_MAPS 64
 
 /* Pinhole observer: position p, forward and up vectors (need not be unit or
  * orthogonal; up must not be parallel to forward), vertical field of view in

@@ -21,7 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librgeo.so")
 
 RGEO_OK, RGEO_EINVAL, RGEO_ENOMEM, RGEO_ECUDA, RGEO_ETIMEOUT, RGEO_EUNSUPPORTED, RGEO_EDEVICE = range(7)
-RGEO_METRIC_GRAPH_BUMPS, RGEO_METRIC_DIFFEO_TWIST = 0, 1
+RGEO_METRIC_GRAPH_BUMPS, RGEO_METRIC_DIFFEO_TWIST, RGEO_METRIC_DIFFEO_LOCAL = 0, 1, 2
+RGEO_MAX_LOCAL_MAPS = 64
+RGEO_ABI_VERSION = 2  # include/rgeo.h; the loaded library must report the same
 RGEO_RK4, RGEO_EULER = 0, 1
 RGEO_SHADE_LAMBERT, RGEO_SHADE_PSEUDO = 0, 1
 RGEO_FLAG_ENERGY_DIAG = 1
@@ -54,7 +56,8 @@ class rgeo_metric_desc(ctypes.Structure):
                 ("center", ctypes.POINTER(ctypes.c_float)), ("amplitude", ctypes.POINTER(ctypes.c_float)),
                 ("sigma", ctypes.POINTER(ctypes.c_float)), ("affine_b", ctypes.c_float * 3),
                 ("quad_A", ctypes.c_float * 9), ("cutoff_sigmas", ctypes.c_float),
-                ("twist_rate", ctypes.c_float), ("cull_grid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("twist_rate", ctypes.c_float), ("cull_grid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("direction", ctypes.POINTER(ctypes.c_float)), ("field", ctypes.POINTER(ctypes.c_float))]
 
 
 class rgeo_camera(ctypes.Structure):
@@ -423,14 +426,23 @@ def metric_desc(m: scenes.Metric):
     s = np.ascontiguousarray(m.sigma, np.float32).reshape(-1)
     d = rgeo_metric_desc()
     d.kind = m.kind
-    d.n_bumps = a.shape[0] if m.kind == RGEO_METRIC_GRAPH_BUMPS else 0
+    d.n_bumps = a.shape[0] if m.kind != RGEO_METRIC_DIFFEO_TWIST else 0
     d.center, d.amplitude, d.sigma = (_fptr(c), _fptr(a), _fptr(s)) if d.n_bumps else (None, None, None)
+    keep = [c, a, s]
+    if m.kind == RGEO_METRIC_DIFFEO_LOCAL:
+        dv = np.ascontiguousarray(m.direction, np.float32).reshape(-1)
+        keep.append(dv)
+        d.direction = _fptr(dv)
+        if getattr(m, "field", None) is not None:
+            fb = np.ascontiguousarray(m.field, np.float32).reshape(-1)
+            keep.append(fb)
+            d.field = _fptr(fb)
     d.affine_b = (ctypes.c_float * 3)(*m.affine_b)
     d.quad_A = (ctypes.c_float * 9)(*m.quad_A)
     d.cutoff_sigmas = m.cutoff
     d.twist_rate = m.twist_rate
     d.cull_grid = getattr(m, "cull_grid", 0)
-    return d, (c, a, s)
+    return d, tuple(keep)
 
 
 def camera_struct(cam: scenes.Camera) -> rgeo_camera:

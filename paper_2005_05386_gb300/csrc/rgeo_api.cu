@@ -125,7 +125,7 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
     p.cull_G = m.cull_G;
     p.cull_words = m.cull_words;
   }
-  p.K = m.kind == RGEO_METRIC_GRAPH_BUMPS ? m.K : 0;
+  p.K = m.kind == RGEO_METRIC_DIFFEO_TWIST ? 0 : m.K;
   p.kind = m.kind;
   p.aniso = m.aniso;
   p.skippable = m.skippable;
@@ -190,14 +190,81 @@ int32_t rgeo_abi_version(void) { return RGEO_ABI_VERSION; }
 
 const char *rgeo_last_error(void) { return g_last_error.c_str(); }
 
+}  // extern "C"
+
+namespace {
+
+// The composition of local maps (kind 2): validated, packed five float4 per map
+// (the layout in rgeo_internal.h) and uploaded.
+rgeo_status create_local_metric(const rgeo_metric_desc *desc, rgeo_metric **out) {
+  const int K = desc->n_bumps;
+  if (K < 1 || K > RGEO_MAX_LOCAL_MAPS)
+    return fail(RGEO_EINVAL, "rgeo_metric_create: local maps need 1 <= n_bumps <= RGEO_MAX_LOCAL_MAPS");
+  for (int i = 0; i < 3; i++)
+    if (desc->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_metric_create: reserved fields must be zero");
+  if (!desc->center || !desc->amplitude || !desc->sigma || !desc->direction)
+    return fail(RGEO_EINVAL, "rgeo_metric_create: local maps need center, amplitude, sigma and direction");
+  for (int i = 0; i < 3; i++)
+    if (desc->affine_b[i] != 0.f) return fail(RGEO_EINVAL, "rgeo_metric_create: local maps take no affine_b");
+  for (int i = 0; i < 9; i++)
+    if (desc->quad_A[i] != 0.f) return fail(RGEO_EINVAL, "rgeo_metric_create: local maps take no quad_A");
+  if (!finite_all(desc->center, 3 * (size_t)K) || !finite_all(desc->amplitude, K) ||
+      !finite_all(desc->sigma, 3 * (size_t)K) || !finite_all(desc->direction, 3 * (size_t)K) ||
+      (desc->field && !finite_all(desc->field, 9 * (size_t)K)))
+    return fail(RGEO_EINVAL, "rgeo_metric_create: non-finite local-map value");
+  std::vector<float4> table((size_t)rgeo::kLocalStride * K);
+  bool any_field = false;
+  for (int k = 0; k < K; k++) {
+    const float *sg = desc->sigma + 3 * k, *c = desc->center + 3 * k, *v = desc->direction + 3 * k;
+    if (!(sg[0] > 0.f) || sg[1] != sg[0] || sg[2] != sg[0])
+      return fail(RGEO_EINVAL, "rgeo_metric_create: local maps need isotropic sigma > 0");
+    const float *B = desc->field ? desc->field + 9 * k : nullptr;
+    bool field = false;
+    if (B)
+      for (int i = 0; i < 9; i++) field |= B[i] != 0.f;
+    any_field |= field;
+    const double vn = std::sqrt((double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2]);
+    if (!field && std::fabs((double)desc->amplitude[k]) * vn * std::exp(-0.5) / sg[0] >= 1.0)
+      return fail(RGEO_EINVAL, "rgeo_metric_create: local map is not a diffeomorphism "
+                               "(|a| |v| e^-1/2 / sigma must be < 1)");
+    const float q = 1.f / (sg[0] * sg[0]);
+    float4 *t = table.data() + (size_t)rgeo::kLocalStride * k;
+    t[0] = make_float4(c[0], c[1], c[2], desc->amplitude[k]);
+    t[1] = make_float4(v[0], v[1], v[2], (float)(-0.5 * q * 1.4426950408889634));
+    t[2] = make_float4(B ? B[0] : 0.f, B ? B[1] : 0.f, B ? B[2] : 0.f, q);
+    t[3] = make_float4(B ? B[3] : 0.f, B ? B[4] : 0.f, B ? B[5] : 0.f, field ? 1.f : 0.f);
+    t[4] = make_float4(B ? B[6] : 0.f, B ? B[7] : 0.f, B ? B[8] : 0.f, 0.f);
+  }
+  (void)any_field;
+  rgeo_metric *m = new rgeo_metric();
+  std::memset(&m->d, 0, sizeof(m->d));
+  cudaGetDevice(&m->device);
+  m->d.kind = desc->kind;
+  m->d.K = K;
+  cudaError_t e = upload(&m->d.bumps, table.data(), table.size());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) {
+    free_metric(m);
+    return cuda_fail(e, "rgeo_metric_create");
+  }
+  *out = m;
+  return RGEO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) {
   g_last_error.clear();
   if (!out) return fail(RGEO_EINVAL, "rgeo_metric_create: out is NULL");
   *out = nullptr;
   if (!desc) return fail(RGEO_EINVAL, "rgeo_metric_create: desc is NULL");
   const int K = desc->n_bumps;
-  if (desc->kind != RGEO_METRIC_GRAPH_BUMPS && desc->kind != RGEO_METRIC_DIFFEO_TWIST)
+  if (desc->kind != RGEO_METRIC_GRAPH_BUMPS && desc->kind != RGEO_METRIC_DIFFEO_TWIST &&
+      desc->kind != RGEO_METRIC_DIFFEO_LOCAL)
     return fail(RGEO_EINVAL, "rgeo_metric_create: unknown metric kind");
+  if (desc->kind == RGEO_METRIC_DIFFEO_LOCAL) return create_local_metric(desc, out);
   if (K < 0 || K > RGEO_MAX_BUMPS) return fail(RGEO_EINVAL, "rgeo_metric_create: n_bumps out of range");
   for (int i = 0; i < 3; i++)
     if (desc->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_metric_create: reserved fields must be zero");
@@ -482,8 +549,7 @@ rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *inst, rgeo_batch *
                            q.shading, q.flags, &q.out);
     table[i].rays_per_thread = 1;
     total += table[i].n_items;
-    if (q.metric->d.kind == RGEO_METRIC_GRAPH_BUMPS)
-      max_f4 = std::max(max_f4, rgeo::packed_float4s(q.metric->d.K, q.metric->d.aniso));
+    max_f4 = std::max(max_f4, rgeo::table_float4s(q.metric->d.kind, q.metric->d.K, q.metric->d.aniso));
   }
   rgeo_batch *b = new rgeo_batch();
   b->n = n;

@@ -30,6 +30,14 @@ constexpr int kIsoPairStride = 4;  // float4 per bump pair
 constexpr int kAnisoStride = 3;    // float4 per bump
 // float4 count of a packed table of K bumps
 __host__ __device__ inline int packed_float4s(int K, int aniso) { return aniso ? kAnisoStride * K : kIsoPairStride * ((K + 1) / 2); }
+// Local maps (metric kind 2), five float4 each:
+//   (c.x, c.y, c.z, a), (v.x, v.y, v.z, qn2), (B row 0, q), (B row 1, has_field), (B row 2, 0)
+// with q = 1 / sigma^2 and qn2 = -q log2(e) / 2, so that f = a * 2^(qn2 |p - c|^2).
+constexpr int kLocalStride = 5;
+// float4s of a metric's device table by kind (0 graph, 1 twist, 2 local maps).
+__host__ __device__ inline int table_float4s(int kind, int K, int aniso) {
+  return kind == 2 ? kLocalStride * K : (kind == 1 ? 0 : packed_float4s(K, aniso));
+}
 
 struct MetricDev {
   int kind;            // 0 graph, 1 twist

@@ -28,6 +28,7 @@ namespace {
 constexpr int MK_GRAPH_ISO = 0;
 constexpr int MK_GRAPH_ANISO = 1;
 constexpr int MK_TWIST = 2;
+constexpr int MK_LOCAL = 3;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kSegTries = 4096;  // candidates per training segment under a far-field bound
 
@@ -266,6 +267,113 @@ __device__ __forceinline__ F3 accel_twist(float k, F3 x, F3 v) {
 
 // Per-launch context of the bump sums: the cull-grid header and the lanes that
 // take part in the current call (for the warp-wide mask reduction).
+// ------------------------------------------------------- local maps
+// One local map of Section 6 ("Using diffeomorphism"): Phi(p) = p + f(p) V(p), f the
+// Gaussian of Eq. 6.1 (isotropic, untruncated), V(p) = v + B (p - c).  local_push moves
+// the 2-jet of a curve through it -- y <- Phi(y), u <- J u, w <- J w + D^2 Phi[u, u] (the
+// Hessian of a composition, Eq. 6.3, taken along u) -- and the Jacobian product M <- J M
+// (the chain rule of Section 6, "Composing diffeomorphisms"), with
+//   J z = z + V (grad f . z) + f B z,  D^2 Phi[u, u] = V (u^T Hess f u) + 2 (grad f . u) B u,
+//   grad f = -q f d,  u^T Hess f u = q f (q (d . u)^2 - |u|^2),  d = y - c.
+struct Jet {
+  F3 y, u, w;
+  float M[9];  // row-major: M[3 s + j] = d_j (x_s)
+};
+
+__device__ __forceinline__ void local_push(const float4 *__restrict__ sb, int k, Jet &j, bool second) {
+  const float4 t0 = sb[kLocalStride * k], t1 = sb[kLocalStride * k + 1], t2 = sb[kLocalStride * k + 2],
+               t3 = sb[kLocalStride * k + 3], t4 = sb[kLocalStride * k + 4];
+  const F3 d = j.y - f3(t0.x, t0.y, t0.z);
+  const float f = t0.w * ex2_approx(t1.w * dot(d, d));
+  const float q = t2.w;
+  const float mqf = -q * f;
+  const F3 gr = mqf * d;
+  const bool field = t3.w != 0.f;
+  const F3 B0 = f3(t2.x, t2.y, t2.z), B1 = f3(t3.x, t3.y, t3.z), B2 = f3(t4.x, t4.y, t4.z);
+  F3 V = f3(t1.x, t1.y, t1.z);
+  if (field) V = V + f3(dot(B0, d), dot(B1, d), dot(B2, d));
+  for (int c = 0; c < 3; ++c) {
+    const F3 col = f3(j.M[c], j.M[3 + c], j.M[6 + c]);
+    F3 nc = axpy(dot(gr, col), V, col);
+    if (field) nc = axpy(f, f3(dot(B0, col), dot(B1, col), dot(B2, col)), nc);
+    j.M[c] = nc.x;
+    j.M[3 + c] = nc.y;
+    j.M[6 + c] = nc.z;
+  }
+  if (second) {
+    const float du = dot(d, j.u);
+    const float hq = q * f * fmaf(q * du, du, -dot(j.u, j.u));  // u^T Hess f u
+    const float gu = mqf * du;                                  // grad f . u
+    F3 w = axpy(dot(gr, j.w) + hq, V, j.w);
+    F3 u = axpy(gu, V, j.u);
+    if (field) {
+      const F3 Bu = f3(dot(B0, j.u), dot(B1, j.u), dot(B2, j.u));
+      const F3 Bw = f3(dot(B0, j.w), dot(B1, j.w), dot(B2, j.w));
+      w = axpy(2.f * gu, Bu, axpy(f, Bw, w));
+      u = axpy(f, Bu, u);
+    }
+    j.w = w;
+    j.u = u;
+  }
+  j.y = axpy(f, V, j.y);
+}
+
+// Jacobian of the composition Phi = Phi_1 o ... o Phi_K at x (map K - 1 acts first).
+__device__ __forceinline__ void local_jacobian(const float4 *sb, int K, F3 x, Jet &j) {
+  j.y = x;
+  j.u = j.w = f3(0.f, 0.f, 0.f);
+  for (int i = 0; i < 9; ++i) j.M[i] = (i % 4 == 0) ? 1.f : 0.f;
+  for (int k = K - 1; k >= 0; --k) local_push(sb, k, j, false);
+}
+
+// x'' = -J^-1 D^2 Phi[v, v]: Theorem 5.1 (Gamma^m_ij v_i v_j = sum_s [J^-1]_ms v^T H(x_s) v)
+// for the composition, with J^-1 w from the adjugate (columns r1 x r2, r2 x r0, r0 x r1 of
+// the rows r_s of J, over det J).
+__device__ __forceinline__ F3 accel_local(const float4 *sb, int K, F3 x, F3 v) {
+  Jet j;
+  j.y = x;
+  j.u = v;
+  j.w = f3(0.f, 0.f, 0.f);
+  for (int i = 0; i < 9; ++i) j.M[i] = (i % 4 == 0) ? 1.f : 0.f;
+  for (int k = K - 1; k >= 0; --k) local_push(sb, k, j, true);
+  const F3 r0 = f3(j.M[0], j.M[1], j.M[2]), r1 = f3(j.M[3], j.M[4], j.M[5]), r2 = f3(j.M[6], j.M[7], j.M[8]);
+  const F3 c0 = cross(r1, r2), c1 = cross(r2, r0), c2 = cross(r0, r1);
+  const float inv = -1.f / dot(r0, c0);
+  return inv * axpy(j.w.x, c0, axpy(j.w.y, c1, j.w.z * c2));
+}
+
+// |J v|^2 in FP64 for the drift diagnostic (Eq. 5.6: g = J^T J).
+__device__ double local_energy(const float4 *sb, int K, F3 x, F3 v) {
+  double y[3] = {x.x, x.y, x.z}, M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  for (int k = K - 1; k >= 0; --k) {
+    const float4 t0 = sb[kLocalStride * k], t1 = sb[kLocalStride * k + 1], t2 = sb[kLocalStride * k + 2],
+                 t3 = sb[kLocalStride * k + 3], t4 = sb[kLocalStride * k + 4];
+    const double d[3] = {y[0] - t0.x, y[1] - t0.y, y[2] - t0.z};
+    const double q = t2.w, f = t0.w * exp(-0.5 * q * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    const double B[9] = {t2.x, t2.y, t2.z, t3.x, t3.y, t3.z, t4.x, t4.y, t4.z};
+    double V[3], gr[3], N[9];
+    for (int s = 0; s < 3; ++s) {
+      V[s] = (double)(s == 0 ? t1.x : (s == 1 ? t1.y : t1.z)) + B[3 * s] * d[0] + B[3 * s + 1] * d[1] +
+             B[3 * s + 2] * d[2];
+      gr[s] = -q * f * d[s];
+    }
+    for (int s = 0; s < 3; ++s)
+      for (int c = 0; c < 3; ++c) {
+        double acc = M[3 * s + c] + V[s] * (gr[0] * M[c] + gr[1] * M[3 + c] + gr[2] * M[6 + c]);
+        acc += f * (B[3 * s] * M[c] + B[3 * s + 1] * M[3 + c] + B[3 * s + 2] * M[6 + c]);
+        N[3 * s + c] = acc;
+      }
+    for (int i = 0; i < 9; ++i) M[i] = N[i];
+    for (int s = 0; s < 3; ++s) y[s] += f * V[s];
+  }
+  double e = 0.0;
+  for (int s = 0; s < 3; ++s) {
+    const double r = M[3 * s] * v.x + M[3 * s + 1] * v.y + M[3 * s + 2] * v.z;
+    e += r * r;
+  }
+  return e;
+}
+
 struct SumCtx {
   float4 ghdr;
   unsigned pmask;
@@ -284,6 +392,7 @@ __device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, cons
     *cx.evals += (unsigned)P.K;
     return accel_graph_aniso<INSIDE>(P, sb, P.K, x, v, inside);
   }
+  if (MK == MK_LOCAL) return accel_local(sb, P.K, x, v);
   return accel_twist(P.twist_k, x, v);
 }
 
@@ -321,6 +430,7 @@ __device__ F3 grad_f(const TraceParams &P, const float4 *sb, F3 x) {
 // g_x(v, v) in FP64 (Eq. 3.1 with Eq. 5.2 or Eq. 5.6); used only by the drift diagnostic.
 template <int MK>
 __device__ double energy(const TraceParams &P, const float4 *sb, F3 x, F3 v) {
+  if (MK == MK_LOCAL) return local_energy(sb, P.K, x, v);
   if (MK == MK_TWIST) {
     const float k = P.twist_k;
     float s, c;
@@ -603,6 +713,12 @@ __device__ void init_ray(const TraceParams &P, const float4 *sb, int pix, Ray &r
     const float j0 = c * d.x - s * d.y - P.twist_k * Y * d.z;
     const float j1 = s * d.x + c * d.y + P.twist_k * X * d.z;
     gdd = j0 * j0 + j1 * j1 + d.z * d.z;
+  } else if (MK == MK_LOCAL) {
+    Jet jt;
+    local_jacobian(sb, P.K, x, jt);
+    const F3 jd = f3(dot(f3(jt.M[0], jt.M[1], jt.M[2]), d), dot(f3(jt.M[3], jt.M[4], jt.M[5]), d),
+                     dot(f3(jt.M[6], jt.M[7], jt.M[8]), d));
+    gdd = dot(jd, jd);
   } else {
     const F3 g = grad_f<MK>(P, sb, x);
     const float gd = dot(g, d);
@@ -643,7 +759,7 @@ __device__ void finish_ray(const TraceParams &P, const float4 *sb, const float4 
 // Stage the bump table and the spheres in shared memory; returns the bump part size.
 template <int MK>
 __device__ __forceinline__ int stage_shared(const TraceParams &P, float4 *smem) {
-  const int nb4 = MK == MK_TWIST ? 0 : packed_float4s(P.K, MK == MK_GRAPH_ANISO);
+  const int nb4 = MK == MK_TWIST ? 0 : (MK == MK_LOCAL ? kLocalStride * P.K : packed_float4s(P.K, MK == MK_GRAPH_ANISO));
   for (int i = threadIdx.x; i < nb4; i += blockDim.x) smem[i] = P.bumps[i];
   if (P.nodes == nullptr)  // spheres are tested one by one only when there is no BVH
     for (int i = threadIdx.x; i < P.S; i += blockDim.x) smem[nb4 + i] = P.spheres[i];
@@ -690,7 +806,7 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
   F3 x = xhi(r);
   const F3 v = vhi(r);
   bool moved = false, finished = false;
-  if (MK != MK_TWIST && P.skippable && !inside) {
+  if (MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
     const float t = support_entry<MK>(sb, P.K, x, v);
     HitRec hr;
     if (scene_hit(P, ss, x, v, t, hr)) {
@@ -983,7 +1099,7 @@ template <bool SMEM>
 __device__ __forceinline__ void warp_load_table(const TraceParams &P, float4 *tab, const float4 *&sb) {
   if (SMEM) {
     const unsigned lane = threadIdx.x & 31u;
-    const int need = P.kind != 1 ? packed_float4s(P.K, P.aniso) : 0;
+    const int need = table_float4s(P.kind, P.K, P.aniso);
     for (int k = (int)lane; k < need; k += 32) tab[k] = __ldg(P.bumps + k);
     sb = tab;
   } else {
@@ -1589,7 +1705,7 @@ __global__ void k_ffma(float *out, int iters, int mode) {
 template <int MK, int INTEG>
 cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   const size_t smem =
-      (size_t)((MK == MK_TWIST ? 0 : packed_float4s(p.K, MK == MK_GRAPH_ANISO)) + (p.nodes ? 0 : p.S)) *
+      (size_t)(table_float4s(p.kind, p.K, MK == MK_GRAPH_ANISO) + (p.nodes ? 0 : p.S)) *
       sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
   const bool x2 = MK == MK_GRAPH_ISO && p.rays_per_thread == 2 && p.cull_masks == nullptr;
@@ -1650,7 +1766,10 @@ cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_in
   if (n <= 0) return cudaSuccess;
   // per-warp bump tables up to 1024 float4 (512 pairs); larger tables are read through L1
   const int table_f4 = max_table_f4 <= 1024 ? max_table_f4 : 0;
-  const int mk = kind == 1 ? MK_TWIST : (aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO);
+  const int mk = kind == 2 ? MK_LOCAL : (kind == 1 ? MK_TWIST : (aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
+  if (mk == MK_LOCAL)
+    return integrator == 0 ? launch_batch_t<MK_LOCAL, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
+                           : launch_batch_t<MK_LOCAL, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
   if (mk == MK_GRAPH_ISO)
     return integrator == 0 ? launch_batch_t<MK_GRAPH_ISO, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
                            : launch_batch_t<MK_GRAPH_ISO, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
@@ -1718,7 +1837,8 @@ cudaError_t launch_set_time(float *t, float value, cudaStream_t st) {
 }
 
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st) {
-  const int mk = p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO);
+  const int mk = p.kind == 2 ? MK_LOCAL : (p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
+  if (mk == MK_LOCAL) return p.integrator == 0 ? launch_one<MK_LOCAL, 0>(p, st) : launch_one<MK_LOCAL, 1>(p, st);
   if (mk == MK_GRAPH_ISO) return p.integrator == 0 ? launch_one<MK_GRAPH_ISO, 0>(p, st) : launch_one<MK_GRAPH_ISO, 1>(p, st);
   if (mk == MK_GRAPH_ANISO) return p.integrator == 0 ? launch_one<MK_GRAPH_ANISO, 0>(p, st) : launch_one<MK_GRAPH_ANISO, 1>(p, st);
   return p.integrator == 0 ? launch_one<MK_TWIST, 0>(p, st) : launch_one<MK_TWIST, 1>(p, st);

@@ -34,6 +34,7 @@ STREAM_BUMPS, STREAM_SPHERES, STREAM_MESH, STREAM_ANIM, STREAM_PIXELS = 1, 2, 3,
 
 METRIC_GRAPH_BUMPS = 0
 METRIC_DIFFEO_TWIST = 1
+METRIC_DIFFEO_LOCAL = 2
 INTEGRATOR_RK4 = 0
 INTEGRATOR_EULER = 1
 SHADING_LAMBERT = 0
@@ -103,6 +104,8 @@ class Metric:
     cutoff: float = 4.0
     twist_rate: float = 1.0
     cull_grid: int = 0          # bump-support cull grid: 0 automatic, -1 none, G in [4, 128]
+    direction: np.ndarray = None  # local maps: [K, 3] v_k of p + f_k(p) (v_k + B_k (p - c_k))
+    field: np.ndarray = None      # local maps: [K, 3, 3] B_k, or None
 
     @property
     def n_bumps(self) -> int:
@@ -216,6 +219,35 @@ def displaced_sphere_mesh(seed: int, n_lon: int, n_lat: int, centre=(0.0, 0.0, 2
     return (np.asarray(verts, np.float32), np.asarray(tris, np.int32), rmax)
 
 
+# the 12 triangles of an axis-aligned box whose corner k has x from bit 0, y from bit 1, z from bit 2
+_BOX_TRIS = ((0, 2, 6), (0, 6, 4), (1, 5, 7), (1, 7, 3), (0, 4, 5), (0, 5, 1),
+             (2, 3, 7), (2, 7, 6), (0, 1, 3), (0, 3, 2), (4, 6, 7), (4, 7, 5))
+
+
+def lattice_mesh(half: float = 4.0, spacing: float = 1.0, width: float = 0.08):
+    """The regular grid of R^3 the paper renders (Section 4, Figures of Sections 5-6): an
+    axis-parallel square bar of the given width through every grid line {-half, -half +
+    spacing, ..., half}^2 along each axis, each bar a closed box of 12 triangles extending
+    to +-(half + width / 2).  Spacing 1 and half 4: 243 bars, 2,916 triangles.
+    Returns (verts [V,3] f32, tris [T,3] i32)."""
+    ticks = np.arange(-half, half + 1e-9, spacing)
+    hw, ext = width / 2.0, half + width / 2.0
+    verts, tris = [], []
+    for axis in range(3):
+        o1, o2 = [a for a in range(3) if a != axis]
+        for p in ticks:
+            for q in ticks:
+                lo, hi = np.empty(3), np.empty(3)
+                lo[axis], hi[axis] = -ext, ext
+                lo[o1], hi[o1] = p - hw, p + hw
+                lo[o2], hi[o2] = q - hw, q + hw
+                base = len(verts)
+                for k in range(8):
+                    verts.append([hi[0] if k & 1 else lo[0], hi[1] if k & 2 else lo[1], hi[2] if k & 4 else lo[2]])
+                tris.extend([base + a, base + b, base + c] for a, b, c in _BOX_TRIS)
+    return np.asarray(verts, np.float32), np.asarray(tris, np.int32)
+
+
 def random_spheres(seed: int, n: int, box: float, r_lo: float, r_hi: float, avoid):
     """n non-overlapping spheres (centres U[-box, box]^3, radii U[r_lo, r_hi]).
 
@@ -289,6 +321,61 @@ def config_4k_1024(seed: int = 4) -> Workload:
 
 
 BATCH_RESOLUTIONS = ((256, 256), (512, 512), (1280, 720), (1920, 1080))
+
+
+def _lattice_scene():
+    verts, tris = lattice_mesh()
+    return Scene(np.zeros((0, 4), np.float32), verts, tris, np.array([[0.85, 0.85, 0.85]], np.float32))
+
+
+def config_quad_lattice(width: int = 1920, height: int = 1080, look: str = "x") -> Workload:
+    """Section 5.1's example: the graph metric of f(x, y, z) = x^2 + y^2 - z^2 (A = diag(2, 2, -2)),
+    seen from the centre of a lattice cell looking along x (or z), through the regular grid
+    (spacing 1, bars 0.08 wide, |x_i| <= 4); pseudo-colour shading, h = 0.005, <= 2000 steps."""
+    metric = Metric(quad_A=(2.0, 0.0, 0.0, 0.0, 2.0, 0.0, 0.0, 0.0, -2.0), cutoff=0.0)
+    fwd, up = ((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)) if look == "x" else ((0.0, 0.0, 1.0), (0.0, 1.0, 0.0))
+    cam = Camera(pos=(0.5, 0.5, 0.5), forward=fwd, up=up)
+    return Workload(f"quad_lattice_look_{look}", width, height, 0.005, 2000, metric, _lattice_scene(), cam,
+                    shading=SHADING_PSEUDO)
+
+
+def config_paraboloid_lattice(width: int = 1920, height: int = 1080) -> Workload:
+    """The paraboloid f = x^2 + y^2 + z^2 (Section 3.3: its exponential map is not injective, so
+    grid points appear more than once) through the same lattice, looking along x."""
+    w = config_quad_lattice(width, height, "x")
+    w.metric = Metric(quad_A=(2.0, 0.0, 0.0, 0.0, 2.0, 0.0, 0.0, 0.0, 2.0), cutoff=0.0)
+    w.name = "paraboloid_lattice_look_x"
+    return w
+
+
+def local_maps(seed: int, K: int, lo=(-2.0, -2.0, -1.5), hi=(2.0, 2.0, 2.5), sigma=(0.5, 1.0),
+               slope: float = 0.6, field_scale: float = 0.1, with_field: bool = True) -> Metric:
+    """K local maps p + f_k(p) (v_k + B_k (p - c_k)) (Section 6): centres U[lo, hi], spreads
+    U[sigma], unit directions v_k, amplitudes a_k = +-slope sigma_k e^{1/2} (so that |a| |v|
+    e^{-1/2} / sigma = slope < 1), and for every other map a field B_k with entries
+    U[-field_scale, field_scale] (none when with_field is False)."""
+    rng = SplitMix64(sub_seed(seed, STREAM_BUMPS))
+    c = np.zeros((K, 3)); a = np.zeros(K); s = np.zeros((K, 3)); v = np.zeros((K, 3)); B = np.zeros((K, 3, 3))
+    for k in range(K):
+        c[k] = [rng.uniform(lo[i], hi[i]) for i in range(3)]
+        sg = rng.uniform(*sigma)
+        s[k] = sg
+        d = np.array([rng.uniform(-1.0, 1.0) for _ in range(3)])
+        v[k] = d / max(np.linalg.norm(d), 1e-6)
+        a[k] = (1.0 if rng.uniform(0.0, 1.0) < 0.5 else -1.0) * slope * sg * math.exp(0.5)
+        if with_field and k % 2 == 1:
+            B[k] = [[rng.uniform(-field_scale, field_scale) for _ in range(3)] for _ in range(3)]
+    return Metric(kind=METRIC_DIFFEO_LOCAL, center=c.astype(np.float32), amplitude=a.astype(np.float32),
+                  sigma=s.astype(np.float32), cutoff=0.0, direction=v.astype(np.float32),
+                  field=B.astype(np.float32) if with_field else None)
+
+
+def config_local_lattice(K: int = 8, seed: int = 5, width: int = 1920, height: int = 1080) -> Workload:
+    """The lattice under the pull-back metric of K composed local maps (Section 6): camera in a
+    cell at (0.5, 0.5, -2.5) looking +z, pseudo-colour, h = 0.005, <= 2000 steps."""
+    cam = Camera(pos=(0.5, 0.5, -2.5), forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0))
+    return Workload(f"local{K}_lattice", width, height, 0.005, 2000, local_maps(seed, K), _lattice_scene(), cam,
+                    shading=SHADING_PSEUDO, seed=seed)
 
 
 def config_batch16(seed: int = 3, n: int = 16):

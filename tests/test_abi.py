@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(rg):
 
 
 def test_abi_version(rg):
-    assert rg.rgeo_abi_version() == 1
+    assert rg.rgeo_abi_version() == rg.RGEO_ABI_VERSION == 2
 
 
 def _desc(rg, **kw):
@@ -66,6 +66,47 @@ def test_metric_validation(rg, bad):
         d.reserved[0] = 1
     elif bad == "count":
         d.n_bumps = rg.RGEO_MAX_BUMPS + 1
+    with pytest.raises(rg.RgeoError) as e:
+        rg.rgeo_metric_create(d)
+    assert e.value.status == rg.RGEO_EINVAL
+    assert rg.rgeo_last_error()
+
+
+def _local_desc(rg, **kw):
+    from paper_2005_05386_gb300 import scenes
+    m = scenes.local_maps(1, 3)
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return rg.metric_desc(m)
+
+
+@pytest.mark.parametrize("bad", ["not_diffeo", "count_zero", "count_max", "aniso", "quad", "affine", "direction",
+                                 "nan_field", "reserved"])
+def test_local_metric_validation(rg, bad):
+    """Compositions of local maps: rejected before any device work (no GPU needed)."""
+    from paper_2005_05386_gb300 import scenes
+    if bad == "not_diffeo":   # |a| |v| e^-1/2 / sigma >= 1 on a map without a field
+        m = scenes.local_maps(1, 3, with_field=False)
+        m.amplitude = m.amplitude * np.float32(2.0)
+        d, keep = rg.metric_desc(m)
+    else:
+        d, keep = _local_desc(rg)
+    if bad == "count_zero":
+        d.n_bumps = 0
+    elif bad == "count_max":
+        d.n_bumps = rg.RGEO_MAX_LOCAL_MAPS + 1
+    elif bad == "aniso":
+        keep[2][1] = keep[2][0] * 2
+    elif bad == "quad":
+        d.quad_A[0] = 1.0
+    elif bad == "affine":
+        d.affine_b[2] = 1.0
+    elif bad == "direction":
+        d.direction = None
+    elif bad == "nan_field":
+        keep[4][3] = np.nan
+    elif bad == "reserved":
+        d.reserved[2] = 1
     with pytest.raises(rg.RgeoError) as e:
         rg.rgeo_metric_create(d)
     assert e.value.status == rg.RGEO_EINVAL

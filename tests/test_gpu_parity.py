@@ -275,3 +275,12 @@ def test_twist_hits_lie_on_preimages_of_lines(rg):
         assert off < 5e-4, (q, off)
         checked += 1
     assert checked > 300
+
+
+@pytest.mark.parametrize("cfg", [scenes.config_quad_lattice, scenes.config_paraboloid_lattice])
+def test_parity_quadratic_metrics_through_the_lattice(rg, cfg):
+    """Section 5.1's f = x^2 + y^2 - z^2 and the paraboloid (non-injective exp map) through the
+    regular lattice (2,916 triangles), full 64x64 frame against the oracle."""
+    w = scenes.scaled(cfg(), 64, 64)
+    st = compare(_run(rg, w), oracle.trace(w), w.scene.n_spheres)
+    assert_parity(st, min_hits=1000)
