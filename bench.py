@@ -49,6 +49,8 @@ def workload(name: str, resolution: str | None = None) -> scenes.Workload:
         w = scenes.config_paraboloid_lattice()
     elif name == "local8_lattice":
         w = scenes.config_local_lattice(K=8)
+    elif name == "4k_1024":
+        w = scenes.config_4k_1024()
     else:
         raise SystemExit(f"unknown workload {name}")
     if resolution:
@@ -197,8 +199,11 @@ def measured_peaks() -> dict:
 
 
 def oracle_sample(w: scenes.Workload):
-    px = scenes.pixel_sample(w.n_pixels, w.seed + 1000, CPU_SAMPLE_FRACTION)
-    return px
+    """Seeded pixel sample for the oracle: 1 in 500, fewer for costly frames (about 10-30 s of
+    CPU work on 16 cores): the fraction shrinks with bumps above 64 and steps above 2000."""
+    cost = max(1.0, w.metric.n_bumps / 64.0) * max(1.0, w.max_steps / 2000.0)
+    frac = CPU_SAMPLE_FRACTION if cost <= 1.0 else min(CPU_SAMPLE_FRACTION, 512.0 / w.n_pixels)
+    return scenes.pixel_sample(w.n_pixels, w.seed + 1000, frac)
 
 
 def run_oracle(w, px, threads):
@@ -218,7 +223,7 @@ def cpu_baseline(w, threads=None):
     steps = int(o["steps"].astype(np.int64).sum())
     return {"value": len(px) / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(px)} seeded pixels of the {w.width}x{w.height} frame "
-                      f"(SplitMix64 1-in-{int(1 / CPU_SAMPLE_FRACTION)} sample), FP64, {dt:.2f} s wall",
+                      f"(SplitMix64 sample, 1 in {w.n_pixels / max(1, len(px)):.0f}), FP64, {dt:.2f} s wall",
             "rk4_steps_per_s": steps / dt}, px, o
 
 
@@ -693,7 +698,7 @@ def main():
     ap.add_argument("--impl", choices=["rgeo", "reference"], default="rgeo")
     ap.add_argument("--workload", default="1080p_64",
                     choices=["1080p_64", "1080p_twist", "parity_64", "quad_lattice", "paraboloid_lattice",
-                             "local8_lattice", "batch16",
+                             "local8_lattice", "4k_1024", "batch16",
                              "anim120", "surrogate", "infer"])
     ap.add_argument("--rows", type=int, default=1 << 23, help="rows for --workload infer")
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
