@@ -795,6 +795,46 @@ __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, b
   }
 }
 
+// Warp-synchronous refill from a warp-private chunk of 32 consecutive items (one 8 x 4 pixel
+// tile) taken from the queue one chunk at a time: the rays a warp starts come from the same
+// tile, so its lanes stay closer together and the union of their cull cells stays smaller.
+// cnext / cend (the chunk's next and end item) are the same on every lane.
+template <int MK>
+__device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *sb, bool &active, bool &drained,
+                                            Ray &r, unsigned &cnext, unsigned &cend) {
+  const unsigned lane = threadIdx.x & 31u;
+  for (int pass = 0; pass < 2; ++pass) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+    if (!need) return;
+    if (cnext >= cend) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(P.counter, 32u);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      cnext = base;
+      cend = base + 32u;
+      if (base >= P.n_items) {
+        drained = true;
+        return;
+      }
+    }
+    const unsigned take = min((unsigned)__popc(need), cend - cnext);
+    const unsigned rank = (unsigned)__popc(need & ((1u << lane) - 1u));
+    if (((need >> lane) & 1u) && rank < take) {
+      const unsigned item = cnext + rank;
+      if (item < P.n_items) {
+        const unsigned tile = item >> 5, sub = item & 31u;
+        const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
+        const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
+        if (px < P.W && py < P.H) {
+          init_ray<MK>(P, sb, py * P.W + px, r);
+          active = true;
+        }
+      }
+    }
+    cnext += take;
+  }
+}
+
 // Before a step: closed-form advance through flat space when x lies outside every
 // truncated support (exact: Hess f = 0 there, Eq. 5.4), then the step budget.
 // a1 is the stage-1 acceleration at x; it is recomputed if x moves.  Returns false
@@ -905,8 +945,9 @@ __global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
   unsigned long long evals = 0;
   bool active = false, drained = false;
   Ray r;
+  unsigned cnext = 0u, cend = 0u;
   for (;;) {
-    refill<MK>(P, sb, active, drained, r);
+    refill_tile<MK>(P, sb, active, drained, r, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
       if (drained) break;
@@ -1144,13 +1185,14 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
   unsigned long long evals = 0;
   bool active = false, drained = false;
   Ray r;
+  unsigned cnext = 0u, cend = 0u;
   const float4 *sb = nullptr;
   src.load(i);
   warp_load_table<SMEM>(src.get(i), src.table(), sb);
   for (;;) {
     const TraceParams &P = src.get(i);
     const float4 *ss = P.spheres;
-    refill<MK>(P, sb, active, drained, r);
+    refill_tile<MK>(P, sb, active, drained, r, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
       if (drained) {
@@ -1162,6 +1204,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
         if (++visited >= n) break;
         i = (i + 1) % n;
         drained = false;
+        cnext = cend = 0u;
         src.load(i);
         warp_load_table<SMEM>(src.get(i), src.table(), sb);
       }
@@ -1240,32 +1283,44 @@ __device__ __forceinline__ void wave_load(const WaveArgs &W, int pix, Ray &r, in
 // As refill, but a ray of a later round resumes from its saved state.
 template <int MK>
 __device__ __forceinline__ void wave_refill(const TraceParams &P, const WaveArgs &W, const float4 *sb,
-                                            bool &active, bool &drained, Ray &r, int &cool) {
+                                            bool &active, bool &drained, Ray &r, int &cool, unsigned &cnext,
+                                            unsigned &cend) {
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
-  if (!need) return;
-  const int leader = __ffs(need) - 1;
-  unsigned base = 0;
-  if ((int)lane == leader) base = atomicAdd(P.counter, (unsigned)__popc(need));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (base + (unsigned)__popc(need) >= P.n_items) drained = true;
-  if (!active && ((need >> lane) & 1u)) {
-    const unsigned item = base + (unsigned)__popc(need & ((1u << lane) - 1u));
-    if (item < P.n_items) {
-      if (W.first) {
-        const unsigned tile = item >> 5, sub = item & 31u;
-        const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
-        const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
-        if (px < P.W && py < P.H) {
-          init_ray<MK>(P, sb, py * P.W + px, r);
-          cool = 0;
-          active = true;
-        }
-      } else {
-        wave_load(W, W.list_in[item], r, cool);
-        active = true;
+  for (int pass = 0; pass < 2; ++pass) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+    if (!need) return;
+    if (cnext >= cend) {  // a warp-private chunk of 32 items (in the first round, one tile)
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(P.counter, 32u);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      cnext = base;
+      cend = base + 32u;
+      if (base >= P.n_items) {
+        drained = true;
+        return;
       }
     }
+    const unsigned take = min((unsigned)__popc(need), cend - cnext);
+    const unsigned rank = (unsigned)__popc(need & ((1u << lane) - 1u));
+    if (((need >> lane) & 1u) && rank < take) {
+      const unsigned item = cnext + rank;
+      if (item < P.n_items) {
+        if (W.first) {
+          const unsigned tile = item >> 5, sub = item & 31u;
+          const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
+          const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
+          if (px < P.W && py < P.H) {
+            init_ray<MK>(P, sb, py * P.W + px, r);
+            cool = 0;
+            active = true;
+          }
+        } else {
+          wave_load(W, W.list_in[item], r, cool);
+          active = true;
+        }
+      }
+    }
+    cnext += take;
   }
 }
 
@@ -1331,8 +1386,9 @@ __global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const W
   bool active = false, drained = false;
   Ray r;
   int cool = 0;
+  unsigned cnext = 0u, cend = 0u;
   for (;;) {
-    wave_refill<MK>(P, W, sb, active, drained, r, cool);
+    wave_refill<MK>(P, W, sb, active, drained, r, cool, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
       if (drained) break;
