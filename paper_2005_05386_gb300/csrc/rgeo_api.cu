@@ -551,6 +551,17 @@ rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *inst, rgeo_batch *
     total += table[i].n_items;
     max_f4 = std::max(max_f4, rgeo::table_float4s(q.metric->d.kind, q.metric->d.K, q.metric->d.aniso));
   }
+  // instances in order of decreasing cost (pixels x bump terms per point, roughly), so that
+  // the last instance the warps drain is a short one; each keeps its own outputs
+  {
+    std::vector<std::pair<double, int>> cost(n);
+    for (int i = 0; i < n; i++)
+      cost[i] = {-(double)inst[i].width * inst[i].height * (1.0 + inst[i].metric->d.K), i};
+    std::stable_sort(cost.begin(), cost.end());
+    std::vector<rgeo::TraceParams> sorted(n);
+    for (int i = 0; i < n; i++) sorted[i] = table[cost[i].second];
+    table.swap(sorted);
+  }
   rgeo_batch *b = new rgeo_batch();
   b->n = n;
   b->kind = inst[0].metric->d.kind;

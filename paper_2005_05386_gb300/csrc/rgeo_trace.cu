@@ -1175,12 +1175,13 @@ struct ParamInstances {
   __device__ __forceinline__ void load(int) const {}
 };
 
-// The batch loop: each warp drains one instance's queue, then moves to the next
-// instance (round robin from its own start), reloading parameters and bump table.
+// The batch loop: every warp starts on instance 0 (the launcher orders instances by
+// decreasing cost) and moves to the next one once the current instance's queue is
+// drained, reloading parameters and bump table; the end of one instance overlaps the
+// start of the next, and only one instance's structures are hot at a time.
 template <int MK, int INTEG, bool SMEM, class Src>
 __device__ __forceinline__ void batch_loop(const Src &src, int n) {
-  const int warp_global = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  int i = warp_global % n;
+  int i = 0;
   int visited = 0;
   unsigned long long evals = 0;
   bool active = false, drained = false;
