@@ -82,12 +82,17 @@ def algorithmic_flops_local(rk4_steps: int, metric) -> int:
     return rk4_steps * (4 * rhs + FLOPS_PER_STEP_EXTRA)
 
 
+TRACE_SOURCES = ("paper_2005_05386_gb300/csrc/rgeo_trace.cu", "paper_2005_05386_gb300/csrc/rgeo_internal.h",
+                 "paper_2005_05386_gb300/csrc/rgeo_api.cu", "paper_2005_05386_gb300/csrc/rgeo_scene_build.cpp",
+                 "include/rgeo.h")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources that shape the trace launch (kernels, launch parameters, scene and
+    cull structures); a committed DRAM count is used only while it matches."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2005_05386_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in TRACE_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 

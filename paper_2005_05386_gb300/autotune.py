@@ -20,7 +20,7 @@ import os
 
 from . import scenes
 
-CANDIDATE_GRIDS = (-1, 32, 48, 64, 96)
+CANDIDATE_GRIDS = (-1, 32, 48, 64, 96, 128)
 
 
 def cache_path() -> str:

@@ -322,7 +322,9 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
     // bump-support cull grid: isotropic truncated bumps only
     int G = 0;
     if (desc->kind == RGEO_METRIC_GRAPH_BUMPS && !aniso && desc->cutoff_sigmas > 0.f)
-      G = desc->cull_grid == 0 ? (K >= 16 ? 64 : 0) : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
+      // automatic: 128^3 cells up to 1024 bumps (masks of 128^3 x ceil(K / 64) words), 64^3 above
+      G = desc->cull_grid == 0 ? (K >= 16 ? (K <= 1024 ? 128 : 64) : 0)
+                               : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
     if (e == cudaSuccess && G > 0) {
       const int words = ((K + 1) / 2 + 31) / 32;
       m->d.cull_G = G;
