@@ -562,23 +562,19 @@ def bench_surrogate(args):
     dm, ds = rg.Metric(w.metric), rg.Scene(w.scene)
     eps, tau, n_train, steps, B = 0.03, 0.03, 1 << 22, 8000, 8192
     peaks = measured_peaks()
-    # training: segments from the device integrator, Adam on the tensor-core kernels
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    # training in one call (rgeo_expmap_train): segments from the device integrator, batches
+    # sampled on the device, Adam on the tensor-core kernels, cosine learning rate
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
     e0.record()
     X, T = rg.Expmap.generate(dm, n_train, seed=11, accel_bound=eps)
     e1.record()
+    torch.cuda.synchronize()
+    gen_s = e0.elapsed_time(e1) / 1e3
     net = rg.Expmap(max_batch=1 << 18, seed=7)
-    g = torch.Generator(device="cuda").manual_seed(0)
-    idx_all = torch.randint(0, n_train, (steps, B), generator=g, device="cuda")
-    torch.cuda.synchronize()
-    e1b = torch.cuda.Event(enable_timing=True)
-    e1b.record()
-    for it in range(steps):
-        lr = 1e-4 + 0.5 * (2e-3 - 1e-4) * (1 + math.cos(math.pi * it / steps))
-        net.train_step(X[idx_all[it]], T[idx_all[it]], lr)
-    e2.record()
-    torch.cuda.synchronize()
-    gen_s, train_s = e0.elapsed_time(e1) / 1e3, e1b.elapsed_time(e2) / 1e3
+    t0 = time.perf_counter()
+    train_loss = net.train(dm, n_segments=n_train, steps=steps, batch=B, lr_max=2e-3, lr_min=1e-4, seed=11,
+                           accel_bound=eps)
+    train_s = time.perf_counter() - t0 - gen_s  # the call regenerates the same segments first
     # tensor-core work per row: two 256x256 layers, forward (1) and backward (2 products)
     mma_flops_row = 2 * 2 * 256 * 256
     # inference throughput on 2^20 rows (transposes off)
@@ -640,6 +636,7 @@ def bench_surrogate(args):
                       "speed_ratio": mp / ms, "agree_1e-3_vs_plain_frame": a_plain,
                       "hit_err_p999_vs_plain": float(np.quantile(d[hit], 0.999)) if hit.any() else 0.0},
         "training": {"generate_s": gen_s, "train_s": train_s, "steps_per_s": steps / train_s,
+                     "final_loss": train_loss,
                      "tensor_tflops": steps * B * 3 * mma_flops_row / train_s / 1e12},
         "inference": {"rows": int(Xi.shape[0]), "ms": inf_s * 1e3, "rows_per_s": Xi.shape[0] / inf_s,
                       "tensor_tflops": inf_tflops, "peak_bf16_tflops": peaks.get("bf16_tflops"),

@@ -322,6 +322,26 @@ rgeo_status rgeo_expmap_set_params(rgeo_expmap *expmap, const float *params, int
 rgeo_status rgeo_expmap_save(const rgeo_expmap *expmap, const char *path);
 rgeo_status rgeo_expmap_load(rgeo_expmap *expmap, const char *path);
 
+/* Training in one call: n_segments segments from rgeo_expmap_generate (seed, box,
+ * s_max, h, accel_bound as there), then `steps` Adam steps (rgeo_expmap_train_step) on
+ * batches of `batch` rows drawn uniformly with replacement (counter-based), the learning
+ * rate following a cosine from lr_max at the first step to lr_min at the last.  Writes
+ * the mean loss of the last 1 % of the steps (at least one) to *loss (HOST, may be NULL)
+ * and synchronises the stream when it does; otherwise asynchronous.  Scratch:
+ * 52 (n_segments + batch) + 4 steps bytes of stream-ordered device memory. */
+typedef struct {
+  int64_t n_segments;  /* >= batch */
+  int32_t steps;       /* >= 1 */
+  int32_t batch;       /* multiple of 128, at most the network's max_batch */
+  float lr_max, lr_min;
+  uint64_t seed;
+  float box, s_max, h, accel_bound;
+  int32_t reserved[4]; /* must be zero */
+} rgeo_train_cfg;
+
+rgeo_status rgeo_expmap_train(rgeo_expmap *expmap, const rgeo_metric *metric, const rgeo_train_cfg *cfg,
+                              float *loss, void *cuda_stream);
+
 /* Tracing with surrogate jumps (Section 3, Eq. 3.5; graph metrics, RK4).
  * As rgeo_trace, except that a ray inside the bumps' supports may replace k RK4
  * steps (k_min <= k, k h <= s_max) by one evaluation of the trained network:

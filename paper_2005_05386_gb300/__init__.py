@@ -40,7 +40,7 @@ EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_me
            "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance", "rgeo_expmap_param_count",
            "rgeo_expmap_create", "rgeo_expmap_destroy", "rgeo_expmap_generate", "rgeo_expmap_forward",
            "rgeo_expmap_gradients", "rgeo_expmap_train_step", "rgeo_expmap_get_params", "rgeo_expmap_set_params",
-           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate")
+           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate", "rgeo_expmap_train")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -73,6 +73,13 @@ class rgeo_tuning(ctypes.Structure):
 class rgeo_outputs(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("hit", ctypes.c_void_p), ("steps", ctypes.c_void_p),
                 ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p), ("bump_evals", ctypes.c_void_p)]
+
+
+class rgeo_train_cfg(ctypes.Structure):
+    _fields_ = [("n_segments", ctypes.c_int64), ("steps", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr_max", ctypes.c_float), ("lr_min", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("box", ctypes.c_float), ("s_max", ctypes.c_float), ("h", ctypes.c_float),
+                ("accel_bound", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
 
 
 class rgeo_surrogate(ctypes.Structure):
@@ -153,6 +160,8 @@ def library() -> ctypes.CDLL:
     L.rgeo_expmap_save.argtypes = [vp, ctypes.c_char_p]
     L.rgeo_expmap_load.restype = i32
     L.rgeo_expmap_load.argtypes = [vp, ctypes.c_char_p]
+    L.rgeo_expmap_train.restype = i32
+    L.rgeo_expmap_train.argtypes = [vp, vp, ctypes.POINTER(rgeo_train_cfg), fp, vp]
     L.rgeo_trace_surrogate.restype = i32
     L.rgeo_trace_surrogate.argtypes = [vp, vp, ctypes.POINTER(rgeo_camera), i32, i32, f32, i32, i32, ctypes.c_uint32,
                                        ctypes.POINTER(rgeo_surrogate), ctypes.POINTER(rgeo_outputs),
@@ -375,6 +384,16 @@ class Expmap:
         _check(library().rgeo_expmap_train_step(self.handle, X.data_ptr(), T.data_ptr(), X.shape[0], lr,
                                                 loss.data_ptr() if loss is not None else None,
                                                 _stream_handle(stream)), "rgeo_expmap_train_step")
+
+    def train(self, metric: "Metric", n_segments: int, steps: int, batch: int = 8192, lr_max: float = 2e-3,
+              lr_min: float = 1e-4, seed: int = 11, box: float = 4.0, s_max: float = 0.5, h: float = 0.005,
+              accel_bound: float = 0.0, stream=None) -> float:
+        """Generate segments and train in one call; returns the mean loss of the last 1 % of steps."""
+        cfg = rgeo_train_cfg(n_segments, steps, batch, lr_max, lr_min, seed, box, s_max, h, accel_bound)
+        loss = ctypes.c_float(0.0)
+        _check(library().rgeo_expmap_train(self.handle, metric.handle, ctypes.byref(cfg), ctypes.byref(loss),
+                                           _stream_handle(stream)), "rgeo_expmap_train")
+        return loss.value
 
     def get_params(self):
         import numpy as np

@@ -680,6 +680,57 @@ rgeo_status rgeo_expmap_generate(const rgeo_metric *metric, int64_t n, uint64_t 
 }
 
 
+rgeo_status rgeo_expmap_train(rgeo_expmap *expmap, const rgeo_metric *metric, const rgeo_train_cfg *cfg,
+                              float *loss, void *cuda_stream) {
+  g_last_error.clear();
+  if (!expmap || !metric || !cfg) return fail(RGEO_EINVAL, "rgeo_expmap_train: NULL argument");
+  for (int i = 0; i < 4; i++)
+    if (cfg->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_expmap_train: reserved fields must be zero");
+  if (cfg->steps < 1 || cfg->batch < 128 || cfg->batch % 128 != 0 || cfg->n_segments < cfg->batch ||
+      !(cfg->lr_max > 0.f) || !(cfg->lr_min >= 0.f) || !(cfg->lr_min <= cfg->lr_max) || !std::isfinite(cfg->lr_max))
+    return fail(RGEO_EINVAL, "rgeo_expmap_train: need steps >= 1, batch a multiple of 128, n_segments >= batch, "
+                             "0 <= lr_min <= lr_max, lr_max > 0 finite");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)cfg->n_segments, B = (size_t)cfg->batch;
+  float *buf = nullptr;
+  RGEO_CUDA(cudaMallocAsync((void **)&buf, sizeof(float) * (13 * n + 13 * B + (size_t)cfg->steps), st),
+            "rgeo_expmap_train: buffers");
+  float *X = buf, *T = X + 7 * n, *Xb = T + 6 * n, *Tb = Xb + 7 * B, *losses = Tb + 6 * B;
+  rgeo_status s = rgeo_expmap_generate(metric, cfg->n_segments, cfg->seed, cfg->box, cfg->s_max, cfg->h,
+                                       cfg->accel_bound, X, T, cuda_stream);
+  const unsigned long long bseed = cfg->seed ^ 0xD1B54A32D192ED03ull;  // batch draws apart from the segments
+  for (int it = 0; s == RGEO_OK && it < cfg->steps; ++it) {
+    // cosine schedule from lr_max (first step) to lr_min (last step)
+    const double c = cfg->steps > 1 ? (double)it / (cfg->steps - 1) : 0.0;
+    const float lr = (float)(cfg->lr_min + 0.5 * (cfg->lr_max - cfg->lr_min) * (1.0 + std::cos(3.141592653589793 * c)));
+    cudaError_t e = rgeo::launch_gather_batch(X, T, (long long)n, (int)B, bseed, it, Xb, Tb, st);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "rgeo_expmap_train: batch");
+      break;
+    }
+    s = rgeo_expmap_train_step(expmap, Xb, Tb, (int32_t)B, lr, losses + it, cuda_stream);
+  }
+  if (s == RGEO_OK && loss) {
+    // mean loss over the last 1 % of the steps (at least one)
+    const int tail = std::max(1, cfg->steps / 100);
+    std::vector<float> h(tail);
+    cudaError_t e = cudaMemcpyAsync(h.data(), losses + (cfg->steps - tail), sizeof(float) * tail,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "rgeo_expmap_train: loss");
+    } else {
+      double acc = 0.0;
+      for (float v : h) acc += v;
+      *loss = (float)(acc / tail);
+    }
+  }
+  cudaError_t e2 = cudaFreeAsync(buf, st);
+  if (s != RGEO_OK) return s;
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rgeo_expmap_train: free");
+  return RGEO_OK;
+}
+
 rgeo_status rgeo_trace_surrogate(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
                                  int32_t width, int32_t height, float h, int32_t max_steps, int32_t shading,
                                  uint32_t flags, const rgeo_surrogate *sur, const rgeo_outputs *out,

@@ -213,6 +213,9 @@ cudaError_t launch_wave_apply(const WaveArgs &w, unsigned n, float h, cudaStream
 cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits, const float *bias,
                              int mode, void *C, int ldc, void *ct, int ldt, cudaStream_t st);
 cudaError_t read_and_clear_mlp_error(unsigned *word);
+// Training batch of B rows sampled (counter-based) from n segments (stream-ordered).
+cudaError_t launch_gather_batch(const float *X, const float *T, long long n, int B, unsigned long long seed,
+                                long long step, float *Xb, float *Tb, cudaStream_t st);
 // Surrogate forward pass over n rows of 7 inputs into n rows of 7 outputs (stream-ordered).
 cudaError_t expmap_infer(const rgeo_expmap *x, const float *X, long long n, float *Y, cudaStream_t st);
 cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);

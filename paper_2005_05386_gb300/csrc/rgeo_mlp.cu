@@ -414,6 +414,19 @@ __device__ __forceinline__ float u01(unsigned long long seed, unsigned long long
   return (float)(z >> 40) * (1.f / 16777216.f);
 }
 
+// Batch sampling for training: row i of the batch takes segment floor(u n) of the training
+// set, u from the counter-based generator at (seed, step * batch + i).
+__global__ void k_gather_batch(const float *__restrict__ X, const float *__restrict__ T, long long n, int B,
+                               unsigned long long seed, long long step, float *Xb, float *Tb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const float u = u01(seed, (unsigned long long)(step * B + i));
+  long long j = (long long)(u * (float)n);
+  if (j >= n) j = n - 1;
+  for (int c = 0; c < kIn; ++c) Xb[(size_t)i * kIn + c] = X[(size_t)j * kIn + c];
+  for (int c = 0; c < 6; ++c) Tb[(size_t)i * 6 + c] = T[(size_t)j * 6 + c];
+}
+
 // He-uniform initialisation of the weights, zero biases.
 __global__ void k_init(float *P, unsigned long long seed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -662,6 +675,12 @@ cudaError_t launch_mlp_infer(const float *X, long long n, const float *P, const 
   const long long tiles = (n + kTileM - 1) / kTileM;
   if (tiles > 0x7fffffffll) return cudaErrorInvalidValue;
   k_mlp_infer<<<(unsigned)tiles, kInferThreads, kInferSmem, st>>>(X, n, P, W2b, W3b, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_batch(const float *X, const float *T, long long n, int B, unsigned long long seed,
+                                long long step, float *Xb, float *Tb, cudaStream_t st) {
+  k_gather_batch<<<(B + 255) / 256, 256, 0, st>>>(X, T, n, B, seed, step, Xb, Tb);
   return cudaGetLastError();
 }
 

@@ -213,3 +213,22 @@ def test_training_reduces_loss_and_checkpoint_roundtrip(rg, tmp_path):
     bad.write_bytes(b"not a checkpoint")
     with pytest.raises(rg.RgeoError):
         y.load(str(bad))
+
+
+def test_train_in_one_call(rg):
+    """rgeo_expmap_train: integrator-generated segments, device-sampled batches, cosine schedule."""
+    import torch
+    dm = rg.Metric(_field_metric())
+    Xv, Tv = rg.Expmap.generate(dm, 4096, seed=77)
+    x = rg.Expmap(max_batch=4096, seed=5)
+    _, L0 = x.gradients(Xv, Tv)
+    l0 = L0.item()
+    tail = x.train(dm, n_segments=1 << 17, steps=400, batch=4096, lr_max=2e-3, lr_min=1e-4, seed=31)
+    _, L1 = x.gradients(Xv, Tv)
+    rg.rgeo_sync()
+    assert np.isfinite(tail) and tail > 0
+    assert L1.item() < 0.5 * l0, (l0, L1.item())
+    with pytest.raises(rg.RgeoError):   # batch above max_batch
+        x.train(dm, n_segments=1 << 14, steps=2, batch=8192)
+    with pytest.raises(rg.RgeoError):   # batch not a multiple of 128
+        x.train(dm, n_segments=1 << 14, steps=2, batch=1000)
