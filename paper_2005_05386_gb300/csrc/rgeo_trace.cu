@@ -170,8 +170,11 @@ __device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const
   const bool ing = fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G;
   const uint32_t *cm =
       P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
+  // word wi + 1 of the cell's mask is loaded while the pairs of word wi are summed
+  unsigned mnext = ing ? __ldg(cm) : 0u;
   for (int wi = 0; wi < P.cull_words; ++wi) {
-    unsigned m = ing ? __ldg(cm + wi) : 0u;
+    unsigned m = mnext;
+    if (wi + 1 < P.cull_words) mnext = ing ? __ldg(cm + wi + 1) : 0u;
     evals += 2u * (unsigned)__popc(m);  // the bumps of this lane's own cell
     m = __reduce_or_sync(pmask, m);
     while (m) {
