@@ -641,7 +641,9 @@ def bench_surrogate(args):
         "inference": {"rows": int(Xi.shape[0]), "ms": inf_s * 1e3, "rows_per_s": Xi.shape[0] / inf_s,
                       "tensor_tflops": inf_tflops, "peak_bf16_tflops": peaks.get("bf16_tflops"),
                       "frac": inf_tflops / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None},
-        "clocks": clk, "gpu_launches": None,
+        # per timed step: the plain frame (one launch) and, per round of the surrogate frame, the
+        # trace kernel, the fused inference and the jump kernel (the last round has no queue)
+        "clocks": clk, "gpu_launches": args.steps * (1 + 3 * st["rounds"] - 2),
     }
     print(json.dumps(line), flush=True)
     return 0
