@@ -74,6 +74,7 @@ def lib():
         L.or_scene_create.restype = ctypes.c_void_p
         L.or_scene_create.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.or_scene_destroy.argtypes = [ctypes.c_void_p]
+        L.or_scene_set_fog.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp]
         L.or_field.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
         L.or_christoffel.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.or_accel.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
@@ -150,7 +151,7 @@ class Metric:
 
 
 class Scene:
-    def __init__(self, spheres, verts=None, tris=None, albedo=None, use_bvh=True):
+    def __init__(self, spheres, verts=None, tris=None, albedo=None, use_bvh=True, fog=0.0, fog_rgb=(0, 0, 0)):
         spheres = np.asarray(spheres, np.float64).reshape(-1, 4)
         S = spheres.shape[0]
         if verts is None or tris is None or len(tris) == 0:
@@ -165,10 +166,15 @@ class Scene:
         self._keep = [_d(spheres), _d(tri9), _d(np.asarray(albedo, np.float64).reshape(-1, 3))]
         (_, ps), (_, pt), (_, pa) = self._keep
         self.ptr = lib().or_scene_create(S, ps, self.T, pt, pa, int(bool(use_bvh)))
+        if fog > 0.0:
+            rgb = _d(fog_rgb)
+            self._keep.append(rgb)
+            lib().or_scene_set_fog(self.ptr, float(fog), rgb[1])
 
     @classmethod
     def from_desc(cls, s, use_bvh=True):
-        return cls(s.spheres, s.verts, s.tris, s.albedo, use_bvh)
+        return cls(s.spheres, s.verts, s.tris, s.albedo, use_bvh, getattr(s, "fog", 0.0),
+                   getattr(s, "fog_rgb", (0.0, 0.0, 0.0)))
 
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:

@@ -518,6 +518,8 @@ typedef struct {
   or_node *nodes;
   int n_nodes;
   int use_bvh;
+  double fog;       /* fog density per unit of arc length (0: none) */
+  double fog_rgb[3];
 } or_scene;
 
 static void tri_bounds(const or_scene *sc, int t, double lo[3], double hi[3]) {
@@ -596,6 +598,13 @@ or_scene *or_scene_create(int S, const double *sph, int T, const double *tri, co
   sc->use_bvh = use_bvh && T > 0;
   if (sc->use_bvh) bvh_build(sc, 0, T);
   return sc;
+}
+
+/* The fog of the paper's grid figures: a hit's colour c becomes c T + fog_rgb (1 - T) with
+ * T = exp(-density * arc length travelled to the hit). */
+void or_scene_set_fog(or_scene *sc, double density, const double rgb[3]) {
+  sc->fog = density;
+  for (int i = 0; i < 3; i++) sc->fog_rgb[i] = rgb ? rgb[i] : 0.0;
 }
 
 void or_scene_destroy(or_scene *sc) {
@@ -831,7 +840,7 @@ typedef struct {
   double *xend;   /* [n*3] final position (diagnostic) */
 } or_outputs;
 
-static void shade(const or_scene *sc, int shading, int id, const double P[3], const double D[3],
+static void shade(const or_scene *sc, int shading, int id, const double P[3], const double D[3], double arc,
                   uint8_t rgba[4]) {
   double rgb[3];
   if (shading == OR_PSEUDO) {
@@ -858,6 +867,10 @@ static void shade(const or_scene *sc, int shading, int id, const double P[3], co
     if (c < 0.0) c = 0.0;
     double inten = 0.1 + 0.9 * c;
     for (int q = 0; q < 3; q++) rgb[q] = sc->alb[3 * obj + q] * inten;
+  }
+  if (sc->fog > 0.0) {
+    double T = exp(-sc->fog * arc);
+    for (int q = 0; q < 3; q++) rgb[q] = rgb[q] * T + sc->fog_rgb[q] * (1.0 - T);
   }
   for (int q = 0; q < 3; q++) {
     double c = rgb[q] < 0.0 ? 0.0 : (rgb[q] > 1.0 ? 1.0 : rgb[q]);
@@ -894,6 +907,9 @@ static void trace_pixel(const or_job *jb, int64_t q) {
   double e0 = or_inner(m, x, v, v);
   int can_skip = skippable(m) && !jb->no_skip;
   int steps = 0, id = OR_BUDGET;
+  /* arc length travelled (for the fog): h per step, s h on the hit chord, and the parameter
+   * length of each straight advance (its g-length: the tangent is g-unit) */
+  double arc = 0.0;
   double P[3] = {x[0], x[1], x[2]}, Dhit[3] = {v[0], v[1], v[2]};
   for (;;) {
     if (can_skip && outside_supports(m, x)) {
@@ -903,10 +919,12 @@ static void trace_pixel(const or_job *jb, int64_t q) {
       if (or_scene_hit(jb->sc, x, v, t, &s, &hid)) {
         id = hid;
         for (int c = 0; c < 3; c++) { P[c] = x[c] + s * v[c]; Dhit[c] = v[c]; }
+        arc += s;
         break;
       }
       if (isinf(t)) { id = OR_MISS; break; }
       for (int c = 0; c < 3; c++) x[c] = x[c] + t * v[c];
+      arc += t;
     }
     if (steps >= jb->max_steps) { id = OR_BUDGET; break; }
     double x0[3] = {x[0], x[1], x[2]};
@@ -918,15 +936,17 @@ static void trace_pixel(const or_job *jb, int64_t q) {
     if (or_scene_hit(jb->sc, x0, D, 1.0, &s, &hid)) {
       id = hid;
       for (int c = 0; c < 3; c++) { P[c] = x0[c] + s * D[c]; Dhit[c] = D[c]; }
+      arc += s * jb->h;
       break;
     }
+    arc += jb->h;
   }
   const or_outputs *o = &jb->out;
   o->id[q] = id;
   o->steps[q] = steps;
   if (id >= 0) {
     for (int c = 0; c < 3; c++) o->hit[3 * q + c] = P[c];
-    shade(jb->sc, jb->shading, id, P, Dhit, o->rgba + 4 * q);
+    shade(jb->sc, jb->shading, id, P, Dhit, arc, o->rgba + 4 * q);
   } else {
     for (int c = 0; c < 3; c++) o->hit[3 * q + c] = x[c];
     memset(o->rgba + 4 * q, 0, 4);

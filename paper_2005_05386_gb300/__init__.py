@@ -40,7 +40,7 @@ EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_me
            "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance", "rgeo_expmap_param_count",
            "rgeo_expmap_create", "rgeo_expmap_destroy", "rgeo_expmap_generate", "rgeo_expmap_forward",
            "rgeo_expmap_gradients", "rgeo_expmap_train_step", "rgeo_expmap_get_params", "rgeo_expmap_set_params",
-           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate", "rgeo_expmap_train")
+           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate", "rgeo_expmap_train", "rgeo_scene_set_fog")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -160,6 +160,8 @@ def library() -> ctypes.CDLL:
     L.rgeo_expmap_save.argtypes = [vp, ctypes.c_char_p]
     L.rgeo_expmap_load.restype = i32
     L.rgeo_expmap_load.argtypes = [vp, ctypes.c_char_p]
+    L.rgeo_scene_set_fog.restype = i32
+    L.rgeo_scene_set_fog.argtypes = [vp, f32, fp]
     L.rgeo_expmap_train.restype = i32
     L.rgeo_expmap_train.argtypes = [vp, vp, ctypes.POINTER(rgeo_train_cfg), fp, vp]
     L.rgeo_trace_surrogate.restype = i32
@@ -489,6 +491,13 @@ class Scene:
 
     def __init__(self, s: scenes.Scene):
         self.handle = rgeo_scene_create(s.spheres, s.verts, s.tris, s.albedo)
+        if getattr(s, "fog", 0.0) > 0.0:
+            self.set_fog(s.fog, s.fog_rgb)
+
+    def set_fog(self, density: float, rgb=(0.0, 0.0, 0.0)):
+        import numpy as np
+        c = np.ascontiguousarray(rgb, np.float32)
+        _check(library().rgeo_scene_set_fog(self.handle, density, _fptr(c)), "rgeo_scene_set_fog")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -149,6 +149,8 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   std::memcpy(p.smax, s.smax, sizeof(p.smax));
   p.has_grid = s.has_grid;
   p.safe_skip = s.has_grid && !(flags & RGEO_FLAG_NO_SAFE_SKIP);
+  p.fog = s.fog;
+  std::memcpy(p.fog_rgb, s.fog_rgb, sizeof(p.fog_rgb));
   std::memcpy(p.cam_pos, cam->pos, sizeof(p.cam_pos));
   std::memcpy(p.cam_fwd, cam->forward, sizeof(p.cam_fwd));
   std::memcpy(p.cam_up, cam->up, sizeof(p.cam_up));
@@ -419,6 +421,16 @@ rgeo_status rgeo_scene_create(const float *spheres, int32_t S, const float *vert
     return cuda_fail(e, "rgeo_scene_create");
   }
   *out = sc;
+  return RGEO_OK;
+}
+
+rgeo_status rgeo_scene_set_fog(rgeo_scene *scene, float density, const float *rgb) {
+  g_last_error.clear();
+  if (!scene) return fail(RGEO_EINVAL, "rgeo_scene_set_fog: NULL scene");
+  if (!std::isfinite(density) || density < 0.f || (rgb && !finite_all(rgb, 3)))
+    return fail(RGEO_EINVAL, "rgeo_scene_set_fog: density must be finite and >= 0, rgb finite");
+  scene->d.fog = density;
+  for (int c = 0; c < 3; c++) scene->d.fog_rgb[c] = rgb ? rgb[c] : 0.f;
   return RGEO_OK;
 }
 
@@ -754,16 +766,16 @@ rgeo_status rgeo_trace_surrogate(const rgeo_metric *metric, const rgeo_scene *sc
   cudaStream_t st = (cudaStream_t)cuda_stream;
   rgeo::TraceParams p = make_params(metric, scene, camera, width, height, h, max_steps, RGEO_RK4, shading, flags, out);
   const size_t N = (size_t)width * height;
-  // one device block: state 14 N floats, steps, cool, two queues, jump_k (N ints each),
+  // one device block: state 15 N floats, steps, cool, two queues, jump_k (N ints each),
   // X and Y (7 N floats each), the work counter, the queue length and two statistics
-  const size_t words = 14 * N + 5 * N + 14 * N;
+  const size_t words = 15 * N + 5 * N + 14 * N;
   char *buf = nullptr;
   RGEO_CUDA(cudaMallocAsync((void **)&buf, words * 4 + 64, st), "rgeo_trace_surrogate: state");
   float *fw = (float *)buf;
   rgeo::WaveArgs w;
   std::memset(&w, 0, sizeof(w));
   w.st = fw;
-  w.steps = (int32_t *)(fw + 14 * N);
+  w.steps = (int32_t *)(fw + 15 * N);
   w.cool = w.steps + N;
   int32_t *qa = w.cool + N, *qb = qa + N;
   w.jump_k = qb + N;

@@ -81,6 +81,7 @@ struct SceneDev {
   float ginv;        // 1 / cell size
   float smin[3], smax[3];  // scene bounding box
   int has_grid;
+  float fog, fog_rgb[3];     // hit colour c -> c T + fog_rgb (1 - T), T = exp(-fog * arc length)
 };
 
 struct TraceParams {
@@ -107,6 +108,7 @@ struct TraceParams {
   float ginv;
   float smin[3], smax[3];
   int has_grid, safe_skip;
+  float fog, fog_rgb[3];
   // camera
   float cam_pos[3], cam_fwd[3], cam_up[3];
   float vfov_deg;
@@ -130,7 +132,7 @@ struct TraceParams {
 // State of the surrogate tracer: per-ray SoA over the N = W * H pixels, the queue of
 // rays waiting for a surrogate jump, and the network's inputs and outputs per slot.
 struct WaveArgs {
-  float *st;            // [14][N]: xh[3], xl[3], vh[3], vl[3], dleft, e0m1
+  float *st;            // [15][N]: xh[3], xl[3], vh[3], vl[3], dleft, e0m1, arc
   int32_t *steps;       // [N] equivalent RK4 steps taken
   int32_t *cool;        // [N] RK4 steps to take before the next jump attempt
   const int32_t *list_in;  // rays advanced this round (round > 0)

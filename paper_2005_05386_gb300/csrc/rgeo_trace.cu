@@ -655,7 +655,7 @@ __device__ __forceinline__ unsigned char to_u8(float c) {
   return (unsigned char)floorf(255.f * c + 0.5f);
 }
 
-__device__ uchar4 shade(const TraceParams &P, const float4 *ss, const HitRec &hr, F3 Ph, F3 D) {
+__device__ uchar4 shade(const TraceParams &P, const float4 *ss, const HitRec &hr, F3 Ph, F3 D, float arc) {
   float r, g, b;
   if (P.shading == 1) {
     r = 0.5f + Ph.x * 0.125f;
@@ -681,6 +681,12 @@ __device__ uchar4 shade(const TraceParams &P, const float4 *ss, const HitRec &hr
     g = P.albedo[3 * obj + 1] * inten;
     b = P.albedo[3 * obj + 2] * inten;
   }
+  if (P.fog > 0.f) {  // the grid figures' fog: c T + fog_rgb (1 - T), T = exp(-density * arc length)
+    const float T = expf(-P.fog * arc), U = 1.f - T;
+    r = fmaf(r, T, P.fog_rgb[0] * U);
+    g = fmaf(g, T, P.fog_rgb[1] * U);
+    b = fmaf(b, T, P.fog_rgb[2] * U);
+  }
   return make_uchar4(to_u8(r), to_u8(g), to_u8(b), 255);
 }
 
@@ -692,6 +698,7 @@ struct Ray {
   int pix;
   float dleft;
   float e0m1;
+  float arc;  // arc length travelled: h per step, the parameter length of straight advances
 };
 
 __device__ __forceinline__ F3 xhi(const Ray &r) { return f3(r.xh[0], r.xh[1], r.xh[2]); }
@@ -738,12 +745,13 @@ __device__ void init_ray(const TraceParams &P, const float4 *sb, int pix, Ray &r
   r.pix = pix;
   r.dleft = 0.f;
   r.e0m1 = 0.f;
+  r.arc = 0.f;
   if (P.energy) r.e0m1 = (float)(energy<MK>(P, sb, x, v) - 1.0);
 }
 
 template <int MK>
 __device__ void finish_ray(const TraceParams &P, const float4 *sb, const float4 *ss, const Ray &r,
-                           int id, const HitRec &hr, F3 Ph, F3 D) {
+                           int id, const HitRec &hr, F3 Ph, F3 D, float arc = 0.f) {
   const int p = r.pix;
   const size_t N = (size_t)P.W * P.H;
   P.id[p] = id;
@@ -752,7 +760,7 @@ __device__ void finish_ray(const TraceParams &P, const float4 *sb, const float4 
   P.hit[p] = o.x;
   P.hit[N + p] = o.y;
   P.hit[2 * N + p] = o.z;
-  P.rgba[p] = id >= 0 ? shade(P, ss, hr, Ph, D) : make_uchar4(0, 0, 0, 0);
+  P.rgba[p] = id >= 0 ? shade(P, ss, hr, Ph, D, arc) : make_uchar4(0, 0, 0, 0);
   if (P.energy) {
     const double e = energy<MK>(P, sb, xhi(r), vhi(r));
     P.drift[p] = e / (1.0 + (double)r.e0m1) - 1.0;
@@ -853,13 +861,14 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
     const float t = support_entry<MK>(sb, P.K, x, v);
     HitRec hr;
     if (scene_hit(P, ss, x, v, t, hr)) {
-      finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v);
+      finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v, r.arc + hr.s);
       finished = true;
     } else if (isinf(t)) {
       finish_ray<MK>(P, sb, ss, r, RGEO_ID_MISS, hr, x, v);
       finished = true;
     } else {
       for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], t * comp(v, c));
+      r.arc += t;  // a straight advance of parameter length t is also its g-length (v is g-unit)
       r.dleft = 0.f;
       x = xhi(r);
       moved = true;
@@ -892,6 +901,7 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
     comp_add(r.vh[c], r.vl[c], comp(dvel, c));
   }
   r.steps++;
+  r.arc += P.h;
   const F3 D = xhi(r) - x;
   if (P.safe_skip) {
     const float L = sqrtf(dot(D, D)) * (1.f + 1e-6f);
@@ -908,7 +918,7 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
   }
   HitRec hr;
   if (scene_hit(P, ss, x, D, 1.f, hr)) {
-    finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, x), D);
+    finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, x), D, fmaf(hr.s - 1.f, P.h, r.arc));
     return false;
   }
   return true;
@@ -937,9 +947,10 @@ __device__ __forceinline__ void step_increments(const TraceParams &P, const floa
   }
 }
 
-// One ray per thread (every metric kind).
+// One ray per thread (every metric kind).  Six 128-thread CTAs per SM (80 registers) for the
+// graph and twist metrics; the local-map jet needs more registers, five CTAs.
 template <int MK, int INTEG>
-__global__ void __launch_bounds__(128) k_trace(const TraceParams P) {
+__global__ void __launch_bounds__(128, MK == MK_LOCAL ? 5 : 6) k_trace(const TraceParams P) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
@@ -1265,6 +1276,7 @@ __device__ __forceinline__ void wave_store(const WaveArgs &W, const Ray &r, int 
   }
   W.st[12 * N + p] = r.dleft;
   W.st[13 * N + p] = r.e0m1;
+  W.st[14 * N + p] = r.arc;
   W.steps[p] = r.steps;
   W.cool[p] = cool;
 }
@@ -1279,6 +1291,7 @@ __device__ __forceinline__ void wave_load(const WaveArgs &W, int pix, Ray &r, in
   }
   r.dleft = W.st[12 * N + p];
   r.e0m1 = W.st[13 * N + p];
+  r.arc = W.st[14 * N + p];
   r.steps = W.steps[p];
   r.pix = pix;
   cool = W.cool[p];
@@ -1459,6 +1472,7 @@ __global__ void k_wave_apply(const WaveArgs W, unsigned n, float h) {
         W.st[(9 + c) * N + p] = vl;
       }
       W.st[12 * N + p] = 0.f;  // the next chord queries the safe distance afresh
+      W.st[14 * N + p] += s;   // arc length of the jump
       W.steps[p] += k;
       W.cool[p] = 0;
       acc = 1;

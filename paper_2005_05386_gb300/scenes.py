@@ -118,6 +118,8 @@ class Scene:
     verts: np.ndarray     # [V, 3] float32
     tris: np.ndarray      # [T, 3] int32
     albedo: np.ndarray    # [S + 1, 3] float32: one colour per sphere, then one for the mesh
+    fog: float = 0.0      # fog density per unit of arc length (the grid figures use a little black fog)
+    fog_rgb: tuple = (0.0, 0.0, 0.0)
 
     @property
     def n_spheres(self) -> int:

@@ -309,3 +309,44 @@ def test_parity_quadratic_metrics_through_the_lattice(rg, cfg):
     w = scenes.scaled(cfg(), 64, 64)
     st = compare(_run(rg, w), oracle.trace(w), w.scene.n_spheres)
     assert_parity(st, min_hits=1000)
+
+
+@pytest.mark.parametrize("shading", [scenes.SHADING_LAMBERT, scenes.SHADING_PSEUDO])
+def test_fog_parity_64x64(rg, shading):
+    """Fog over the arc length (Section 6's grid figures): full frame against the oracle with
+    the same fog, through the curved one-bump metric; fog darkens the hits."""
+    w = scenes.config_parity_64()
+    w.shading = shading
+    plain = _run(rg, w)
+    w.scene.fog, w.scene.fog_rgb = 0.12, (0.05, 0.1, 0.2)
+    g = _run(rg, w)
+    st = compare(g, oracle.trace(w), w.scene.n_spheres)
+    assert_parity(st, min_hits=60)
+    hit = g["id"] >= 0
+    assert (g["rgba"][hit] != plain["rgba"][hit]).any()
+
+
+def test_fog_validation(rg):
+    w = scenes.config_parity_64()
+    sc = rg.Scene(w.scene)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(rg.RgeoError):
+            sc.set_fog(bad)
+    with pytest.raises(rg.RgeoError):
+        sc.set_fog(0.1, (0.0, float("nan"), 0.0))
+    sc.set_fog(0.0)
+
+
+def test_fog_survives_surrogate_rounds(rg):
+    """The surrogate tracer saves and restores each ray's arc length between rounds: with
+    tau = 0 and fog on, its image equals the plain tracer's."""
+    w = scenes.scaled(scenes.config_1080p_64(), 96, 54)
+    w.scene.fog = 0.08
+    dm, ds = rg.Metric(w.metric), rg.Scene(w.scene)
+    plain = rg.trace(w, dm, ds)
+    rg.rgeo_sync()
+    out, st = rg.trace_surrogate(w, rg.Expmap(max_batch=128, seed=1), 0.0, metric=dm, scene=ds)
+    rg.rgeo_sync()
+    assert st["rounds"] > 1
+    for k in ("id", "rgba", "steps"):
+        assert np.array_equal(out[k].cpu().numpy(), plain[k].cpu().numpy()), k

@@ -41,6 +41,9 @@ MUTANTS = {
                                  "acc += J[3 * a + k] * Hj[9 * s + 3 * k + l] * J[3 * b + l];", "local"),
     "jinv_product_order": ("t += inv[3 * r + k] * Jinv[3 * k + c];", "t += Jinv[3 * r + k] * inv[3 * k + c];",
                            "local"),
+    "fog_skip_arc": ("      for (int c = 0; c < 3; c++) x[c] = x[c] + t * v[c];\n      arc += t;\n",
+                     "      for (int c = 0; c < 3; c++) x[c] = x[c] + t * v[c];\n", "fog"),
+    "fog_step_arc": ("    arc += jb->h;\n  }", "  }", "fog"),
     "local_field_term": ("hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i] + gr[i] * B[3 * s + j];",
                          "hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i];", "local"),
 }

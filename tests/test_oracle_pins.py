@@ -540,3 +540,29 @@ def test_local_zero_amplitude_is_flat():
                       direction=[[1.0, 0.0, 0.0]])
     xs, _ = oracle.integrate(m, oracle.RK4, 0.01, 50, [0.1, 0.2, 0.3], [0.0, 0.6, 0.8])
     np.testing.assert_allclose(xs[-1], [0.1, 0.2 + 0.3, 0.3 + 0.4], atol=1e-14)
+
+
+@pytest.mark.parametrize("no_skip", [False, True])
+def test_fog_attenuates_by_arc_length_on_straight_rays(no_skip):
+    """Fog (the grid figures' black fog): colour c exp(-d * arc length).  One bump of amplitude
+    1e-12 leaves the rays straight lines of unit speed (to ~1e-12) while its support ball makes
+    them advance in closed form, march through the ball and advance again, so the arc length
+    to a hit must be its distance from the camera along every path (or when marching only)."""
+    from paper_2005_05386_gb300 import scenes
+    w = scenes.scaled(scenes.config_parity_64(), 48, 48)
+    w.metric = scenes.Metric(center=np.zeros((1, 3), np.float32), amplitude=np.array([1e-12], np.float32),
+                             sigma=np.full((1, 3), 0.5, np.float32))
+    w.h, w.max_steps = 0.01, 2000
+    base = oracle.trace(w, no_skip=no_skip)
+    d = 0.15
+    w.scene.fog = d
+    fogged = oracle.trace(w, no_skip=no_skip)
+    hit = base["id"] >= 0
+    assert hit.sum() > 40
+    np.testing.assert_array_equal(base["id"], fogged["id"])
+    dist = np.linalg.norm(base["hit"][hit] - np.asarray(w.camera.pos), axis=1)
+    expect = base["rgba"][hit][:, :3] / 255.0 * np.exp(-d * dist)[:, None]
+    got = fogged["rgba"][hit][:, :3] / 255.0
+    assert np.abs(got - expect).max() <= 1.0 / 255.0 + 1e-9
+    assert (fogged["rgba"][hit][:, :3] < base["rgba"][hit][:, :3]).any()
+    assert (fogged["rgba"][~hit] == 0).all()
