@@ -1256,9 +1256,6 @@ __global__ void __launch_bounds__(128) k_trace_batch_param(const __grid_constant
   batch_loop<MK, INTEG, SMEM>(ParamInstances{&T, tab}, n);
 }
 
-// Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
-// table; t is read from and advanced in device memory so that a captured graph
-// animates without host input.  motion = [K*3 c0 | K*3 A | K f | K phi].
 // ------------------------------------------------------- surrogate tracer
 // Rays advance in rounds.  In a round each ray runs RK4 steps (as k_trace) until it
 // finishes or reaches a point from which a surrogate jump is allowed; it then saves
@@ -1488,6 +1485,9 @@ __global__ void k_wave_apply(const WaveArgs W, unsigned n, float h) {
   }
 }
 
+// Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
+// table; t is read from and advanced in device memory so that a captured graph
+// animates without host input.  motion = [K*3 c0 | K*3 A | K f | K phi].
 __global__ void k_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
                                  float dt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
