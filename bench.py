@@ -377,8 +377,13 @@ def bench_gpu(args):
         hstruct = rg.outputs_struct(host)
         centers = np.ascontiguousarray(w.metric.center, np.float32)
 
+        # graph metrics upload their bump centres each frame (an animation's input); the other
+        # kinds have no per-frame array input, only the camera passed by value
+        upload = w.metric.kind == scenes.METRIC_GRAPH_BUMPS and K > 0
+
         def e2e_frame():
-            rg.rgeo_metric_set_centers(metric.handle, centers, stream.cuda_stream)
+            if upload:
+                rg.rgeo_metric_set_centers(metric.handle, centers, stream.cuda_stream)
             rg.rgeo_trace_host(metric.handle, scene.handle, cam, w.width, w.height, w.h, w.max_steps,
                                w.integrator, w.shading, 0, hstruct, stream.cuda_stream)
 
@@ -390,7 +395,7 @@ def bench_gpu(args):
             e2e_frame()
         e2e_s = reduce_max(time.perf_counter() - t0, world)
         assert np.array_equal(host["id"].numpy(), ids), "e2e outputs differ from the device-timed frame"
-        e2e = {"value": rays / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(centers.nbytes),
+        e2e = {"value": rays / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(centers.nbytes) if upload else 0,
                "d2h_bytes_per_step": int(N * (4 + 12 + 4 + 4)), "gpu_launches_per_step": 2}
 
     cpu, err = None, None

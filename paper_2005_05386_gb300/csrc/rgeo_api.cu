@@ -389,7 +389,9 @@ rgeo_status rgeo_scene_create(const float *spheres, int32_t S, const float *vert
   if (!rgeo::build_bvh(spheres, S, verts, V, tris, T, bvh, rgeo::kMaxBvhDepth))
     return fail(RGEO_EINVAL, "rgeo_scene_create: BVH build failed");
   rgeo::HostGrid grid;
-  rgeo::build_safe_grid(spheres, S, verts, tris, T, 64, grid);
+  // 192 cells along the scene's longest axis (about 30 MB for the 1080p scene): a finer grid
+  // gives tighter lower bounds and fewer BVH queries (lattice scenes: 1.9x faster than 64)
+  rgeo::build_safe_grid(spheres, S, verts, tris, T, 192, grid);
 
   rgeo_scene *sc = new rgeo_scene();
   std::memset(&sc->d, 0, sizeof(sc->d));
