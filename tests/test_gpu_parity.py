@@ -350,3 +350,46 @@ def test_fog_survives_surrogate_rounds(rg):
     assert st["rounds"] > 1
     for k in ("id", "rgba", "steps"):
         assert np.array_equal(out[k].cpu().numpy(), plain[k].cpu().numpy()), k
+
+
+def test_concurrent_traces_on_two_streams(rg):
+    """Two traces in flight at once on separate streams (each owns its queue counter, taken from
+    the stream-ordered pool) give the images they give alone."""
+    import torch
+    wa = scenes.config_1080p_64(width=320, height=180)
+    wb = scenes.scaled(scenes.config_quad_lattice(), 256, 144)
+    ha, hb = (rg.Metric(wa.metric), rg.Scene(wa.scene)), (rg.Metric(wb.metric), rg.Scene(wb.scene))
+    alone = []
+    for w, (m, s) in ((wa, ha), (wb, hb)):
+        alone.append(gpu_arrays(rg.trace(w, m, s)))
+        rg.rgeo_sync()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    oa = rg.trace(wa, *ha, stream=sa.cuda_stream)
+    ob = rg.trace(wb, *hb, stream=sb.cuda_stream)
+    rg.rgeo_sync(sa.cuda_stream)
+    rg.rgeo_sync(sb.cuda_stream)
+    for got, ref in zip((gpu_arrays(oa), gpu_arrays(ob)), alone):
+        for k in ("id", "steps", "rgba", "hit"):
+            assert np.array_equal(got[k], ref[k]), k
+
+
+def test_trace_captured_in_a_graph_replays_exactly(rg):
+    import torch
+    w = scenes.config_1080p_64(width=240, height=136)
+    m, s = rg.Metric(w.metric), rg.Scene(w.scene)
+    ref = gpu_arrays(rg.trace(w, m, s))
+    rg.rgeo_sync()
+    out = rg.alloc_outputs(w.n_pixels)
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        rg.trace(w, m, s, out=out, stream=st.cuda_stream)
+    for _ in range(2):
+        for t in out.values():
+            if isinstance(t, torch.Tensor):
+                t.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = gpu_arrays(out)
+        for k in ("id", "steps", "rgba", "hit"):
+            assert np.array_equal(got[k], ref[k]), k
