@@ -164,3 +164,27 @@ def test_autotuner_returns_a_candidate_and_caches(rg, tmp_path, monkeypatch):
     ref = rg.trace(w)
     rg.rgeo_sync()
     _close(gpu_arrays(out), gpu_arrays(ref), w.scene.n_spheres)
+
+
+def test_batch16_full_size_against_oracle(rg):
+    """The 16-instance batch at its full sizes (resolutions up to 1920x1080, 8-256 bumps), in the
+    launch the benchmark times (one persistent launch over all instances), against the oracle
+    on a seeded sample of each instance."""
+    import oracle
+    ws = scenes.config_batch16()
+    scene = rg.Scene(ws[0].scene)
+    metrics = [rg.Metric(w.metric) for w in ws]
+    outs = [rg.alloc_outputs(w.n_pixels) for w in ws]
+    rg.Batch([rg.instance(w, m, scene, o) for w, m, o in zip(ws, metrics, outs)]).launch()
+    rg.rgeo_sync()
+    oscene = oracle.Scene.from_desc(ws[0].scene)
+    total, agreed = 0, 0.0
+    for w, o in zip(ws, outs):
+        px = scenes.pixel_sample(w.n_pixels, w.seed + 7, min(1.0, 300.0 / w.n_pixels))
+        ref = oracle.trace(w, px, scene=oscene)
+        st = compare(gpu_arrays(o, px), ref, w.scene.n_spheres)
+        assert st["same_object"] >= 0.99 and st["agree"] >= 0.99, (w.name, st)
+        total += len(px)
+        agreed += st["agree"] * len(px)
+    # the bar over the whole batch: >= 99.9 % of the sampled pixels agree
+    assert total > 3000 and agreed / total >= 0.999, (agreed / total, total)

@@ -125,3 +125,26 @@ def test_surrogate_rejects_bad_arguments(rg):
         rg.trace_surrogate(w, x, 0.1, accel_bound=0.01, metric=rg.Metric(aniso), scene=ds)
     with pytest.raises(rg.RgeoError):
         rg.Expmap.generate(rg.Metric(aniso), 128, seed=1, accel_bound=0.01)
+
+
+def test_surrogate_full_1080p_sample_within_1e3_of_oracle(rg):
+    """The benchmark's surrogate frame (1920x1080, far-field bound 0.03, tau 0.03, network
+    trained in one call) against the oracle on a seeded pixel sample at the 1e-3 bar."""
+    w = scenes.config_1080p_64()
+    dm, ds = rg.Metric(w.metric), rg.Scene(w.scene)
+    net = rg.Expmap(max_batch=1 << 16, seed=7)
+    net.train(dm, n_segments=1 << 21, steps=3000, batch=8192, accel_bound=0.03, seed=11)
+    out, st = rg.trace_surrogate(w, net, 0.03, accel_bound=0.03, metric=dm, scene=ds)
+    rg.rgeo_sync()
+    assert st["accepted"] > 10000, st
+    px = scenes.pixel_sample(w.n_pixels, 1234, 0.002)
+    ref = oracle.trace(w, px)
+    g = gpu_arrays(out, px)
+    S = w.scene.n_spheres
+    go, ro = objects(g["id"], S), objects(ref["id"], S)
+    same = go == ro
+    hit = same & (go >= 0)
+    d = np.zeros(len(go))
+    d[hit] = np.abs(g["hit"][hit] - ref["hit"][hit]).max(axis=1)
+    ok = same & (d <= 1e-3)
+    assert ok.mean() >= 0.999 and hit.sum() > 500, (ok.mean(), hit.sum())
