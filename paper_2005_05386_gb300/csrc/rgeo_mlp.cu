@@ -645,6 +645,358 @@ __global__ void __launch_bounds__(kInferThreads, 2)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWid) : "memory");
 }
+
+// ------------------------------------ persistent, warp-specialised fused inference
+// The same four layers and the same arithmetic as k_mlp_infer, reorganised so that the
+// tensor core, the weight stream and the CUDA-core work overlap.  One CTA per SM walks
+// the tiles blockIdx.x + i * gridDim.x; tile i uses slot s = i % 2 (shared-memory
+// activations H[s], TMEM accumulator s, columns 256 s .. 256 s + 255).  Roles:
+//   warp 0 (producer): lane 0 streams the 16 KB weight chunks, pre-packed in the MMA
+//     layout, with single bulk copies into a ring of kWsRing slots, in the order the
+//     MMAs consume them;
+//   warp 1 (MMA): lane 0 waits for a tile's input in H[s], issues 8 chunks x 2 MMAs
+//     into accumulator s and commits to acc_full[s];
+//   warps 2..9 and 10..17 (worker groups 0 and 1): group g owns slot g, i.e. the tiles
+//     i = g, g + 2, ...: layer 1 into H[g], the layer-2 epilogue back into H[g], the
+//     layer-3 epilogue with layer 4, then layer 1 of its next tile.
+// The MMAs follow the fixed order L2(2j), L2(2j + 1), L3(2j), L3(2j + 1), j = 0, 1, ...,
+// so one group's CUDA-core phase runs while the tensor core works for the other.
+constexpr int kWsGroupThreads = 256;
+constexpr int kWsThreads = 64 + 2 * kWsGroupThreads;
+constexpr int kWsRing = 4;
+// shared memory: H[2] | weight ring | W1^T, b1 | W4, b2, b3, b4 (8) | layer-4 partial sums [2][7][128]
+constexpr int kWsSmallFloats = kIn * kWid + kWid + kOut * kWid + 2 * kWid + 8 + 2 * kOut * kTileM;
+constexpr int kWsSmem = 2 * kHBytes + kWsRing * kWChunkBytes + kWsSmallFloats * 4;
+constexpr long long kWsSpin = 1ll << 21;
+static_assert(kWsSmem <= 227 * 1024, "shared memory of the persistent inference kernel");
+
+// Chunk c (K columns 32 c .. 32 c + 31) of layer l (0: W2, 1: W3) at element offset
+// (8 l + c) * kWid * kChunkK, laid out exactly as load_w_chunk stages it.
+__global__ void k_pack_chunks(const __nv_bfloat16 *__restrict__ W2b, const __nv_bfloat16 *__restrict__ W3b,
+                              __nv_bfloat16 *__restrict__ Wp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * kWid * kWid) return;
+  const int l = i / (kWid * kWid), r = i % (kWid * kWid);
+  const int nn = r / kWid, k = r % kWid, c = k / kChunkK, kk = k % kChunkK;
+  const int byte = ((nn >> 3) * 4 + (kk >> 3)) * 128 + (nn & 7) * 16 + (kk & 7) * 2;
+  Wp[(size_t)(l * 8 + c) * (kWChunkBytes / 2) + byte / 2] = (l == 0 ? W2b : W3b)[r];
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait that also gives up once another role has raised the abort flag; a wait
+// that runs out raises it.
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kWsSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+// OR of pred over the 256 threads of named barrier id (1 or 2).
+__device__ __forceinline__ bool group_any(int id, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, p;\n setp.ne.u32 q, %2, 0;\n bar.red.or.pred p, %1, %3, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(id), "r"((uint32_t)pred), "n"(kWsGroupThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kWsGroupThreads) : "memory");
+}
+
+// The q-th MMA layer of the fixed order: tile i and layer (0: W2, 1: W3).
+__device__ __forceinline__ void ws_sched(long long q, long long &i, int &layer) {
+  const long long j = q >> 2;
+  const int r = (int)(q & 3);
+  i = 2 * j + (r & 1);
+  layer = r >> 1;
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_mlp_infer_ws(const float *__restrict__ X, long long n, const float *__restrict__ P,
+                   const __nv_bfloat16 *__restrict__ Wp, float *__restrict__ Y) {
+  extern __shared__ __align__(1024) uint8_t wsm[];
+  uint8_t *ring = wsm + 2 * kHBytes;
+  float *w1t = reinterpret_cast<float *>(ring + kWsRing * kWChunkBytes);  // [7][256]
+  float *b1s = w1t + kIn * kWid;
+  float *w4s = b1s + kWid;       // [7][256]
+  float *b23s = w4s + kOut * kWid;  // b2 | b3
+  float *b4s = b23s + 2 * kWid;  // [8]
+  float *parts = b4s + 8;        // [2][7][128]
+  __shared__ uint64_t chunk_full[kWsRing], chunk_empty[kWsRing], h_full[2], acc_full[2], drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  volatile int *abortp = &abort_flag;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const long long ntiles = (n + kTileM - 1) / kTileM;
+  const long long T = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long nq = 4 * ((T + 1) / 2);  // MMA layers of the fixed order, skipped ones included
+
+  if (t == 0) {
+    for (int r = 0; r < kWsRing; ++r) {
+      mbar_init(&chunk_full[r], 1);
+      mbar_init(&chunk_empty[r], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&h_full[s], kWsGroupThreads);
+      mbar_init(&acc_full[s], 1);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(2 * kWid)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int i = t; i < kIn * kWid; i += blockDim.x) w1t[(i % kIn) * kWid + i / kIn] = P[oW1 + i];
+  for (int i = t; i < kWid; i += blockDim.x) {
+    b1s[i] = P[ob1 + i];
+    b23s[i] = P[ob2 + i];
+    b23s[kWid + i] = P[ob3 + i];
+  }
+  for (int i = t; i < kOut * kWid; i += blockDim.x) w4s[i] = P[oW4 + i];
+  if (t < 8) b4s[t] = t < kOut ? P[ob4 + t] : 0.f;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ---- producer
+    long long chunk = 0;
+    bool ok = true;
+    for (long long q = 0; q < nq && ok; ++q) {
+      long long i;
+      int layer;
+      ws_sched(q, i, layer);
+      if (i >= T) continue;
+      for (int c = 0; c < kWid / kChunkK && ok; ++c, ++chunk) {
+        const int r = (int)(chunk % kWsRing);
+        if (lane == 0) {
+          if (chunk >= kWsRing) ok = ws_wait(&chunk_empty[r], (uint32_t)((chunk / kWsRing - 1) & 1), abortp);
+          if (ok) {
+            mbar_expect_tx(&chunk_full[r], kWChunkBytes);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(ring + r * kWChunkBytes)),
+                "l"(Wp + (size_t)(layer * 8 + c) * (kWChunkBytes / 2)), "r"((uint32_t)kWChunkBytes),
+                "r"(smem_u32(&chunk_full[r]))
+                : "memory");
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) --chunk;  // this chunk was not issued
+      }
+    }
+    // every copy issued has landed before the CTA may leave (immediate when all were consumed)
+    if (lane == 0)
+      for (long long c = chunk - 1; c >= 0 && c >= chunk - kWsRing; --c)
+        mbar_wait(&chunk_full[c % kWsRing], (uint32_t)((c / kWsRing) & 1));
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_bf16(kTileM, kWid);
+    long long chunk = 0;
+    uint32_t hwait0 = 0u, hwait1 = 0u;  // completions of h_full[0], h_full[1] waited for
+    bool ok = true;
+    for (long long q = 0; q < nq && ok; ++q) {
+      long long i;
+      int layer;
+      ws_sched(q, i, layer);
+      if (i >= T) continue;
+      const int s = (int)(i & 1);
+      if (lane == 0) {
+        ok = ws_wait(&h_full[s], (s ? hwait1 : hwait0) & 1u, abortp);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(s * kWid);
+        const uint32_t hb = smem_u32(wsm + s * kHBytes);
+        for (int c = 0; c < kWid / kChunkK && ok; ++c, ++chunk) {
+          const int r = (int)(chunk % kWsRing);
+          ok = ws_wait(&chunk_full[r], (uint32_t)((chunk / kWsRing) & 1), abortp);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int j = 0; j < kChunkK / 16; ++j) {
+            const uint64_t ad = smem_desc(hb + (uint32_t)((c * (kChunkK / 16) + j) * 256), 128, 4096);
+            const uint64_t bd = smem_desc(smem_u32(ring + r * kWChunkBytes) + (uint32_t)(j * 256), 128, 512);
+            const uint32_t accum = (c > 0 || j > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&chunk_empty[r]))
+                       : "memory");
+        }
+        if (ok)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&acc_full[s]))
+                       : "memory");
+      }
+      if (s) ++hwait1; else ++hwait0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    }
+    // all MMAs issued have completed before the tensor memory is released
+    if (lane == 0) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&drain))
+                   : "memory");
+      if (!mbar_wait(&drain, 0u)) *abortp = 1;
+    }
+    __syncwarp();
+  } else {
+    // ---- worker group g: 256 threads, slot g, tiles g, g + 2, ...
+    const int g = (warp - 2) >> 3, bar_id = 1 + g;
+    const int wt = t - 64 - g * kWsGroupThreads;
+    const int wq = warp & 3, half = ((warp - 2) >> 2) & 1, row = wq * 32 + lane;
+    uint8_t *sH = wsm + g * kHBytes;
+    float *part = parts + g * kOut * kTileM;  // [7][128]
+    const uint32_t acc = tmem + (uint32_t)(g * kWid);
+    uint32_t await_n = 0u;
+    bool bad = false;
+    // X rows of tile i into L2 ahead of its layer 1 (one 128-byte line per thread)
+    auto prefetch_x = [&](long long i) {
+      const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
+      const long long b0 = row0 * kIn * 4, b1 = (row0 + kTileM < n ? row0 + kTileM : n) * kIn * 4;
+      const long long b = (b0 & ~127ll) + (long long)wt * 128;
+      if (wt < (kTileM * kIn * 4) / 128 + 1 && b < b1)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(X) + b));
+    };
+    // layer 1 in FP32 (paired FMAs): thread wt computes row wt % 128, outputs (wt / 128) * 128 .. + 127
+    auto layer1 = [&](long long i) {
+      const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
+      const int r = wt & (kTileM - 1), hh = wt >> 7;
+      float2 x2[kIn];
+      const long long gr = row0 + r;
+      for (int k = 0; k < kIn; ++k) {
+        const float xv = gr < n ? __ldg(X + gr * kIn + k) : 0.f;
+        x2[k] = make_float2(xv, xv);
+      }
+      for (int jc = 0; jc < 16; ++jc) {
+        const int j0 = hh * 128 + jc * 8;
+        const float4 ba = *reinterpret_cast<const float4 *>(b1s + j0);
+        const float4 bb = *reinterpret_cast<const float4 *>(b1s + j0 + 4);
+        float2 z[4] = {make_float2(ba.x, ba.y), make_float2(ba.z, ba.w), make_float2(bb.x, bb.y),
+                       make_float2(bb.z, bb.w)};
+        for (int k = 0; k < kIn; ++k) {
+          const float4 wa = *reinterpret_cast<const float4 *>(w1t + k * kWid + j0);
+          const float4 wb = *reinterpret_cast<const float4 *>(w1t + k * kWid + j0 + 4);
+          z[0] = __ffma2_rn(make_float2(wa.x, wa.y), x2[k], z[0]);
+          z[1] = __ffma2_rn(make_float2(wa.z, wa.w), x2[k], z[1]);
+          z[2] = __ffma2_rn(make_float2(wb.x, wb.y), x2[k], z[2]);
+          z[3] = __ffma2_rn(make_float2(wb.z, wb.w), x2[k], z[3]);
+        }
+        const float zz[8] = {fmaxf(z[0].x, 0.f), fmaxf(z[0].y, 0.f), fmaxf(z[1].x, 0.f), fmaxf(z[1].y, 0.f),
+                             fmaxf(z[2].x, 0.f), fmaxf(z[2].y, 0.f), fmaxf(z[3].x, 0.f), fmaxf(z[3].y, 0.f)};
+        store_h8(sH, r, j0, zz);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&h_full[g]);
+    };
+    if (g < T) {
+      prefetch_x(g);
+      layer1(g);
+    }
+    for (long long i = g; i < T; i += 2) {
+      const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
+      if (i + 2 < T) prefetch_x(i + 2);
+      float2 y2[kOut];
+      for (int o = 0; o < kOut; ++o) y2[o] = make_float2(0.f, 0.f);
+      for (int layer = 0; layer < 2 && !bad; ++layer) {
+        if (!ws_wait(&acc_full[g], await_n & 1u, abortp)) {
+          bad = true;
+          break;
+        }
+        ++await_n;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float *bias = b23s + layer * kWid;
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const int c0 = half * 128 + k4 * 32;
+          uint32_t v[32];
+          tmem_ld32(acc + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
+          // bias and ReLU, then BF16 pairs (the A operand of layer 3, or the rounded H3 of layer 4)
+          uint32_t hp[16];
+          for (int q = 0; q < 8; ++q) {
+            const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + 4 * q);
+            const float2 u0 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1])),
+                                         make_float2(b.x, b.y));
+            const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])),
+                                         make_float2(b.z, b.w));
+            hp[2 * q] = pack_bf16(fmaxf(u0.x, 0.f), fmaxf(u0.y, 0.f));
+            hp[2 * q + 1] = pack_bf16(fmaxf(u1.x, 0.f), fmaxf(u1.y, 0.f));
+          }
+          if (layer == 0) {
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<uint4 *>(sH + ((row >> 3) * 32 + ((c0 >> 3) + q)) * 128 + (row & 7) * 16) =
+                  make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+          } else {
+            // layer 4 on the BF16-rounded H3 (as the training forward), FP32 paired FMAs:
+            // y2[o] holds the sums over the even and the odd columns
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float2 h0 = make_float2(__uint_as_float(hp[2 * q] << 16), __uint_as_float(hp[2 * q] & 0xffff0000u));
+              const float2 h1 =
+                  make_float2(__uint_as_float(hp[2 * q + 1] << 16), __uint_as_float(hp[2 * q + 1] & 0xffff0000u));
+#pragma unroll
+              for (int o = 0; o < kOut; ++o) {
+                const float4 w = *reinterpret_cast<const float4 *>(w4s + o * kWid + c0 + 4 * q);
+                y2[o] = __ffma2_rn(make_float2(w.x, w.y), h0, y2[o]);
+                y2[o] = __ffma2_rn(make_float2(w.z, w.w), h1, y2[o]);
+              }
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (layer == 0) {  // H2 is in H[g] and accumulator g is drained: layer 3 may start
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(&h_full[g]);
+        }
+      }
+      // every thread of the group takes the same branch from here on
+      if (group_any(bar_id, bad)) {
+        bad = true;
+        break;
+      }
+      if (half == 1)
+        for (int o = 0; o < kOut; ++o) part[o * kTileM + row] = y2[o].x + y2[o].y;
+      group_sync(bar_id);
+      if (half == 0 && row0 + row < n) {
+        float *yr = Y + (row0 + row) * kOut;
+        for (int o = 0; o < kOut; ++o) yr[o] = (y2[o].x + y2[o].y) + part[o * kTileM + row] + b4s[o];
+      }
+      group_sync(bar_id);
+      if (i + 2 < T) layer1(i + 2);
+    }
+    if (bad) *abortp = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (t == 0 && *abortp) atomicOr(&g_mlp_error, kErrTimeout);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWid) : "memory");
+}
 }  // namespace
 
 cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits, const float *bias,
@@ -678,6 +1030,23 @@ cudaError_t launch_mlp_infer(const float *X, long long n, const float *P, const 
   return cudaGetLastError();
 }
 
+// Persistent form: one CTA per SM (at most one per tile); Wp holds W2 and W3 as packed
+// by k_pack_chunks and must start on a 16-byte boundary (bulk copies).
+cudaError_t launch_mlp_infer_ws(const float *X, long long n, const float *P, const __nv_bfloat16 *Wp, float *Y,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(Wp) & 15u) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_infer_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (n + kTileM - 1) / kTileM;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+  k_mlp_infer_ws<<<grid, kWsThreads, kWsSmem, st>>>(X, n, P, Wp, Y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather_batch(const float *X, const float *T, long long n, int B, unsigned long long seed,
                                 long long step, float *Xb, float *Tb, cudaStream_t st) {
   k_gather_batch<<<(B + 255) / 256, 256, 0, st>>>(X, T, n, B, seed, step, Xb, Tb);
@@ -701,6 +1070,7 @@ struct ExpmapDev {
   long long step;
   float *P, *G, *m, *v;
   __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
+  __nv_bfloat16 *Wp;  // W2 and W3 as the 16 KB K-chunks of the persistent inference kernel
   __nv_bfloat16 *H1, *H2, *H3, *H1t, *H2t, *H3t, *dZ, *dZt;
   float *Y, *dY, *dH, *dZ1, *loss;
 };
@@ -711,7 +1081,7 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_all(ExpmapDev &d) {
-  void *ptrs[] = {d.P, d.G, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.H1, d.H2, d.H3, d.H1t, d.H2t, d.H3t,
+  void *ptrs[] = {d.P, d.G, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.Wp, d.H1, d.H2, d.H3, d.H1t, d.H2t, d.H3t,
                   d.dZ, d.dZt, d.Y, d.dY, d.dH, d.dZ1, d.loss};
   for (void *q : ptrs) cudaFree(q);
 }
@@ -759,6 +1129,7 @@ cudaError_t gradients(ExpmapDev &d, const float *X, const float *T, int B, float
 
 cudaError_t refresh(ExpmapDev &d, cudaStream_t st) {
   k_refresh_bf16<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.W2t, d.W3t);
+  k_pack_chunks<<<(2 * kWid * kWid + 255) / 256, 256, 0, st>>>(d.W2b, d.W3b, d.Wp);
   return cudaGetLastError();
 }
 
@@ -785,9 +1156,9 @@ struct rgeo_expmap {
 };
 
 namespace rgeo {
-// Inference over n rows: the fused kernel, one 128-row tile per CTA (no host sync).
+// Inference over n rows: the persistent fused kernel (no host sync).
 cudaError_t expmap_infer(const rgeo_expmap *x, const float *X, long long n, float *Y, cudaStream_t st) {
-  return launch_mlp_infer(X, n, x->d.P, x->d.W2b, x->d.W3b, Y, st);
+  return launch_mlp_infer_ws(X, n, x->d.P, x->d.Wp, Y, st);
 }
 }  // namespace rgeo
 
@@ -815,6 +1186,7 @@ rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **o
   if (e == cudaSuccess) e = dalloc(&d.W3b, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.W2t, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.W3t, (size_t)kWid * kWid);
+  if (e == cudaSuccess) e = dalloc(&d.Wp, (size_t)2 * kWid * kWid);
   __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H3, &d.H1t, &d.H2t, &d.H3t, &d.dZ, &d.dZt};
   for (auto b : bufs)
     if (e == cudaSuccess) e = dalloc(b, HW);

@@ -142,6 +142,36 @@ def test_forward_matches_oracle(rg):
     assert x.forward(torch.empty(0, 7, device="cuda")).shape == (0, 7)
 
 
+def test_forward_rows_independent_of_tile_and_slot(rg):
+    """The persistent inference kernel walks several 128-row tiles per CTA, two in flight.
+    A row's output must not depend on which tile, CTA or slot it lands in: the full batch
+    (5-6 tiles per CTA, ragged tail), a row permutation of it and short slices at odd
+    offsets must agree bit for bit, and a sample must match the FP64 oracle."""
+    import torch
+    x = rg.Expmap(max_batch=128, seed=4)
+    params = x.get_params().astype(np.float64)
+    n = 152 * 128 * 5 + 77
+    r = np.random.default_rng(1)
+    Xh = np.concatenate([r.uniform(-1, 1, (n, 3)), r.normal(size=(n, 3)), r.uniform(0, 1, (n, 1))], axis=1)
+    Xh[:, 3:6] /= np.linalg.norm(Xh[:, 3:6], axis=1, keepdims=True)
+    X = torch.tensor(Xh, dtype=torch.float32, device="cuda")
+    Y = x.forward(X)
+    perm = torch.from_numpy(r.permutation(n)).cuda()
+    Yp = x.forward(X[perm].contiguous())
+    rg.rgeo_sync()
+    assert torch.equal(Yp, Y[perm])
+    for a, b in [(0, 1), (5, 300), (n - 200, n), (12345, 12345 + 129), (70000, 97000)]:
+        Ys = x.forward(X[a:b].contiguous())
+        rg.rgeo_sync()
+        assert torch.equal(Ys, Y[a:b]), (a, b)
+    px = r.choice(n, 3000, replace=False)
+    Yr, _ = mlp.forward(params, Xh[px].astype(np.float32).astype(np.float64))
+    Yc = Y.cpu().numpy()[px]
+    for o in range(7):
+        rel = np.linalg.norm(Yc[:, o] - Yr[:, o]) / np.linalg.norm(Yr[:, o])
+        assert rel < 3e-2, (o, rel)
+
+
 @pytest.mark.parametrize("batch", [256, 2048])
 def test_gradients_match_oracle(rg, batch):
     """Back-propagation on the tensor cores against the oracle's FP64 back-propagation
