@@ -647,47 +647,120 @@ __global__ void __launch_bounds__(kInferThreads, 2)
 }
 
 // ------------------------------------ persistent, warp-specialised fused inference
-// The same four layers and the same arithmetic as k_mlp_infer, reorganised so that the
-// tensor core, the weight stream and the CUDA-core work overlap.  One CTA per SM walks
-// the tiles blockIdx.x + i * gridDim.x; tile i uses slot s = i % 2 (shared-memory
-// activations H[s], TMEM accumulator s, columns 256 s .. 256 s + 255).  Roles:
-//   warp 0 (producer): lane 0 streams the 16 KB weight chunks, pre-packed in the MMA
-//     layout, with single bulk copies into a ring of kWsRing slots, in the order the
-//     MMAs consume them;
-//   warp 1 (MMA): lane 0 waits for a tile's input in H[s], issues 8 chunks x 2 MMAs
-//     into accumulator s and commits to acc_full[s];
-//   warps 2..9 and 10..17 (worker groups 0 and 1): group g owns slot g, i.e. the tiles
-//     i = g, g + 2, ...: layer 1 into H[g], the layer-2 epilogue back into H[g], the
-//     layer-3 epilogue with layer 4, then layer 1 of its next tile.
-// The MMAs follow the fixed order L2(2j), L2(2j + 1), L3(2j), L3(2j + 1), j = 0, 1, ...,
-// so one group's CUDA-core phase runs while the tensor core works for the other.
+// All four layers on the tensor core, with the epilogues on the CUDA cores overlapping
+// the MMAs of the other tile in flight.  One CTA per SM walks the tiles
+// blockIdx.x + i * gridDim.x; tile i uses slot s = i % 2 (shared-memory operand H[s],
+// TMEM accumulator s, columns 256 s .. 256 s + 255).
+//
+// Layers 1 and 4 take FP32 operands.  To keep their products at FP32 accuracy on the BF16
+// tensor core, each FP32 value a is split into a_hi = bf16(a) and a_lo = bf16(a - a_hi)
+// (16 significant bits together), and every cross term is kept:
+//   layer 1 (K = 32): A row = [x_hi 1 | x_hi 1 | x_lo 0 | x_lo 0],
+//                     B row = [w_hi b_hi | w_lo b_lo | w_hi 0 | w_lo 0]  (b1 folded in);
+//   layer 4 (N = 16): columns 0..6 take W4_hi, columns 8..14 take W4_lo, and the epilogue
+//                     adds the two halves and b4.  Its A operand is H3 rounded to BF16, as
+//                     in the training forward.
+// Layers 2 and 3 are the BF16 products of the training forward.
+//
+// Roles:
+//   warp 0 (producer): lane 0 bulk-copies the resident layer-1 and layer-4 operands once,
+//     then streams the 16 KB K-chunks of W2 and W3 into a ring of kWsRing slots, one pass
+//     over both per pair of tiles;
+//   warp 1 (MMA): lane 0 takes the tiles in pairs (2 j in slot 0, 2 j + 1 in slot 1):
+//     layer 1 of each, then layers 2 and 3 chunk by chunk with each chunk's MMAs issued for
+//     both tiles before the chunk is released, then layer 4 of each; it commits every
+//     finished layer to acc_full[s];
+//   warps 2..9 and 10..17 (worker groups 0 and 1): group g owns slot g (tiles g, g + 2, ...):
+//     it writes the layer-1 operand from X, then after each of the first three layers reads
+//     the accumulator, adds the bias, applies ReLU and writes the next layer's BF16 operand
+//     into H[g]; after layer 4 it writes Y.
+// Sharing each chunk between the two tiles halves the weight traffic from L2, which bounds
+// the rate at which the ring can be refilled.
 constexpr int kWsGroupThreads = 256;
 constexpr int kWsThreads = 64 + 2 * kWsGroupThreads;
 constexpr int kWsRing = 4;
-// shared memory: H[2] | weight ring | W1^T, b1 | W4, b2, b3, b4 (8) | layer-4 partial sums [2][7][128]
-constexpr int kWsSmallFloats = kIn * kWid + kWid + kOut * kWid + 2 * kWid + 8 + 2 * kOut * kTileM;
-constexpr int kWsSmem = 2 * kHBytes + kWsRing * kWChunkBytes + kWsSmallFloats * 4;
+constexpr int kK1 = 32;                              // layer-1 K (split inputs and bias)
+constexpr int kN4 = 16;                              // layer-4 N (split W4)
+constexpr int kB1Bytes = kWid * kK1 * 2;             // 16 KB
+constexpr int kB4Bytes = kN4 * kWid * 2;             // 8 KB
+constexpr int kPackedElems = 2 * kWid * kWid + (kB1Bytes + kB4Bytes) / 2;
+// shared memory: H[2] | weight ring | B1 | B4 | biases of layers 1..3 (layer 1: zeros) | b4 (8)
+constexpr int kWsSmem = 2 * kHBytes + kWsRing * kWChunkBytes + kB1Bytes + kB4Bytes + (3 * kWid + 8) * 4;
 constexpr long long kWsSpin = 1ll << 21;
 static_assert(kWsSmem <= 227 * 1024, "shared memory of the persistent inference kernel");
 
-// Chunk c (K columns 32 c .. 32 c + 31) of layer l (0: W2, 1: W3) at element offset
-// (8 l + c) * kWid * kChunkK, laid out exactly as load_w_chunk stages it.
-__global__ void k_pack_chunks(const __nv_bfloat16 *__restrict__ W2b, const __nv_bfloat16 *__restrict__ W3b,
-                              __nv_bfloat16 *__restrict__ Wp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * kWid * kWid) return;
-  const int l = i / (kWid * kWid), r = i % (kWid * kWid);
-  const int nn = r / kWid, k = r % kWid, c = k / kChunkK, kk = k % kChunkK;
-  const int byte = ((nn >> 3) * 4 + (kk >> 3)) * 128 + (nn & 7) * 16 + (kk & 7) * 2;
-  Wp[(size_t)(l * 8 + c) * (kWChunkBytes / 2) + byte / 2] = (l == 0 ? W2b : W3b)[r];
+__device__ __forceinline__ void split_bf16(float a, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(a);
+  lo = __float2bfloat16_rn(a - __bfloat162float(hi));
 }
 
+// Wp = [W2 chunks 0..7 | W3 chunks 0..7 | B1 | B4], every piece in the canonical K-major
+// layout its MMAs read (8-row x 16-byte core matrices):
+//   chunk c of W2 / W3 (K columns 32 c .. 32 c + 31): core (n / 8, k / 8) at (4 (n / 8) + k / 8) * 128;
+//   B1 (256 x 32): the same layout as a chunk;
+//   B4 (16 x 256): core (n / 8, k / 8) at (32 (n / 8) + k / 8) * 128.
+__global__ void k_pack_chunks(const float *__restrict__ P, const __nv_bfloat16 *__restrict__ W2b,
+                              const __nv_bfloat16 *__restrict__ W3b, __nv_bfloat16 *__restrict__ Wp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 * kWid * kWid) {
+    const int l = i / (kWid * kWid), r = i % (kWid * kWid);
+    const int nn = r / kWid, k = r % kWid, c = k / kChunkK, kk = k % kChunkK;
+    const int byte = ((nn >> 3) * 4 + (kk >> 3)) * 128 + (nn & 7) * 16 + (kk & 7) * 2;
+    Wp[(size_t)(l * 8 + c) * (kWChunkBytes / 2) + byte / 2] = (l == 0 ? W2b : W3b)[r];
+  } else if (i < 2 * kWid * kWid + kWid * kK1) {
+    const int r = i - 2 * kWid * kWid, nn = r / kK1, k = r % kK1, blk = k >> 3, kk = k & 7;
+    // blocks: 0 [w_hi b_hi], 1 [w_lo b_lo], 2 [w_hi 0], 3 [w_lo 0]
+    const float a = kk < kIn ? P[oW1 + nn * kIn + kk] : (blk < 2 ? P[ob1 + nn] : 0.f);
+    __nv_bfloat16 hi, lo;
+    split_bf16(a, hi, lo);
+    const int byte = ((nn >> 3) * 4 + blk) * 128 + (nn & 7) * 16 + kk * 2;
+    Wp[(size_t)2 * kWid * kWid + byte / 2] = (blk & 1) ? lo : hi;
+  } else if (i < kPackedElems) {
+    const int r = i - 2 * kWid * kWid - kWid * kK1, nn = r / kWid, k = r % kWid, o = nn & 7;
+    __nv_bfloat16 hi, lo;
+    split_bf16(o < kOut ? P[oW4 + o * kWid + k] : 0.f, hi, lo);
+    const int byte = ((nn >> 3) * 32 + (k >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2;
+    Wp[(size_t)2 * kWid * kWid + kWid * kK1 + byte / 2] = nn < 8 ? hi : lo;
+  }
+}
+
+// max(a, 0), max(b, 0) rounded to BF16 and packed (a in the low half), in one conversion
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t acc, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 // Bounded wait that also gives up once another role has raised the abort flag; a wait
 // that runs out raises it.
@@ -716,37 +789,24 @@ __device__ __forceinline__ bool group_any(int id, bool pred) {
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void group_sync(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kWsGroupThreads) : "memory");
-}
-
-// The q-th MMA layer of the fixed order: tile i and layer (0: W2, 1: W3).
-__device__ __forceinline__ void ws_sched(long long q, long long &i, int &layer) {
-  const long long j = q >> 2;
-  const int r = (int)(q & 3);
-  i = 2 * j + (r & 1);
-  layer = r >> 1;
-}
 
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_mlp_infer_ws(const float *__restrict__ X, long long n, const float *__restrict__ P,
                    const __nv_bfloat16 *__restrict__ Wp, float *__restrict__ Y) {
   extern __shared__ __align__(1024) uint8_t wsm[];
   uint8_t *ring = wsm + 2 * kHBytes;
-  float *w1t = reinterpret_cast<float *>(ring + kWsRing * kWChunkBytes);  // [7][256]
-  float *b1s = w1t + kIn * kWid;
-  float *w4s = b1s + kWid;       // [7][256]
-  float *b23s = w4s + kOut * kWid;  // b2 | b3
-  float *b4s = b23s + 2 * kWid;  // [8]
-  float *parts = b4s + 8;        // [2][7][128]
-  __shared__ uint64_t chunk_full[kWsRing], chunk_empty[kWsRing], h_full[2], acc_full[2], drain;
+  uint8_t *B1 = ring + kWsRing * kWChunkBytes;
+  uint8_t *B4 = B1 + kB1Bytes;
+  float *bias_s = reinterpret_cast<float *>(B4 + kB4Bytes);  // [3][256]: 0 | b2 | b3
+  float *b4s = bias_s + 3 * kWid;                            // [8]
+  __shared__ uint64_t chunk_full[kWsRing], chunk_empty[kWsRing], h_full[2], acc_full[2], const_full, drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   volatile int *abortp = &abort_flag;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const long long ntiles = (n + kTileM - 1) / kTileM;
   const long long T = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long nq = 4 * ((T + 1) / 2);  // MMA layers of the fixed order, skipped ones included
+  const long long npairs = (T + 1) / 2;
 
   if (t == 0) {
     for (int r = 0; r < kWsRing; ++r) {
@@ -754,9 +814,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       mbar_init(&chunk_empty[r], 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&h_full[s], kWsGroupThreads);
+      mbar_init(&h_full[s], kWsGroupThreads / 32);  // one arrival per worker warp
       mbar_init(&acc_full[s], 1);
     }
+    mbar_init(&const_full, 1);
     mbar_init(&drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -767,13 +828,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int i = t; i < kIn * kWid; i += blockDim.x) w1t[(i % kIn) * kWid + i / kIn] = P[oW1 + i];
   for (int i = t; i < kWid; i += blockDim.x) {
-    b1s[i] = P[ob1 + i];
-    b23s[i] = P[ob2 + i];
-    b23s[kWid + i] = P[ob3 + i];
+    bias_s[i] = 0.f;
+    bias_s[kWid + i] = P[ob2 + i];
+    bias_s[2 * kWid + i] = P[ob3 + i];
   }
-  for (int i = t; i < kOut * kWid; i += blockDim.x) w4s[i] = P[oW4 + i];
   if (t < 8) b4s[t] = t < kOut ? P[ob4 + t] : 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -782,85 +841,102 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 
   if (warp == 0) {
     // ---- producer
+    if (lane == 0) {
+      mbar_expect_tx(&const_full, kB1Bytes + kB4Bytes);
+      bulk_copy(B1, Wp + 2 * kWid * kWid, kB1Bytes, &const_full);
+      bulk_copy(B4, Wp + 2 * kWid * kWid + kB1Bytes / 2, kB4Bytes, &const_full);
+    }
     long long chunk = 0;
     bool ok = true;
-    for (long long q = 0; q < nq && ok; ++q) {
-      long long i;
-      int layer;
-      ws_sched(q, i, layer);
-      if (i >= T) continue;
-      for (int c = 0; c < kWid / kChunkK && ok; ++c, ++chunk) {
-        const int r = (int)(chunk % kWsRing);
-        if (lane == 0) {
-          if (chunk >= kWsRing) ok = ws_wait(&chunk_empty[r], (uint32_t)((chunk / kWsRing - 1) & 1), abortp);
-          if (ok) {
-            mbar_expect_tx(&chunk_full[r], kWChunkBytes);
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(ring + r * kWChunkBytes)),
-                "l"(Wp + (size_t)(layer * 8 + c) * (kWChunkBytes / 2)), "r"((uint32_t)kWChunkBytes),
-                "r"(smem_u32(&chunk_full[r]))
-                : "memory");
+    // one pass over W2 and W3 per pair of tiles: each chunk serves both tiles
+    for (long long j = 0; j < npairs && ok; ++j) {
+      for (int l = 0; l < 2 && ok; ++l) {
+        for (int c = 0; c < kWid / kChunkK && ok; ++c, ++chunk) {
+          const int r = (int)(chunk % kWsRing);
+          if (lane == 0) {
+            if (chunk >= kWsRing) ok = ws_wait(&chunk_empty[r], (uint32_t)((chunk / kWsRing - 1) & 1), abortp);
+            if (ok) {
+              mbar_expect_tx(&chunk_full[r], kWChunkBytes);
+              bulk_copy(ring + r * kWChunkBytes, Wp + (size_t)(l * 8 + c) * (kWChunkBytes / 2), kWChunkBytes,
+                        &chunk_full[r]);
+            }
           }
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) --chunk;  // this chunk was not issued
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) --chunk;  // this chunk was not issued
       }
     }
     // every copy issued has landed before the CTA may leave (immediate when all were consumed)
-    if (lane == 0)
+    if (lane == 0) {
+      mbar_wait(&const_full, 0u);
       for (long long c = chunk - 1; c >= 0 && c >= chunk - kWsRing; --c)
         mbar_wait(&chunk_full[c % kWsRing], (uint32_t)((c / kWsRing) & 1));
+    }
     __syncwarp();
   } else if (warp == 1) {
-    // ---- MMA issuer
-    const uint32_t idesc = idesc_bf16(kTileM, kWid);
+    // ---- MMA issuer.  Per pair of tiles (a = 2 j in slot 0, b = 2 j + 1 in slot 1):
+    // L1(a), L1(b); L2 and L3 chunk by chunk, each chunk's MMAs for a then b; L4(a), L4(b).
+    const uint32_t idesc_n256 = idesc_bf16(kTileM, kWid), idesc_n16 = idesc_bf16(kTileM, kN4);
+    // descriptors of the operand bases; an offset of o bytes adds o / 16 to the address field
+    const uint64_t dH[2] = {smem_desc(smem_u32(wsm), 128, 4096), smem_desc(smem_u32(wsm + kHBytes), 128, 4096)};
+    const uint64_t dRing = smem_desc(smem_u32(ring), 128, 512);
+    const uint64_t dB1 = smem_desc(smem_u32(B1), 128, 512), dB4 = smem_desc(smem_u32(B4), 128, 4096);
     long long chunk = 0;
-    uint32_t hwait0 = 0u, hwait1 = 0u;  // completions of h_full[0], h_full[1] waited for
+    uint32_t hwait[2] = {0u, 0u};  // completions of h_full[s] waited for
     bool ok = true;
-    for (long long q = 0; q < nq && ok; ++q) {
-      long long i;
-      int layer;
-      ws_sched(q, i, layer);
-      if (i >= T) continue;
-      const int s = (int)(i & 1);
+    if (lane == 0) ok = ws_wait(&const_full, 0u, abortp);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    for (long long j = 0; j < npairs && ok; ++j) {
+      const int ns = 2 * j + 1 < T ? 2 : 1;
       if (lane == 0) {
-        ok = ws_wait(&h_full[s], (s ? hwait1 : hwait0) & 1u, abortp);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc = tmem + (uint32_t)(s * kWid);
-        const uint32_t hb = smem_u32(wsm + s * kHBytes);
-        for (int c = 0; c < kWid / kChunkK && ok; ++c, ++chunk) {
-          const int r = (int)(chunk % kWsRing);
-          ok = ws_wait(&chunk_full[r], (uint32_t)((chunk / kWsRing) & 1), abortp);
+        auto wait_operand = [&](int s) {
+          ok = ok && ws_wait(&h_full[s], hwait[s] & 1u, abortp);
+          ++hwait[s];
+        };
+        for (int s = 0; s < ns; ++s) {  // layer 1: K = 32 (split inputs, folded bias)
+          wait_operand(s);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          for (int j = 0; j < kChunkK / 16; ++j) {
-            const uint64_t ad = smem_desc(hb + (uint32_t)((c * (kChunkK / 16) + j) * 256), 128, 4096);
-            const uint64_t bd = smem_desc(smem_u32(ring + r * kWChunkBytes) + (uint32_t)(j * 256), 128, 512);
-            const uint32_t accum = (c > 0 || j > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-                : "memory");
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&chunk_empty[r]))
-                       : "memory");
+          const uint32_t acc = tmem + (uint32_t)(s * kWid);
+          mma_bf16(acc, dH[s], dB1, idesc_n256, 0u);
+          mma_bf16(acc, dH[s] + 16, dB1 + 16, idesc_n256, 1u);
+          mma_commit(&acc_full[s]);
         }
-        if (ok)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&acc_full[s]))
-                       : "memory");
+        for (int l = 0; l < 2 && ok; ++l) {  // layers 2 and 3: 8 chunks of K = 32
+          for (int s = 0; s < ns; ++s) wait_operand(s);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int c = 0; c < kWid / kChunkK; ++c, ++chunk) {
+            const int r = (int)(chunk % kWsRing);
+            ok = ws_wait(&chunk_full[r], (uint32_t)((chunk / kWsRing) & 1), abortp);
+            if (!ok) break;
+            const uint64_t dB = dRing + (uint64_t)(r * (kWChunkBytes >> 4));
+            for (int s = 0; s < ns; ++s) {
+              const uint32_t acc = tmem + (uint32_t)(s * kWid);
+              const uint64_t dA = dH[s] + (uint64_t)(c * 32);
+              mma_bf16(acc, dA, dB, idesc_n256, c > 0 ? 1u : 0u);
+              mma_bf16(acc, dA + 16, dB + 16, idesc_n256, 1u);
+              if (c == kWid / kChunkK - 1) mma_commit(&acc_full[s]);
+            }
+            mma_commit(&chunk_empty[r]);
+          }
+        }
+        for (int s = 0; s < ns && ok; ++s) {  // layer 4: N = 16 (split W4)
+          wait_operand(s);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t acc = tmem + (uint32_t)(s * kWid);
+#pragma unroll
+          for (int k = 0; k < kWid / 16; ++k)
+            mma_bf16(acc, dH[s] + (uint64_t)(k * 16), dB4 + (uint64_t)(k * 16), idesc_n16, k > 0 ? 1u : 0u);
+          mma_commit(&acc_full[s]);
+        }
       }
-      if (s) ++hwait1; else ++hwait0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
     }
     // all MMAs issued have completed before the tensor memory is released
     if (lane == 0) {
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&drain))
-                   : "memory");
+      mma_commit(&drain);
       if (!mbar_wait(&drain, 0u)) *abortp = 1;
     }
     __syncwarp();
@@ -870,11 +946,18 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     const int wt = t - 64 - g * kWsGroupThreads;
     const int wq = warp & 3, half = ((warp - 2) >> 2) & 1, row = wq * 32 + lane;
     uint8_t *sH = wsm + g * kHBytes;
-    float *part = parts + g * kOut * kTileM;  // [7][128]
-    const uint32_t acc = tmem + (uint32_t)(g * kWid);
+    const uint32_t acc = tmem + (uint32_t)(g * kWid) + ((uint32_t)(wq * 32) << 16);
     uint32_t await_n = 0u;
     bool bad = false;
-    // X rows of tile i into L2 ahead of its layer 1 (one 128-byte line per thread)
+    // This thread's part of H[g] is written (and its accumulator reads are done): make the
+    // writes visible to the tensor core, then one arrival per warp.
+    auto operand_ready = [&]() {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&h_full[g]);
+    };
+    // X rows of tile i into L2 ahead of use (one 128-byte line per thread)
     auto prefetch_x = [&](long long i) {
       const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
       const long long b0 = row0 * kIn * 4, b1 = (row0 + kTileM < n ? row0 + kTileM : n) * kIn * 4;
@@ -882,111 +965,86 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       if (wt < (kTileM * kIn * 4) / 128 + 1 && b < b1)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(X) + b));
     };
-    // layer 1 in FP32 (paired FMAs): thread wt computes row wt % 128, outputs (wt / 128) * 128 .. + 127
-    auto layer1 = [&](long long i) {
+    // the layer-1 operand of tile i: thread wt writes K blocks 2 (wt / 128) and 2 (wt / 128) + 1
+    // of row wt % 128 (blocks 0, 1: [x_hi 1]; blocks 2, 3: [x_lo 0])
+    auto operand1 = [&](long long i) {
       const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
       const int r = wt & (kTileM - 1), hh = wt >> 7;
-      float2 x2[kIn];
       const long long gr = row0 + r;
-      for (int k = 0; k < kIn; ++k) {
-        const float xv = gr < n ? __ldg(X + gr * kIn + k) : 0.f;
-        x2[k] = make_float2(xv, xv);
+      uint32_t w[4];
+      float xv[8];
+      for (int k = 0; k < kIn; ++k) xv[k] = gr < n ? __ldg(X + gr * kIn + k) : 0.f;
+      xv[7] = hh == 0 ? 1.f : 0.f;
+      for (int k = 0; k < 8; k += 2) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(xv[k], h0, l0);
+        split_bf16(xv[k + 1], h1, l1);
+        const __nv_bfloat162 p = hh == 0 ? __halves2bfloat162(h0, h1) : __halves2bfloat162(l0, l1);
+        w[k >> 1] = *reinterpret_cast<const uint32_t *>(&p);
       }
-      for (int jc = 0; jc < 16; ++jc) {
-        const int j0 = hh * 128 + jc * 8;
-        const float4 ba = *reinterpret_cast<const float4 *>(b1s + j0);
-        const float4 bb = *reinterpret_cast<const float4 *>(b1s + j0 + 4);
-        float2 z[4] = {make_float2(ba.x, ba.y), make_float2(ba.z, ba.w), make_float2(bb.x, bb.y),
-                       make_float2(bb.z, bb.w)};
-        for (int k = 0; k < kIn; ++k) {
-          const float4 wa = *reinterpret_cast<const float4 *>(w1t + k * kWid + j0);
-          const float4 wb = *reinterpret_cast<const float4 *>(w1t + k * kWid + j0 + 4);
-          z[0] = __ffma2_rn(make_float2(wa.x, wa.y), x2[k], z[0]);
-          z[1] = __ffma2_rn(make_float2(wa.z, wa.w), x2[k], z[1]);
-          z[2] = __ffma2_rn(make_float2(wb.x, wb.y), x2[k], z[2]);
-          z[3] = __ffma2_rn(make_float2(wb.z, wb.w), x2[k], z[3]);
-        }
-        const float zz[8] = {fmaxf(z[0].x, 0.f), fmaxf(z[0].y, 0.f), fmaxf(z[1].x, 0.f), fmaxf(z[1].y, 0.f),
-                             fmaxf(z[2].x, 0.f), fmaxf(z[2].y, 0.f), fmaxf(z[3].x, 0.f), fmaxf(z[3].y, 0.f)};
-        store_h8(sH, r, j0, zz);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&h_full[g]);
+      const uint4 q = make_uint4(w[0], w[1], w[2], w[3]);
+      uint8_t *base = sH + (r >> 3) * 4096 + (r & 7) * 16 + hh * 256;
+      *reinterpret_cast<uint4 *>(base) = q;
+      *reinterpret_cast<uint4 *>(base + 128) = q;
+      operand_ready();
     };
     if (g < T) {
       prefetch_x(g);
-      layer1(g);
+      operand1(g);
     }
     for (long long i = g; i < T; i += 2) {
       const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
       if (i + 2 < T) prefetch_x(i + 2);
-      float2 y2[kOut];
-      for (int o = 0; o < kOut; ++o) y2[o] = make_float2(0.f, 0.f);
-      for (int layer = 0; layer < 2 && !bad; ++layer) {
+      for (int layer = 0; layer < 4 && !bad; ++layer) {
         if (!ws_wait(&acc_full[g], await_n & 1u, abortp)) {
           bad = true;
           break;
         }
         ++await_n;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float *bias = b23s + layer * kWid;
-        for (int k4 = 0; k4 < 4; ++k4) {
-          const int c0 = half * 128 + k4 * 32;
-          uint32_t v[32];
-          tmem_ld32(acc + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
-          // bias and ReLU, then BF16 pairs (the A operand of layer 3, or the rounded H3 of layer 4)
-          uint32_t hp[16];
-          for (int q = 0; q < 8; ++q) {
-            const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + 4 * q);
-            const float2 u0 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1])),
-                                         make_float2(b.x, b.y));
-            const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])),
-                                         make_float2(b.z, b.w));
-            hp[2 * q] = pack_bf16(fmaxf(u0.x, 0.f), fmaxf(u0.y, 0.f));
-            hp[2 * q + 1] = pack_bf16(fmaxf(u1.x, 0.f), fmaxf(u1.y, 0.f));
-          }
-          if (layer == 0) {
+        if (layer < 3) {
+          // bias, ReLU and BF16 into the next layer's operand; this half's 128 columns
+          const float *bias = bias_s + layer * kWid;
+#pragma unroll 1
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const int c0 = half * 128 + k4 * 32;
+            uint32_t v[32];
+            tmem_ld32(acc + (uint32_t)c0, v);
+            uint32_t hp[16];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + 4 * q);
+              const float2 u0 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1])),
+                                           make_float2(b.x, b.y));
+              const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])),
+                                           make_float2(b.z, b.w));
+              hp[2 * q] = pack_bf16_relu(u0.x, u0.y);
+              hp[2 * q + 1] = pack_bf16_relu(u1.x, u1.y);
+            }
+#pragma unroll
             for (int q = 0; q < 4; ++q)
               *reinterpret_cast<uint4 *>(sH + ((row >> 3) * 32 + ((c0 >> 3) + q)) * 128 + (row & 7) * 16) =
                   make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-          } else {
-            // layer 4 on the BF16-rounded H3 (as the training forward), FP32 paired FMAs:
-            // y2[o] holds the sums over the even and the odd columns
+          }
+          operand_ready();
+        } else if (half == 0) {
+          // layer 4: hi + lo columns, plus b4
+          uint32_t v[16];
+          tmem_ld16(acc, v);
+          if (row0 + row < n) {
+            float *yr = Y + (row0 + row) * kOut;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float2 h0 = make_float2(__uint_as_float(hp[2 * q] << 16), __uint_as_float(hp[2 * q] & 0xffff0000u));
-              const float2 h1 =
-                  make_float2(__uint_as_float(hp[2 * q + 1] << 16), __uint_as_float(hp[2 * q + 1] & 0xffff0000u));
-#pragma unroll
-              for (int o = 0; o < kOut; ++o) {
-                const float4 w = *reinterpret_cast<const float4 *>(w4s + o * kWid + c0 + 4 * q);
-                y2[o] = __ffma2_rn(make_float2(w.x, w.y), h0, y2[o]);
-                y2[o] = __ffma2_rn(make_float2(w.z, w.w), h1, y2[o]);
-              }
-            }
+            for (int o = 0; o < kOut; ++o) yr[o] = (__uint_as_float(v[o]) + __uint_as_float(v[8 + o])) + b4s[o];
           }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (layer == 0) {  // H2 is in H[g] and accumulator g is drained: layer 3 may start
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(&h_full[g]);
-        }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       // every thread of the group takes the same branch from here on
       if (group_any(bar_id, bad)) {
         bad = true;
         break;
       }
-      if (half == 1)
-        for (int o = 0; o < kOut; ++o) part[o * kTileM + row] = y2[o].x + y2[o].y;
-      group_sync(bar_id);
-      if (half == 0 && row0 + row < n) {
-        float *yr = Y + (row0 + row) * kOut;
-        for (int o = 0; o < kOut; ++o) yr[o] = (y2[o].x + y2[o].y) + part[o * kTileM + row] + b4s[o];
-      }
-      group_sync(bar_id);
-      if (i + 2 < T) layer1(i + 2);
+      if (i + 2 < T) operand1(i + 2);
     }
     if (bad) *abortp = 1;
   }
@@ -1070,7 +1128,7 @@ struct ExpmapDev {
   long long step;
   float *P, *G, *m, *v;
   __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
-  __nv_bfloat16 *Wp;  // W2 and W3 as the 16 KB K-chunks of the persistent inference kernel
+  __nv_bfloat16 *Wp;  // the operands of the persistent inference kernel, packed by k_pack_chunks
   __nv_bfloat16 *H1, *H2, *H3, *H1t, *H2t, *H3t, *dZ, *dZt;
   float *Y, *dY, *dH, *dZ1, *loss;
 };
@@ -1129,7 +1187,7 @@ cudaError_t gradients(ExpmapDev &d, const float *X, const float *T, int B, float
 
 cudaError_t refresh(ExpmapDev &d, cudaStream_t st) {
   k_refresh_bf16<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.W2t, d.W3t);
-  k_pack_chunks<<<(2 * kWid * kWid + 255) / 256, 256, 0, st>>>(d.W2b, d.W3b, d.Wp);
+  k_pack_chunks<<<(kPackedElems + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.Wp);
   return cudaGetLastError();
 }
 
@@ -1186,7 +1244,7 @@ rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **o
   if (e == cudaSuccess) e = dalloc(&d.W3b, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.W2t, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.W3t, (size_t)kWid * kWid);
-  if (e == cudaSuccess) e = dalloc(&d.Wp, (size_t)2 * kWid * kWid);
+  if (e == cudaSuccess) e = dalloc(&d.Wp, (size_t)kPackedElems);
   __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H3, &d.H1t, &d.H2t, &d.H3t, &d.dZ, &d.dZt};
   for (auto b : bufs)
     if (e == cudaSuccess) e = dalloc(b, HW);
