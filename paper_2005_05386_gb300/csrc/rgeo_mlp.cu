@@ -660,7 +660,10 @@ __global__ void __launch_bounds__(kInferThreads, 2)
 //   layer 4 (N = 16): columns 0..6 take W4_hi, columns 8..14 take W4_lo, and the epilogue
 //                     adds the two halves and b4.  Its A operand is H3 rounded to BF16, as
 //                     in the training forward.
-// Layers 2 and 3 are the BF16 products of the training forward.
+// Layers 2 and 3 are the BF16 products of the training forward; their biases enter as one
+// more K = 16 step: the activations carry a constant block [1 1 0 ... 0] after their 256
+// columns, and the matching "bias chunk" of B holds [b_hi b_lo 0 ... 0].  Every epilogue is
+// then ReLU and BF16 rounding only.
 //
 // Roles:
 //   warp 0 (producer): lane 0 bulk-copies the resident layer-1 and layer-4 operands once,
@@ -683,9 +686,13 @@ constexpr int kK1 = 32;                              // layer-1 K (split inputs 
 constexpr int kN4 = 16;                              // layer-4 N (split W4)
 constexpr int kB1Bytes = kWid * kK1 * 2;             // 16 KB
 constexpr int kB4Bytes = kN4 * kWid * 2;             // 8 KB
-constexpr int kPackedElems = 2 * kWid * kWid + (kB1Bytes + kB4Bytes) / 2;
-// shared memory: H[2] | weight ring | B1 | B4 | biases of layers 1..3 (layer 1: zeros) | b4 (8)
-constexpr int kWsSmem = 2 * kHBytes + kWsRing * kWChunkBytes + kB1Bytes + kB4Bytes + (3 * kWid + 8) * 4;
+constexpr int kBiasChunkBytes = kWid * 16 * 2;       // 8 KB: the bias step of layers 2 and 3
+constexpr int kPackedElems = 2 * kWid * kWid + (kB1Bytes + kB4Bytes + 2 * kBiasChunkBytes) / 2;
+// activations of one tile: 16 row groups of 34 core matrices (256 columns + the bias block)
+constexpr int kHGroupBytes = (kWid / 8 + 2) * 128;  // 4352
+constexpr int kHsBytes = (kTileM / 8) * kHGroupBytes;  // 68 KB
+// shared memory: H[2] | weight ring | B1 | B4 | b4 (8)
+constexpr int kWsSmem = 2 * kHsBytes + kWsRing * kWChunkBytes + kB1Bytes + kB4Bytes + 8 * 4;
 constexpr long long kWsSpin = 1ll << 21;
 static_assert(kWsSmem <= 227 * 1024, "shared memory of the persistent inference kernel");
 
@@ -694,11 +701,12 @@ __device__ __forceinline__ void split_bf16(float a, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16_rn(a - __bfloat162float(hi));
 }
 
-// Wp = [W2 chunks 0..7 | W3 chunks 0..7 | B1 | B4], every piece in the canonical K-major
-// layout its MMAs read (8-row x 16-byte core matrices):
+// Wp = [W2 chunks 0..7 | W3 chunks 0..7 | B1 | B4 | bias chunk of W2 | bias chunk of W3], every
+// piece in the canonical K-major layout its MMAs read (8-row x 16-byte core matrices):
 //   chunk c of W2 / W3 (K columns 32 c .. 32 c + 31): core (n / 8, k / 8) at (4 (n / 8) + k / 8) * 128;
 //   B1 (256 x 32): the same layout as a chunk;
-//   B4 (16 x 256): core (n / 8, k / 8) at (32 (n / 8) + k / 8) * 128.
+//   B4 (16 x 256): core (n / 8, k / 8) at (32 (n / 8) + k / 8) * 128;
+//   bias chunk (256 x 16, row n = [b_hi b_lo 0 ... 0]): core (n / 8, k / 8) at (2 (n / 8) + k / 8) * 128.
 __global__ void k_pack_chunks(const float *__restrict__ P, const __nv_bfloat16 *__restrict__ W2b,
                               const __nv_bfloat16 *__restrict__ W3b, __nv_bfloat16 *__restrict__ Wp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -715,12 +723,20 @@ __global__ void k_pack_chunks(const float *__restrict__ P, const __nv_bfloat16 *
     split_bf16(a, hi, lo);
     const int byte = ((nn >> 3) * 4 + blk) * 128 + (nn & 7) * 16 + kk * 2;
     Wp[(size_t)2 * kWid * kWid + byte / 2] = (blk & 1) ? lo : hi;
-  } else if (i < kPackedElems) {
+  } else if (i < 2 * kWid * kWid + kWid * kK1 + kN4 * kWid) {
     const int r = i - 2 * kWid * kWid - kWid * kK1, nn = r / kWid, k = r % kWid, o = nn & 7;
     __nv_bfloat16 hi, lo;
     split_bf16(o < kOut ? P[oW4 + o * kWid + k] : 0.f, hi, lo);
     const int byte = ((nn >> 3) * 32 + (k >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2;
     Wp[(size_t)2 * kWid * kWid + kWid * kK1 + byte / 2] = nn < 8 ? hi : lo;
+  } else if (i < kPackedElems) {
+    const int r = i - 2 * kWid * kWid - kWid * kK1 - kN4 * kWid, l = r / (kWid * 16), nn = (r / 16) % kWid,
+              k = r % 16;
+    __nv_bfloat16 hi, lo;
+    split_bf16(P[(l == 0 ? ob2 : ob3) + nn], hi, lo);
+    const __nv_bfloat16 v = k == 0 ? hi : (k == 1 ? lo : __float2bfloat16_rn(0.f));
+    const int byte = ((nn >> 3) * 2 + (k >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2;
+    Wp[(size_t)2 * kWid * kWid + kWid * kK1 + kN4 * kWid + (size_t)l * (kBiasChunkBytes / 2) + byte / 2] = v;
   }
 }
 
@@ -753,6 +769,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t acc, uint64_t ad, uint64_t bd,
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+        "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
@@ -794,11 +821,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     k_mlp_infer_ws(const float *__restrict__ X, long long n, const float *__restrict__ P,
                    const __nv_bfloat16 *__restrict__ Wp, float *__restrict__ Y) {
   extern __shared__ __align__(1024) uint8_t wsm[];
-  uint8_t *ring = wsm + 2 * kHBytes;
+  uint8_t *ring = wsm + 2 * kHsBytes;
   uint8_t *B1 = ring + kWsRing * kWChunkBytes;
   uint8_t *B4 = B1 + kB1Bytes;
-  float *bias_s = reinterpret_cast<float *>(B4 + kB4Bytes);  // [3][256]: 0 | b2 | b3
-  float *b4s = bias_s + 3 * kWid;                            // [8]
+  float *b4s = reinterpret_cast<float *>(B4 + kB4Bytes);  // [8]
   __shared__ uint64_t chunk_full[kWsRing], chunk_empty[kWsRing], h_full[2], acc_full[2], const_full, drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -828,11 +854,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  for (int i = t; i < kWid; i += blockDim.x) {
-    bias_s[i] = 0.f;
-    bias_s[kWid + i] = P[ob2 + i];
-    bias_s[2 * kWid + i] = P[ob3 + i];
+  // the constant bias block of both slots' activations: core matrices 32 ([1 1 0 ... 0]) and 33 (0)
+  for (int i = t; i < 2 * kTileM; i += blockDim.x) {
+    const int s = i / kTileM, r = i % kTileM;
+    uint8_t *q = wsm + s * kHsBytes + (r >> 3) * kHGroupBytes + (kWid / 8) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4 *>(q) = make_uint4(0x3F803F80u, 0u, 0u, 0u);  // BF16 1.0, 1.0
+    *reinterpret_cast<uint4 *>(q + 128) = make_uint4(0u, 0u, 0u, 0u);
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (t < 8) b4s[t] = t < kOut ? P[ob4 + t] : 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -851,14 +880,18 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     // one pass over W2 and W3 per pair of tiles: each chunk serves both tiles
     for (long long j = 0; j < npairs && ok; ++j) {
       for (int l = 0; l < 2 && ok; ++l) {
-        for (int c = 0; c < kWid / kChunkK && ok; ++c, ++chunk) {
+        for (int c = 0; c <= kWid / kChunkK && ok; ++c, ++chunk) {  // 8 chunks, then the bias chunk
           const int r = (int)(chunk % kWsRing);
           if (lane == 0) {
             if (chunk >= kWsRing) ok = ws_wait(&chunk_empty[r], (uint32_t)((chunk / kWsRing - 1) & 1), abortp);
             if (ok) {
-              mbar_expect_tx(&chunk_full[r], kWChunkBytes);
-              bulk_copy(ring + r * kWChunkBytes, Wp + (size_t)(l * 8 + c) * (kWChunkBytes / 2), kWChunkBytes,
-                        &chunk_full[r]);
+              const bool bias = c == kWid / kChunkK;
+              const uint32_t bytes = bias ? kBiasChunkBytes : kWChunkBytes;
+              const __nv_bfloat16 *src =
+                  bias ? Wp + 2 * kWid * kWid + (kB1Bytes + kB4Bytes) / 2 + (size_t)l * (kBiasChunkBytes / 2)
+                       : Wp + (size_t)(l * 8 + c) * (kWChunkBytes / 2);
+              mbar_expect_tx(&chunk_full[r], bytes);
+              bulk_copy(ring + r * kWChunkBytes, src, bytes, &chunk_full[r]);
             }
           }
           ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -878,7 +911,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     // L1(a), L1(b); L2 and L3 chunk by chunk, each chunk's MMAs for a then b; L4(a), L4(b).
     const uint32_t idesc_n256 = idesc_bf16(kTileM, kWid), idesc_n16 = idesc_bf16(kTileM, kN4);
     // descriptors of the operand bases; an offset of o bytes adds o / 16 to the address field
-    const uint64_t dH[2] = {smem_desc(smem_u32(wsm), 128, 4096), smem_desc(smem_u32(wsm + kHBytes), 128, 4096)};
+    const uint64_t dH[2] = {smem_desc(smem_u32(wsm), 128, kHGroupBytes),
+                            smem_desc(smem_u32(wsm + kHsBytes), 128, kHGroupBytes)};
+    const uint64_t dRingBias = smem_desc(smem_u32(ring), 128, 256);  // bias chunk: 2 core matrices per row group
     const uint64_t dRing = smem_desc(smem_u32(ring), 128, 512);
     const uint64_t dB1 = smem_desc(smem_u32(B1), 128, 512), dB4 = smem_desc(smem_u32(B4), 128, 4096);
     long long chunk = 0;
@@ -906,17 +941,24 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           for (int s = 0; s < ns; ++s) wait_operand(s);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          for (int c = 0; c < kWid / kChunkK; ++c, ++chunk) {
+          for (int c = 0; c <= kWid / kChunkK; ++c, ++chunk) {
             const int r = (int)(chunk % kWsRing);
             ok = ws_wait(&chunk_full[r], (uint32_t)((chunk / kWsRing) & 1), abortp);
             if (!ok) break;
-            const uint64_t dB = dRing + (uint64_t)(r * (kWChunkBytes >> 4));
-            for (int s = 0; s < ns; ++s) {
-              const uint32_t acc = tmem + (uint32_t)(s * kWid);
-              const uint64_t dA = dH[s] + (uint64_t)(c * 32);
-              mma_bf16(acc, dA, dB, idesc_n256, c > 0 ? 1u : 0u);
-              mma_bf16(acc, dA + 16, dB + 16, idesc_n256, 1u);
-              if (c == kWid / kChunkK - 1) mma_commit(&acc_full[s]);
+            if (c < kWid / kChunkK) {
+              const uint64_t dB = dRing + (uint64_t)(r * (kWChunkBytes >> 4));
+              for (int s = 0; s < ns; ++s) {
+                const uint32_t acc = tmem + (uint32_t)(s * kWid);
+                const uint64_t dA = dH[s] + (uint64_t)(c * 32);
+                mma_bf16(acc, dA, dB, idesc_n256, c > 0 ? 1u : 0u);
+                mma_bf16(acc, dA + 16, dB + 16, idesc_n256, 1u);
+              }
+            } else {  // the bias step: K columns 256..271 of the activations
+              const uint64_t dB = dRingBias + (uint64_t)(r * (kWChunkBytes >> 4));
+              for (int s = 0; s < ns; ++s) {
+                mma_bf16(tmem + (uint32_t)(s * kWid), dH[s] + (uint64_t)((kWid / 8) * 8), dB, idesc_n256, 1u);
+                mma_commit(&acc_full[s]);
+              }
             }
             mma_commit(&chunk_empty[r]);
           }
@@ -945,7 +987,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     const int g = (warp - 2) >> 3, bar_id = 1 + g;
     const int wt = t - 64 - g * kWsGroupThreads;
     const int wq = warp & 3, half = ((warp - 2) >> 2) & 1, row = wq * 32 + lane;
-    uint8_t *sH = wsm + g * kHBytes;
+    uint8_t *sH = wsm + g * kHsBytes;
     const uint32_t acc = tmem + (uint32_t)(g * kWid) + ((uint32_t)(wq * 32) << 16);
     uint32_t await_n = 0u;
     bool bad = false;
@@ -983,7 +1025,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         w[k >> 1] = *reinterpret_cast<const uint32_t *>(&p);
       }
       const uint4 q = make_uint4(w[0], w[1], w[2], w[3]);
-      uint8_t *base = sH + (r >> 3) * 4096 + (r & 7) * 16 + hh * 256;
+      uint8_t *base = sH + (r >> 3) * kHGroupBytes + (r & 7) * 16 + hh * 256;
       *reinterpret_cast<uint4 *>(base) = q;
       *reinterpret_cast<uint4 *>(base + 128) = q;
       operand_ready();
@@ -1003,28 +1045,26 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         ++await_n;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (layer < 3) {
-          // bias, ReLU and BF16 into the next layer's operand; this half's 128 columns
-          const float *bias = bias_s + layer * kWid;
+          // ReLU and BF16 (the bias is in the accumulator) into the next layer's operand; this
+          // half's 128 columns, two 32-column loads in flight
 #pragma unroll 1
-          for (int k4 = 0; k4 < 4; ++k4) {
-            const int c0 = half * 128 + k4 * 32;
-            uint32_t v[32];
-            tmem_ld32(acc + (uint32_t)c0, v);
-            uint32_t hp[16];
+          for (int k2 = 0; k2 < 2; ++k2) {
+            uint32_t v[2][32];
+            tmem_ld32_nowait(acc + (uint32_t)(half * 128 + k2 * 64), v[0]);
+            tmem_ld32_nowait(acc + (uint32_t)(half * 128 + k2 * 64 + 32), v[1]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + 4 * q);
-              const float2 u0 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1])),
-                                           make_float2(b.x, b.y));
-              const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])),
-                                           make_float2(b.z, b.w));
-              hp[2 * q] = pack_bf16_relu(u0.x, u0.y);
-              hp[2 * q + 1] = pack_bf16_relu(u1.x, u1.y);
+            for (int u = 0; u < 2; ++u) {
+              const int c0 = half * 128 + k2 * 64 + u * 32;
+              uint8_t *dst = sH + (row >> 3) * kHGroupBytes + (c0 >> 3) * 128 + (row & 7) * 16;
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4 *>(dst + q * 128) =
+                    make_uint4(pack_bf16_relu(__uint_as_float(v[u][8 * q]), __uint_as_float(v[u][8 * q + 1])),
+                               pack_bf16_relu(__uint_as_float(v[u][8 * q + 2]), __uint_as_float(v[u][8 * q + 3])),
+                               pack_bf16_relu(__uint_as_float(v[u][8 * q + 4]), __uint_as_float(v[u][8 * q + 5])),
+                               pack_bf16_relu(__uint_as_float(v[u][8 * q + 6]), __uint_as_float(v[u][8 * q + 7])));
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<uint4 *>(sH + ((row >> 3) * 32 + ((c0 >> 3) + q)) * 128 + (row & 7) * 16) =
-                  make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
           }
           operand_ready();
         } else if (half == 0) {
