@@ -6,11 +6,13 @@
 // both backward products -- run on the 5th-generation tensor cores:
 //   * tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulation) issued by one thread,
 //   * accumulators in tensor memory (TMEM), read back with tcgen05.ld,
-//   * operands staged in shared memory in the canonical K-major layout without
-//     swizzle (8-row x 16-byte core matrices), double-buffered with cp.async,
+//   * operands in shared memory in the canonical K-major layout without swizzle
+//     (8-row x 16-byte core matrices): staged with cp.async by the training GEMM,
+//     bulk-copied (cp.async.bulk) by the persistent inference kernel,
 //   * completion signalled through mbarriers by tcgen05.commit.
-// Every wait is bounded: a wait that runs out records kErrTimeout in the error
-// word and the kernel returns after releasing its tensor memory.
+// Inference runs all four layers in one persistent, warp-specialised kernel
+// (k_mlp_infer_ws).  Every wait is bounded: a wait that runs out records kErrTimeout
+// in the error word and the kernel returns after releasing its tensor memory.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -440,217 +442,11 @@ __global__ void k_init(float *P, unsigned long long seed) {
 }
 
 
-// ------------------------------------------------------ fused inference
-// All four layers for one 128-row tile per CTA (256 threads, two CTAs per SM):
-//   layer 1 (FP32) writes H1 straight into shared memory as the BF16 A operand;
-//   layers 2 and 3 are tcgen05 MMAs (M 128, N 256, K 16) into one TMEM accumulator,
-//   with W2 / W3 streamed in K-chunks of 32 through two cp.async buffers;
-//   their epilogues (bias, ReLU, BF16) go back to shared memory (H2) or, for H3,
-//   straight into the FP32 layer 4.  Activations never leave the SM.
-constexpr int kInferThreads = 256;
-constexpr int kChunkK = 32;
-constexpr int kHBytes = kTileM * kWid * 2;        // 64 KB
-constexpr int kWChunkBytes = kWid * kChunkK * 2;  // 16 KB
-constexpr int kInferSmem = kHBytes + 2 * kWChunkBytes + (kIn * kWid + kWid) * 4;  // 104 KB
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-        "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
-  return *reinterpret_cast<const uint32_t *>(&p);
-}
-
-// Eight consecutive columns j0..j0+7 of tile row r in the canonical K-major layout of
-// the A operand (8-row x 16-byte core matrices, 32 per row group: LBO 128, SBO 4096).
-__device__ __forceinline__ void store_h8(uint8_t *sH, int r, int j0, const float (&z)[8]) {
-  const uint4 q = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]),
-                             pack_bf16(z[6], z[7]));
-  *reinterpret_cast<uint4 *>(sH + ((r >> 3) * 32 + (j0 >> 3)) * 128 + (r & 7) * 16) = q;
-}
-
-// K-chunk c (columns 32 c .. 32 c + 31) of a row-major [256 x 256] bf16 weight as the B
-// operand: core matrix (row group g, chunk cc) at (4 g + cc) * 128 (LBO 128, SBO 512).
-__device__ __forceinline__ void load_w_chunk(uint8_t *dst, const __nv_bfloat16 *W, int c) {
-  for (int q = threadIdx.x; q < kWid * 4; q += blockDim.x) {
-    const int n = q >> 2, cc = q & 3;
-    cp_async16(dst + ((n >> 3) * 4 + cc) * 128 + (n & 7) * 16, W + (size_t)n * kWid + c * kChunkK + cc * 8);
-  }
-  cp_async_commit();
-}
-
-__global__ void __launch_bounds__(kInferThreads, 2)
-    k_mlp_infer(const float *__restrict__ X, long long n, const float *__restrict__ P,
-                const __nv_bfloat16 *__restrict__ W2b, const __nv_bfloat16 *__restrict__ W3b, float *__restrict__ Y) {
-  extern __shared__ __align__(1024) uint8_t ism[];
-  uint8_t *sH = ism;
-  uint8_t *sW[2] = {ism + kHBytes, ism + kHBytes + kWChunkBytes};
-  float *w1t = reinterpret_cast<float *>(ism + kHBytes + 2 * kWChunkBytes);  // [7][256]
-  float *b1s = w1t + kIn * kWid;
-  __shared__ uint64_t bar_buf[2], bar_done;
-  __shared__ uint32_t tmem_slot;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const long long row0 = (long long)blockIdx.x * kTileM;
-
-  if (t == 0) {
-    mbar_init(&bar_buf[0], 1);
-    mbar_init(&bar_buf[1], 1);
-    mbar_init(&bar_done, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(kWid)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  for (int i = t; i < kIn * kWid; i += blockDim.x) w1t[(i % kIn) * kWid + i / kIn] = P[oW1 + i];
-  for (int i = t; i < kWid; i += blockDim.x) b1s[i] = P[ob1 + i];
-  load_w_chunk(sW[0], W2b, 0);  // the first chunk of W2 flies while layer 1 runs
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_slot;
-
-  // layer 1: thread t computes tile row t % 128, outputs (t / 128) * 128 .. + 127
-  {
-    const int r = t & (kTileM - 1), half = t >> 7;
-    float x[kIn];
-    const long long gr = row0 + r;
-    for (int k = 0; k < kIn; ++k) x[k] = gr < n ? __ldg(X + gr * kIn + k) : 0.f;
-    for (int jc = 0; jc < 16; ++jc) {
-      const int j0 = half * 128 + jc * 8;
-      const float4 ba = *reinterpret_cast<const float4 *>(b1s + j0), bb = *reinterpret_cast<const float4 *>(b1s + j0 + 4);
-      float z[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-      for (int k = 0; k < kIn; ++k) {
-        const float4 wa = *reinterpret_cast<const float4 *>(w1t + k * kWid + j0);
-        const float4 wb = *reinterpret_cast<const float4 *>(w1t + k * kWid + j0 + 4);
-        z[0] = fmaf(wa.x, x[k], z[0]); z[1] = fmaf(wa.y, x[k], z[1]);
-        z[2] = fmaf(wa.z, x[k], z[2]); z[3] = fmaf(wa.w, x[k], z[3]);
-        z[4] = fmaf(wb.x, x[k], z[4]); z[5] = fmaf(wb.y, x[k], z[5]);
-        z[6] = fmaf(wb.z, x[k], z[6]); z[7] = fmaf(wb.w, x[k], z[7]);
-      }
-      for (int i = 0; i < 8; ++i) z[i] = fmaxf(z[i], 0.f);
-      store_h8(sH, r, j0, z);
-    }
-  }
-
-  const uint32_t idesc = idesc_bf16(kTileM, kWid);
-  uint32_t ncommit[2] = {0u, 0u}, ndone = 0u;
-  bool ok = true;
-  const int wq = warp & 3, half = warp >> 2, row = wq * 32 + lane;
-  float y[kOut];
-  for (int o = 0; o < kOut; ++o) y[o] = 0.f;
-  for (int layer = 0; layer < 2; ++layer) {
-    const __nv_bfloat16 *W = layer == 0 ? W2b : W3b;
-    if (layer == 1) load_w_chunk(sW[0], W, 0);
-    for (int c = 0; c < kWid / kChunkK; ++c) {
-      const int buf = c & 1;
-      cp_async_wait_all();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (t == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int j = 0; j < kChunkK / 16; ++j) {
-          const uint64_t ad = smem_desc(smem_u32(sH) + (uint32_t)((c * (kChunkK / 16) + j) * 256), 128, 4096);
-          const uint64_t bd = smem_desc(smem_u32(sW[buf]) + (uint32_t)(j * 256), 128, 512);
-          const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&bar_buf[buf]))
-                     : "memory");
-      }
-      ncommit[buf]++;
-      if (c + 1 < kWid / kChunkK) {
-        const int nb = buf ^ 1;
-        // the other buffer is free once the MMAs that last read it have completed
-        if (ncommit[nb] > 0 && !mbar_wait(&bar_buf[nb], (ncommit[nb] - 1u) & 1u)) ok = false;
-        load_w_chunk(sW[nb], W, c + 1);
-      }
-    }
-    if (t == 0)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&bar_done))
-                   : "memory");
-    ++ndone;
-    if (!mbar_wait(&bar_done, (ndone - 1u) & 1u)) ok = false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns (w / 4) * 128 .. + 127
-    const float *bias = P + (layer == 0 ? ob2 : ob3);
-    for (int i = 0; i < 4; ++i) {
-      const int c0 = half * 128 + i * 32;
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
-      float h[32];
-      for (int q = 0; q < 8; ++q) {
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(bias + c0) + q);
-        h[4 * q] = fmaxf(__uint_as_float(v[4 * q]) + b.x, 0.f);
-        h[4 * q + 1] = fmaxf(__uint_as_float(v[4 * q + 1]) + b.y, 0.f);
-        h[4 * q + 2] = fmaxf(__uint_as_float(v[4 * q + 2]) + b.z, 0.f);
-        h[4 * q + 3] = fmaxf(__uint_as_float(v[4 * q + 3]) + b.w, 0.f);
-      }
-      if (layer == 0) {
-        for (int q = 0; q < 4; ++q) {
-          const float z[8] = {h[8 * q], h[8 * q + 1], h[8 * q + 2], h[8 * q + 3],
-                              h[8 * q + 4], h[8 * q + 5], h[8 * q + 6], h[8 * q + 7]};
-          store_h8(sH, row, c0 + 8 * q, z);
-        }
-      } else {
-        // layer 4 on the BF16-rounded H3, as the training forward does
-        for (int q = 0; q < 32; ++q) h[q] = __bfloat162float(__float2bfloat16_rn(h[q]));
-        for (int o = 0; o < kOut; ++o) {
-          const float4 *w4 = reinterpret_cast<const float4 *>(P + oW4 + o * kWid + c0);
-          float acc = y[o];
-          for (int q = 0; q < 8; ++q) {
-            const float4 w = __ldg(w4 + q);
-            acc = fmaf(w.x, h[4 * q], acc);
-            acc = fmaf(w.y, h[4 * q + 1], acc);
-            acc = fmaf(w.z, h[4 * q + 2], acc);
-            acc = fmaf(w.w, h[4 * q + 3], acc);
-          }
-          y[o] = acc;
-        }
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  }
-  // combine the two column halves of layer 4 (the weight buffers are free now)
-  __syncthreads();
-  float *part = reinterpret_cast<float *>(sW[0]);
-  if (half == 1)
-    for (int o = 0; o < kOut; ++o) part[row * 8 + o] = y[o];
-  __syncthreads();
-  if (half == 0 && row0 + row < n) {
-    float *yr = Y + (row0 + row) * kOut;
-    for (int o = 0; o < kOut; ++o) yr[o] = y[o] + part[row * 8 + o] + __ldg(P + ob4 + o);
-  }
-  if (!ok && t == 0) atomicOr(&g_mlp_error, kErrTimeout);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWid) : "memory");
-}
-
 // ------------------------------------ persistent, warp-specialised fused inference
-// All four layers on the tensor core, with the epilogues on the CUDA cores overlapping
-// the MMAs of the other tile in flight.  One CTA per SM walks the tiles
+// All four layers on the tensor core; the CUDA cores only build the layer-1 operand and
+// run the epilogues (ReLU, BF16 rounding, the final sum).  One CTA per SM walks the tiles
 // blockIdx.x + i * gridDim.x; tile i uses slot s = i % 2 (shared-memory operand H[s],
-// TMEM accumulator s, columns 256 s .. 256 s + 255).
+// TMEM accumulator s, columns 256 s .. 256 s + 255), so two tiles are in flight.
 //
 // Layers 1 and 4 take FP32 operands.  To keep their products at FP32 accuracy on the BF16
 // tensor core, each FP32 value a is split into a_hi = bf16(a) and a_lo = bf16(a - a_hi)
@@ -679,6 +475,8 @@ __global__ void __launch_bounds__(kInferThreads, 2)
 //     into H[g]; after layer 4 it writes Y.
 // Sharing each chunk between the two tiles halves the weight traffic from L2, which bounds
 // the rate at which the ring can be refilled.
+constexpr int kChunkK = 32;                       // K columns per streamed weight chunk
+constexpr int kWChunkBytes = kWid * kChunkK * 2;  // 16 KB
 constexpr int kWsGroupThreads = 256;
 constexpr int kWsThreads = 64 + 2 * kWsGroupThreads;
 constexpr int kWsRing = 4;
@@ -1114,17 +912,6 @@ cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, 
   k_gemm_bf16<<<grid, 128, smem, st>>>(reinterpret_cast<const __nv_bfloat16 *>(A),
                                         reinterpret_cast<const __nv_bfloat16 *>(B), M, N, K, kchunk, bias, mode, C,
                                         ldc, reinterpret_cast<__nv_bfloat16 *>(ct), ldt);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_infer(const float *X, long long n, const float *P, const __nv_bfloat16 *W2b,
-                             const __nv_bfloat16 *W3b, float *Y, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
-  if (e != cudaSuccess) return e;
-  const long long tiles = (n + kTileM - 1) / kTileM;
-  if (tiles > 0x7fffffffll) return cudaErrorInvalidValue;
-  k_mlp_infer<<<(unsigned)tiles, kInferThreads, kInferSmem, st>>>(X, n, P, W2b, W3b, Y);
   return cudaGetLastError();
 }
 
