@@ -129,7 +129,10 @@ def test_surrogate_rejects_bad_arguments(rg):
 
 def test_surrogate_full_1080p_sample_within_1e3_of_oracle(rg):
     """The benchmark's surrogate frame (1920x1080, far-field bound 0.03, tau 0.03, network
-    trained in one call) against the oracle on a seeded pixel sample at the 1e-3 bar."""
+    trained in one call) against the oracle on a seeded pixel sample at the 1e-3 bar.  The
+    sample is 1 % of the frame (about 20,700 pixels), so that the 0.999 bar tolerates about
+    20 misses; silhouette pixels miss at a rate of a few 1e-4, and a 0.2 % sample (4
+    tolerated misses) left the outcome to chance."""
     w = scenes.config_1080p_64()
     dm, ds = rg.Metric(w.metric), rg.Scene(w.scene)
     net = rg.Expmap(max_batch=1 << 16, seed=7)
@@ -137,7 +140,7 @@ def test_surrogate_full_1080p_sample_within_1e3_of_oracle(rg):
     out, st = rg.trace_surrogate(w, net, 0.03, accel_bound=0.03, metric=dm, scene=ds)
     rg.rgeo_sync()
     assert st["accepted"] > 10000, st
-    px = scenes.pixel_sample(w.n_pixels, 1234, 0.002)
+    px = scenes.pixel_sample(w.n_pixels, 1234, 0.01)
     ref = oracle.trace(w, px)
     g = gpu_arrays(out, px)
     S = w.scene.n_spheres
@@ -147,4 +150,4 @@ def test_surrogate_full_1080p_sample_within_1e3_of_oracle(rg):
     d = np.zeros(len(go))
     d[hit] = np.abs(g["hit"][hit] - ref["hit"][hit]).max(axis=1)
     ok = same & (d <= 1e-3)
-    assert ok.mean() >= 0.999 and hit.sum() > 500, (ok.mean(), hit.sum())
+    assert ok.mean() >= 0.999 and hit.sum() > 2500, (ok.mean(), (~ok).sum(), len(ok), hit.sum())
