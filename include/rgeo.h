@@ -186,8 +186,9 @@ rgeo_status rgeo_scene_create(const float *spheres, int32_t n_spheres, const flo
                               int32_t n_verts, const int32_t *tris, int32_t n_tris,
                               const float *albedo, rgeo_scene **out);
 
-/* Fog (the grid figures of Section 6 are rendered "with a small (black) fog
- * component"): a hit's colour c (Lambert or pseudo-colour) becomes
+/* Fog (Section 6 renders its grid figures with a faint black fog; the paper gives no
+ * formula, so this is exponential attenuation along the ray): a hit's colour c
+ * (Lambert or pseudo-colour) becomes
  * c T + rgb (1 - T), T = exp(-density * L), with L the arc length travelled to the hit
  * (h per integration step, the fraction of h on the hit segment, and the length of
  * each closed-form advance through flat space).  density = 0 (the default) turns it
