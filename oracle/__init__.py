@@ -22,6 +22,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   trace              straight-line scenes against analytic hits; curved scenes are
                      "parity unpinned" beyond the invariants above (the paper prints no
                      worked image or number)
+  illuminate         light geodesics by shooting: the segment q -> L in flat space, the
+                     Riemannian cosine under affine f (Sherman-Morrison), preimages of lines
+                     under the twist, the axis of a radial bump, re-integration to the light;
+                     shadows by analytic occluders (tests/test_oracle_illum.py)
 """
 from __future__ import annotations
 
@@ -107,6 +111,15 @@ def lib():
                                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int64, _ip, _dp, _ip,
                                _u8p, _dp, _dp, ctypes.c_int, ctypes.c_int]
+        L.or_trace_lit.restype = ctypes.c_int
+        L.or_trace_lit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   _dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_double, _i64p, ctypes.c_int64, _ip, _dp, _ip, _u8p, _ip, ctypes.c_int]
+        L.or_illuminate.restype = ctypes.c_int
+        L.or_illuminate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    _dp, _dp, _u8p, _dp, _ip, _dp]
         _lib = L
     return _lib
 
@@ -360,3 +373,50 @@ def trace(work, pixels=None, nthreads=None, metric: Metric = None, scene: Scene 
     out["pixels"] = pixels
     out["threads"] = nt
     return out
+
+
+def trace_lit(work, light, pixels=None, nthreads=None, metric: Metric = None, scene: Scene = None):
+    """Trace ``work`` with Riemannian illumination of every hit by the point light ``light``
+    (a ``scenes.Light``): the hits are shaded by the light geodesics (Section 4).
+
+    Returns a dict of numpy arrays: id, hit [n,3], steps, rgba [n,4], lit."""
+    m = metric or Metric.from_desc(work.metric)
+    sc = scene or Scene.from_desc(work.scene)
+    if pixels is None:
+        pixels = np.arange(work.width * work.height, dtype=np.int64)
+    pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+    n = pixels.shape[0]
+    out = dict(id=np.zeros(n, np.int32), hit=np.zeros((n, 3)), steps=np.zeros(n, np.int32),
+               rgba=np.zeros((n, 4), np.uint8), lit=np.zeros(n, np.int32))
+    cam = work.camera
+    keep = [_d(cam.pos), _d(cam.forward), _d(cam.up), _d(light.pos)]
+    (_, pp), (_, pf), (_, pu), (_, pl) = keep
+    nt = nthreads or default_threads()
+    lib().or_trace_lit(m.ptr, sc.ptr, pp, pf, pu, float(cam.vfov_deg), work.width, work.height, float(work.h),
+                       int(work.max_steps), int(work.integrator), pl, float(light.h), int(light.max_steps),
+                       int(light.iters), float(light.tol), float(light.delta), pixels.ctypes.data_as(_i64p), n,
+                       out["id"].ctypes.data_as(_ip), out["hit"].ctypes.data_as(_dp),
+                       out["steps"].ctypes.data_as(_ip), out["rgba"].ctypes.data_as(_u8p),
+                       out["lit"].ctypes.data_as(_ip), int(nt))
+    del keep
+    out["pixels"] = pixels
+    out["threads"] = nt
+    return out
+
+
+def illuminate(m: Metric, sc: Scene, light, integrator: int, obj_id: int, P, D):
+    """Illumination of one hit (point P on object obj_id, reached along direction D).
+
+    Returns (lit, rgba [4], Riemannian cosine, Gauss-Newton steps, initial g-unit tangent [3])."""
+    keep = [_d(light.pos), _d(P), _d(D)]
+    (_, pl), (_, pp), (_, pd) = keep
+    rgba = np.zeros(4, np.uint8)
+    cosg = np.zeros(1)
+    it = np.zeros(1, np.int32)
+    u = np.zeros(3)
+    lit = lib().or_illuminate(m.ptr, sc.ptr, pl, float(light.h), int(light.max_steps), int(light.iters),
+                              float(light.tol), float(light.delta), int(integrator), int(obj_id), pp, pd,
+                              rgba.ctypes.data_as(_u8p), cosg.ctypes.data_as(_dp), it.ctypes.data_as(_ip),
+                              u.ctypes.data_as(_dp))
+    del keep
+    return bool(lit), rgba, float(cosg[0]), int(it[0]), u

@@ -879,9 +879,21 @@ static void shade(const or_scene *sc, int shading, int id, const double P[3], co
   rgba[3] = 255;
 }
 
+/* A point light and the parameters of the shooting solve (Riemannian illumination, below). */
+typedef struct or_light_s {
+  double L[3];
+  double h;
+  int max_steps;
+  int iters;
+  double tol;
+  double delta;
+} or_light;
+
 typedef struct {
   const or_metric *m;
   const or_scene *sc;
+  const struct or_light_s *light; /* non-NULL: Riemannian illumination of the hits */
+  int32_t *lit;                   /* with light: 1 when lit */
   or_camera cam;
   int W, H;
   double h;
@@ -894,6 +906,10 @@ typedef struct {
 } or_job;
 
 /* One pixel: Riemannian shading of one direction of the view field. */
+int or_illuminate_hit(const or_metric *m, const or_scene *sc, const struct or_light_s *lt, int integrator, int id,
+                      const double P[3], const double Dhit[3], uint8_t rgba[4], double *cos_out,
+                      int *iters_out, double u_out[3]);
+
 static void trace_pixel(const or_job *jb, int64_t q) {
   const or_metric *m = jb->m;
   int64_t px = jb->pixels[q];
@@ -947,7 +963,11 @@ static void trace_pixel(const or_job *jb, int64_t q) {
   if (id >= 0) {
     for (int c = 0; c < 3; c++) o->hit[3 * q + c] = P[c];
     shade(jb->sc, jb->shading, id, P, Dhit, arc, o->rgba + 4 * q);
+    if (jb->light)
+      jb->lit[q] = or_illuminate_hit(m, jb->sc, jb->light, jb->integrator, id, P, Dhit, o->rgba + 4 * q, NULL,
+                                     NULL, NULL);
   } else {
+    if (jb->light) jb->lit[q] = 0;
     for (int c = 0; c < 3; c++) o->hit[3 * q + c] = x[c];
     memset(o->rgba + 4 * q, 0, 4);
   }
@@ -962,17 +982,68 @@ static void *trace_worker(void *arg) {
   return NULL;
 }
 
+static int trace_job(const or_metric *m, const or_scene *sc, const struct or_light_s *light, int32_t *lit,
+                     const double cam_pos[3], const double cam_fwd[3], const double cam_up[3], double vfov_deg,
+                     int W, int H, double h, int max_steps, int integrator, int shading, const int64_t *pixels,
+                     int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba, double *drift,
+                     double *xend, int flags, int nthreads);
+
 /* Trace the listed pixels (p = j * W + i).  Returns 0 on success. */
 int or_trace(const or_metric *m, const or_scene *sc, const double cam_pos[3],
              const double cam_fwd[3], const double cam_up[3], double vfov_deg, int W, int H,
              double h, int max_steps, int integrator, int shading, const int64_t *pixels,
              int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba, double *drift,
              double *xend, int flags, int nthreads) {
+  return trace_job(m, sc, NULL, NULL, cam_pos, cam_fwd, cam_up, vfov_deg, W, H, h, max_steps, integrator, shading,
+                   pixels, n, id, hit, steps, rgba, drift, xend, flags, nthreads);
+}
+
+/* As or_trace, with every hit shaded by Riemannian illumination from the point light
+ * (position L; light geodesics with step lh, at most lsteps steps each; at most
+ * iters Gauss-Newton steps to a miss of at most tol; difference step delta).
+ * lit[q] = 1 when pixel q is lit. */
+int or_trace_lit(const or_metric *m, const or_scene *sc, const double cam_pos[3], const double cam_fwd[3],
+                 const double cam_up[3], double vfov_deg, int W, int H, double h, int max_steps, int integrator,
+                 const double L[3], double lh, int lsteps, int iters, double tol, double delta,
+                 const int64_t *pixels, int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba,
+                 int32_t *lit, int nthreads) {
+  or_light lt;
+  for (int c = 0; c < 3; c++) lt.L[c] = L[c];
+  lt.h = lh;
+  lt.max_steps = lsteps;
+  lt.iters = iters;
+  lt.tol = tol;
+  lt.delta = delta;
+  return trace_job(m, sc, &lt, lit, cam_pos, cam_fwd, cam_up, vfov_deg, W, H, h, max_steps, integrator, OR_LAMBERT,
+                   pixels, n, id, hit, steps, rgba, NULL, NULL, 0, nthreads);
+}
+
+/* Single-hit form for the pins: illumination of hit point P (segment direction D) of object id. */
+int or_illuminate(const or_metric *m, const or_scene *sc, const double L[3], double lh, int lsteps, int iters,
+                  double tol, double delta, int integrator, int id, const double P[3], const double D[3],
+                  uint8_t rgba[4], double *cos_out, int *iters_out, double u_out[3]) {
+  or_light lt;
+  for (int c = 0; c < 3; c++) lt.L[c] = L[c];
+  lt.h = lh;
+  lt.max_steps = lsteps;
+  lt.iters = iters;
+  lt.tol = tol;
+  lt.delta = delta;
+  return or_illuminate_hit(m, sc, &lt, integrator, id, P, D, rgba, cos_out, iters_out, u_out);
+}
+
+static int trace_job(const or_metric *m, const or_scene *sc, const struct or_light_s *light, int32_t *lit,
+                     const double cam_pos[3], const double cam_fwd[3], const double cam_up[3], double vfov_deg,
+                     int W, int H, double h, int max_steps, int integrator, int shading, const int64_t *pixels,
+                     int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba, double *drift,
+                     double *xend, int flags, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   or_job base;
   memset(&base, 0, sizeof(base));
   base.m = m;
   base.sc = sc;
+  base.light = light;
+  base.lit = lit;
   for (int c = 0; c < 3; c++) {
     base.cam.pos[c] = cam_pos[c];
     base.cam.fwd[c] = cam_fwd[c];
@@ -1007,4 +1078,199 @@ int or_trace(const or_metric *m, const or_scene *sc, const double cam_pos[3],
   free(jobs);
   free(th);
   return 0;
+}
+
+/* ---------------------------------------------------- Riemannian illumination */
+
+/* Section 4 ("Riemannian illumination"): a surface point q is lit by a light
+ * source through the geodesics that connect q to it; the radiant intensity is
+ * Lambertian and depends on the metric.  Readings (also in the design notes):
+ *   - one point light L, direct geodesics only (no indirect ones);
+ *   - the geodesic from q to L is found by shooting: a Gauss-Newton solve on the
+ *     initial direction d(alpha, beta) = normalize(d0 + alpha e1 + beta e2), with
+ *     d0 = normalize(L - q), for a zero miss vector (closest approach of the
+ *     marched polygon to L, minus L); the Jacobian by forward differences;
+ *   - q = P + 1e-3 n, just off the hit surface along the normal n facing the
+ *     incoming ray (as in the headlight shading);
+ *   - the Lambert factor is the Riemannian cosine between the surface normal and
+ *     the initial tangent u (g-unit): <N, u>_q / |N|_q with N = g^-1 n, that is
+ *     n.u / sqrt(n^T g^-1 n); a point is lit when the solve converged, the cosine
+ *     is positive and no polygon segment between q and the closest approach to L
+ *     meets the scene;
+ *   - colour albedo * (0.1 + 0.9 cos) when lit, albedo * 0.1 when not. */
+
+
+/* Marches the geodesic from q with Euclidean initial direction d until its
+ * closest approach to L.  Returns 1 with the miss vector e = closest point - L,
+ * or 0 when the step budget ran out first.  With shadow != 0, also tests every
+ * polygon segment (and every straight advance) up to the closest point against
+ * the scene and sets *blocked. */
+static int shoot(const or_metric *m, const or_scene *sc, const or_light *lt, int integrator,
+                 const double q[3], const double d[3], double e[3], double u[3], int shadow, int *blocked) {
+  double x[3] = {q[0], q[1], q[2]};
+  double nd = sqrt(or_inner(m, x, d, d));
+  double v[3] = {d[0] / nd, d[1] / nd, d[2] / nd};
+  for (int c = 0; c < 3; c++) u[c] = v[c];
+  const int can_skip = skippable(m);
+  if (blocked) *blocked = 0;
+  int steps = 0;
+  for (;;) {
+    if (can_skip && outside_supports(m, x)) {
+      /* straight line x + t v: closest approach to L at tL, next support ball at te */
+      double te = support_entry(m, x, v);
+      double w[3] = {lt->L[0] - x[0], lt->L[1] - x[1], lt->L[2] - x[2]};
+      double tL = (w[0] * v[0] + w[1] * v[1] + w[2] * v[2]) / (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      if (tL < 0.0) tL = 0.0;
+      double tend = tL <= te ? tL : te;
+      if (shadow && tend > 0.0) {
+        double s;
+        int hid;
+        if (or_scene_hit(sc, x, v, tend, &s, &hid)) {
+          *blocked = 1;
+          return 1;
+        }
+      }
+      if (tL <= te) {
+        for (int c = 0; c < 3; c++) e[c] = x[c] + tL * v[c] - lt->L[c];
+        return 1;
+      }
+      for (int c = 0; c < 3; c++) x[c] = x[c] + te * v[c];
+    }
+    if (steps >= lt->max_steps) return 0;
+    double x0[3] = {x[0], x[1], x[2]};
+    or_step(m, integrator, lt->h, x, v);
+    steps++;
+    double D[3] = {x[0] - x0[0], x[1] - x0[1], x[2] - x0[2]};
+    double w[3] = {lt->L[0] - x0[0], lt->L[1] - x0[1], lt->L[2] - x0[2]};
+    double t = (w[0] * D[0] + w[1] * D[1] + w[2] * D[2]) / (D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    if (t < 1.0) { /* the closest approach lies on this segment (or the distance grows) */
+      if (t < 0.0) t = 0.0;
+      if (shadow && t > 0.0) {
+        double s;
+        int hid;
+        if (or_scene_hit(sc, x0, D, t, &s, &hid)) {
+          *blocked = 1;
+          return 1;
+        }
+      }
+      for (int c = 0; c < 3; c++) e[c] = x0[c] + t * D[c] - lt->L[c];
+      return 1;
+    }
+    if (shadow) {
+      double s;
+      int hid;
+      if (or_scene_hit(sc, x0, D, 1.0, &s, &hid)) {
+        *blocked = 1;
+        return 1;
+      }
+    }
+  }
+}
+
+/* Illumination of one hit: P the hit point, Dhit the direction of the segment
+ * that hit object id.  Writes the colour and returns 1 when lit (cos_out: the
+ * Riemannian cosine, iters_out: Gauss-Newton steps taken, u_out: the initial
+ * g-unit tangent). */
+int or_illuminate_hit(const or_metric *m, const or_scene *sc, const or_light *lt, int integrator, int id,
+                      const double P[3], const double Dhit[3], uint8_t rgba[4], double *cos_out,
+                      int *iters_out, double u_out[3]) {
+  double n[3];
+  int obj = id < sc->S ? id : sc->S;
+  if (id < sc->S) {
+    const double *sp = sc->sph + 4 * id;
+    for (int c = 0; c < 3; c++) n[c] = P[c] - sp[c];
+  } else {
+    const double *t9 = sc->tri + 9 * (id - sc->S);
+    double e1[3] = {t9[3] - t9[0], t9[4] - t9[1], t9[5] - t9[2]};
+    double e2[3] = {t9[6] - t9[0], t9[7] - t9[1], t9[8] - t9[2]};
+    cross3(e1, e2, n);
+  }
+  if (n[0] * Dhit[0] + n[1] * Dhit[1] + n[2] * Dhit[2] > 0.0) {
+    n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
+  }
+  normalize3(n);
+  double q[3];
+  for (int c = 0; c < 3; c++) q[c] = P[c] + 1e-3 * n[c];
+  double d0[3] = {lt->L[0] - q[0], lt->L[1] - q[1], lt->L[2] - q[2]};
+  normalize3(d0);
+  /* e1 across the axis least aligned with d0 (lowest index on ties), e2 = d0 x e1 */
+  int ax = 0;
+  for (int c = 1; c < 3; c++)
+    if (fabs(d0[c]) < fabs(d0[ax])) ax = c;
+  double a[3] = {0.0, 0.0, 0.0}, b1[3], b2[3];
+  a[ax] = 1.0;
+  cross3(a, d0, b1);
+  normalize3(b1);
+  cross3(d0, b1, b2);
+  double al = 0.0, be = 0.0;
+  int lit = 0, k = 0;
+  double u[3] = {d0[0], d0[1], d0[2]}, cosg = 0.0;
+  for (k = 0;; k++) {
+    double d[3], e[3];
+    for (int c = 0; c < 3; c++) d[c] = d0[c] + al * b1[c] + be * b2[c];
+    normalize3(d);
+    if (!shoot(m, sc, lt, integrator, q, d, e, u, 0, NULL)) break;
+    double en = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    if (en <= lt->tol) { lit = 1; break; }
+    if (k == lt->iters) break;
+    /* forward-difference Jacobian columns de/dalpha, de/dbeta */
+    double Jc[2][3], ud[3];
+    int ok = 1;
+    for (int col = 0; col < 2 && ok; col++) {
+      double dd[3], ee[3];
+      double aa = al + (col == 0 ? lt->delta : 0.0), bb = be + (col == 1 ? lt->delta : 0.0);
+      for (int c = 0; c < 3; c++) dd[c] = d0[c] + aa * b1[c] + bb * b2[c];
+      normalize3(dd);
+      ok = shoot(m, sc, lt, integrator, q, dd, ee, ud, 0, NULL);
+      for (int c = 0; c < 3; c++) Jc[col][c] = (ee[c] - e[c]) / lt->delta;
+    }
+    if (!ok) break;
+    /* Gauss-Newton: (J^T J) step = -J^T e, by Cramer's rule */
+    double A00 = 0, A01 = 0, A11 = 0, r0 = 0, r1 = 0;
+    for (int c = 0; c < 3; c++) {
+      A00 += Jc[0][c] * Jc[0][c];
+      A01 += Jc[0][c] * Jc[1][c];
+      A11 += Jc[1][c] * Jc[1][c];
+      r0 -= Jc[0][c] * e[c];
+      r1 -= Jc[1][c] * e[c];
+    }
+    double det = A00 * A11 - A01 * A01;
+    if (!(det > 1e-12 * (A00 * A11))) break;
+    double s0 = (r0 * A11 - r1 * A01) / det, s1 = (A00 * r1 - A01 * r0) / det;
+    double sn = sqrt(s0 * s0 + s1 * s1);
+    if (sn > 0.25) { s0 *= 0.25 / sn; s1 *= 0.25 / sn; }
+    al += s0;
+    be += s1;
+  }
+  if (iters_out) *iters_out = k;
+  if (lit) {
+    /* Riemannian cosine between the normal and the initial g-unit tangent */
+    double g[9], gi[9];
+    or_metric_tensor(m, q, g);
+    or_inverse_by_minors(g, gi);
+    double nn = 0.0;
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) nn += n[i] * gi[3 * i + j] * n[j];
+    cosg = (n[0] * u[0] + n[1] * u[1] + n[2] * u[2]) / sqrt(nn);
+    if (!(cosg > 0.0)) lit = 0;
+  }
+  if (lit) {
+    double d[3], e[3], uu[3];
+    for (int c = 0; c < 3; c++) d[c] = d0[c] + al * b1[c] + be * b2[c];
+    normalize3(d);
+    int blocked = 0;
+    shoot(m, sc, lt, integrator, q, d, e, uu, 1, &blocked);
+    if (blocked) lit = 0;
+  }
+  if (cos_out) *cos_out = cosg;
+  if (u_out)
+    for (int c = 0; c < 3; c++) u_out[c] = u[c];
+  double inten = lit ? 0.1 + 0.9 * cosg : 0.1;
+  for (int c = 0; c < 3; c++) {
+    double v = sc->alb[3 * obj + c] * inten;
+    v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    rgba[c] = (uint8_t)floor(255.0 * v + 0.5);
+  }
+  rgba[3] = 255;
+  return lit;
 }

@@ -89,6 +89,19 @@ class Camera:
 
 
 @dataclasses.dataclass
+class Light:
+    """A point light for Riemannian illumination and the parameters of the geodesic shooting
+    toward it: step h and step budget of each light geodesic, at most ``iters`` Gauss-Newton
+    steps to a miss of at most ``tol`` scene units, forward-difference step ``delta``."""
+    pos: tuple = (1.0, 6.0, -3.0)
+    h: float = 0.005
+    max_steps: int = 4000
+    iters: int = 8
+    tol: float = 1e-4
+    delta: float = 1e-3
+
+
+@dataclasses.dataclass
 class Metric:
     """Metric description: graph of a sum of Gaussian bumps, or the twist diffeomorphism.
 

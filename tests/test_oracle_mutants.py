@@ -46,12 +46,20 @@ MUTANTS = {
     "fog_step_arc": ("    arc += jb->h;\n  }", "  }", "fog"),
     "local_field_term": ("hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i] + gr[i] * B[3 * s + j];",
                          "hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i];", "local"),
+    # Riemannian illumination (pins in test_oracle_illum.py)
+    "illum_euclidean_cosine": ("cosg = (n[0] * u[0] + n[1] * u[1] + n[2] * u[2]) / sqrt(nn);",
+                               "cosg = (n[0] * u[0] + n[1] * u[1] + n[2] * u[2]);", "affine or radial",
+                               "test_oracle_illum.py"),
+    "illum_no_shadow": ("    if (blocked) lit = 0;\n", "", "flat", "test_oracle_illum.py"),
+    "illum_gauss_newton_sign": ("      r1 -= Jc[1][c] * e[c];", "      r1 += Jc[1][c] * e[c];", "twist or radial",
+                                "test_oracle_illum.py"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_reject_mutant(name, tmp_path):
-    old, new, select = MUTANTS[name]
+    old, new, select = MUTANTS[name][:3]
+    pins = MUTANTS[name][3] if len(MUTANTS[name]) > 3 else "test_oracle_pins.py"
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     mut = tmp_path / "mutant.c"
@@ -61,7 +69,7 @@ def test_pins_reject_mutant(name, tmp_path):
                            "-o", str(so), str(mut), "-lm", "-lpthread"])
     env = dict(os.environ, RGEO_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", select],
+                        os.path.join(ROOT, "tests", pins), "-k", select],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
