@@ -1108,9 +1108,10 @@ static int trace_job(const or_metric *m, const or_scene *sc, const struct or_lig
 static int shoot(const or_metric *m, const or_scene *sc, const or_light *lt, int integrator,
                  const double q[3], const double d[3], double e[3], double u[3], int shadow, int *blocked) {
   double x[3] = {q[0], q[1], q[2]};
-  double nd = sqrt(or_inner(m, x, d, d));
-  double v[3] = {d[0] / nd, d[1] / nd, d[2] / nd};
-  for (int c = 0; c < 3; c++) u[c] = v[c];
+  /* g-unit initial tangent along d (Eq. 3.1) */
+  const double nd = sqrt(or_inner(m, x, d, d));
+  double v[3];
+  for (int c = 0; c < 3; c++) u[c] = v[c] = d[c] / nd;
   const int can_skip = skippable(m);
   if (blocked) *blocked = 0;
   int steps = 0;
