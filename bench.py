@@ -654,6 +654,104 @@ def bench_surrogate(args):
     return 0
 
 
+def bench_lit(args):
+    """The 1080p / 64-bump frame with Riemannian illumination of its hits by one point light
+    (rgeo_trace_lit: the view rays, then the light geodesics found by shooting).  The roofline
+    is the illumination kernel's: 27 flops per bump term it summed, over its time (the lit
+    frame's time minus the plain frame's, both by CUDA events)."""
+    import torch
+    import paper_2005_05386_gb300 as rg
+    torch.cuda.set_device(0)
+    w = workload("1080p_64", args.resolution)
+    light = scenes.Light()
+    N = w.n_pixels
+    metric, scene = rg.Metric(w.metric), rg.Scene(w.scene)
+    cam = rg.camera_struct(w.camera)
+    lstruct = rg.light_struct(light)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def lit_frame(out):
+        rg.rgeo_trace_lit(metric.handle, scene.handle, cam, w.width, w.height, w.h, w.max_steps, w.integrator,
+                          lstruct, rg.outputs_struct(out), out["lit"].data_ptr(), stream.cuda_stream)
+
+    def plain_frame(out):
+        rg.rgeo_trace(metric.handle, scene.handle, cam, w.width, w.height, w.h, w.max_steps, w.integrator,
+                      scenes.SHADING_LAMBERT, 0, rg.outputs_struct(out), stream.cuda_stream)
+
+    def with_lit(o):
+        o["lit"] = torch.zeros(N, dtype=torch.int32, device="cuda")
+        return o
+
+    out = with_lit(rg.alloc_outputs(N))
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lit_frame(out)
+        cp, cl = rg.alloc_outputs(N, count=True), with_lit(rg.alloc_outputs(N, count=True))
+        plain_frame(cp)
+        lit_frame(cl)
+        rg.rgeo_sync(stream.cuda_stream)
+        terms_plain, terms_lit = int(cp["bump_evals"].item()), int(cl["bump_evals"].item())
+        clocks = ClockSampler(0)
+        torch.cuda.synchronize()
+        clocks.start()
+        t_lit, t_plain = [], []
+        for _ in range(args.steps):
+            for fn, acc, o in ((lit_frame, t_lit, out), (plain_frame, t_plain, cp)):
+                flush.zero_()                  # L2 flushed between timed frames (256 MiB write)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn(o)
+                b.record(stream)
+                acc.append((a, b))
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        rg.rgeo_sync(stream.cuda_stream)
+    ms_lit = sum(a.elapsed_time(b) for a, b in t_lit) / args.steps
+    ms_plain = sum(a.elapsed_time(b) for a, b in t_plain) / args.steps
+    ms_illum = max(ms_lit - ms_plain, 1e-6)
+    terms_illum = terms_lit - terms_plain
+    flops = terms_illum * FLOPS_PER_BUMP
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = float(measured_peaks().get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
+    peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms_illum * 1e-3) / 1e12
+    ids = out["id"].cpu().numpy()
+    lit = out["lit"].cpu().numpy()
+    cpu = err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = oracle.default_threads()
+        px = scenes.pixel_sample(N, w.seed + 2000, CPU_SAMPLE_FRACTION)
+        t0 = time.perf_counter()
+        o = oracle.trace_lit(w, light, px, nthreads=threads)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(px) / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(px)} seeded pixels of the lit {w.width}x{w.height} frame, FP64, {dt:.2f} s wall"}
+        err = error_vs_oracle(out, px, o, w.scene.n_spheres)
+        both = (ids[px] == o["id"]) & (o["id"] >= 0)
+        err["same_lit"] = float((lit[px][both] == o["lit"][both]).mean()) if both.any() else 1.0
+    line = {
+        "metric": "Mrays/s of the 1080p/64-bump frame with Riemannian illumination (light geodesics by shooting)",
+        "value": N / ms_lit / 1e3, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_lit, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded SplitMix64 bumps, spheres and displaced-sphere mesh)",
+        "config": {"workload": "1080p_64bumps_lit", "width": w.width, "height": w.height, "light": light.pos,
+                   "light_h": light.h, "light_max_steps": light.max_steps, "gauss_newton_iters": light.iters,
+                   "tol": light.tol, "l2": "flushed between timed frames (256 MiB write)"},
+        "plain_ms": ms_plain, "illumination_ms": ms_illum,
+        "hits_lit_unlit": [int(((ids >= 0) & (lit == 1)).sum()), int(((ids >= 0) & (lit == 0)).sum())],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_illuminate (dense bump sums)",
+                     "flops_per_launch": flops, "bump_terms_per_launch": terms_illum,
+                     "kernel_ms": ms_illum, "timing": "lit frame minus plain frame, CUDA events"},
+        "clocks": clk, "gpu_launches": args.steps * 3,
+        "cpu_baseline": cpu, "fp32_error_vs_oracle": err,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def bench_infer(args):
     """Throughput of the fused tensor-core inference of the learned map on ``--rows`` rows
     (inputs and outputs larger than L2), with the roofline of its two 256x256 layers."""
@@ -708,7 +806,7 @@ def main():
     ap.add_argument("--workload", default="1080p_64",
                     choices=["1080p_64", "1080p_twist", "parity_64", "quad_lattice", "paraboloid_lattice",
                              "local8_lattice", "4k_1024", "batch16",
-                             "anim120", "surrogate", "infer"])
+                             "anim120", "surrogate", "infer", "lit"])
     ap.add_argument("--rows", type=int, default=1 << 23, help="rows for --workload infer")
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -724,6 +822,8 @@ def main():
         return bench_surrogate(args)
     if args.workload == "infer":
         return bench_infer(args)
+    if args.workload == "lit":
+        return bench_lit(args)
     return bench_gpu(args)
 
 

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define RGEO_ABI_VERSION 2
+#define RGEO_ABI_VERSION 3 /* 3: rgeo_trace_lit; 2: composed local maps */
 
 typedef enum {
   RGEO_OK = 0,
@@ -219,6 +219,45 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
                             const rgeo_camera *camera, int32_t width, int32_t height, float h,
                             int32_t max_steps, int32_t integrator, int32_t shading,
                             uint32_t flags, const rgeo_outputs *host_out, void *cuda_stream);
+
+/* Riemannian illumination (Section 4): a surface point q is lit by a light source
+ * through the geodesics that connect q to it, and its radiant intensity is
+ * Lambertian with an angle measured by the metric.  rgeo_trace_lit traces the view
+ * field as rgeo_trace does (Lambert shading, no flags) and then re-shades every hit
+ * from one point light:
+ *   - q = hit + 1e-3 n, with n the unit surface normal facing the segment that hit;
+ *   - the light geodesic from q is found by shooting: Gauss-Newton on the initial
+ *     direction d0 + alpha e1 + beta e2 (d0 = (L - q) / |L - q|, e1 across the axis
+ *     least aligned with d0, e2 = d0 x e1) for a zero miss vector (the closest
+ *     approach of the marched polygon to L, minus L), with forward differences of
+ *     step `delta`, at most `iters` steps, each clamped to 0.25;
+ *   - each light geodesic is marched like a view ray (g-unit start, step h, the
+ *     flat-space advance of truncated bumps) for at most max_steps steps;
+ *   - the hit is lit when the miss fell to `tol` or below, the Riemannian cosine
+ *     n.u / sqrt(n^T g^-1 n) of the initial g-unit tangent u is positive, and no
+ *     segment of the light geodesic up to its closest approach meets the scene;
+ *   - colour albedo * (0.1 + 0.9 cos) when lit, albedo * 0.1 otherwise (no fog).
+ * The light geodesics sum every bump (the cull grid serves the view rays only).
+ * `lit` (DEVICE [W*H] int32, may be NULL) receives 1 for lit hits, else 0.
+ * Allocates a work counter and a 12-byte-per-pixel normal buffer with
+ * cudaMallocAsync on the stream.  Asynchronous on the stream.
+ * Errors: those of rgeo_trace, and RGEO_EINVAL for a NULL light, a non-finite
+ * light position, h or tol or delta not finite or <= 0, max_steps < 1, iters < 0
+ * or nonzero reserved fields. */
+typedef struct {
+  float pos[3];      /* the point light L */
+  float h;           /* step of the light geodesics */
+  int32_t max_steps; /* step budget of each light geodesic */
+  int32_t iters;     /* Gauss-Newton steps at most */
+  float tol;         /* miss distance that counts as reaching the light */
+  float delta;       /* forward-difference step of the Jacobian */
+  int32_t reserved[4]; /* must be zero */
+} rgeo_light;
+
+rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                           int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
+                           const rgeo_light *light, const rgeo_outputs *out, int32_t *lit,
+                           void *cuda_stream);
 
 /* ---------------------------------------------------------------- batches
  * Time- or user-dependent metrics (Introduction) and many views at once: a batch

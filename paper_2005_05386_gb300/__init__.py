@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "librgeo.so")
 RGEO_OK, RGEO_EINVAL, RGEO_ENOMEM, RGEO_ECUDA, RGEO_ETIMEOUT, RGEO_EUNSUPPORTED, RGEO_EDEVICE = range(7)
 RGEO_METRIC_GRAPH_BUMPS, RGEO_METRIC_DIFFEO_TWIST, RGEO_METRIC_DIFFEO_LOCAL = 0, 1, 2
 RGEO_MAX_LOCAL_MAPS = 64
-RGEO_ABI_VERSION = 2  # include/rgeo.h; the loaded library must report the same
+RGEO_ABI_VERSION = 3  # include/rgeo.h; the loaded library must report the same
 RGEO_RK4, RGEO_EULER = 0, 1
 RGEO_SHADE_LAMBERT, RGEO_SHADE_PSEUDO = 0, 1
 RGEO_FLAG_ENERGY_DIAG = 1
@@ -40,7 +40,8 @@ EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_me
            "rgeo_metric_set_motion", "rgeo_metric_set_time", "rgeo_metric_advance", "rgeo_expmap_param_count",
            "rgeo_expmap_create", "rgeo_expmap_destroy", "rgeo_expmap_generate", "rgeo_expmap_forward",
            "rgeo_expmap_gradients", "rgeo_expmap_train_step", "rgeo_expmap_get_params", "rgeo_expmap_set_params",
-           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate", "rgeo_expmap_train", "rgeo_scene_set_fog")
+           "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate", "rgeo_expmap_train", "rgeo_scene_set_fog",
+           "rgeo_trace_lit")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -63,6 +64,12 @@ class rgeo_metric_desc(ctypes.Structure):
 class rgeo_camera(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_float * 3), ("forward", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
                 ("vfov_deg", ctypes.c_float)]
+
+
+class rgeo_light(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("h", ctypes.c_float), ("max_steps", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("tol", ctypes.c_float), ("delta", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class rgeo_tuning(ctypes.Structure):
@@ -135,6 +142,9 @@ def library() -> ctypes.CDLL:
     L.rgeo_trace.argtypes = trace_args
     L.rgeo_trace_host.restype = i32
     L.rgeo_trace_host.argtypes = trace_args
+    L.rgeo_trace_lit.restype = i32
+    L.rgeo_trace_lit.argtypes = [vp, vp, ctypes.POINTER(rgeo_camera), i32, i32, f32, i32, i32,
+                                 ctypes.POINTER(rgeo_light), ctypes.POINTER(rgeo_outputs), vp, vp]
     L.rgeo_sync.restype = i32
     L.rgeo_sync.argtypes = [vp]
     i64, u64 = ctypes.c_int64, ctypes.c_uint64
@@ -259,6 +269,14 @@ def rgeo_trace(metric: int, scene: int, camera: rgeo_camera, width: int, height:
                max_steps: int, integrator: int, shading: int, flags: int, out: rgeo_outputs, stream=None):
     _check(library().rgeo_trace(metric, scene, ctypes.byref(camera), width, height, h, max_steps, integrator,
                                 shading, flags, ctypes.byref(out), _stream_handle(stream)), "rgeo_trace")
+
+
+def rgeo_trace_lit(metric: int, scene: int, camera: rgeo_camera, width: int, height: int, h: float,
+                   max_steps: int, integrator: int, light: rgeo_light, out: rgeo_outputs, lit: int = 0,
+                   stream=None):
+    _check(library().rgeo_trace_lit(metric, scene, ctypes.byref(camera), width, height, h, max_steps, integrator,
+                                    ctypes.byref(light), ctypes.byref(out), lit or None, _stream_handle(stream)),
+           "rgeo_trace_lit")
 
 
 def rgeo_trace_host(metric: int, scene: int, camera: rgeo_camera, width: int, height: int, h: float,
@@ -564,5 +582,28 @@ def trace(work: scenes.Workload, metric: Metric = None, scene: Scene = None, out
         out = alloc_outputs(work.n_pixels, drift=bool(flags & RGEO_FLAG_ENERGY_DIAG))
     rgeo_trace(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height, work.h,
                work.max_steps, work.integrator, work.shading, flags, outputs_struct(out), stream)
+    out["_handles"] = (metric, scene)
+    return out
+
+
+def light_struct(light: scenes.Light) -> rgeo_light:
+    return rgeo_light((ctypes.c_float * 3)(*light.pos), light.h, light.max_steps, light.iters, light.tol,
+                      light.delta, (ctypes.c_int32 * 4)())
+
+
+def trace_lit(work: scenes.Workload, light: scenes.Light, metric: Metric = None, scene: Scene = None, out=None,
+              stream=None):
+    """Trace a workload with Riemannian illumination of its hits by a point light (torch tensors,
+    asynchronous on ``stream``); out["lit"] holds 1 for lit hits."""
+    import torch
+    metric = metric or Metric(work.metric)
+    scene = scene or Scene(work.scene)
+    if out is None:
+        out = alloc_outputs(work.n_pixels)
+    if out.get("lit") is None:
+        out["lit"] = torch.zeros(work.n_pixels, dtype=torch.int32, device=out["id"].device)
+    rgeo_trace_lit(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height, work.h,
+                   work.max_steps, work.integrator, light_struct(light), outputs_struct(out),
+                   out["lit"].data_ptr(), stream)
     out["_handles"] = (metric, scene)
     return out

@@ -459,6 +459,47 @@ rgeo_status rgeo_trace(const rgeo_metric *metric, const rgeo_scene *scene, const
   return RGEO_OK;
 }
 
+rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                           int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
+                           const rgeo_light *light, const rgeo_outputs *out, int32_t *lit, void *cuda_stream) {
+  g_last_error.clear();
+  rgeo_status s = validate_trace(metric, scene, camera, width, height, h, max_steps, integrator, RGEO_SHADE_LAMBERT,
+                                 0u, out);
+  if (s != RGEO_OK) return s;
+  if (!light) return fail(RGEO_EINVAL, "rgeo_trace_lit: light is NULL");
+  if (!finite_all(light->pos, 3) || !std::isfinite(light->h) || !(light->h > 0.f) || light->max_steps < 1 ||
+      light->iters < 0 || !std::isfinite(light->tol) || !(light->tol > 0.f) || !std::isfinite(light->delta) ||
+      !(light->delta > 0.f))
+    return fail(RGEO_EINVAL, "rgeo_trace_lit: light position, h, tol and delta must be finite, h, tol, delta > 0, "
+                             "max_steps >= 1, iters >= 0");
+  for (int i = 0; i < 4; i++)
+    if (light->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_trace_lit: reserved fields must be zero");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  rgeo::TraceParams p = make_params(metric, scene, camera, width, height, h, max_steps, integrator,
+                                    RGEO_SHADE_LAMBERT, 0u, out);
+  p.fog = 0.f;
+  const size_t N = (size_t)width * height;
+  char *buf = nullptr;
+  RGEO_CUDA(cudaMallocAsync((void **)&buf, 16 + 12 * N, st), "rgeo_trace_lit: work counter and normals");
+  p.counter = (uint32_t *)buf;
+  p.hit_nrm = (float *)(buf + 16);
+  rgeo::LightParams l;
+  for (int c = 0; c < 3; c++) l.L[c] = light->pos[c];
+  l.h = light->h;
+  l.max_steps = light->max_steps;
+  l.iters = light->iters;
+  l.tol = light->tol;
+  l.delta = light->delta;
+  l.lit = lit;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 16, st);
+  if (e == cudaSuccess) e = rgeo::launch_trace(p, st);
+  if (e == cudaSuccess) e = rgeo::launch_illuminate(p, l, st);
+  cudaError_t e2 = cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "rgeo_trace_lit: launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "rgeo_trace_lit: free");
+  return RGEO_OK;
+}
+
 rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
                             int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
                             int32_t shading, uint32_t flags, const rgeo_outputs *host_out,

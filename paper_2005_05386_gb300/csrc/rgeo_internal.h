@@ -124,6 +124,7 @@ struct TraceParams {
   uchar4 *rgba;
   double *drift;
   unsigned long long *bump_evals;  // optional work counter
+  float *hit_nrm;                  // optional [3][N]: unit normal of each hit, facing the incoming segment
   uint32_t *counter;
   // launch shape
   int rays_per_thread;  // 1, or 2 (isotropic graph metric only)
@@ -149,8 +150,18 @@ struct WaveArgs {
   long long N;
 };
 
+// Riemannian illumination by one point light (rgeo_trace_lit): the light geodesics'
+// step, budget and Gauss-Newton parameters, and the optional lit flags.
+struct LightParams {
+  float L[3];
+  float h;
+  int max_steps, iters;
+  float tol, delta;
+  int32_t *lit;  // optional [N]
+};
+
 // Instance table of a batch passed by value in the kernel's parameter space (CUDA
-// allows 32 KB of parameters; 64 x 368 B fits).
+// allows 32 KB of parameters; 64 x 392 B = 24.5 KB fits).
 constexpr int kMaxParamInstances = 64;
 struct BatchTable {
   TraceParams inst[kMaxParamInstances];
@@ -196,6 +207,8 @@ constexpr unsigned kErrTimeout = 2u;
 cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
                               cudaStream_t st);
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
+// Illumination pass over the hits of a finished trace p (p.hit_nrm filled by it).
+cudaError_t launch_illuminate(const TraceParams &p, const LightParams &l, cudaStream_t st);
 cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
 cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
                               cudaStream_t st);

@@ -690,6 +690,21 @@ __device__ uchar4 shade(const TraceParams &P, const float4 *ss, const HitRec &hr
   return make_uchar4(to_u8(r), to_u8(g), to_u8(b), 255);
 }
 
+// Unit normal of the hit surface, facing the segment D that reached it (sphere: radial;
+// triangle: geometric), for the illumination pass.
+__device__ F3 hit_normal(const TraceParams &P, const float4 *ss, const HitRec &hr, F3 Ph, F3 D) {
+  F3 n;
+  if (hr.id < P.S) {
+    const float4 sp = P.nodes ? __ldg(&P.spheres[hr.id]) : ss[hr.id];
+    n = f3(Ph.x - sp.x, Ph.y - sp.y, Ph.z - sp.z);
+  } else {
+    const float4 a4 = P.prims[3 * hr.tq], b4 = P.prims[3 * hr.tq + 1], c4 = P.prims[3 * hr.tq + 2];
+    n = cross(f3(b4.x - a4.x, b4.y - a4.y, b4.z - a4.z), f3(c4.x - a4.x, c4.y - a4.y, c4.z - a4.z));
+  }
+  if (dot(n, D) > 0.f) n = -1.f * n;
+  return normalize(n);
+}
+
 // ----------------------------------------------------------------- kernel
 
 struct Ray {
@@ -761,6 +776,12 @@ __device__ void finish_ray(const TraceParams &P, const float4 *sb, const float4 
   P.hit[N + p] = o.y;
   P.hit[2 * N + p] = o.z;
   P.rgba[p] = id >= 0 ? shade(P, ss, hr, Ph, D, arc) : make_uchar4(0, 0, 0, 0);
+  if (P.hit_nrm && id >= 0) {
+    const F3 n = hit_normal(P, ss, hr, Ph, D);
+    P.hit_nrm[p] = n.x;
+    P.hit_nrm[N + p] = n.y;
+    P.hit_nrm[2 * N + p] = n.z;
+  }
   if (P.energy) {
     const double e = energy<MK>(P, sb, xhi(r), vhi(r));
     P.drift[p] = e / (1.0 + (double)r.e0m1) - 1.0;
@@ -984,6 +1005,224 @@ __global__ void __launch_bounds__(128, MK == MK_LOCAL ? 5 : 6) k_trace(const Tra
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
     if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
   }
+}
+
+// ------------------------------------------------------ Riemannian illumination
+
+// g_x(d, d) (Eq. 3.1 with Eq. 5.2, Eq. 5.6 or the composed maps).
+template <int MK>
+__device__ float metric_dd(const TraceParams &P, const float4 *sb, F3 x, F3 d) {
+  if (MK == MK_TWIST) {
+    float s, c;
+    sincosf(P.twist_k * x.z, &s, &c);
+    const float X = c * x.x - s * x.y, Y = s * x.x + c * x.y;
+    const float j0 = c * d.x - s * d.y - P.twist_k * Y * d.z;
+    const float j1 = s * d.x + c * d.y + P.twist_k * X * d.z;
+    return j0 * j0 + j1 * j1 + d.z * d.z;
+  }
+  if (MK == MK_LOCAL) {
+    Jet jt;
+    local_jacobian(sb, P.K, x, jt);
+    const F3 jd = f3(dot(f3(jt.M[0], jt.M[1], jt.M[2]), d), dot(f3(jt.M[3], jt.M[4], jt.M[5]), d),
+                     dot(f3(jt.M[6], jt.M[7], jt.M[8]), d));
+    return dot(jd, jd);
+  }
+  const F3 g = grad_f<MK>(P, sb, x);
+  const float gd = dot(g, d);
+  return fmaf(gd, gd, dot(d, d));
+}
+
+// n^T g_x^-1 n: Sherman-Morrison for the graph metric (g^-1 = I - grad f grad f^T / (1 + |grad f|^2),
+// Eq. 5.2), |J^-T n|^2 for a pull-back metric g = J^T J (Eq. 5.6).
+template <int MK>
+__device__ float metric_inv_nn(const TraceParams &P, const float4 *sb, F3 x, F3 n) {
+  if (MK == MK_GRAPH_ISO || MK == MK_GRAPH_ANISO) {
+    const F3 g = grad_f<MK>(P, sb, x);
+    const float gn = dot(g, n);
+    return dot(n, n) - gn * gn / fmaf(g.z, g.z, fmaf(g.y, g.y, fmaf(g.x, g.x, 1.f)));
+  }
+  float M[9];
+  if (MK == MK_TWIST) {
+    float s, c;
+    sincosf(P.twist_k * x.z, &s, &c);
+    const float X = c * x.x - s * x.y, Y = s * x.x + c * x.y;
+    const float k = P.twist_k;
+    M[0] = c; M[1] = -s; M[2] = -k * Y;
+    M[3] = s; M[4] = c;  M[5] = k * X;
+    M[6] = 0.f; M[7] = 0.f; M[8] = 1.f;
+  } else {
+    Jet jt;
+    local_jacobian(sb, P.K, x, jt);
+    for (int i = 0; i < 9; i++) M[i] = jt.M[i];
+  }
+  // J^-1 has the columns r1 x r2, r2 x r0, r0 x r1 (rows r_i of J) over det J, so
+  // y = J^-T n = (c0.n, c1.n, c2.n) / det J
+  const F3 r0 = f3(M[0], M[1], M[2]), r1 = f3(M[3], M[4], M[5]), r2 = f3(M[6], M[7], M[8]);
+  const F3 c0 = cross(r1, r2), c1 = cross(r2, r0), c2 = cross(r0, r1);
+  const F3 y = (1.f / dot(r0, c0)) * f3(dot(c0, n), dot(c1, n), dot(c2, n));
+  return dot(y, y);
+}
+
+// The light geodesic from q with Euclidean initial direction d, marched (compensated RK4 or
+// Euler at the light's step) until its closest approach to L.  Returns false when the step
+// budget ran out first; else e = closest point - L.  With SHADOW, every polygon segment (and
+// straight advance) up to the closest point is tested against the scene and a hit sets
+// blocked.  u: the initial g-unit tangent.
+template <int MK, int INTEG, bool SHADOW>
+__device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, F3 L, F3 q, F3 d, F3 &e, F3 &u,
+                      bool &blocked, unsigned long long &evals) {
+  u = rsqrtf(metric_dd<MK>(P, sb, q, d)) * d;
+  float xh[3] = {q.x, q.y, q.z}, xl[3] = {0.f, 0.f, 0.f}, vh[3] = {u.x, u.y, u.z}, vl[3] = {0.f, 0.f, 0.f};
+  const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), 0u, &evals};
+  blocked = false;
+  for (int steps = 0;;) {
+    F3 x = f3(xh[0], xh[1], xh[2]);
+    const F3 v = f3(vh[0], vh[1], vh[2]);
+    bool inside = true;
+    F3 a1 = accel<MK, true>(P, sb, cx, x, v, inside);
+    if (MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
+      // straight line x + t v: closest approach to L at tL, next support ball at te
+      const float te = support_entry<MK>(sb, P.K, x, v);
+      const F3 w = L - x;
+      const float tL = fmaxf(dot(w, v) / dot(v, v), 0.f);
+      const float tend = fminf(tL, te);
+      if (SHADOW && tend > 0.f) {
+        HitRec hr;
+        if (scene_hit(P, ss, x, v, tend, hr)) {
+          blocked = true;
+          return true;
+        }
+      }
+      if (tL <= te) {
+        e = axpy(tL, v, x) - L;
+        return true;
+      }
+      for (int c = 0; c < 3; c++) comp_add(xh[c], xl[c], te * comp(v, c));
+      x = f3(xh[0], xh[1], xh[2]);
+      bool dummy;
+      a1 = accel<MK, false>(P, sb, cx, x, v, dummy);
+    }
+    if (steps >= P.max_steps) return false;
+    F3 dx, dvel;
+    step_increments<MK, INTEG>(P, sb, cx, x, v, a1, dx, dvel);
+    for (int c = 0; c < 3; c++) {
+      comp_add(xh[c], xl[c], comp(dx, c));
+      comp_add(vh[c], vl[c], comp(dvel, c));
+    }
+    ++steps;
+    const F3 D = f3(xh[0], xh[1], xh[2]) - x;
+    const float t = dot(L - x, D) / dot(D, D);
+    if (t < 1.f) {  // the closest approach lies on this segment (or the distance grows)
+      const float tc = fmaxf(t, 0.f);
+      if (SHADOW && tc > 0.f) {
+        HitRec hr;
+        if (scene_hit(P, ss, x, D, tc, hr)) {
+          blocked = true;
+          return true;
+        }
+      }
+      e = axpy(tc, D, x) - L;
+      return true;
+    }
+    if (SHADOW) {
+      HitRec hr;
+      if (scene_hit(P, ss, x, D, 1.f, hr)) {
+        blocked = true;
+        return true;
+      }
+    }
+  }
+}
+
+// Riemannian illumination of every hit of a finished trace (Section 4): the geodesic from
+// q = hit + 1e-3 n to the light is found by shooting (Gauss-Newton on the initial
+// direction d0 + alpha e1 + beta e2, forward-difference Jacobian), and the hit is lit
+// when it converged, the Riemannian cosine n.u / sqrt(n^T g^-1 n) is positive and the
+// geodesic meets no object on the way; colour albedo (0.1 + 0.9 cos) lit, albedo 0.1 not.
+// One thread per pixel, pixels in 8 x 4 tiles; the bump sums are dense (no cull grid),
+// so lanes may follow their own geodesics.
+template <int MK, int INTEG>
+__global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const LightParams LP) {
+  extern __shared__ float4 smem[];
+  const int nb4 = stage_shared<MK>(P, smem);
+  const float4 *sb = smem;
+  const float4 *ss = smem + nb4;
+  const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= P.n_items) return;
+  const unsigned tile = item >> 5, sub = item & 31u;
+  const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
+  const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
+  if (px >= P.W || py >= P.H) return;
+  const int p = py * P.W + px;
+  const size_t N = (size_t)P.W * P.H;
+  const int id = P.id[p];
+  if (id < 0) {
+    if (LP.lit) LP.lit[p] = 0;
+    return;
+  }
+  const F3 Ph = f3(P.hit[p], P.hit[N + p], P.hit[2 * N + p]);
+  const F3 n = f3(P.hit_nrm[p], P.hit_nrm[N + p], P.hit_nrm[2 * N + p]);
+  const F3 L = f3(LP.L[0], LP.L[1], LP.L[2]);
+  const F3 q = axpy(1e-3f, n, Ph);
+  const F3 d0 = normalize(L - q);
+  // e1 across the axis least aligned with d0 (lowest index on ties), e2 = d0 x e1
+  int ax = 0;
+  if (fabsf(d0.y) < fabsf(d0.x)) ax = 1;
+  if (fabsf(d0.z) < fabsf(ax == 0 ? d0.x : d0.y)) ax = 2;
+  const F3 b1 = normalize(cross(f3(ax == 0 ? 1.f : 0.f, ax == 1 ? 1.f : 0.f, ax == 2 ? 1.f : 0.f), d0));
+  const F3 b2 = cross(d0, b1);
+  float al = 0.f, be = 0.f;
+  bool lit = false, blocked;
+  F3 u = d0;
+  unsigned long long evals = 0;  // bump terms summed (work counter)
+  for (int k = 0;; k++) {
+    const F3 d = normalize(axpy(be, b2, axpy(al, b1, d0)));
+    F3 e;
+    if (!shoot<MK, INTEG, false>(P, sb, ss, L, q, d, e, u, blocked, evals)) break;
+    if (sqrtf(dot(e, e)) <= LP.tol) {
+      lit = true;
+      break;
+    }
+    if (k == LP.iters) break;
+    F3 J0, J1, ud, ee;
+    if (!shoot<MK, INTEG, false>(P, sb, ss, L, q, normalize(axpy(be, b2, axpy(al + LP.delta, b1, d0))), ee, ud,
+                                 blocked, evals))
+      break;
+    J0 = (1.f / LP.delta) * (ee - e);
+    if (!shoot<MK, INTEG, false>(P, sb, ss, L, q, normalize(axpy(be + LP.delta, b2, axpy(al, b1, d0))), ee, ud,
+                                 blocked, evals))
+      break;
+    J1 = (1.f / LP.delta) * (ee - e);
+    // Gauss-Newton: (J^T J) step = -J^T e, by Cramer's rule
+    const float A00 = dot(J0, J0), A01 = dot(J0, J1), A11 = dot(J1, J1);
+    const float r0 = -dot(J0, e), r1 = -dot(J1, e);
+    const float det = A00 * A11 - A01 * A01;
+    if (!(det > 1e-12f * (A00 * A11))) break;
+    float s0 = (r0 * A11 - r1 * A01) / det, s1 = (A00 * r1 - A01 * r0) / det;
+    const float sn = sqrtf(s0 * s0 + s1 * s1);
+    if (sn > 0.25f) {
+      s0 *= 0.25f / sn;
+      s1 *= 0.25f / sn;
+    }
+    al += s0;
+    be += s1;
+  }
+  float cosg = 0.f;
+  if (lit) {
+    cosg = dot(n, u) * rsqrtf(metric_inv_nn<MK>(P, sb, q, n));
+    if (!(cosg > 0.f)) lit = false;
+  }
+  if (lit) {
+    F3 e, uu;
+    shoot<MK, INTEG, true>(P, sb, ss, L, q, normalize(axpy(be, b2, axpy(al, b1, d0))), e, uu, blocked, evals);
+    if (blocked) lit = false;
+  }
+  const int obj = id < P.S ? id : P.S;
+  const float inten = lit ? fmaf(0.9f, cosg, 0.1f) : 0.1f;
+  P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
+                          to_u8(P.albedo[3 * obj + 2] * inten), 255);
+  if (LP.lit) LP.lit[p] = lit ? 1 : 0;
+  if (P.bump_evals) atomicAdd(P.bump_evals, evals);
 }
 
 // Eq. 5.4 for two rays against the same isotropic bump pairs: each loaded pair
@@ -1916,6 +2155,35 @@ cudaError_t launch_trace(const TraceParams &p, cudaStream_t st) {
   if (mk == MK_GRAPH_ISO) return p.integrator == 0 ? launch_one<MK_GRAPH_ISO, 0>(p, st) : launch_one<MK_GRAPH_ISO, 1>(p, st);
   if (mk == MK_GRAPH_ANISO) return p.integrator == 0 ? launch_one<MK_GRAPH_ANISO, 0>(p, st) : launch_one<MK_GRAPH_ANISO, 1>(p, st);
   return p.integrator == 0 ? launch_one<MK_TWIST, 0>(p, st) : launch_one<MK_TWIST, 1>(p, st);
+}
+
+template <int MK, int INTEG>
+cudaError_t launch_illuminate_t(const TraceParams &p, const LightParams &l, cudaStream_t st) {
+  const size_t smem =
+      (size_t)(table_float4s(p.kind, p.K, MK == MK_GRAPH_ANISO) + (p.nodes ? 0 : p.S)) * sizeof(float4);
+  if (smem > 227u * 1024u) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_illuminate<MK, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (p.n_items + 127u) / 128u;
+  if (blocks == 0) return cudaSuccess;
+  k_illuminate<MK, INTEG><<<blocks, 128, smem, st>>>(p, l);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaStream_t st) {
+  if (!p0.hit_nrm) return cudaErrorInvalidValue;
+  TraceParams p = p0;
+  p.cull_masks = nullptr;  // dense sums: the lanes of a warp follow their own light geodesics
+  p.h = l.h;
+  p.max_steps = l.max_steps;
+  p.energy = 0;
+  const int mk = p.kind == 2 ? MK_LOCAL : (p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
+  const bool rk4 = p.integrator == 0;
+  if (mk == MK_LOCAL) return rk4 ? launch_illuminate_t<MK_LOCAL, 0>(p, l, st) : launch_illuminate_t<MK_LOCAL, 1>(p, l, st);
+  if (mk == MK_TWIST) return rk4 ? launch_illuminate_t<MK_TWIST, 0>(p, l, st) : launch_illuminate_t<MK_TWIST, 1>(p, l, st);
+  if (mk == MK_GRAPH_ANISO)
+    return rk4 ? launch_illuminate_t<MK_GRAPH_ANISO, 0>(p, l, st) : launch_illuminate_t<MK_GRAPH_ANISO, 1>(p, l, st);
+  return rk4 ? launch_illuminate_t<MK_GRAPH_ISO, 0>(p, l, st) : launch_illuminate_t<MK_GRAPH_ISO, 1>(p, l, st);
 }
 
 cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,

@@ -96,7 +96,7 @@ class Light:
     pos: tuple = (1.0, 6.0, -3.0)
     h: float = 0.005
     max_steps: int = 4000
-    iters: int = 8
+    iters: int = 24
     tol: float = 1e-4
     delta: float = 1e-3
 

@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(rg):
 
 
 def test_abi_version(rg):
-    assert rg.rgeo_abi_version() == rg.RGEO_ABI_VERSION == 2
+    assert rg.rgeo_abi_version() == rg.RGEO_ABI_VERSION == 3
 
 
 def _desc(rg, **kw):
@@ -146,3 +146,28 @@ def test_trace_validation(rg):
     with pytest.raises(rg.RgeoError) as e:
         rg.rgeo_trace(fake, fake, bad_cam, 4, 4, 0.01, 10, 0, 0, 0, out, stream=0)
     assert "parallel" in str(e.value)
+
+
+def test_trace_lit_validation(rg):
+    """rgeo_trace_lit checks the light before touching the device (fake handles are never used)."""
+    from paper_2005_05386_gb300 import scenes
+    cam = rg.camera_struct(scenes.Camera())
+    out = rg.rgeo_outputs(1, 1, 1, 1, None)
+    fake = 1
+    st = rg.library().rgeo_trace_lit(fake, fake, ctypes.byref(cam), 4, 4, 0.01, 10, 0, None, ctypes.byref(out),
+                                     None, None)
+    assert st == rg.RGEO_EINVAL and "light" in rg.rgeo_last_error()
+    good = scenes.Light()
+    bad = [dict(h=0.0), dict(h=float("nan")), dict(pos=(0.0, float("inf"), 0.0)), dict(max_steps=0),
+           dict(iters=-1), dict(tol=0.0), dict(delta=-1e-3)]
+    for kw in bad:
+        import dataclasses
+        lt = rg.light_struct(dataclasses.replace(good, **kw))
+        with pytest.raises(rg.RgeoError) as e:
+            rg.rgeo_trace_lit(fake, fake, cam, 4, 4, 0.01, 10, 0, lt, out, 0, stream=0)
+        assert e.value.status == rg.RGEO_EINVAL, kw
+    lt = rg.light_struct(good)
+    lt.reserved[2] = 7
+    with pytest.raises(rg.RgeoError) as e:
+        rg.rgeo_trace_lit(fake, fake, cam, 4, 4, 0.01, 10, 0, lt, out, 0, stream=0)
+    assert "reserved" in str(e.value)
