@@ -1009,6 +1009,67 @@ __global__ void __launch_bounds__(128, MK == MK_LOCAL ? 5 : 6) k_trace(const Tra
 
 // ------------------------------------------------------ Riemannian illumination
 
+// Eq. 5.4 over the bump pairs of the lane's own cull cell only, with no warp collective:
+// for lanes that follow their own paths (the light geodesics), each walks its own list and
+// SIMT serialises the differences.  Pairs outside the cell add exactly zero there, so the
+// result equals the dense sum.  Other metric kinds, and metrics without a cull grid, take
+// the dense sums.
+template <int MK, bool INSIDE>
+__device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside,
+                                         unsigned long long &evals) {
+  if (MK != MK_GRAPH_ISO || !P.cull_masks) {
+    const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), 0u, &evals};
+    if (MK == MK_GRAPH_ISO) {  // dense: cull_masks is null here
+      evals += (unsigned)P.K;
+      return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
+    }
+    return accel<MK, INSIDE>(P, sb, cx, x, v, inside);
+  }
+  PairAcc a;
+  pair_acc_init(a, x, v);
+  const float4 ghdr = __ldg(P.cull_hdr);
+  const int G = P.cull_G;
+  const float fx = (x.x - ghdr.x) * ghdr.w, fy = (x.y - ghdr.y) * ghdr.w, fz = (x.z - ghdr.z) * ghdr.w;
+  const bool ing = fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G;
+  if (ing) {
+    const uint32_t *cm = P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
+    for (int wi = 0; wi < P.cull_words; ++wi) {
+      unsigned m = __ldg(cm + wi);
+      evals += 2u * (unsigned)__popc(m);
+      while (m) {
+        const int j = (wi << 5) + __ffs(m) - 1;
+        m &= m - 1u;
+        pair_eval<INSIDE>(a, sb, j);
+      }
+    }
+  }
+  if (INSIDE) inside = a.in;
+  return pair_acc_finish(P, a, x, v);
+}
+
+// One RK4 (or Euler) step's increments with per-lane sums (the light geodesics).
+template <int MK, int INTEG>
+__device__ __forceinline__ void step_increments_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, F3 a1,
+                                                     F3 &dx, F3 &dvel, unsigned long long &evals) {
+  const float h = P.h;
+  if (INTEG == 0) {
+    bool dummy;
+    const float h2 = 0.5f * h;
+    const F3 v2 = axpy(h2, a1, v);
+    const F3 a2 = accel_lane<MK, false>(P, sb, axpy(h2, v, x), v2, dummy, evals);
+    const F3 v3 = axpy(h2, a2, v);
+    const F3 a3 = accel_lane<MK, false>(P, sb, axpy(h2, v2, x), v3, dummy, evals);
+    const F3 v4 = axpy(h, a3, v);
+    const F3 a4 = accel_lane<MK, false>(P, sb, axpy(h, v3, x), v4, dummy, evals);
+    const float h6 = h * (1.f / 6.f);
+    dx = h6 * (v + 2.f * (v2 + v3) + v4);
+    dvel = h6 * (a1 + 2.f * (a2 + a3) + a4);
+  } else {
+    dx = h * v;
+    dvel = h * a1;
+  }
+}
+
 // g_x(d, d) (Eq. 3.1 with Eq. 5.2, Eq. 5.6 or the composed maps).
 template <int MK>
 __device__ float metric_dd(const TraceParams &P, const float4 *sb, F3 x, F3 d) {
@@ -1073,13 +1134,12 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
                       bool &blocked, unsigned long long &evals) {
   u = rsqrtf(metric_dd<MK>(P, sb, q, d)) * d;
   float xh[3] = {q.x, q.y, q.z}, xl[3] = {0.f, 0.f, 0.f}, vh[3] = {u.x, u.y, u.z}, vl[3] = {0.f, 0.f, 0.f};
-  const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), 0u, &evals};
   blocked = false;
   for (int steps = 0;;) {
     F3 x = f3(xh[0], xh[1], xh[2]);
     const F3 v = f3(vh[0], vh[1], vh[2]);
     bool inside = true;
-    F3 a1 = accel<MK, true>(P, sb, cx, x, v, inside);
+    F3 a1 = accel_lane<MK, true>(P, sb, x, v, inside, evals);
     if (MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
       // straight line x + t v: closest approach to L at tL, next support ball at te
       const float te = support_entry<MK>(sb, P.K, x, v);
@@ -1100,11 +1160,11 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
       for (int c = 0; c < 3; c++) comp_add(xh[c], xl[c], te * comp(v, c));
       x = f3(xh[0], xh[1], xh[2]);
       bool dummy;
-      a1 = accel<MK, false>(P, sb, cx, x, v, dummy);
+      a1 = accel_lane<MK, false>(P, sb, x, v, dummy, evals);
     }
     if (steps >= P.max_steps) return false;
     F3 dx, dvel;
-    step_increments<MK, INTEG>(P, sb, cx, x, v, a1, dx, dvel);
+    step_increments_lane<MK, INTEG>(P, sb, x, v, a1, dx, dvel, evals);
     for (int c = 0; c < 3; c++) {
       comp_add(xh[c], xl[c], comp(dx, c));
       comp_add(vh[c], vl[c], comp(dvel, c));
@@ -1139,8 +1199,8 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
 // direction d0 + alpha e1 + beta e2, forward-difference Jacobian), and the hit is lit
 // when it converged, the Riemannian cosine n.u / sqrt(n^T g^-1 n) is positive and the
 // geodesic meets no object on the way; colour albedo (0.1 + 0.9 cos) lit, albedo 0.1 not.
-// One thread per pixel, pixels in 8 x 4 tiles; the bump sums are dense (no cull grid),
-// so lanes may follow their own geodesics.
+// One thread per pixel, pixels in 8 x 4 tiles; each lane sums the bumps of its own cull
+// cell (no warp collective), so lanes may follow their own geodesics.
 template <int MK, int INTEG>
 __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const LightParams LP) {
   extern __shared__ float4 smem[];
@@ -2172,8 +2232,7 @@ cudaError_t launch_illuminate_t(const TraceParams &p, const LightParams &l, cuda
 
 cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaStream_t st) {
   if (!p0.hit_nrm) return cudaErrorInvalidValue;
-  TraceParams p = p0;
-  p.cull_masks = nullptr;  // dense sums: the lanes of a warp follow their own light geodesics
+  TraceParams p = p0;  // keeps the cull grid: the light geodesics sum per lane (accel_lane)
   p.h = l.h;
   p.max_steps = l.max_steps;
   p.energy = 0;
