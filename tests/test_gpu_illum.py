@@ -115,3 +115,30 @@ def test_lit_flat_space_is_the_euclidean_lambert_law(rg):
             assert np.abs(g["rgba"][p, :3].astype(np.int64) - expect).max() <= 1, (p, cos)
             checked += 1
     assert checked >= 30
+
+
+def test_lit_ragged_frame(rg):
+    """A frame that leaves partial 8x4 tiles on both edges, against the oracle."""
+    w = scenes.scaled(scenes.config_parity_64(), 67, 29)
+    light = scenes.Light(pos=(1.0, 4.0, -3.0))
+    g = _lit(rg, w, light)
+    ref = oracle.trace_lit(w, light)
+    _check(w, light, None, g, ref, min_hits=15, min_lit=10)
+
+
+def test_lit_single_pixel(rg):
+    """A 1x1 frame (one partial tile): its ray misses every object, so nothing is lit."""
+    w = scenes.scaled(scenes.config_parity_64(), 1, 1)
+    g = _lit(rg, w, scenes.Light(pos=(1.0, 4.0, -3.0)))
+    ref = oracle.trace_lit(w, scenes.Light(pos=(1.0, 4.0, -3.0)))
+    assert np.array_equal(g["id"], ref["id"]) and ref["id"][0] < 0
+    assert g["lit"][0] == 0 and np.all(g["rgba"] == 0)
+
+
+def test_lit_without_hits(rg):
+    """An empty scene: no hit, nothing lit, every pixel black."""
+    w = scenes.config_parity_64()
+    w.scene = scenes.Scene(np.zeros((0, 4), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32),
+                           np.full((1, 3), 0.8, np.float32))
+    g = _lit(rg, w, scenes.Light())
+    assert np.all(g["id"] < 0) and np.all(g["lit"] == 0) and np.all(g["rgba"] == 0)
