@@ -1,7 +1,8 @@
 """Golden fixtures (tests/golden/): frozen FP64 oracle answers on seeded inputs.
 
 The paper prints no worked example or number, so the fixtures are the oracle's
-own output, written by tests/golden/make_golden.py.  On the CPU the oracle must
+own output, written by tests/golden/make_golden.py (one of them with Riemannian
+illumination by a point light).  On the CPU the oracle must
 still reproduce them: a change to its arithmetic shows up here and has to be
 justified by the passage of the paper it follows.  On a GPU the CUDA path must
 match them at the parity bar of the other GPU tests, without running the oracle.
@@ -18,17 +19,17 @@ sys.path.insert(0, os.path.join(HERE, "golden"))
 import make_golden  # noqa: E402
 from parity import assert_parity, compare, gpu_arrays  # noqa: E402
 
-FIXTURES = {name: (cite, work, pixels) for name, cite, work, pixels in make_golden.fixtures()}
-MIN_HITS = {"graph_one_bump_64x64": 20, "twist_24x16": 150, "graph_64_bumps_1080p_sample": 40}
+FIXTURES = {name: (cite, work, pixels, light) for name, cite, work, pixels, light in make_golden.fixtures()}
+MIN_HITS = {"graph_one_bump_64x64": 20, "twist_24x16": 150, "graph_64_bumps_1080p_sample": 40,
+            "lit_one_bump_64x64": 20}
 
 
 @pytest.mark.parametrize("name", sorted(FIXTURES))
 def test_oracle_reproduces_golden(name):
-    import oracle
-    _, work, pixels = FIXTURES[name]
+    _, work, pixels, light = FIXTURES[name]
     gpix, gold = make_golden.read(name)
     assert np.array_equal(gpix, pixels), "the fixture's pixels are no longer the generator's"
-    ref = oracle.trace(work, pixels)
+    ref = make_golden.trace(work, pixels, light)
     # FP64 with contraction off: exact on the machine that wrote the fixtures; another libm
     # may move a chaotic ray, which the 0.1 % allowance of the parity bar covers
     same = (ref["id"] == gold["id"]) & (ref["steps"] == gold["steps"])
@@ -37,6 +38,8 @@ def test_oracle_reproduces_golden(name):
     assert hit.sum() >= MIN_HITS[name]
     assert np.abs(ref["hit"][hit] - gold["hit"][hit]).max() <= 1e-9
     assert np.array_equal(ref["rgba"][hit], gold["rgba"][hit])
+    if light is not None:
+        assert np.array_equal(ref["lit"], gold["lit"]) and gold["lit"].sum() >= 10
 
 
 @pytest.mark.gpu
@@ -45,9 +48,16 @@ def test_gpu_matches_golden(name):
     import torch
     import paper_2005_05386_gb300 as rg
     torch.cuda.set_device(0)
-    _, work, pixels = FIXTURES[name]
+    _, work, pixels, light = FIXTURES[name]
     _, gold = make_golden.read(name)
-    out = rg.trace(work)
+    out = rg.trace(work) if light is None else rg.trace_lit(work, light)
     rg.rgeo_sync()
-    st = compare(gpu_arrays(out, pixels), gold, work.scene.n_spheres)
-    assert_parity(st, min_hits=MIN_HITS[name])
+    g = gpu_arrays(out, pixels)
+    if light is None:
+        assert_parity(compare(g, gold, work.scene.n_spheres), min_hits=MIN_HITS[name])
+    else:
+        # the view rays at the parity bar; the lit pixels as the illumination tests allow (a
+        # hit with several light geodesics may take another one in FP32: at most 2 here)
+        assert_parity(compare(g, dict(gold, rgba=g["rgba"]), work.scene.n_spheres), min_hits=MIN_HITS[name])
+        lit = out["lit"].cpu().numpy()[pixels]
+        assert (lit != gold["lit"]).sum() <= 2 and lit.sum() >= 10
