@@ -142,3 +142,25 @@ def test_lit_without_hits(rg):
                            np.full((1, 3), 0.8, np.float32))
     g = _lit(rg, w, scenes.Light())
     assert np.all(g["id"] < 0) and np.all(g["lit"] == 0) and np.all(g["rgba"] == 0)
+
+
+def test_lit_parity_anisotropic_bump(rg):
+    """An anisotropic bump (three spreads, Eq. 6.1): the light geodesics sum the anisotropic
+    field and the Riemannian cosine uses its gradient."""
+    w = scenes.config_parity_64()
+    w.metric.sigma = np.array([[0.5, 0.6, 0.45]], np.float32)
+    w.max_steps = 1000
+    light = scenes.Light(pos=(1.0, 4.0, -3.0))
+    g = _lit(rg, w, light)
+    ref = oracle.trace_lit(w, light)
+    _check(w, light, None, g, ref, min_hits=100, min_lit=50)
+
+
+def test_lit_parity_composed_local_maps(rg):
+    """Eight composed local diffeomorphisms through the lattice (Eq. 6.3, Theorem 5.1): the light
+    geodesics march the pull-back metric and the cosine uses n^T (J^T J)^-1 n."""
+    w = scenes.scaled(scenes.config_local_lattice(K=8), 32, 18)
+    light = scenes.Light(pos=(0.5, 0.5, -1.5), max_steps=1500)
+    g = _lit(rg, w, light)
+    ref = oracle.trace_lit(w, light)
+    _check(w, light, None, g, ref, min_hits=300, min_lit=100)
