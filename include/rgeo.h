@@ -237,7 +237,9 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
  *     n.u / sqrt(n^T g^-1 n) of the initial g-unit tangent u is positive, and no
  *     segment of the light geodesic up to its closest approach meets the scene;
  *   - colour albedo * (0.1 + 0.9 cos) when lit, albedo * 0.1 otherwise (no fog).
- * The light geodesics sum every bump (the cull grid serves the view rays only).
+ * The light geodesics sum, at each point, the bumps of its cull-grid cell (every bump
+ * when the metric has no cull grid), each lane on its own; out->bump_evals, when given,
+ * receives the bump terms of the view rays and of the light geodesics together.
  * `lit` (DEVICE [W*H] int32, may be NULL) receives 1 for lit hits, else 0.
  * Allocates a work counter and a 12-byte-per-pixel normal buffer with
  * cudaMallocAsync on the stream.  Asynchronous on the stream.
