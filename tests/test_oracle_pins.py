@@ -566,3 +566,41 @@ def test_fog_attenuates_by_arc_length_on_straight_rays(no_skip):
     assert np.abs(got - expect).max() <= 1.0 / 255.0 + 1e-9
     assert (fogged["rgba"][hit][:, :3] < base["rgba"][hit][:, :3]).any()
     assert (fogged["rgba"][~hit] == 0).all()
+
+
+def _refined_hits(w, steps_h, pixels=None, arc=None):
+    """Hit points of the same frame traced at each step in steps_h (budget arc / h, or the frame's
+    own arc length budget), on the pixels that hit the same object every time."""
+    import dataclasses
+    arc = arc if arc is not None else w.max_steps * w.h
+    res = [oracle.trace(dataclasses.replace(w, h=h, max_steps=int(round(arc / h))), pixels) for h in steps_h]
+    same = np.all([r["id"] == res[0]["id"] for r in res], axis=0) & (res[0]["id"] >= 0)
+    return [r["hit"][same] for r in res], int(same.sum())
+
+
+def test_full_trace_converges_at_fourth_order_without_truncation():
+    """The whole pipeline (camera, RK4 marching, segment tests) on a curved frame: with the bump
+    untruncated the metric is smooth, so hit points converge at the order of RK4 (Eq. 3.3):
+    halving h divides their change by 16."""
+    import dataclasses
+    w = scenes.config_parity_64()
+    w.metric = dataclasses.replace(w.metric, cutoff=0.0)
+    hits, n = _refined_hits(w, (0.04, 0.02, 0.01), np.arange(0, 4096, 3), arc=12.0)
+    assert n >= 40
+    e1 = np.abs(hits[0] - hits[1]).max()
+    e2 = np.abs(hits[1] - hits[2]).max()
+    assert 11.0 < e1 / e2 < 22.0, (e1, e2)
+    assert e2 < 1e-10
+
+
+def test_truncation_costs_one_order_with_a_tiny_constant():
+    """With truncated bumps (reading R4) the acceleration jumps where a ray crosses a support
+    sphere, so RK4 converges at first order there; the jump is of size a e^-8, and the hit points
+    move by less than 1e-7 between h = 0.02 and 0.01."""
+    w = scenes.config_parity_64()
+    hits, n = _refined_hits(w, (0.02, 0.01, 0.005))
+    assert n >= 60
+    e1 = np.abs(hits[0] - hits[1]).max()
+    e2 = np.abs(hits[1] - hits[2]).max()
+    assert 1.4 < e1 / e2 < 3.0, (e1, e2)
+    assert e1 < 1e-7
