@@ -19,9 +19,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                      convergence orders 4 (RK4) and 1 (Euler) against dopri5
   dopri5             closed-form twist geodesics to 1e-9
   scene_hit          analytic ray-sphere hits, BVH vs brute force, closed-mesh watertightness
-  trace              straight-line scenes against analytic hits; curved scenes are
-                     "parity unpinned" beyond the invariants above (the paper prints no
-                     worked image or number)
+  trace              straight-line scenes against analytic hits; curved frames by step
+                     refinement (fourth-order convergence of the hit points untruncated,
+                     first order with a constant below 1e-7 truncated); the paper prints
+                     no worked image or number
   illuminate         light geodesics by shooting: the segment q -> L in flat space, the
                      Riemannian cosine under affine f (Sherman-Morrison), preimages of lines
                      under the twist, the axis of a radial bump, re-integration to the light;
