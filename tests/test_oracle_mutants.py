@@ -46,6 +46,12 @@ MUTANTS = {
     "fog_step_arc": ("    arc += jb->h;\n  }", "  }", "fog"),
     "local_field_term": ("hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i] + gr[i] * B[3 * s + j];",
                          "hs[3 * i + j] * V[s] + gr[j] * B[3 * s + i];", "local"),
+    # full traces
+    "hit_at_segment_end": ("      for (int c = 0; c < 3; c++) { P[c] = x0[c] + s * D[c]; Dhit[c] = D[c]; }",
+                           "      for (int c = 0; c < 3; c++) { P[c] = x[c]; Dhit[c] = D[c]; }",
+                           "twist_frame_hits or fourth_order"),
+    "twist_hessian_dropped_zz": ("  H[1 * 9 + 2 * 3 + 2] = -k * k * (s * x + c * y);", "  H[1 * 9 + 2 * 3 + 2] = 0.0;",
+                                 "twist_frame_hits"),
     # Riemannian illumination (pins in test_oracle_illum.py)
     "illum_euclidean_cosine": ("cosg = (n[0] * u[0] + n[1] * u[1] + n[2] * u[2]) / sqrt(nn);",
                                "cosg = (n[0] * u[0] + n[1] * u[1] + n[2] * u[2]);", "affine or radial",
