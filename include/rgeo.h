@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define RGEO_ABI_VERSION 3 /* 3: rgeo_trace_lit; 2: composed local maps */
+#define RGEO_ABI_VERSION 4 /* 4: rgeo_trace_tiles, tuning knobs; 3: rgeo_trace_lit; 2: composed local maps */
 
 typedef enum {
   RGEO_OK = 0,
@@ -210,6 +210,33 @@ rgeo_status rgeo_trace(const rgeo_metric *metric, const rgeo_scene *scene,
                        const rgeo_camera *camera, int32_t width, int32_t height, float h,
                        int32_t max_steps, int32_t integrator, int32_t shading, uint32_t flags,
                        const rgeo_outputs *out, void *cuda_stream);
+
+/* One part of a frame (Section 4: the view field V of the observer, one geodesic
+ * per direction), for splitting a frame across GPUs or calls: the pixels of
+ * the frame tiles tile_begin, tile_begin + tile_step, ... below tile_end, in
+ * the row-major order of the frame's tiles of 32 pixels in the tuning's tile
+ * shape (rgeo_frame_tiles gives their number, rgeo_frame_tile_pixels their
+ * pixels; tile_end = -1 means all).  Part r of N is (r, -1, N): interleaved
+ * tiles spread the costly regions of a frame evenly.  Only the pixels of the
+ * part are written in the full-frame output buffers; each pixel's result equals
+ * that of rgeo_trace bit for bit, and the parts (r, -1, N), r = 0 .. N - 1,
+ * write every pixel exactly once.  Otherwise as rgeo_trace.  Errors: as
+ * rgeo_trace, and RGEO_EINVAL for tile_step < 1 or a range outside
+ * [0, rgeo_frame_tiles(width, height)]. */
+rgeo_status rgeo_trace_tiles(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                             int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
+                             int32_t shading, uint32_t flags, int32_t tile_begin, int32_t tile_end,
+                             int32_t tile_step, const rgeo_outputs *out, void *cuda_stream);
+
+/* Number of queue tiles of a width x height frame in the current tile shape
+ * (0 for an empty frame).  Host only. */
+int32_t rgeo_frame_tiles(int32_t width, int32_t height);
+
+/* The pixel indices (j * width + i) of frame tile `tile` in the current tile
+ * shape, written to pixels[0 .. n) (at most 32; fewer at the frame's right and
+ * bottom edges).  Returns n, or -1 for a bad argument.  Host only (the kernels
+ * use the same mapping). */
+int32_t rgeo_frame_tile_pixels(int32_t width, int32_t height, int32_t tile, int32_t *pixels);
 
 /* rgeo_trace with HOST output buffers (same layout as rgeo_outputs; drift may be
  * NULL).  Stages the outputs in device memory, traces on the stream, copies the
@@ -463,7 +490,7 @@ rgeo_status rgeo_sync(void *cuda_stream);
  * inputs as DEVICE arrays the caller owns and allocates nothing: it calls no
  * cudaMalloc, cudaMallocAsync, cudaFree or other allocating routine.  Its
  * scratch (the packed bump table and the work counter) is a file-scope device
- * array of 33,024 bytes that every GPU loading the library holds until the
+ * array of 33,056 bytes that every GPU loading the library holds until the
  * process exits.
  *
  * Scope: the graph metric of up to RGEO_NOALLOC_MAX_BUMPS isotropic Gaussian
@@ -478,12 +505,15 @@ rgeo_status rgeo_sync(void *cuda_stream);
  * device values are non-finite or whose spread is <= 0 is treated as inert.
  *
  * The first call on a device looks up the scratch address with that device
- * current (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the one scratch array per device and it keeps the
+ * current (cudaGetSymbolAddress) and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not use this entry
+ * point across a cudaDeviceReset (the module reloads and the kept address goes
+ * stale).  Every call shares the one scratch array per device and it keeps the
  * last call's contents: calls whose work overlaps on the GPU (different streams
  * without ordering between them) race and must not be issued.  Asynchronous on
  * the stream.  Errors: RGEO_EINVAL (counts beyond the maxima, NULL pointers,
- * bad camera, size, step or enum), RGEO_ECUDA. */
+ * spheres not 16-byte aligned, an array that is not device or managed memory of
+ * the current device, bad camera, size, step or enum), RGEO_ECUDA. */
 #define RGEO_NOALLOC_MAX_BUMPS 1024
 #define RGEO_NOALLOC_MAX_SPHERES 1024
 
@@ -494,20 +524,44 @@ rgeo_status rgeo_trace_noalloc(const float *center, const float *amplitude, cons
                                int32_t integrator, int32_t shading, const rgeo_outputs *out,
                                void *cuda_stream);
 
-/* Process-wide launch tuning of rgeo_trace and rgeo_batch_launch (no effect on
- * results beyond the order of float32 summation).  rays_per_thread: 1 or 2 rays
- * advanced together by each thread (2 applies to isotropic graph metrics only; 0
- * restores the default).  batch_params: where a batch's warps read their
- * instance's parameters: 0 (default) from the kernel's parameter space when the
- * batch has at most 64 instances, else from a per-warp shared-memory copy; 1
- * always from the shared-memory copy.  A setting is read when a trace or batch is
- * enqueued (a captured graph keeps the choice made at capture); it is not
- * synchronised between host threads.  Errors: RGEO_EINVAL (NULL, bad value,
- * nonzero reserved fields). */
+/* Process-wide launch tuning (the knobs the autotuner searches).  None of them
+ * changes a result bit of a trace: every lane sums its own bumps in the same
+ * order whatever shares its warp.
+ *   rays_per_thread  1 or 2 rays advanced together by each thread (2 applies to
+ *                    isotropic graph metrics with dense sums only); 0 restores 1.
+ *   batch_params     where a batch's warps read their instance's parameters: 0
+ *                    (default) from the kernel's parameter space when the batch
+ *                    has at most 64 instances, else from a per-warp shared-memory
+ *                    copy; 1 always from the shared-memory copy.
+ *   wait_limit       polls of each bounded barrier wait in the tensor-core kernels'
+ *                    work (rgeo_gemm_bf16, the surrogate's inference): 0 the
+ *                    default, n > 0 that many, -1 none, so that every such wait
+ *                    gives up at once (for testing the timeout path).  A wait that
+ *                    gives up makes the kernel drain its own copies and MMAs, free
+ *                    its tensor memory and return; rgeo_sync then reports
+ *                    RGEO_ETIMEOUT.
+ *   ctas_per_sm      persistent trace launches: 0 (default) as many 128-thread
+ *                    CTAs per SM as fit, else at most this many (1 .. 32).
+ *   tile_shape       pixels a warp takes from the queue at a time (32 per tile):
+ *                    0 default (8 x 4), 1 8 x 4, 2 4 x 8, 3 16 x 2; read by
+ *                    rgeo_frame_tiles and every trace.
+ *   batch_order      rgeo_batch_create's instance order: 0 (default) by
+ *                    decreasing cost (pixels x bumps), 1 as given.
+ *   sum_lists        culled bump sums of a warp: 0 (default) one list of bumps per
+ *                    RK4 step where the step's reach allows it (up to 512 bumps),
+ *                    else per right-hand side; 1 always per right-hand side.
+ * A setting is read when a trace or batch is enqueued or created (a captured
+ * graph keeps the choice made at capture); it is not synchronised between host
+ * threads.  Errors: RGEO_EINVAL (NULL, bad value, nonzero reserved fields). */
 typedef struct {
   int32_t rays_per_thread;
   int32_t batch_params;
-  int32_t reserved[6]; /* must be zero */
+  int32_t wait_limit;
+  int32_t ctas_per_sm;
+  int32_t tile_shape;
+  int32_t batch_order;
+  int32_t sum_lists;
+  int32_t reserved[1]; /* must be zero */
 } rgeo_tuning;
 
 rgeo_status rgeo_set_tuning(const rgeo_tuning *tuning);

@@ -112,6 +112,9 @@ def lib():
                                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int64, _ip, _dp, _ip,
                                _u8p, _dp, _dp, ctypes.c_int, ctypes.c_int]
+        L.or_trace_dirs.restype = ctypes.c_int
+        L.or_trace_dirs.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _dp, _dp, ctypes.c_int64, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _dp, _ip, _u8p, ctypes.c_int]
         L.or_trace_lit.restype = ctypes.c_int
         L.or_trace_lit.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -374,6 +377,53 @@ def trace(work, pixels=None, nthreads=None, metric: Metric = None, scene: Scene 
     out["pixels"] = pixels
     out["threads"] = nt
     return out
+
+
+def trace_dirs(work, dirs, nthreads=None, metric: Metric = None, scene: Scene = None):
+    """Trace rays from ``work``'s camera position with the given Euclidean initial directions
+    ``dirs`` [n, 3] (normalised by the oracle) instead of the pixels' own: the same marching,
+    segment tests and shading as ``trace``.  Returns id, hit [n,3], steps, rgba [n,4]."""
+    m = metric or Metric.from_desc(work.metric)
+    sc = scene or Scene.from_desc(work.scene)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    n = dirs.shape[0]
+    out = dict(id=np.zeros(n, np.int32), hit=np.zeros((n, 3)), steps=np.zeros(n, np.int32),
+               rgba=np.zeros((n, 4), np.uint8))
+    _, pp = pos = _d(work.camera.pos)
+    lib().or_trace_dirs(m.ptr, sc.ptr, pp, dirs.ctypes.data_as(_dp), n, float(work.h), int(work.max_steps),
+                        int(work.integrator), int(work.shading), out["id"].ctypes.data_as(_ip),
+                        out["hit"].ctypes.data_as(_dp), out["steps"].ctypes.data_as(_ip),
+                        out["rgba"].ctypes.data_as(_u8p), int(nthreads or default_threads()))
+    del pos
+    return out
+
+
+def conditioning(work, pixels, eps=2.0 ** -23, nthreads=None, metric: Metric = None, scene: Scene = None):
+    """How far each listed pixel's answer moves when its initial direction turns by eps radians
+    (default one float32 ulp at 1): the ray is re-traced in FP64 with the direction tilted by
+    eps along +-e1 and +-e2 (an orthonormal frame across it).  Returns (same_object [n] bool,
+    largest hit-point move [n]) over the four tilts; a MISS or BUDGET answer counts as an
+    object."""
+    m = metric or Metric.from_desc(work.metric)
+    sc = scene or Scene.from_desc(work.scene)
+    pixels = np.asarray(pixels, np.int64)
+    base = trace(work, pixels, nthreads=nthreads, metric=m, scene=sc)
+    dirs = []
+    for p in pixels:
+        d = camera_dir(work.camera, work.width, work.height, int(p % work.width), int(p // work.width))
+        a = np.eye(3)[int(np.argmin(np.abs(d)))]
+        e1 = np.cross(d, a)
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(d, e1)
+        dirs += [d + eps * e1, d - eps * e1, d + eps * e2, d - eps * e2]
+    t = trace_dirs(work, np.array(dirs), nthreads=nthreads, metric=m, scene=sc)
+    S = sc.S
+    obj = lambda i: np.where(np.asarray(i) >= S, S, np.asarray(i))  # noqa: E731
+    n = len(pixels)
+    tid = obj(t["id"]).reshape(n, 4)
+    same = (tid == obj(base["id"])[:, None]).all(axis=1)
+    move = np.abs(t["hit"].reshape(n, 4, 3) - base["hit"][:, None, :]).max(axis=(1, 2))
+    return same, move
 
 
 def trace_lit(work, light, pixels=None, nthreads=None, metric: Metric = None, scene: Scene = None):

@@ -899,6 +899,7 @@ typedef struct {
   double h;
   int max_steps, integrator, shading;
   const int64_t *pixels;
+  const double *dirs; /* [n*3] Euclidean initial directions in place of the camera's (or NULL) */
   int64_t n;
   or_outputs out;
   int no_skip; /* pins only: march through flat space step by step */
@@ -912,10 +913,15 @@ int or_illuminate_hit(const or_metric *m, const or_scene *sc, const struct or_li
 
 static void trace_pixel(const or_job *jb, int64_t q) {
   const or_metric *m = jb->m;
-  int64_t px = jb->pixels[q];
-  int i = (int)(px % jb->W), j = (int)(px / jb->W);
   double d[3];
-  or_camera_dir(&jb->cam, jb->W, jb->H, i, j, d);
+  if (jb->dirs) {
+    for (int c = 0; c < 3; c++) d[c] = jb->dirs[3 * q + c];
+    normalize3(d);
+  } else {
+    int64_t px = jb->pixels[q];
+    int i = (int)(px % jb->W), j = (int)(px / jb->W);
+    or_camera_dir(&jb->cam, jb->W, jb->H, i, j, d);
+  }
   double x[3] = {jb->cam.pos[0], jb->cam.pos[1], jb->cam.pos[2]};
   /* g-unit initial tangent: v = d / sqrt(<d, d>_p) (Eq. 3.1) */
   double nd = sqrt(or_inner(m, x, d, d));
@@ -986,7 +992,7 @@ static int trace_job(const or_metric *m, const or_scene *sc, const struct or_lig
                      const double cam_pos[3], const double cam_fwd[3], const double cam_up[3], double vfov_deg,
                      int W, int H, double h, int max_steps, int integrator, int shading, const int64_t *pixels,
                      int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba, double *drift,
-                     double *xend, int flags, int nthreads);
+                     double *xend, int flags, int nthreads, const double *dirs);
 
 /* Trace the listed pixels (p = j * W + i).  Returns 0 on success. */
 int or_trace(const or_metric *m, const or_scene *sc, const double cam_pos[3],
@@ -995,7 +1001,19 @@ int or_trace(const or_metric *m, const or_scene *sc, const double cam_pos[3],
              int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba, double *drift,
              double *xend, int flags, int nthreads) {
   return trace_job(m, sc, NULL, NULL, cam_pos, cam_fwd, cam_up, vfov_deg, W, H, h, max_steps, integrator, shading,
-                   pixels, n, id, hit, steps, rgba, drift, xend, flags, nthreads);
+                   pixels, n, id, hit, steps, rgba, drift, xend, flags, nthreads, NULL);
+}
+
+/* As or_trace for n rays with the given Euclidean initial directions dirs[n*3] (each
+ * normalised here) from the camera position, in place of the pixels' directions: the
+ * same marching, intersection and shading.  Used to measure how a ray's hit depends on
+ * its initial direction. */
+int or_trace_dirs(const or_metric *m, const or_scene *sc, const double cam_pos[3], const double *dirs, int64_t n,
+                  double h, int max_steps, int integrator, int shading, int32_t *id, double *hit, int32_t *steps,
+                  uint8_t *rgba, int nthreads) {
+  const double fwd[3] = {0.0, 0.0, 1.0}, up[3] = {0.0, 1.0, 0.0};
+  return trace_job(m, sc, NULL, NULL, cam_pos, fwd, up, 60.0, 1, 1, h, max_steps, integrator, shading, NULL, n, id,
+                   hit, steps, rgba, NULL, NULL, 0, nthreads, dirs);
 }
 
 /* As or_trace, with every hit shaded by Riemannian illumination from the point light
@@ -1015,7 +1033,7 @@ int or_trace_lit(const or_metric *m, const or_scene *sc, const double cam_pos[3]
   lt.tol = tol;
   lt.delta = delta;
   return trace_job(m, sc, &lt, lit, cam_pos, cam_fwd, cam_up, vfov_deg, W, H, h, max_steps, integrator, OR_LAMBERT,
-                   pixels, n, id, hit, steps, rgba, NULL, NULL, 0, nthreads);
+                   pixels, n, id, hit, steps, rgba, NULL, NULL, 0, nthreads, NULL);
 }
 
 /* Single-hit form for the pins: illumination of hit point P (segment direction D) of object id. */
@@ -1036,7 +1054,7 @@ static int trace_job(const or_metric *m, const or_scene *sc, const struct or_lig
                      const double cam_pos[3], const double cam_fwd[3], const double cam_up[3], double vfov_deg,
                      int W, int H, double h, int max_steps, int integrator, int shading, const int64_t *pixels,
                      int64_t n, int32_t *id, double *hit, int32_t *steps, uint8_t *rgba, double *drift,
-                     double *xend, int flags, int nthreads) {
+                     double *xend, int flags, int nthreads, const double *dirs) {
   if (nthreads < 1) nthreads = 1;
   or_job base;
   memset(&base, 0, sizeof(base));
@@ -1057,6 +1075,7 @@ static int trace_job(const or_metric *m, const or_scene *sc, const struct or_lig
   base.integrator = integrator;
   base.shading = shading;
   base.pixels = pixels;
+  base.dirs = dirs;
   base.n = n;
   base.out.id = id;
   base.out.hit = hit;

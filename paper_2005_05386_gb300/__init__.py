@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "librgeo.so")
 RGEO_OK, RGEO_EINVAL, RGEO_ENOMEM, RGEO_ECUDA, RGEO_ETIMEOUT, RGEO_EUNSUPPORTED, RGEO_EDEVICE = range(7)
 RGEO_METRIC_GRAPH_BUMPS, RGEO_METRIC_DIFFEO_TWIST, RGEO_METRIC_DIFFEO_LOCAL = 0, 1, 2
 RGEO_MAX_LOCAL_MAPS = 64
-RGEO_ABI_VERSION = 3  # include/rgeo.h; the loaded library must report the same
+RGEO_ABI_VERSION = 4  # include/rgeo.h; the loaded library must report the same
 RGEO_RK4, RGEO_EULER = 0, 1
 RGEO_SHADE_LAMBERT, RGEO_SHADE_PSEUDO = 0, 1
 RGEO_FLAG_ENERGY_DIAG = 1
@@ -41,7 +41,7 @@ EXPORTS = ("rgeo_abi_version", "rgeo_last_error", "rgeo_metric_create", "rgeo_me
            "rgeo_expmap_create", "rgeo_expmap_destroy", "rgeo_expmap_generate", "rgeo_expmap_forward",
            "rgeo_expmap_gradients", "rgeo_expmap_train_step", "rgeo_expmap_get_params", "rgeo_expmap_set_params",
            "rgeo_expmap_save", "rgeo_expmap_load", "rgeo_gemm_bf16", "rgeo_trace_surrogate", "rgeo_expmap_train", "rgeo_scene_set_fog",
-           "rgeo_trace_lit")
+           "rgeo_trace_lit", "rgeo_trace_tiles", "rgeo_frame_tiles", "rgeo_frame_tile_pixels")
 RGEO_NOALLOC_MAX_BUMPS = 1024
 RGEO_NOALLOC_MAX_SPHERES = 1024
 
@@ -74,7 +74,13 @@ class rgeo_light(ctypes.Structure):
 
 class rgeo_tuning(ctypes.Structure):
     _fields_ = [("rays_per_thread", ctypes.c_int32), ("batch_params", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("wait_limit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("tile_shape", ctypes.c_int32), ("batch_order", ctypes.c_int32), ("sum_lists", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
+
+
+TUNING_FIELDS = ("rays_per_thread", "batch_params", "wait_limit", "ctas_per_sm", "tile_shape", "batch_order",
+                 "sum_lists")
 
 
 class rgeo_outputs(ctypes.Structure):
@@ -142,6 +148,12 @@ def library() -> ctypes.CDLL:
     L.rgeo_trace.argtypes = trace_args
     L.rgeo_trace_host.restype = i32
     L.rgeo_trace_host.argtypes = trace_args
+    L.rgeo_trace_tiles.restype = i32
+    L.rgeo_trace_tiles.argtypes = trace_args[:10] + [i32, i32, i32] + trace_args[10:]
+    L.rgeo_frame_tiles.restype = i32
+    L.rgeo_frame_tiles.argtypes = [i32, i32]
+    L.rgeo_frame_tile_pixels.restype = i32
+    L.rgeo_frame_tile_pixels.argtypes = [i32, i32, i32, ctypes.POINTER(i32)]
     L.rgeo_trace_lit.restype = i32
     L.rgeo_trace_lit.argtypes = [vp, vp, ctypes.POINTER(rgeo_camera), i32, i32, f32, i32, i32,
                                  ctypes.POINTER(rgeo_light), ctypes.POINTER(rgeo_outputs), vp, vp]
@@ -269,6 +281,35 @@ def rgeo_trace(metric: int, scene: int, camera: rgeo_camera, width: int, height:
                max_steps: int, integrator: int, shading: int, flags: int, out: rgeo_outputs, stream=None):
     _check(library().rgeo_trace(metric, scene, ctypes.byref(camera), width, height, h, max_steps, integrator,
                                 shading, flags, ctypes.byref(out), _stream_handle(stream)), "rgeo_trace")
+
+
+def rgeo_trace_tiles(metric: int, scene: int, camera: rgeo_camera, width: int, height: int, h: float,
+                     max_steps: int, integrator: int, shading: int, flags: int, tile_begin: int, tile_end: int,
+                     tile_step: int, out: rgeo_outputs, stream=None):
+    _check(library().rgeo_trace_tiles(metric, scene, ctypes.byref(camera), width, height, h, max_steps, integrator,
+                                      shading, flags, tile_begin, tile_end, tile_step, ctypes.byref(out),
+                                      _stream_handle(stream)), "rgeo_trace_tiles")
+
+
+def rgeo_frame_tiles(width: int, height: int) -> int:
+    return int(library().rgeo_frame_tiles(width, height))
+
+
+def rgeo_frame_tile_pixels(width: int, height: int, tile: int):
+    """Pixel indices of one frame tile (numpy int32 array), as the kernels map them."""
+    import numpy as np
+    buf = np.empty(32, np.int32)
+    n = library().rgeo_frame_tile_pixels(width, height, tile, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if n < 0:
+        raise RgeoError(RGEO_EINVAL, "rgeo_frame_tile_pixels", "bad argument")
+    return buf[:n].copy()
+
+
+def part_pixels(width: int, height: int, part: int, n_parts: int):
+    """Pixels of part `part` of `n_parts` (interleaved tiles part, part + n_parts, ...)."""
+    import numpy as np
+    tiles = range(part, rgeo_frame_tiles(width, height), n_parts)
+    return np.concatenate([rgeo_frame_tile_pixels(width, height, t) for t in tiles] or [np.empty(0, np.int32)])
 
 
 def rgeo_trace_lit(metric: int, scene: int, camera: rgeo_camera, width: int, height: int, h: float,
@@ -437,17 +478,18 @@ def rgeo_sync(stream=None):
     _check(library().rgeo_sync(_stream_handle(stream)), "rgeo_sync")
 
 
-def rgeo_set_tuning(rays_per_thread: int = 0, batch_params: int = 0):
+def rgeo_set_tuning(rays_per_thread: int = 0, batch_params: int = 0, wait_limit: int = 0, ctas_per_sm: int = 0,
+                    tile_shape: int = 0, batch_order: int = 0, sum_lists: int = 0):
     t = rgeo_tuning()
-    t.rays_per_thread = rays_per_thread
-    t.batch_params = batch_params
+    t.rays_per_thread, t.batch_params, t.wait_limit = rays_per_thread, batch_params, wait_limit
+    t.ctas_per_sm, t.tile_shape, t.batch_order, t.sum_lists = ctas_per_sm, tile_shape, batch_order, sum_lists
     _check(library().rgeo_set_tuning(ctypes.byref(t)), "rgeo_set_tuning")
 
 
 def rgeo_get_tuning() -> dict:
     t = rgeo_tuning()
     _check(library().rgeo_get_tuning(ctypes.byref(t)), "rgeo_get_tuning")
-    return {"rays_per_thread": t.rays_per_thread, "batch_params": t.batch_params}
+    return {k: getattr(t, k) for k in TUNING_FIELDS}
 
 
 def rgeo_ffma_probe(mode: int = 0):
@@ -574,14 +616,20 @@ class Batch:
 
 
 def trace(work: scenes.Workload, metric: Metric = None, scene: Scene = None, out=None, stream=None,
-          flags: int = 0):
-    """Trace a workload on the current CUDA device into torch tensors (asynchronous on ``stream``)."""
+          flags: int = 0, tiles=None):
+    """Trace a workload on the current CUDA device into torch tensors (asynchronous on ``stream``).
+    ``tiles`` = (begin, end, step): only those of the frame's queue tiles (rgeo_trace_tiles)."""
     metric = metric or Metric(work.metric)
     scene = scene or Scene(work.scene)
     if out is None:
         out = alloc_outputs(work.n_pixels, drift=bool(flags & RGEO_FLAG_ENERGY_DIAG))
-    rgeo_trace(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height, work.h,
-               work.max_steps, work.integrator, work.shading, flags, outputs_struct(out), stream)
+    if tiles is None:
+        rgeo_trace(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height, work.h,
+                   work.max_steps, work.integrator, work.shading, flags, outputs_struct(out), stream)
+    else:
+        rgeo_trace_tiles(metric.handle, scene.handle, camera_struct(work.camera), work.width, work.height, work.h,
+                         work.max_steps, work.integrator, work.shading, flags, int(tiles[0]), int(tiles[1]),
+                         int(tiles[2]) if len(tiles) > 2 else 1, outputs_struct(out), stream)
     out["_handles"] = (metric, scene)
     return out
 

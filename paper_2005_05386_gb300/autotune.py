@@ -2,25 +2,40 @@
 
 Candidates are timed on the GPU, through the C ABI, on a proxy of the workload:
 the same metric, scene, camera and stepping at a reduced resolution (about a
-quarter of a million rays).  The tuned knobs change the schedule only, never the
-result beyond float32 summation order:
+quarter of a million rays).  Every knob changes the schedule only: each lane sums
+its own bumps in the same order whatever shares its warp, so every candidate gives
+the same image bit for bit.
 
   cull_grid        G of the bump-support cull grid (-1: dense sums over all bumps)
   rays_per_thread  1, or 2 (two rays share each bump pair; dense sums only)
+  ctas_per_sm      persistent CTAs per SM (0: as many as fit; 5 or fewer take the
+                   96-register build of the kernel)
+  tile_shape       the refill tile a warp takes from the queue: 1 (8 x 4), 2 (4 x 8),
+                   3 (16 x 2) pixels
+  sum_lists        culled bump sums from one list per RK4 step (0) or per right-hand
+                   side (1)
+  batch_order      batches: instances by decreasing cost (0) or as given (1)
 
-The winner is cached per (device name, workload signature) in a JSON file
-(``$RGEO_TUNING_CACHE``, default ``~/.cache/rgeo/tuning.json``).
+The candidate set is the product of the knobs that apply to the workload's metric
+(the grid, list and thread knobs only to isotropic truncated bumps).  The winner is
+cached per (device name, workload signature) in a JSON file (``$RGEO_TUNING_CACHE``,
+default ``~/.cache/rgeo/tuning.json``).
 """
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import json
 import math
 import os
 
 from . import scenes
 
-CANDIDATE_GRIDS = (-1, 32, 48, 64, 96, 128)
+CANDIDATE_GRIDS = (-1, 64, 96, 128)
+CANDIDATE_CTAS = (0, 5, 4)
+CANDIDATE_TILES = (1, 2, 3)
+CANDIDATE_LISTS = (0, 1)
+KNOBS = ("cull_grid", "rays_per_thread", "ctas_per_sm", "tile_shape", "sum_lists", "batch_order")
 
 
 def cache_path() -> str:
@@ -58,18 +73,39 @@ def proxy(work: scenes.Workload, rays: int = 1 << 18) -> scenes.Workload:
     return scenes.scaled(work, max(8, int(work.width * f)), max(4, int(work.height * f)))
 
 
-def candidates(work: scenes.Workload):
+def candidates(work: scenes.Workload, batch: bool = False):
+    """Every schedule to time for ``work``: dicts over KNOBS."""
     m = work.metric
     iso = m.kind == scenes.METRIC_GRAPH_BUMPS and m.n_bumps > 0 and not (m.sigma != m.sigma[:, :1]).any()
-    if not iso or m.cutoff <= 0:
-        return [dict(cull_grid=-1, rays_per_thread=1)]
-    out = [dict(cull_grid=g, rays_per_thread=1) for g in CANDIDATE_GRIDS]
-    out.append(dict(cull_grid=-1, rays_per_thread=2))
+    culled = iso and m.cutoff > 0
+    orders = (0, 1) if batch else (0,)
+    out = []
+    if culled:
+        for g, c, t, s, b in itertools.product(CANDIDATE_GRIDS, CANDIDATE_CTAS, CANDIDATE_TILES, CANDIDATE_LISTS,
+                                               orders):
+            if g == -1 and s == 1:
+                continue  # dense sums take no lists
+            out.append(dict(cull_grid=g, rays_per_thread=1, ctas_per_sm=c, tile_shape=t, sum_lists=s,
+                            batch_order=b))
+        out += [dict(cull_grid=-1, rays_per_thread=2, ctas_per_sm=0, tile_shape=t, sum_lists=0, batch_order=b)
+                for t, b in itertools.product(CANDIDATE_TILES, orders)]
+    else:
+        for c, t, b in itertools.product(CANDIDATE_CTAS, CANDIDATE_TILES, orders):
+            out.append(dict(cull_grid=-1, rays_per_thread=1, ctas_per_sm=c, tile_shape=t, sum_lists=0,
+                            batch_order=b))
     return out
 
 
+def set_schedule(choice: dict, batch_params: int = 0):
+    """Sets the process-wide launch tuning of a schedule (its cull grid belongs to the metric)."""
+    from . import rgeo_set_tuning
+    rgeo_set_tuning(rays_per_thread=int(choice["rays_per_thread"]), batch_params=batch_params,
+                    ctas_per_sm=int(choice["ctas_per_sm"]), tile_shape=int(choice["tile_shape"]),
+                    batch_order=int(choice.get("batch_order", 0)), sum_lists=int(choice["sum_lists"]))
+
+
 def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbose: bool = False) -> dict:
-    """Best schedule for ``work`` on the current device: {'cull_grid', 'rays_per_thread', 'ms'}."""
+    """Best schedule for ``work`` on the current device: the KNOBS and its time 'ms'."""
     import torch
 
     from . import Metric, Scene, alloc_outputs, rgeo_get_tuning, rgeo_set_tuning, rgeo_sync, trace
@@ -77,17 +113,21 @@ def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbos
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
     key = f"{dev}|{signature(work)}"
     db = _load() if use_cache else {}
-    if use_cache and key in db:
+    if use_cache and key in db and all(k in db[key] for k in KNOBS):
         return dict(db[key], cached=True)
     pw = proxy(work)
     scene = Scene(pw.scene)
     out = alloc_outputs(pw.n_pixels)
     saved = rgeo_get_tuning()
     results = []
+    metrics = {}
     try:
         for cand in candidates(pw):
-            metric = Metric(dataclasses.replace(pw.metric, cull_grid=cand["cull_grid"]))
-            rgeo_set_tuning(cand["rays_per_thread"], saved["batch_params"])
+            g = cand["cull_grid"]
+            if g not in metrics:
+                metrics[g] = Metric(dataclasses.replace(pw.metric, cull_grid=g))
+            metric = metrics[g]
+            set_schedule(cand, saved["batch_params"])
             trace(pw, metric, scene, out)           # warm-up
             rgeo_sync()
             best = float("inf")
@@ -103,7 +143,7 @@ def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbos
             if verbose:
                 print(f"autotune {signature(pw)} {cand} {best:.2f} ms", flush=True)
     finally:
-        rgeo_set_tuning(saved["rays_per_thread"], saved["batch_params"])
+        rgeo_set_tuning(**saved)
     win = min(results, key=lambda r: r["ms"])
     if use_cache:
         db[key] = win
@@ -112,7 +152,7 @@ def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbos
 
 
 def apply(work: scenes.Workload, choice: dict) -> scenes.Workload:
-    """The workload with the tuned cull grid; sets the process-wide rays-per-thread."""
-    from . import rgeo_get_tuning, rgeo_set_tuning
-    rgeo_set_tuning(int(choice["rays_per_thread"]), rgeo_get_tuning()["batch_params"])
+    """The workload with the tuned cull grid; sets the process-wide launch tuning."""
+    from . import rgeo_get_tuning
+    set_schedule(choice, rgeo_get_tuning()["batch_params"])
     return dataclasses.replace(work, metric=dataclasses.replace(work.metric, cull_grid=int(choice["cull_grid"])))

@@ -124,6 +124,12 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
     p.cull_hdr = m.cull_hdr;
     p.cull_G = m.cull_G;
     p.cull_words = m.cull_words;
+    // one list per RK4 step when every stage point of a step stays within kStepReach of its
+    // start: |v| <= 1 for a g-unit tangent (g >= I; 1% for its float32 drift) and
+    // |x_stage - x| <= h (|v| + h |x''| / 2)
+    const double reach = (double)h * (1.01 + 0.5 * (double)h * m.accel_max) * 1.001 + 1e-5;
+    p.step_lists = integrator == RGEO_RK4 && rgeo::tuning().sum_lists == 0 && reach <= rgeo::kStepReach &&
+                   m.K <= 512;
   }
   p.K = m.kind == RGEO_METRIC_DIFFEO_TWIST ? 0 : m.K;
   p.kind = m.kind;
@@ -157,8 +163,12 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   p.vfov_deg = cam->vfov_deg;
   p.W = W;
   p.H = H;
-  p.tiles_x = (W + 7) / 8;
-  const int tiles_y = (H + 3) / 4;
+  p.tile_lw = rgeo::tuning().tile_lw;
+  p.tiles_x = (W + (1 << p.tile_lw) - 1) >> p.tile_lw;
+  const int th = 32 >> p.tile_lw;
+  const int tiles_y = (H + th - 1) / th;
+  p.tile0 = 0;
+  p.tile_step = 1;
   p.n_items = (uint32_t)p.tiles_x * (uint32_t)tiles_y * 32u;
   p.h = h;
   p.max_steps = max_steps;
@@ -313,6 +323,15 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
   m->d.cutoff = desc->cutoff_sigmas;
   m->d.twist_k = desc->twist_rate;
   m->d.skippable = desc->kind == RGEO_METRIC_GRAPH_BUMPS && desc->cutoff_sigmas > 0.f && !quad;
+  {
+    double hs = 0.0, a2 = 0.0;  // sum |a_k| / sigma_k^2 (largest sigma per bump), ||A||_F
+    for (int k = 0; k < K; k++) {
+      const double sg = std::min(desc->sigma[3 * k], std::min(desc->sigma[3 * k + 1], desc->sigma[3 * k + 2]));
+      hs += std::fabs((double)desc->amplitude[k]) / (sg * sg);
+    }
+    for (int i = 0; i < 9; i++) a2 += (double)desc->quad_A[i] * desc->quad_A[i];
+    m->d.accel_max = (float)(0.5 * (hs + std::sqrt(a2)) * 1.0001);
+  }
   if (K > 0) {
     std::vector<float> raw(7 * (size_t)K);
     std::memcpy(raw.data(), desc->center, sizeof(float) * 3 * K);
@@ -324,11 +343,11 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
     // bump-support cull grid: isotropic truncated bumps only
     int G = 0;
     if (desc->kind == RGEO_METRIC_GRAPH_BUMPS && !aniso && desc->cutoff_sigmas > 0.f)
-      // automatic: 128^3 cells up to 1024 bumps (masks of 128^3 x ceil(K / 64) words), 64^3 above
+      // automatic: 128^3 cells up to 1024 bumps (masks of 128^3 x ceil(K / 32) words), 64^3 above
       G = desc->cull_grid == 0 ? (K >= 16 ? (K <= 1024 ? 128 : 64) : 0)
                                : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
     if (e == cudaSuccess && G > 0) {
-      const int words = ((K + 1) / 2 + 31) / 32;
+      const int words = rgeo::cull_words_for(K);
       m->d.cull_G = G;
       m->d.cull_words = words;
       e = cudaMalloc(&m->d.cull_masks, sizeof(uint32_t) * (size_t)G * G * G * words);
@@ -441,6 +460,32 @@ void rgeo_scene_destroy(rgeo_scene *scene) { free_scene(scene); }
 rgeo_status rgeo_trace(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
                        int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
                        int32_t shading, uint32_t flags, const rgeo_outputs *out, void *cuda_stream) {
+  return rgeo_trace_tiles(metric, scene, camera, width, height, h, max_steps, integrator, shading, flags, 0, -1, 1,
+                          out, cuda_stream);
+}
+
+int32_t rgeo_frame_tiles(int32_t width, int32_t height) {
+  if (width < 1 || height < 1) return 0;
+  const int lw = rgeo::tuning().tile_lw;
+  return (int32_t)(((width + (1 << lw) - 1) >> lw) * ((height + (32 >> lw) - 1) / (32 >> lw)));
+}
+
+int32_t rgeo_frame_tile_pixels(int32_t width, int32_t height, int32_t tile, int32_t *pixels) {
+  if (width < 1 || height < 1 || tile < 0 || tile >= rgeo_frame_tiles(width, height) || !pixels) return -1;
+  const int lw = rgeo::tuning().tile_lw;
+  const int tiles_x = (width + (1 << lw) - 1) >> lw;
+  int n = 0;
+  for (unsigned sub = 0; sub < 32u; ++sub) {
+    int pix;
+    if (rgeo::tile_pixel(width, height, tiles_x, lw, (unsigned)tile, sub, pix)) pixels[n++] = pix;
+  }
+  return n;
+}
+
+rgeo_status rgeo_trace_tiles(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,
+                             int32_t width, int32_t height, float h, int32_t max_steps, int32_t integrator,
+                             int32_t shading, uint32_t flags, int32_t tile_begin, int32_t tile_end,
+                             int32_t tile_step, const rgeo_outputs *out, void *cuda_stream) {
   g_last_error.clear();
   rgeo_status s = validate_trace(metric, scene, camera, width, height, h, max_steps, integrator, shading,
                                  flags, out);
@@ -448,6 +493,15 @@ rgeo_status rgeo_trace(const rgeo_metric *metric, const rgeo_scene *scene, const
   cudaStream_t st = (cudaStream_t)cuda_stream;
   rgeo::TraceParams p = make_params(metric, scene, camera, width, height, h, max_steps, integrator, shading,
                                     flags, out);
+  const int64_t tiles = (int64_t)p.n_items / 32;
+  if (tile_end < 0) tile_end = (int32_t)tiles;
+  if (tile_begin < 0 || tile_begin > tile_end || tile_end > tiles || tile_step < 1)
+    return fail(RGEO_EINVAL, "rgeo_trace_tiles: need 0 <= tile_begin <= tile_end <= rgeo_frame_tiles(width, height) "
+                             "and tile_step >= 1");
+  if (tile_begin == tile_end) return RGEO_OK;
+  p.tile0 = (uint32_t)tile_begin;
+  p.tile_step = (uint32_t)tile_step;
+  p.n_items = (uint32_t)((tile_end - tile_begin + tile_step - 1) / tile_step) * 32u;
   uint32_t *counter = nullptr;
   RGEO_CUDA(cudaMallocAsync((void **)&counter, sizeof(uint32_t), st), "rgeo_trace: work counter");
   p.counter = counter;
@@ -558,14 +612,27 @@ rgeo_status rgeo_sync(void *cuda_stream) {
 rgeo_status rgeo_set_tuning(const rgeo_tuning *t) {
   g_last_error.clear();
   if (!t) return fail(RGEO_EINVAL, "rgeo_set_tuning: NULL");
-  for (int i = 0; i < 6; i++)
-    if (t->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_set_tuning: reserved fields must be zero");
+  if (t->reserved[0] != 0) return fail(RGEO_EINVAL, "rgeo_set_tuning: reserved fields must be zero");
   if (t->rays_per_thread != 0 && t->rays_per_thread != 1 && t->rays_per_thread != 2)
     return fail(RGEO_EINVAL, "rgeo_set_tuning: rays_per_thread must be 0, 1 or 2");
   if (t->batch_params != 0 && t->batch_params != 1)
     return fail(RGEO_EINVAL, "rgeo_set_tuning: batch_params must be 0 or 1");
-  rgeo::tuning().rays_per_thread = t->rays_per_thread == 0 ? rgeo::Tuning().rays_per_thread : t->rays_per_thread;
-  rgeo::tuning().batch_params = t->batch_params;
+  if (t->wait_limit < -1) return fail(RGEO_EINVAL, "rgeo_set_tuning: wait_limit must be >= -1");
+  if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(RGEO_EINVAL, "rgeo_set_tuning: ctas_per_sm must be in [0, 32]");
+  if (t->tile_shape < 0 || t->tile_shape > 3)
+    return fail(RGEO_EINVAL, "rgeo_set_tuning: tile_shape must be 0 (default), 1 (8x4), 2 (4x8) or 3 (16x2)");
+  if (t->batch_order != 0 && t->batch_order != 1)
+    return fail(RGEO_EINVAL, "rgeo_set_tuning: batch_order must be 0 or 1");
+  if (t->sum_lists != 0 && t->sum_lists != 1) return fail(RGEO_EINVAL, "rgeo_set_tuning: sum_lists must be 0 or 1");
+  rgeo::Tuning &g = rgeo::tuning();
+  const rgeo::Tuning d;
+  g.rays_per_thread = t->rays_per_thread == 0 ? d.rays_per_thread : t->rays_per_thread;
+  g.batch_params = t->batch_params;
+  g.wait_limit = t->wait_limit;
+  g.ctas_per_sm = t->ctas_per_sm;
+  g.tile_lw = t->tile_shape == 0 ? d.tile_lw : (t->tile_shape == 1 ? 3 : (t->tile_shape == 2 ? 2 : 4));
+  g.batch_order = t->batch_order;
+  g.sum_lists = t->sum_lists;
   return RGEO_OK;
 }
 
@@ -573,8 +640,14 @@ rgeo_status rgeo_get_tuning(rgeo_tuning *t) {
   g_last_error.clear();
   if (!t) return fail(RGEO_EINVAL, "rgeo_get_tuning: NULL");
   std::memset(t, 0, sizeof(*t));
-  t->rays_per_thread = rgeo::tuning().rays_per_thread;
-  t->batch_params = rgeo::tuning().batch_params;
+  const rgeo::Tuning &g = rgeo::tuning();
+  t->rays_per_thread = g.rays_per_thread;
+  t->batch_params = g.batch_params;
+  t->wait_limit = g.wait_limit;
+  t->ctas_per_sm = g.ctas_per_sm;
+  t->tile_shape = g.tile_lw == 3 ? 1 : (g.tile_lw == 2 ? 2 : 3);
+  t->batch_order = g.batch_order;
+  t->sum_lists = g.sum_lists;
   return RGEO_OK;
 }
 
@@ -610,7 +683,7 @@ rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *inst, rgeo_batch *
   }
   // instances in order of decreasing cost (pixels x bump terms per point, roughly), so that
   // the last instance the warps drain is a short one; each keeps its own outputs
-  {
+  if (rgeo::tuning().batch_order == 0) {
     std::vector<std::pair<double, int>> cost(n);
     for (int i = 0; i < n; i++)
       cost[i] = {-(double)inst[i].width * inst[i].height * (1.0 + inst[i].metric->d.K), i};

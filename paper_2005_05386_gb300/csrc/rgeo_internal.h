@@ -11,25 +11,60 @@
 
 namespace rgeo {
 
-// Bump table, isotropic fast form: bumps are packed in pairs (2j, 2j+1) so that
-// the device evaluates both with one paired-FP32 instruction per operation.
-// Pair j occupies four float4 (lo = bump 2j, hi = bump 2j+1):
-//   P0 = (-cx_lo, -cx_hi, -cy_lo, -cy_hi)
-//   P1 = (-cz_lo, -cz_hi, R2_lo, R2_hi)   R2 = (cutoff sigma)^2, +inf untruncated, -1 inert (a = 0)
-//   P2 = (qn2_lo, qn2_hi, la_lo, la_hi)   q = 1 / sigma^2, qn2 = -q log2(e) / 2, la = log2 |a|
-//   P3 = (qs_lo, qs_hi, q_lo, q_hi)       qs = -q sign(a)
-// An odd bump count is padded with one inert bump.  With d = x - c, r2 = |d|^2 and
-// w = 2^(r2 qn2 + la) = |a| exp(-q r2 / 2):
+// Bump table, isotropic form: two float4 per bump,
+//   A_k = (-cx, -cy, -cz, R2)   R2 = (cutoff sigma)^2, +inf untruncated, -1 inert (a = 0)
+//   B_k = (qn2, la, qs, q)      q = 1 / sigma^2, qn2 = -q log2(e) / 2, la = log2 |a|, qs = -q sign(a)
+// at float4 2k and 2k + 1.  The table holds Ke + 1 bumps, Ke = K rounded up to even:
+// bumps K .. Ke are inert, so that the dense sums can take bumps (2i, 2i + 1) two at a
+// time and bump Ke (the pad) can fill the second half of a paired evaluation.  With
+// d = x - c, r2 = |d|^2 and w = 2^(r2 qn2 + la) = |a| exp(-q r2 / 2):
 //   grad f        += (w qs) d
 //   -v^T Hess f v += (w qs) (q (d.v)^2 - |v|^2)
 // Anisotropic bumps use three float4 per bump:
 //   b0 = (cx, cy, cz, Rball2)  Rball2 = (cutoff * max_i sigma_i)^2 (support ball for the flat skip)
 //   b1 = (qx, qy, qz, sgn)     q_i = 1 / sigma_i^2, sgn = sign(a)
 //   b2 = (la, c2, 0, 0)        c2 = cutoff^2 (+inf when untruncated, -1 when inert)
-constexpr int kIsoPairStride = 4;  // float4 per bump pair
-constexpr int kAnisoStride = 3;    // float4 per bump
+constexpr int kIsoBumpStride = 2;  // float4 per isotropic bump
+constexpr int kAnisoStride = 3;    // float4 per anisotropic bump
+// Ke: the isotropic bump count rounded up to even (the pad bump's index)
+__host__ __device__ inline int iso_pad_index(int K) { return (K + 1) & ~1; }
 // float4 count of a packed table of K bumps
-__host__ __device__ inline int packed_float4s(int K, int aniso) { return aniso ? kAnisoStride * K : kIsoPairStride * ((K + 1) / 2); }
+__host__ __device__ inline int packed_float4s(int K, int aniso) {
+  return aniso ? kAnisoStride * K : (K > 0 ? kIsoBumpStride * (iso_pad_index(K) + 1) : 0);
+}
+#ifdef __CUDACC__
+// Writes isotropic bump k of the table from its centre, amplitude and spread (a = 0:
+// inert).  Shared by the metric's packer and the allocation-free entry point.
+__device__ __forceinline__ void pack_iso_bump(float4 *table, int k, float cx, float cy, float cz, float a,
+                                              float sigma, float cutoff) {
+  const float inf = __int_as_float(0x7f800000);
+  const bool inert = a == 0.f;
+  const float q = 1.f / (sigma * sigma);
+  float R2 = cutoff > 0.f ? (cutoff * sigma) * (cutoff * sigma) : inf;
+  if (inert) R2 = -1.f;
+  const float sgn = a > 0.f ? 1.f : (a < 0.f ? -1.f : 0.f);
+  table[kIsoBumpStride * k] = make_float4(-cx, -cy, -cz, R2);
+  table[kIsoBumpStride * k + 1] =
+      make_float4(-0.5f * q * 1.4426950408889634f, inert ? -inf : log2f(fabsf(a)), -q * sgn, q);
+}
+#endif
+// Pixel of item `sub` (0..31) of frame tile `tile`: tiles of 2^lw x 2^(5 - lw) pixels in
+// row-major order over a W x H frame, tiles_x of them per row.  False for the part of an
+// edge tile outside the frame.  Shared by the kernels and the host partition helper.
+__host__ __device__ inline bool tile_pixel(int W, int H, int tiles_x, int lw, unsigned tile, unsigned sub,
+                                           int &pix) {
+  const unsigned tw = 1u << lw, th = 32u >> lw;
+  const int px = (int)((tile % (unsigned)tiles_x) * tw + (sub & (tw - 1u)));
+  const int py = (int)((tile / (unsigned)tiles_x) * th + (sub >> lw));
+  if (px >= W || py >= H) return false;
+  pix = py * W + px;
+  return true;
+}
+// Cull-grid bit masks: bit k of a cell's words marks bump k.
+__host__ __device__ inline int cull_words_for(int K) { return (K + 31) / 32; }
+// Per-warp list of the bump pairs a warp evaluates for one right-hand side (the culled
+// sums): int2 entries, x = float4 index of an even bump, y = of an odd bump.
+constexpr int kListPairs = 64;
 // Local maps (metric kind 2), five float4 each:
 //   (c.x, c.y, c.z, a), (v.x, v.y, v.z, qn2), (B row 0, q), (B row 1, has_field), (B row 2, 0)
 // with q = 1 / sigma^2 and qn2 = -q log2(e) / 2, so that f = a * 2^(qn2 |p - c|^2).
@@ -51,18 +86,25 @@ struct MetricDev {
   int has_affine, has_quad;
   float cutoff;
   float twist_k;
-  // bump-support cull grid (isotropic, truncated): G^3 cells, `words` uint32 of pair bits per cell
+  // bump-support cull grid (isotropic, truncated): G^3 cells, `words` uint32 of bump bits per cell
   int cull_G, cull_words;
   uint32_t *cull_masks;  // [G^3 * words]
   float4 *cull_hdr;      // (gmin.xyz, 1 / cell)
+  // bound on |x''| over the whole space for a g-unit tangent: (sum_k |a_k| / sigma_k^2 +
+  // ||A||_F) / 2 (Eq. 5.4 with |grad f| / (1 + |grad f|^2) <= 1/2, ||Hess f_k|| <= |a_k| q_k)
+  float accel_max;
   // sinusoidal motion of the centres: [K*3 c0 | K*3 A | K f | K phi] and the time t
   float *motion;
   float *time;
 };
 
-// Cull grid: inflation of every support radius (absolute), covering float32 rounding
-// of the cell look-up.
+// Cull grid: inflation of every support radius (absolute): kCullInflate covers float32
+// rounding of the cell look-up, kStepReach the distance from a step's start to its RK4
+// stage points, so that the cell of a step's start lists every bump whose support can
+// meet any stage point of the step (step lists, below) when that distance is at most
+// kStepReach.
 constexpr float kCullInflate = 1e-3f;
+constexpr float kStepReach = 0.02f;
 
 // BVH node: two float4.  n0 = (lo.xyz, int first_or_left), n1 = (hi.xyz, int count);
 // count > 0: leaf over primitives [first, first + count); count == 0: children at
@@ -91,6 +133,7 @@ struct TraceParams {
   const uint32_t *cull_masks;  // null: dense sums over all bumps
   const float4 *cull_hdr;
   int cull_G, cull_words;
+  int step_lists;              // culled sums from one list per step (the step's reach <= kStepReach)
   float b[3];
   float A[9];
   int has_affine, has_quad;
@@ -113,7 +156,10 @@ struct TraceParams {
   float cam_pos[3], cam_fwd[3], cam_up[3];
   float vfov_deg;
   int W, H, tiles_x;
-  uint32_t n_items;
+  int tile_lw;          // refill tiles of 2^tile_lw x 2^(5 - tile_lw) pixels (32 items each)
+  uint32_t tile0;       // first frame tile of this launch
+  uint32_t tile_step;   // launch tile i is frame tile tile0 + i tile_step
+  uint32_t n_items;     // items of this launch (32 per launch tile)
   // integration
   float h;
   int max_steps, integrator, shading, energy;
@@ -171,6 +217,11 @@ struct BatchTable {
 struct Tuning {
   int rays_per_thread = 1;  // measured faster on GB300 at 64 bumps (occupancy beats shared traffic)
   int batch_params = 0;     // 0: parameter space when n <= kMaxParamInstances; 1: shared-memory copies
+  int wait_limit = 0;       // tensor-core kernels' work waits: 0 default, n > 0 polls, -1 none (give up at once)
+  int ctas_per_sm = 0;      // persistent trace grids: 0 as many as fit, else at most this many per SM
+  int tile_lw = 3;          // refill tile width log2: 3 (8 x 4, default), 2 (4 x 8), 4 (16 x 2)
+  int batch_order = 0;      // batch instances: 0 by decreasing cost, 1 as given
+  int sum_lists = 0;        // culled sums: 0 one list per RK4 step where it applies, 1 one per right-hand side
 };
 Tuning &tuning();
 

@@ -58,10 +58,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false when the limit (polls of the
+// barrier) ran out.  The waits that drain a kernel's own copies and MMAs before it
+// releases tensor memory keep the fixed limit; the waits of the work itself take the
+// launch's polls (rgeo_tuning.wait_limit), which a test may set to give up at once.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -107,7 +110,7 @@ __device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *sr
 __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restrict__ A,
                                                    const __nv_bfloat16 *__restrict__ B, int M, int N, int K,
                                                    int k_per_split, const float *__restrict__ bias, int mode,
-                                                   void *C, int ldc, __nv_bfloat16 *ct, int ldt) {
+                                                   void *C, int ldc, __nv_bfloat16 *ct, int ldt, long long polls) {
   extern __shared__ __align__(1024) uint8_t gsm[];
   uint8_t *sA[2] = {gsm, gsm + kTileM * kTileK * 2};
   uint8_t *sB[2] = {gsm + 2 * kTileM * kTileK * 2, gsm + 2 * kTileM * kTileK * 2 + kMaxTileN * kTileK * 2};
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restri
     if (s + 1 < nstages) {
       const int nb = buf ^ 1;
       if (s >= 1) {
-        if (!mbar_wait(&bar_stage[nb], phase[nb])) abort_flag = 1;
+        if (!mbar_wait(&bar_stage[nb], phase[nb], polls)) abort_flag = 1;
         phase[nb] ^= 1u;
       }
       __syncthreads();
@@ -589,9 +592,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 // Bounded wait that also gives up once another role has raised the abort flag; a wait
 // that runs out raises it.
-__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *abort, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kWsSpin; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -617,7 +620,7 @@ __device__ __forceinline__ bool group_any(int id, bool pred) {
 
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_mlp_infer_ws(const float *__restrict__ X, long long n, const float *__restrict__ P,
-                   const __nv_bfloat16 *__restrict__ Wp, float *__restrict__ Y) {
+                   const __nv_bfloat16 *__restrict__ Wp, float *__restrict__ Y, long long polls) {
   extern __shared__ __align__(1024) uint8_t wsm[];
   uint8_t *ring = wsm + 2 * kHsBytes;
   uint8_t *B1 = ring + kWsRing * kWChunkBytes;
@@ -681,7 +684,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         for (int c = 0; c <= kWid / kChunkK && ok; ++c, ++chunk) {  // 8 chunks, then the bias chunk
           const int r = (int)(chunk % kWsRing);
           if (lane == 0) {
-            if (chunk >= kWsRing) ok = ws_wait(&chunk_empty[r], (uint32_t)((chunk / kWsRing - 1) & 1), abortp);
+            if (chunk >= kWsRing) ok = ws_wait(&chunk_empty[r], (uint32_t)((chunk / kWsRing - 1) & 1), abortp, polls);
             if (ok) {
               const bool bias = c == kWid / kChunkK;
               const uint32_t bytes = bias ? kBiasChunkBytes : kWChunkBytes;
@@ -717,13 +720,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     long long chunk = 0;
     uint32_t hwait[2] = {0u, 0u};  // completions of h_full[s] waited for
     bool ok = true;
-    if (lane == 0) ok = ws_wait(&const_full, 0u, abortp);
+    if (lane == 0) ok = ws_wait(&const_full, 0u, abortp, polls);
     ok = __shfl_sync(0xffffffffu, ok, 0);
     for (long long j = 0; j < npairs && ok; ++j) {
       const int ns = 2 * j + 1 < T ? 2 : 1;
       if (lane == 0) {
         auto wait_operand = [&](int s) {
-          ok = ok && ws_wait(&h_full[s], hwait[s] & 1u, abortp);
+          ok = ok && ws_wait(&h_full[s], hwait[s] & 1u, abortp, polls);
           ++hwait[s];
         };
         for (int s = 0; s < ns; ++s) {  // layer 1: K = 32 (split inputs, folded bias)
@@ -741,7 +744,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           for (int c = 0; c <= kWid / kChunkK; ++c, ++chunk) {
             const int r = (int)(chunk % kWsRing);
-            ok = ws_wait(&chunk_full[r], (uint32_t)((chunk / kWsRing) & 1), abortp);
+            ok = ws_wait(&chunk_full[r], (uint32_t)((chunk / kWsRing) & 1), abortp, polls);
             if (!ok) break;
             if (c < kWid / kChunkK) {
               const uint64_t dB = dRing + (uint64_t)(r * (kWChunkBytes >> 4));
@@ -836,7 +839,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       const long long row0 = ((long long)blockIdx.x + i * gridDim.x) * kTileM;
       if (i + 2 < T) prefetch_x(i + 2);
       for (int layer = 0; layer < 4 && !bad; ++layer) {
-        if (!ws_wait(&acc_full[g], await_n & 1u, abortp)) {
+        if (!ws_wait(&acc_full[g], await_n & 1u, abortp, polls)) {
           bad = true;
           break;
         }
@@ -895,6 +898,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 }
 }  // namespace
 
+// Polls of the work's own barrier waits for a launch: the kernel's default, or the
+// process-wide tuning (rgeo_tuning.wait_limit: n > 0 polls, -1 none).
+long long wait_polls(long long dflt) {
+  const int w = tuning().wait_limit;
+  return w == 0 ? dflt : (w < 0 ? 0ll : (long long)w);
+}
+
 cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits, const float *bias,
                              int mode, void *C, int ldc, void *ct, int ldt, cudaStream_t st) {
   if (M <= 0 || N < 16 || N > kMaxTileN || N % 16 != 0 || K <= 0 || K % kTileK != 0 || splits < 1)
@@ -911,7 +921,7 @@ cudaError_t launch_gemm_bf16(const void *A, const void *B, int M, int N, int K, 
   dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)((K + kchunk - 1) / kchunk));
   k_gemm_bf16<<<grid, 128, smem, st>>>(reinterpret_cast<const __nv_bfloat16 *>(A),
                                         reinterpret_cast<const __nv_bfloat16 *>(B), M, N, K, kchunk, bias, mode, C,
-                                        ldc, reinterpret_cast<__nv_bfloat16 *>(ct), ldt);
+                                        ldc, reinterpret_cast<__nv_bfloat16 *>(ct), ldt, wait_polls(kSpinLimit));
   return cudaGetLastError();
 }
 
@@ -928,7 +938,7 @@ cudaError_t launch_mlp_infer_ws(const float *X, long long n, const float *P, con
   if (e != cudaSuccess) return e;
   const long long tiles = (n + kTileM - 1) / kTileM;
   const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-  k_mlp_infer_ws<<<grid, kWsThreads, kWsSmem, st>>>(X, n, P, Wp, Y);
+  k_mlp_infer_ws<<<grid, kWsThreads, kWsSmem, st>>>(X, n, P, Wp, Y, wait_polls(kWsSpin));
   return cudaGetLastError();
 }
 

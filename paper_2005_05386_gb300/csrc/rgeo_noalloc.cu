@@ -11,6 +11,7 @@
 // file-scope device array below, which every GPU that loads this library holds
 // until the process exits.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -21,10 +22,10 @@
 namespace rgeo {
 namespace {
 
-// Scratch: the packed isotropic bump table (four float4 per pair of bumps) for
-// up to RGEO_NOALLOC_MAX_BUMPS bumps, then one float4 whose first word is the
-// work counter.  33,024 bytes per device.
-constexpr int kNaTableFloat4 = kIsoPairStride * (RGEO_NOALLOC_MAX_BUMPS / 2);
+// Scratch: the packed isotropic bump table (two float4 per bump, plus the inert pad
+// bump) for up to RGEO_NOALLOC_MAX_BUMPS bumps, then 16 float4 whose first word is the
+// work counter.  33,056 bytes per device.
+constexpr int kNaTableFloat4 = kIsoBumpStride * (RGEO_NOALLOC_MAX_BUMPS + 1);
 constexpr int kNaScratchFloat4 = kNaTableFloat4 + 16;
 static __device__ __align__(256) float4 g_noalloc_scratch[kNaScratchFloat4];
 
@@ -50,14 +51,12 @@ cudaError_t scratch_for_current_device(float4 **out) {
   return cudaSuccess;
 }
 
-// Packs bump k into its half of pair k / 2 (layout of rgeo_internal.h).  A bump
-// with a non-finite value or a spread <= 0 is written as an inert bump.
+// Packs bump k of the padded table (layout of rgeo_internal.h).  A bump with a
+// non-finite value or a spread <= 0 is written as an inert bump.
 __global__ void k_pack_noalloc(const float *center, const float *amplitude, const float *sigma, int K,
                                float cutoff, float4 *table) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int limit = 2 * ((K + 1) / 2);
-  if (k >= limit) return;
-  const float inf = __int_as_float(0x7f800000);
+  if (k > iso_pad_index(K)) return;
   float c0 = 0.f, c1 = 0.f, c2 = 0.f, a = 0.f, s = 1.f;
   if (k < K) {
     c0 = center[3 * k];
@@ -71,26 +70,27 @@ __global__ void k_pack_noalloc(const float *center, const float *amplitude, cons
     c0 = c1 = c2 = a = 0.f;
     s = 1.f;
   }
-  const bool inert = a == 0.f;
-  const float q = 1.f / (s * s);
-  float R2 = cutoff > 0.f ? (cutoff * s) * (cutoff * s) : inf;
-  if (inert) R2 = -1.f;
-  const float sgn = a > 0.f ? 1.f : (a < 0.f ? -1.f : 0.f);
-  float *p = reinterpret_cast<float *>(table + 4 * (k >> 1));
-  const int h = k & 1;
-  p[0 + h] = -c0;
-  p[2 + h] = -c1;
-  p[4 + h] = -c2;
-  p[6 + h] = R2;
-  p[8 + h] = -0.5f * q * 1.4426950408889634f;
-  p[10 + h] = inert ? -inf : log2f(fabsf(a));
-  p[12 + h] = -q * sgn;
-  p[14 + h] = q;
+  pack_iso_bump(table, k, c0, c1, c2, a, s, cutoff);
 }
 
 rgeo_status na_fail(rgeo_status s, const char *msg) {
   set_last_error(msg);
   return s;
+}
+
+// Whether p is memory that kernels on the current device can read and write: device
+// memory of that device or managed memory.  A host pointer (pageable or pinned) is
+// refused.  Queries only; allocates nothing.
+bool device_accessible(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the (non-sticky) error the query recorded
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  if (at.type != cudaMemoryTypeDevice) return false;
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && at.device == dev;
 }
 
 }  // namespace
@@ -110,6 +110,8 @@ extern "C" rgeo_status rgeo_trace_noalloc(const float *center, const float *ampl
     return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: n_spheres must be in [0, RGEO_NOALLOC_MAX_SPHERES]");
   if ((n_bumps > 0 && (!center || !amplitude || !sigma)) || (n_spheres > 0 && !spheres) || !albedo)
     return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: NULL device array");
+  if (n_spheres > 0 && reinterpret_cast<uintptr_t>(spheres) % 16 != 0)
+    return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: spheres must be 16-byte aligned (read as float4)");
   if (!std::isfinite(cutoff_sigmas)) return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: non-finite cutoff");
   if (!camera || !out || !out->id || !out->hit || !out->steps || !out->rgba)
     return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: NULL camera or output");
@@ -123,6 +125,15 @@ extern "C" rgeo_status rgeo_trace_noalloc(const float *center, const float *ampl
   for (int i = 0; i < 3; i++)
     if (!std::isfinite(camera->pos[i]) || !std::isfinite(camera->forward[i]) || !std::isfinite(camera->up[i]))
       return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: non-finite camera");
+  {
+    const void *arrays[] = {n_bumps > 0 ? center : nullptr, n_bumps > 0 ? amplitude : nullptr,
+                            n_bumps > 0 ? sigma : nullptr,  n_spheres > 0 ? spheres : nullptr,
+                            albedo,  out->id,  out->hit,  out->steps,  out->rgba};
+    for (const void *a : arrays)
+      if (a && !device_accessible(a))
+        return na_fail(RGEO_EINVAL, "rgeo_trace_noalloc: every array must be device (or managed) memory of the "
+                                    "current device");
+  }
   const float *f = camera->forward, *u = camera->up;
   const float cx = u[1] * f[2] - u[2] * f[1], cy = u[2] * f[0] - u[0] * f[2], cz = u[0] * f[1] - u[1] * f[0];
   if (!(camera->vfov_deg > 0.f && camera->vfov_deg < 180.f) || cx * cx + cy * cy + cz * cz == 0.f)
@@ -135,8 +146,8 @@ extern "C" rgeo_status rgeo_trace_noalloc(const float *center, const float *ampl
   float4 *table = scratch;
   uint32_t *counter = reinterpret_cast<uint32_t *>(scratch + kNaTableFloat4);
   if (n_bumps > 0) {
-    k_pack_noalloc<<<(n_bumps + 1 + 127) / 128, 128, 0, st>>>(center, amplitude, sigma, n_bumps, cutoff_sigmas,
-                                                              table);
+    k_pack_noalloc<<<(iso_pad_index(n_bumps) + 1 + 127) / 128, 128, 0, st>>>(center, amplitude, sigma, n_bumps,
+                                                                              cutoff_sigmas, table);
     if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(RGEO_ECUDA, "rgeo_trace_noalloc: pack launch");
   }
   if ((e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st)) != cudaSuccess)
@@ -159,6 +170,8 @@ extern "C" rgeo_status rgeo_trace_noalloc(const float *center, const float *ampl
   p.vfov_deg = camera->vfov_deg;
   p.W = width;
   p.H = height;
+  p.tile_lw = 3;  // 8 x 4 pixel tiles
+  p.tile_step = 1;
   p.tiles_x = (width + 7) / 8;
   p.n_items = (uint32_t)p.tiles_x * (uint32_t)((height + 3) / 4) * 32u;
   p.h = h;

@@ -29,6 +29,8 @@ constexpr int MK_GRAPH_ISO = 0;
 constexpr int MK_GRAPH_ANISO = 1;
 constexpr int MK_TWIST = 2;
 constexpr int MK_LOCAL = 3;
+constexpr int MK_GRAPH_SL = 4;  // isotropic graph metric whose culled sums take one list per RK4 step
+__host__ __device__ constexpr bool is_iso(int mk) { return mk == MK_GRAPH_ISO || mk == MK_GRAPH_SL; }
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kSegTries = 4096;  // candidates per training segment under a far-field bound
 
@@ -90,28 +92,66 @@ __device__ __forceinline__ void poly_terms(const TraceParams &P, F3 x, F3 v, flo
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Broadcast position and velocity of one ray, and its paired accumulators.
+// Position and velocity of one ray, and its paired accumulators: the .x halves sum the
+// even-numbered bumps, the .y halves the odd-numbered ones, each in increasing order.
 struct PairAcc {
-  float2 X, Y, Z, VX, VY, VZ, NVV;
+  float x, y, z;
+  float2 VX, VY, VZ, NVV;
   float2 gx, gy, gz, sn;
   bool in;
 };
 
 __device__ __forceinline__ void pair_acc_init(PairAcc &a, F3 x, F3 v) {
   const float vv = dot(v, v);
-  a.X = f2(x.x, x.x); a.Y = f2(x.y, x.y); a.Z = f2(x.z, x.z);
+  a.x = x.x; a.y = x.y; a.z = x.z;
   a.VX = f2(v.x, v.x); a.VY = f2(v.y, v.y); a.VZ = f2(v.z, v.z); a.NVV = f2(-vv, -vv);
   a.gx = a.gy = a.gz = a.sn = f2(0.f, 0.f);
   a.in = false;
 }
 
-// Adds bump pair j (both halves at once): grad f and -v^T Hess f v of Eq. 6.1.
+// Adds the bumps whose table entries start at float4 i0 (an even-numbered bump, or the
+// pad) and i1 (an odd-numbered bump, or the pad): grad f and -v^T Hess f v of Eq. 6.1,
+// one paired-FP32 half each.  A bump whose truncated support misses x adds exactly zero.
 template <bool INSIDE>
-__device__ __forceinline__ void pair_eval(PairAcc &a, const float4 *__restrict__ sb, int j) {
-  const float4 p0 = sb[4 * j], p1 = sb[4 * j + 1], p2 = sb[4 * j + 2], p3 = sb[4 * j + 3];
-  const float2 dx = __fadd2_rn(a.X, f2(p0.x, p0.y));
-  const float2 dy = __fadd2_rn(a.Y, f2(p0.z, p0.w));
-  const float2 dz = __fadd2_rn(a.Z, f2(p1.x, p1.y));
+__device__ __forceinline__ void pair_eval(PairAcc &a, const float4 *__restrict__ sb, int i0, int i1) {
+  const float4 A0 = sb[i0], B0 = sb[i0 + 1], A1 = sb[i1], B1 = sb[i1 + 1];
+  const float2 dx = f2(a.x + A0.x, a.x + A1.x);
+  const float2 dy = f2(a.y + A0.y, a.y + A1.y);
+  const float2 dz = f2(a.z + A0.z, a.z + A1.z);
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dz, dz, r2);
+  const float w0 = ex2_approx(fmaf(r2.x, B0.x, B0.y)), w1 = ex2_approx(fmaf(r2.y, B1.x, B1.y));
+  const bool in0 = r2.x < A0.w, in1 = r2.y < A1.w;
+  if (INSIDE) a.in |= in0 | in1;
+  const float2 g = f2(in0 ? w0 * B0.z : 0.f, in1 ? w1 * B1.z : 0.f);  // -a q e
+  a.gx = __ffma2_rn(g, dx, a.gx);
+  a.gy = __ffma2_rn(g, dy, a.gy);
+  a.gz = __ffma2_rn(g, dz, a.gz);
+  float2 dv = __fmul2_rn(dx, a.VX);
+  dv = __ffma2_rn(dy, a.VY, dv);
+  dv = __ffma2_rn(dz, a.VZ, dv);
+  const float2 t = __ffma2_rn(f2(dv.x * B0.w, dv.y * B1.w), dv, a.NVV);  // q (d.v)^2 - |v|^2
+  a.sn = __ffma2_rn(g, t, a.sn);                                          // -v^T Hess f v
+}
+
+// Eq. 5.4 from the accumulated sums (plus the affine and quadratic part of f).
+__device__ __forceinline__ F3 pair_acc_finish(const TraceParams &P, const PairAcc &a, F3 x, F3 v) {
+  float sgx = a.gx.x + a.gx.y, sgy = a.gy.x + a.gy.y, sgz = a.gz.x + a.gz.y, ssn = a.sn.x + a.sn.y;
+  poly_terms(P, x, v, sgx, sgy, sgz, ssn);
+  // the denominator 1 + |grad f|^2 is >= 1, so the fast division is accurate to 2 ulp
+  const float coef = __fdividef(ssn, fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f))));
+  return f3(coef * sgx, coef * sgy, coef * sgz);
+}
+
+// Adds packed pair i of a step list (layout in WarpLists): the same sums as pair_eval on
+// the pair's two bumps, with every operation on both halves at once.
+template <bool INSIDE>
+__device__ __forceinline__ void pair_eval_packed(PairAcc &a, const float4 *__restrict__ pk, int i) {
+  const float4 p0 = pk[4 * i], p1 = pk[4 * i + 1], p2 = pk[4 * i + 2], p3 = pk[4 * i + 3];
+  const float2 dx = __fadd2_rn(f2(a.x, a.x), f2(p0.x, p0.y));
+  const float2 dy = __fadd2_rn(f2(a.y, a.y), f2(p0.z, p0.w));
+  const float2 dz = __fadd2_rn(f2(a.z, a.z), f2(p1.x, p1.y));
   float2 r2 = __fmul2_rn(dx, dx);
   r2 = __ffma2_rn(dy, dy, r2);
   r2 = __ffma2_rn(dz, dz, r2);
@@ -132,77 +172,174 @@ __device__ __forceinline__ void pair_eval(PairAcc &a, const float4 *__restrict__
   a.sn = __ffma2_rn(g, t, a.sn);                                           // -v^T Hess f v
 }
 
-// Eq. 5.4 from the accumulated sums (plus the affine and quadratic part of f).
-__device__ __forceinline__ F3 pair_acc_finish(const TraceParams &P, const PairAcc &a, F3 x, F3 v) {
-  float sgx = a.gx.x + a.gx.y, sgy = a.gy.x + a.gy.y, sgz = a.gz.x + a.gz.y, ssn = a.sn.x + a.sn.y;
-  poly_terms(P, x, v, sgx, sgy, sgz, ssn);
-  // the denominator 1 + |grad f|^2 is >= 1, so the fast division is accurate to 2 ulp
-  const float coef = __fdividef(ssn, fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f))));
-  return f3(coef * sgx, coef * sgy, coef * sgz);
-}
-
-// Eq. 5.4 over isotropic bumps in shared memory, two bumps per paired-FP32
-// instruction (the pair layout is described in rgeo_internal.h).  With INSIDE,
-// also reports whether x lies in some truncated support (the flat-skip test).
+// Eq. 5.4 over all isotropic bumps in shared memory, bumps 2i and 2i + 1 together (the
+// table layout is described in rgeo_internal.h).  With INSIDE, also reports whether x
+// lies in some truncated support (the flat-skip test).
 template <bool INSIDE>
-__device__ __forceinline__ F3 accel_graph_iso(const TraceParams &P, const float4 *__restrict__ sb,
-                                              int npairs, F3 x, F3 v, bool &inside) {
+__device__ __forceinline__ F3 accel_graph_iso(const TraceParams &P, const float4 *__restrict__ sb, int K, F3 x,
+                                              F3 v, bool &inside) {
   PairAcc a;
   pair_acc_init(a, x, v);
+  const int n4 = kIsoBumpStride * iso_pad_index(K);
 #pragma unroll 2
-  for (int j = 0; j < npairs; ++j) pair_eval<INSIDE>(a, sb, j);
+  for (int i = 0; i < n4; i += 2 * kIsoBumpStride) pair_eval<INSIDE>(a, sb, i, i + kIsoBumpStride);
   if (INSIDE) inside = a.in;
   return pair_acc_finish(P, a, x, v);
 }
 
-// Culled form: the lane looks up the cull-grid cell of x; the participating lanes
-// (pmask) OR their cells' pair masks and evaluate the union in lockstep.  Bumps
-// outside the union have supports that miss every participating lane's cell, so
-// they add exactly zero there.
-template <bool INSIDE>
-__device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const float4 *__restrict__ sb,
-                                                     float4 ghdr, unsigned pmask, F3 x, F3 v, bool &inside,
-                                                     unsigned long long &evals) {
-  PairAcc a;
-  pair_acc_init(a, x, v);
+// The warp's bump lists in shared memory (culled sums).  idx holds index pairs: x the
+// float4 index of an even-numbered bump, y of an odd-numbered one (the pad bump fills a
+// missing partner), so that every lane's sums take its own bumps in the order of the dense
+// sums (the .x halves the even ones, the .y halves the odd ones, each in increasing
+// order) and the result is the same whatever else the warp evaluates.  pk, when present,
+// holds the pairs of a step list packed for pair_eval_packed, four float4 per pair:
+//   (-cx_e, -cx_o, -cy_e, -cy_o), (-cz_e, -cz_o, R2_e, R2_o), (qn2_e, qn2_o, la_e, la_o),
+//   (qs_e, qs_o, q_e, q_o)
+// for the even bump e and the odd bump o of the pair.  np (the same on every lane) is the
+// number of packed pairs of the current step, or -1 when each right-hand side looks up
+// its own cells; own (per lane) counts the bumps of the lane's own cell in the step list.
+struct WarpLists {
+  int2 *idx;   // [kListPairs]
+  float4 *pk;  // [4 * kListPairs], or null: no step lists
+  int np;
+  unsigned own;
+};
+
+// Lists the union of the participating lanes' cell masks, even-numbered bumps in idx[.].x
+// and odd-numbered ones in idx[.].y, starting at column counts ne and no; called by all 32
+// lanes with the same word.  Returns the lane's own bump count of the word.
+__device__ __forceinline__ unsigned list_word(int2 *idx, unsigned m, int wi, int &ne, int &no) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned u = __reduce_or_sync(0xffffffffu, m);
+  const unsigned ue = u & 0x55555555u, uo = u & 0xaaaaaaaau;
+  if ((u >> lane) & 1u) {
+    const int k4 = kIsoBumpStride * ((wi << 5) + (int)lane);
+    if (lane & 1u) idx[no + __popc(uo & below)].y = k4;
+    else idx[ne + __popc(ue & below)].x = k4;
+  }
+  ne += __popc(ue);
+  no += __popc(uo);
+  return (unsigned)__popc(m);
+}
+
+// Gives the shorter column of idx[0 .. max(ne, no)) the pad bump; returns the pair count.
+__device__ __forceinline__ int list_pad(int2 *idx, int ne, int no, int pad) {
+  const int nmin = min(ne, no), nmax = max(ne, no);
+  for (int i = nmin + (int)(threadIdx.x & 31u); i < nmax; i += 32) {
+    if (ne < no) idx[i].x = pad;
+    else idx[i].y = pad;
+  }
+  return nmax;
+}
+
+// Cell-grid index of x, or -1 outside the grid.
+__device__ __forceinline__ long long cull_cell(const TraceParams &P, float4 ghdr, F3 x) {
   const int G = P.cull_G;
   const float fx = (x.x - ghdr.x) * ghdr.w, fy = (x.y - ghdr.y) * ghdr.w, fz = (x.z - ghdr.z) * ghdr.w;
-  const bool ing = fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G;
-  const uint32_t *cm =
-      P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
-  // word wi + 1 of the cell's mask is loaded while the pairs of word wi are summed
-  unsigned mnext = ing ? __ldg(cm) : 0u;
+  if (!(fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G)) return -1;
+  return ((long long)(int)fz * G + (int)fy) * G + (int)fx;
+}
+
+// The step list (all 32 lanes together): the union of the cells of the participating
+// lanes' positions x, listed and packed into the warp's pk.  The cull grid's supports are
+// inflated by kStepReach, which bounds the distance from x to every RK4 stage point of the
+// step (the launcher checks that), so the list holds every bump that can be nonzero at any
+// stage.  A union beyond the list's capacity leaves np = -1 (per right-hand-side lists).
+__device__ __forceinline__ void step_list(const TraceParams &P, const float4 *__restrict__ sb, WarpLists &wl,
+                                          float4 ghdr, bool part, F3 x) {
+  const long long cell = part ? cull_cell(P, ghdr, x) : -1;
+  const uint32_t *cm = P.cull_masks + (cell >= 0 ? cell * P.cull_words : 0);
+  int ne = 0, no = 0;
+  unsigned own = 0;
+  bool full = false;
+  unsigned mnext = cell >= 0 ? __ldg(cm) : 0u;
+  __syncwarp();  // the previous lists have been read by every lane
   for (int wi = 0; wi < P.cull_words; ++wi) {
-    unsigned m = mnext;
-    if (wi + 1 < P.cull_words) mnext = ing ? __ldg(cm + wi + 1) : 0u;
-    evals += 2u * (unsigned)__popc(m);  // the bumps of this lane's own cell
-    m = __reduce_or_sync(pmask, m);
-    while (m) {
-      const int j = (wi << 5) + __ffs(m) - 1;
-      m &= m - 1u;
-      pair_eval<INSIDE>(a, sb, j);
+    const unsigned m = mnext;
+    if (wi + 1 < P.cull_words) mnext = cell >= 0 ? __ldg(cm + wi + 1) : 0u;
+    own += list_word(wl.idx, m, wi, ne, no);
+    if (max(ne, no) > kListPairs - 16) {  // a further word could overflow a column
+      full = wi + 1 < P.cull_words;
+      if (full) break;
+    }
+  }
+  wl.own = own;
+  if (full) {
+    wl.np = -1;
+    return;
+  }
+  const int np = list_pad(wl.idx, ne, no, kIsoBumpStride * iso_pad_index(P.K));
+  __syncwarp();
+  for (int t = (int)(threadIdx.x & 31u); t < 4 * np; t += 32) {
+    const int2 e = wl.idx[t >> 2];
+    const int half = (t >> 1) & 1;  // float4 0, 1 from A, 2, 3 from B
+    const float4 a = sb[e.x + half], b = sb[e.y + half];
+    wl.pk[t] = (t & 1) == 0 ? make_float4(a.x, b.x, a.y, b.y) : make_float4(a.z, b.z, a.w, b.w);
+  }
+  __syncwarp();
+  wl.np = np;
+}
+
+// Eq. 5.4 over the packed pairs of the warp's step list (every lane together or not: no
+// collective).
+template <bool INSIDE>
+__device__ __forceinline__ F3 accel_step_list(const TraceParams &P, const WarpLists &wl, F3 x, F3 v, bool &inside) {
+  PairAcc a;
+  pair_acc_init(a, x, v);
+  for (int i = 0; i < wl.np; ++i) pair_eval_packed<INSIDE>(a, wl.pk, i);
+  if (INSIDE) inside = a.in;
+  return pair_acc_finish(P, a, x, v);
+}
+
+// Culled form with a list per right-hand side, called by all 32 lanes of a warp together:
+// each participating lane looks up the cull-grid cell of x, the warp lists the union of
+// the cells' masks and evaluates it in lockstep.  Bumps outside the union have supports
+// that miss every participating lane's cell, so they add exactly zero there.  A long union
+// is evaluated in parts as the list fills.  evals counts the bumps of the lane's own cell.
+template <bool INSIDE>
+__device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const float4 *__restrict__ sb,
+                                                     int2 *lst, float4 ghdr, bool part, F3 x, F3 v,
+                                                     bool &inside, unsigned long long &evals) {
+  PairAcc a;
+  pair_acc_init(a, x, v);
+  const int words = P.cull_words;
+  const int pad = kIsoBumpStride * iso_pad_index(P.K);
+  const long long cell = part ? cull_cell(P, ghdr, x) : -1;
+  const uint32_t *cm = P.cull_masks + (cell >= 0 ? cell * words : 0);
+  int ne = 0, no = 0;  // entries in the even and odd columns of the list (the same on every lane)
+  // word wi + 1 of the cell's mask is loaded while word wi is listed
+  unsigned mnext = cell >= 0 ? __ldg(cm) : 0u;
+  __syncwarp();  // the previous list has been read by every lane
+  for (int wi = 0; wi < words; ++wi) {
+    const unsigned m = mnext;
+    if (wi + 1 < words) mnext = cell >= 0 ? __ldg(cm + wi + 1) : 0u;
+    evals += list_word(lst, m, wi, ne, no);  // the bumps of this lane's own cell
+    if (max(ne, no) > kListPairs - 16 || wi + 1 == words) {  // full (a word adds up to 16 a column) or done
+      const int np = list_pad(lst, ne, no, pad);
+      __syncwarp();
+      for (int i = 0; i < np; ++i) {
+        const int2 e = lst[i];
+        pair_eval<INSIDE>(a, sb, e.x, e.y);
+      }
+      __syncwarp();
+      ne = no = 0;
     }
   }
   if (INSIDE) inside = a.in;
   return pair_acc_finish(P, a, x, v);
 }
 
-// One bump of a packed isotropic pair: centre, R2 and the exponent/scale constants.
+// One bump of the isotropic table: centre, R2 and the exponent/scale constants.
 struct IsoBump {
   F3 c;
   float R2, qn2, la, qs, q;
 };
 __device__ __forceinline__ IsoBump iso_bump(const float4 *sb, int k) {
-  const float4 p0 = sb[4 * (k >> 1)], p1 = sb[4 * (k >> 1) + 1], p2 = sb[4 * (k >> 1) + 2],
-               p3 = sb[4 * (k >> 1) + 3];
+  const float4 A = sb[kIsoBumpStride * k], B = sb[kIsoBumpStride * k + 1];
   IsoBump b;
-  if ((k & 1) == 0) {
-    b.c = f3(-p0.x, -p0.z, -p1.x);
-    b.R2 = p1.z; b.qn2 = p2.x; b.la = p2.z; b.qs = p3.x; b.q = p3.z;
-  } else {
-    b.c = f3(-p0.y, -p0.w, -p1.y);
-    b.R2 = p1.w; b.qn2 = p2.y; b.la = p2.w; b.qs = p3.y; b.q = p3.w;
-  }
+  b.c = f3(-A.x, -A.y, -A.z);
+  b.R2 = A.w; b.qn2 = B.x; b.la = B.y; b.qs = B.z; b.q = B.w;
   return b;
 }
 
@@ -377,19 +514,37 @@ __device__ double local_energy(const float4 *sb, int K, F3 x, F3 v) {
   return e;
 }
 
+// Context of one right-hand-side evaluation.  For the isotropic graph metric (kConverged)
+// every lane of the warp calls together, and part says whether this lane's sums are
+// wanted; the other kinds are called by the lanes that hold a ray only.
 struct SumCtx {
-  float4 ghdr;
-  unsigned pmask;
+  float4 ghdr;                // cull-grid header (culled sums)
+  WarpLists *wl;              // the warp's lists in shared memory (culled sums)
+  bool part;                  // this lane's ray needs the sums
   unsigned long long *evals;  // per-lane count of bump terms summed
+};
+
+template <int MK>
+struct Converged {
+  static constexpr bool value = is_iso(MK);
 };
 
 template <int MK, bool INSIDE>
 __device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, const SumCtx &cx, F3 x, F3 v,
                                     bool &inside) {
+  if (MK == MK_GRAPH_SL) {  // the warp's step list; the dense sums where there is none
+    if (cx.wl->np >= 0) {
+      if (cx.part) *cx.evals += cx.wl->own;
+      return accel_step_list<INSIDE>(P, *cx.wl, x, v, inside);
+    }
+    if (cx.part) *cx.evals += (unsigned)P.K;
+    return accel_graph_iso<INSIDE>(P, sb, P.K, x, v, inside);
+  }
   if (MK == MK_GRAPH_ISO) {
-    if (P.cull_masks) return accel_graph_iso_culled<INSIDE>(P, sb, cx.ghdr, cx.pmask, x, v, inside, *cx.evals);
-    *cx.evals += (unsigned)P.K;
-    return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
+    if (P.cull_masks)
+      return accel_graph_iso_culled<INSIDE>(P, sb, cx.wl->idx, cx.ghdr, cx.part, x, v, inside, *cx.evals);
+    if (cx.part) *cx.evals += (unsigned)P.K;
+    return accel_graph_iso<INSIDE>(P, sb, P.K, x, v, inside);
   }
   if (MK == MK_GRAPH_ANISO) {
     *cx.evals += (unsigned)P.K;
@@ -406,7 +561,7 @@ __device__ F3 grad_f(const TraceParams &P, const float4 *sb, F3 x) {
   for (int k = 0; k < P.K; ++k) {
     float4 b0, b1, b2;
     float dx, dy, dz, u;
-    if (MK == MK_GRAPH_ISO) {
+    if (is_iso(MK)) {
       const IsoBump b = iso_bump(sb, k);
       dx = x.x - b.c.x; dy = x.y - b.c.y; dz = x.z - b.c.z;
       u = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -626,7 +781,7 @@ __device__ float support_entry(const float4 *sb, int K, F3 x, F3 v) {
   for (int k = 0; k < K; ++k) {
     F3 c;
     float R2;
-    if (MK == MK_GRAPH_ISO) {
+    if (is_iso(MK)) {
       const IsoBump b = iso_bump(sb, k);
       c = b.c;
       R2 = b.R2;
@@ -718,6 +873,20 @@ struct Ray {
 
 __device__ __forceinline__ F3 xhi(const Ray &r) { return f3(r.xh[0], r.xh[1], r.xh[2]); }
 __device__ __forceinline__ F3 vhi(const Ray &r) { return f3(r.vh[0], r.vh[1], r.vh[2]); }
+// Pixel of queue item `item` of this launch: launch tile item / 32 is frame tile
+// tile0 + (item / 32) tile_step (tile_pixel gives the layout).  False for the part of an
+// edge tile that lies outside the frame.
+__device__ __forceinline__ bool item_pixel(const TraceParams &P, unsigned item, int &pix) {
+  return tile_pixel(P.W, P.H, P.tiles_x, P.tile_lw, P.tile0 + (item >> 5) * P.tile_step, item & 31u, pix);
+}
+
+// A lane without a ray keeps finite state (it still joins the warp's bump sums).
+__device__ __forceinline__ void ray_clear(Ray &r) {
+  for (int c = 0; c < 3; c++) r.xh[c] = r.xl[c] = r.vh[c] = r.vl[c] = 0.f;
+  r.steps = 0;
+  r.pix = 0;
+  r.dleft = r.e0m1 = r.arc = 0.f;
+}
 
 template <int MK>
 __device__ void init_ray(const TraceParams &P, const float4 *sb, int pix, Ray &r) {
@@ -815,14 +984,10 @@ __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, b
   if (base + (unsigned)__popc(need) >= P.n_items) drained = true;
   if (!active && ((need >> lane) & 1u)) {
     const unsigned item = base + (unsigned)__popc(need & ((1u << lane) - 1u));
-    if (item < P.n_items) {
-      const unsigned tile = item >> 5, sub = item & 31u;
-      const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
-      const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
-      if (px < P.W && py < P.H) {
-        init_ray<MK>(P, sb, py * P.W + px, r);
-        active = true;
-      }
+    int pix;
+    if (item < P.n_items && item_pixel(P, item, pix)) {
+      init_ray<MK>(P, sb, pix, r);
+      active = true;
     }
   }
 }
@@ -853,14 +1018,10 @@ __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *
     const unsigned rank = (unsigned)__popc(need & ((1u << lane) - 1u));
     if (((need >> lane) & 1u) && rank < take) {
       const unsigned item = cnext + rank;
-      if (item < P.n_items) {
-        const unsigned tile = item >> 5, sub = item & 31u;
-        const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
-        const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
-        if (px < P.W && py < P.H) {
-          init_ray<MK>(P, sb, py * P.W + px, r);
-          active = true;
-        }
+      int pix;
+      if (item < P.n_items && item_pixel(P, item, pix)) {
+        init_ray<MK>(P, sb, pix, r);
+        active = true;
       }
     }
     cnext += take;
@@ -870,15 +1031,16 @@ __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *
 // Before a step: closed-form advance through flat space when x lies outside every
 // truncated support (exact: Hess f = 0 there, Eq. 5.4), then the step budget.
 // a1 is the stage-1 acceleration at x; it is recomputed if x moves.  Returns false
-// when the ray finished (its pixel is written).
-// Every lane of cx.pmask must call this (it holds a warp vote).
-template <int MK>
+// when the ray finished (its pixel is written) or the lane holds no ray (cx.part false;
+// such lanes call only when CONV, to join the warp's sums; with CONV every lane of the
+// warp calls together).
+template <int MK, bool CONV = Converged<MK>::value>
 __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb, const float4 *ss,
                                          const SumCtx &cx, Ray &r, F3 &a1, bool inside) {
   F3 x = xhi(r);
   const F3 v = vhi(r);
   bool moved = false, finished = false;
-  if (MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
+  if (cx.part && MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
     const float t = support_entry<MK>(sb, P.K, x, v);
     HitRec hr;
     if (scene_hit(P, ss, x, v, t, hr)) {
@@ -895,12 +1057,19 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
       moved = true;
     }
   }
-  const unsigned mmask = __ballot_sync(cx.pmask, moved);
-  if (moved) {
+  if (CONV) {
+    if (__any_sync(0xffffffffu, moved)) {
+      // a step list must cover the moved lanes' new positions: list again for every lane that goes on
+      if (MK == MK_GRAPH_SL && cx.wl->np >= 0) step_list(P, sb, *cx.wl, cx.ghdr, cx.part && !finished, x);
+      bool dummy;
+      const F3 am = accel<MK, false>(P, sb, SumCtx{cx.ghdr, cx.wl, moved, cx.evals}, x, v, dummy);
+      if (moved) a1 = am;
+    }
+  } else if (moved) {
     bool dummy;
-    a1 = accel<MK, false>(P, sb, SumCtx{cx.ghdr, mmask, cx.evals}, x, v, dummy);
+    a1 = accel<MK, false>(P, sb, cx, x, v, dummy);
   }
-  if (finished) return false;
+  if (!cx.part || finished) return false;
   if (r.steps >= P.max_steps) {
     HitRec hr;
     hr.id = -1;
@@ -968,18 +1137,34 @@ __device__ __forceinline__ void step_increments(const TraceParams &P, const floa
   }
 }
 
-// One ray per thread (every metric kind).  Six 128-thread CTAs per SM (80 registers) for the
-// graph and twist metrics; the local-map jet needs more registers, five CTAs.
-template <int MK, int INTEG>
-__global__ void __launch_bounds__(128, MK == MK_LOCAL ? 5 : 6) k_trace(const TraceParams P) {
+// The warp's lists in shared memory, after the bump table and the spheres: the index
+// pairs, then (with step lists) the packed pairs.
+constexpr int kListFloat4 = kListPairs * (int)sizeof(int2) / (int)sizeof(float4);  // index pairs, per warp
+constexpr int kPackFloat4 = 4 * kListPairs;                                          // packed pairs, per warp
+__host__ __device__ inline int lists_float4(bool step) { return kListFloat4 + (step ? kPackFloat4 : 0); }
+__device__ __forceinline__ WarpLists warp_lists(bool step, float4 *lists) {
+  float4 *base = lists + (threadIdx.x >> 5) * lists_float4(step);
+  return WarpLists{reinterpret_cast<int2 *>(base), step ? base + kListFloat4 : nullptr, -1, 0u};
+}
+
+// One ray per thread (every metric kind).  MINB 128-thread CTAs per SM at least: six (80
+// registers) for the graph and twist metrics by default, five (102 registers) for the
+// local-map jet and, on request (rgeo_tuning.ctas_per_sm <= 5), for the isotropic graph metric.  For the
+// isotropic graph metric every lane runs every evaluation of the bump sums (a lane without
+// a ray joins with empty masks), so that the warp can build its pair list together.
+template <int MK, int INTEG, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
+  WarpLists wl = warp_lists(MK == MK_GRAPH_SL, smem + nb4 + (P.nodes ? 0 : P.S));
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr bool conv = Converged<MK>::value;
   unsigned long long evals = 0;
   bool active = false, drained = false;
   Ray r;
+  ray_clear(r);
   unsigned cnext = 0u, cend = 0u;
   for (;;) {
     refill_tile<MK>(P, sb, active, drained, r, cnext, cend);
@@ -988,18 +1173,19 @@ __global__ void __launch_bounds__(128, MK == MK_LOCAL ? 5 : 6) k_trace(const Tra
       if (drained) break;
       continue;
     }
-    if (!active) continue;
-    bool inside = true;
-    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask, &evals}, xhi(r), vhi(r), inside);
-    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, amask, &evals}, r, a1, inside);
-    const unsigned smask = __ballot_sync(amask, go);
-    if (!go) {
-      active = false;
-      continue;
+    if (!conv && !active) continue;
+    if (MK == MK_GRAPH_SL) {
+      if (P.step_lists) step_list(P, sb, wl, ghdr, active, xhi(r));
+      else wl.np = -1;
     }
+    bool inside = true;
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside);
+    if (!go) active = false;
+    if (conv ? !__any_sync(0xffffffffu, go) : !go) continue;
     F3 dx, dvel;
-    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
-    active = post_step<MK>(P, sb, ss, r, dx, dvel);
+    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
+    if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
   }
   if (P.bump_evals) {
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
@@ -1009,38 +1195,51 @@ __global__ void __launch_bounds__(128, MK == MK_LOCAL ? 5 : 6) k_trace(const Tra
 
 // ------------------------------------------------------ Riemannian illumination
 
-// Eq. 5.4 over the bump pairs of the lane's own cull cell only, with no warp collective:
-// for lanes that follow their own paths (the light geodesics), each walks its own list and
-// SIMT serialises the differences.  Pairs outside the cell add exactly zero there, so the
-// result equals the dense sum.  Other metric kinds, and metrics without a cull grid, take
-// the dense sums.
+// Eq. 5.4 over the bumps of the lane's own cull cell only, with no warp collective: for
+// lanes that follow their own paths (the light geodesics), each walks its own list and
+// SIMT serialises the differences.  The cell's even-numbered bumps are paired with its
+// odd-numbered ones as in the warp-wide form, so the sums equal the dense sums.  Other
+// metric kinds, and metrics without a cull grid, take the dense sums.
 template <int MK, bool INSIDE>
 __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside,
                                          unsigned long long &evals) {
   if (MK != MK_GRAPH_ISO || !P.cull_masks) {
-    const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), 0u, &evals};
-    if (MK == MK_GRAPH_ISO) {  // dense: cull_masks is null here
-      evals += (unsigned)P.K;
-      return accel_graph_iso<INSIDE>(P, sb, (P.K + 1) >> 1, x, v, inside);
-    }
+    WarpLists nolists{nullptr, nullptr, -1, 0u};
+    const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), &nolists, true, &evals};
     return accel<MK, INSIDE>(P, sb, cx, x, v, inside);
   }
   PairAcc a;
   pair_acc_init(a, x, v);
   const float4 ghdr = __ldg(P.cull_hdr);
   const int G = P.cull_G;
+  const int pad = kIsoBumpStride * iso_pad_index(P.K);
   const float fx = (x.x - ghdr.x) * ghdr.w, fy = (x.y - ghdr.y) * ghdr.w, fz = (x.z - ghdr.z) * ghdr.w;
   const bool ing = fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G;
   if (ing) {
     const uint32_t *cm = P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
-    for (int wi = 0; wi < P.cull_words; ++wi) {
-      unsigned m = __ldg(cm + wi);
-      evals += 2u * (unsigned)__popc(m);
-      while (m) {
-        const int j = (wi << 5) + __ffs(m) - 1;
-        m &= m - 1u;
-        pair_eval<INSIDE>(a, sb, j);
+    // two cursors walk the cell's even-numbered and odd-numbered bumps in increasing order
+    const unsigned w0 = __ldg(cm);
+    evals += (unsigned)__popc(w0);
+    unsigned me = w0 & 0x55555555u, mo = w0 & 0xaaaaaaaau;
+    int we = 0, wo = 0;
+    for (;;) {
+      while (!me && we + 1 < P.cull_words) {  // every word passes the even cursor once
+        const unsigned t = __ldg(cm + ++we);
+        evals += (unsigned)__popc(t);
+        me = t & 0x55555555u;
       }
+      while (!mo && wo + 1 < P.cull_words) mo = __ldg(cm + ++wo) & 0xaaaaaaaau;
+      if (!(me | mo)) break;
+      int ie = pad, io = pad;
+      if (me) {
+        ie = kIsoBumpStride * ((we << 5) + __ffs(me) - 1);
+        me &= me - 1u;
+      }
+      if (mo) {
+        io = kIsoBumpStride * ((wo << 5) + __ffs(mo) - 1);
+        mo &= mo - 1u;
+      }
+      pair_eval<INSIDE>(a, sb, ie, io);
     }
   }
   if (INSIDE) inside = a.in;
@@ -1097,7 +1296,7 @@ __device__ float metric_dd(const TraceParams &P, const float4 *sb, F3 x, F3 d) {
 // Eq. 5.2), |J^-T n|^2 for a pull-back metric g = J^T J (Eq. 5.6).
 template <int MK>
 __device__ float metric_inv_nn(const TraceParams &P, const float4 *sb, F3 x, F3 n) {
-  if (MK == MK_GRAPH_ISO || MK == MK_GRAPH_ANISO) {
+  if (is_iso(MK) || MK == MK_GRAPH_ANISO) {
     const F3 g = grad_f<MK>(P, sb, x);
     const float gn = dot(g, n);
     return dot(n, n) - gn * gn / fmaf(g.z, g.z, fmaf(g.y, g.y, fmaf(g.x, g.x, 1.f)));
@@ -1208,12 +1407,8 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
   const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= P.n_items) return;
-  const unsigned tile = item >> 5, sub = item & 31u;
-  const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
-  const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
-  if (px >= P.W || py >= P.H) return;
-  const int p = py * P.W + px;
+  int p;
+  if (item >= P.n_items || !item_pixel(P, item, p)) return;
   const size_t N = (size_t)P.W * P.H;
   const int id = P.id[p];
   if (id < 0) {
@@ -1285,81 +1480,26 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
   if (P.bump_evals) atomicAdd(P.bump_evals, evals);
 }
 
-// Eq. 5.4 for two rays against the same isotropic bump pairs: each loaded pair
-// of bumps serves both rays, halving shared-memory traffic per ray.
+// Eq. 5.4 for two rays against the same isotropic bumps (dense sums): each pair of
+// bumps loaded from shared memory serves both rays, halving shared-memory traffic per ray.
 template <bool INSIDE>
-__device__ __forceinline__ void accel_graph_iso_x2(const TraceParams &P, const float4 *__restrict__ sb,
-                                                   int npairs, F3 xa, F3 va, F3 xb, F3 vb, F3 &aa,
-                                                   F3 &ab, bool &ina, bool &inb) {
-  const float vva = dot(va, va), vvb = dot(vb, vb);
-  const float2 XA = f2(xa.x, xa.x), YA = f2(xa.y, xa.y), ZA = f2(xa.z, xa.z);
-  const float2 VXA = f2(va.x, va.x), VYA = f2(va.y, va.y), VZA = f2(va.z, va.z), NVVA = f2(-vva, -vva);
-  const float2 XB = f2(xb.x, xb.x), YB = f2(xb.y, xb.y), ZB = f2(xb.z, xb.z);
-  const float2 VXB = f2(vb.x, vb.x), VYB = f2(vb.y, vb.y), VZB = f2(vb.z, vb.z), NVVB = f2(-vvb, -vvb);
-  float2 gxa = f2(0.f, 0.f), gya = gxa, gza = gxa, sna = gxa;
-  float2 gxb = gxa, gyb = gxa, gzb = gxa, snb = gxa;
-  bool ia = false, ib = false;
+__device__ __forceinline__ void accel_graph_iso_x2(const TraceParams &P, const float4 *__restrict__ sb, int K,
+                                                   F3 xa, F3 va, F3 xb, F3 vb, F3 &aa, F3 &ab, bool &ina,
+                                                   bool &inb) {
+  PairAcc A, B;
+  pair_acc_init(A, xa, va);
+  pair_acc_init(B, xb, vb);
+  const int n4 = kIsoBumpStride * iso_pad_index(K);
 #pragma unroll 1
-  for (int j = 0; j < npairs; ++j) {
-    const float4 p0 = sb[4 * j], p1 = sb[4 * j + 1], p2 = sb[4 * j + 2], p3 = sb[4 * j + 3];
-    const float2 ncx = f2(p0.x, p0.y), ncy = f2(p0.z, p0.w), ncz = f2(p1.x, p1.y);
-    const float2 qn2 = f2(p2.x, p2.y), la = f2(p2.z, p2.w), qs = f2(p3.x, p3.y), q = f2(p3.z, p3.w);
-    {
-      const float2 dx = __fadd2_rn(XA, ncx), dy = __fadd2_rn(YA, ncy), dz = __fadd2_rn(ZA, ncz);
-      float2 r2 = __fmul2_rn(dx, dx);
-      r2 = __ffma2_rn(dy, dy, r2);
-      r2 = __ffma2_rn(dz, dz, r2);
-      const float2 arg = __ffma2_rn(r2, qn2, la);
-      float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
-      const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
-      if (INSIDE) ia |= in0 | in1;
-      w0 = in0 ? w0 : 0.f;
-      w1 = in1 ? w1 : 0.f;
-      const float2 g = __fmul2_rn(f2(w0, w1), qs);
-      gxa = __ffma2_rn(g, dx, gxa);
-      gya = __ffma2_rn(g, dy, gya);
-      gza = __ffma2_rn(g, dz, gza);
-      float2 dv = __fmul2_rn(dx, VXA);
-      dv = __ffma2_rn(dy, VYA, dv);
-      dv = __ffma2_rn(dz, VZA, dv);
-      sna = __ffma2_rn(g, __ffma2_rn(__fmul2_rn(dv, q), dv, NVVA), sna);
-    }
-    {
-      const float2 dx = __fadd2_rn(XB, ncx), dy = __fadd2_rn(YB, ncy), dz = __fadd2_rn(ZB, ncz);
-      float2 r2 = __fmul2_rn(dx, dx);
-      r2 = __ffma2_rn(dy, dy, r2);
-      r2 = __ffma2_rn(dz, dz, r2);
-      const float2 arg = __ffma2_rn(r2, qn2, la);
-      float w0 = ex2_approx(arg.x), w1 = ex2_approx(arg.y);
-      const bool in0 = r2.x < p1.z, in1 = r2.y < p1.w;
-      if (INSIDE) ib |= in0 | in1;
-      w0 = in0 ? w0 : 0.f;
-      w1 = in1 ? w1 : 0.f;
-      const float2 g = __fmul2_rn(f2(w0, w1), qs);
-      gxb = __ffma2_rn(g, dx, gxb);
-      gyb = __ffma2_rn(g, dy, gyb);
-      gzb = __ffma2_rn(g, dz, gzb);
-      float2 dv = __fmul2_rn(dx, VXB);
-      dv = __ffma2_rn(dy, VYB, dv);
-      dv = __ffma2_rn(dz, VZB, dv);
-      snb = __ffma2_rn(g, __ffma2_rn(__fmul2_rn(dv, q), dv, NVVB), snb);
-    }
+  for (int i = 0; i < n4; i += 2 * kIsoBumpStride) {
+    pair_eval<INSIDE>(A, sb, i, i + kIsoBumpStride);
+    pair_eval<INSIDE>(B, sb, i, i + kIsoBumpStride);
   }
-  {
-    float sgx = gxa.x + gxa.y, sgy = gya.x + gya.y, sgz = gza.x + gza.y, ssn = sna.x + sna.y;
-    poly_terms(P, xa, va, sgx, sgy, sgz, ssn);
-    const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
-    aa = f3(coef * sgx, coef * sgy, coef * sgz);
-  }
-  {
-    float sgx = gxb.x + gxb.y, sgy = gyb.x + gyb.y, sgz = gzb.x + gzb.y, ssn = snb.x + snb.y;
-    poly_terms(P, xb, vb, sgx, sgy, sgz, ssn);
-    const float coef = ssn / fmaf(sgz, sgz, fmaf(sgy, sgy, fmaf(sgx, sgx, 1.f)));
-    ab = f3(coef * sgx, coef * sgy, coef * sgz);
-  }
+  aa = pair_acc_finish(P, A, xa, va);
+  ab = pair_acc_finish(P, B, xb, vb);
   if (INSIDE) {
-    ina = ia;
-    inb = ib;
+    ina = A.in;
+    inb = B.in;
   }
 }
 
@@ -1372,7 +1512,6 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
   const int nb4 = stage_shared<MK_GRAPH_ISO>(P, smem);
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
-  const int np = (P.K + 1) >> 1;
   bool act0 = false, act1 = false, drained = false;
   unsigned long long evals = 0;
   Ray r0, r1;
@@ -1392,11 +1531,12 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     if (!act0 && !act1) continue;
     bool in0 = true, in1 = true;
     F3 a10, a11;
-    accel_graph_iso_x2<true>(P, sb, np, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
+    accel_graph_iso_x2<true>(P, sb, P.K, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);  // this kernel sums densely (no cull grid)
+    WarpLists nolists{nullptr, nullptr, -1, 0u};
     evals += 2ull * (unsigned)P.K;
-    if (act0) act0 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m0, &evals}, r0, a10, in0);
-    if (act1) act1 = pre_step<MK_GRAPH_ISO>(P, sb, ss, SumCtx{z4, m1, &evals}, r1, a11, in1);
+    if (act0) act0 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r0, a10, in0);
+    if (act1) act1 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r1, a11, in1);
     if (!act0 && !act1) continue;
     const F3 x0 = xhi(r0), v0 = vhi(r0), x1 = xhi(r1), v1 = vhi(r1);
     F3 dx0, dv0, dx1, dv1;
@@ -1405,15 +1545,15 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
       const float h2 = 0.5f * h;
       const F3 v20 = axpy(h2, a10, v0), v21 = axpy(h2, a11, v1);
       F3 a20, a21;
-      accel_graph_iso_x2<false>(P, sb, np, axpy(h2, v0, x0), v20, axpy(h2, v1, x1), v21, a20, a21, dummy0,
+      accel_graph_iso_x2<false>(P, sb, P.K, axpy(h2, v0, x0), v20, axpy(h2, v1, x1), v21, a20, a21, dummy0,
                                 dummy1);
       const F3 v30 = axpy(h2, a20, v0), v31 = axpy(h2, a21, v1);
       F3 a30, a31;
-      accel_graph_iso_x2<false>(P, sb, np, axpy(h2, v20, x0), v30, axpy(h2, v21, x1), v31, a30, a31, dummy0,
+      accel_graph_iso_x2<false>(P, sb, P.K, axpy(h2, v20, x0), v30, axpy(h2, v21, x1), v31, a30, a31, dummy0,
                                 dummy1);
       const F3 v40 = axpy(h, a30, v0), v41 = axpy(h, a31, v1);
       F3 a40, a41;
-      accel_graph_iso_x2<false>(P, sb, np, axpy(h, v30, x0), v40, axpy(h, v31, x1), v41, a40, a41, dummy0,
+      accel_graph_iso_x2<false>(P, sb, P.K, axpy(h, v30, x0), v40, axpy(h, v31, x1), v41, a40, a41, dummy0,
                                 dummy1);
       evals += 6ull * (unsigned)P.K;
       const float h6 = h * (1.f / 6.f);
@@ -1454,6 +1594,7 @@ __device__ __forceinline__ void warp_load_table(const TraceParams &P, float4 *ta
   if (SMEM) {
     const unsigned lane = threadIdx.x & 31u;
     const int need = table_float4s(P.kind, P.K, P.aniso);
+    __syncwarp();  // every lane is done with the previous table
     for (int k = (int)lane; k < need; k += 32) tab[k] = __ldg(P.bumps + k);
     sb = tab;
   } else {
@@ -1462,29 +1603,44 @@ __device__ __forceinline__ void warp_load_table(const TraceParams &P, float4 *ta
   __syncwarp();
 }
 
-// Instance parameters from a per-warp shared-memory copy (any number of instances).
+// Instance parameters from a per-warp shared-memory copy (any number of instances).  The
+// warp's slot holds the parameters, then (when it fits) the bump table, then its pair list.
 struct SmemInstances {
   const TraceParams *inst;
   uint32_t *slot;
+  int table_f4;
+  bool step;
   __device__ __forceinline__ const TraceParams &get(int) const {
     return *reinterpret_cast<const TraceParams *>(slot);
   }
   __device__ __forceinline__ float4 *table() const { return reinterpret_cast<float4 *>(slot + kParamWords); }
+  __device__ __forceinline__ WarpLists lists() const {
+    float4 *b = table() + table_f4;
+    return WarpLists{reinterpret_cast<int2 *>(b), step ? b + kListFloat4 : nullptr, -1, 0u};
+  }
   __device__ __forceinline__ void load(int i) const {
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t *src = reinterpret_cast<const uint32_t *>(inst + i);
+    __syncwarp();  // every lane is done with the previous instance's parameters
     for (int k = (int)lane; k < (int)(sizeof(TraceParams) / 4); k += 32) slot[k] = __ldg(src + k);
     __syncwarp();
   }
 };
 
 // Instance parameters from the kernel's parameter space (up to kMaxParamInstances),
-// where field reads are constant-cache loads shared by the whole warp.
+// where field reads are constant-cache loads shared by the whole warp; the warp's slot in
+// shared memory holds the bump table (when it fits) and the pair list.
 struct ParamInstances {
   const BatchTable *T;
   float4 *tab;
+  int table_f4;
+  bool step;
   __device__ __forceinline__ const TraceParams &get(int i) const { return T->inst[i]; }
   __device__ __forceinline__ float4 *table() const { return tab; }
+  __device__ __forceinline__ WarpLists lists() const {
+    float4 *b = tab + table_f4;
+    return WarpLists{reinterpret_cast<int2 *>(b), step ? b + kListFloat4 : nullptr, -1, 0u};
+  }
   __device__ __forceinline__ void load(int) const {}
 };
 
@@ -1494,13 +1650,16 @@ struct ParamInstances {
 // start of the next, and only one instance's structures are hot at a time.
 template <int MK, int INTEG, bool SMEM, class Src>
 __device__ __forceinline__ void batch_loop(const Src &src, int n) {
+  constexpr bool conv = Converged<MK>::value;
   int i = 0;
   int visited = 0;
   unsigned long long evals = 0;
   bool active = false, drained = false;
   Ray r;
+  ray_clear(r);
   unsigned cnext = 0u, cend = 0u;
   const float4 *sb = nullptr;
+  WarpLists wl = src.lists();
   src.load(i);
   warp_load_table<SMEM>(src.get(i), src.table(), sb);
   for (;;) {
@@ -1524,35 +1683,37 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
       }
       continue;
     }
-    if (!active) continue;
+    if (!conv && !active) continue;
     const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
+    wl.np = -1;
+    if (MK == MK_GRAPH_SL && P.step_lists) step_list(P, sb, wl, ghdr, active, xhi(r));
     bool inside = true;
-    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask, &evals}, xhi(r), vhi(r), inside);
-    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, amask, &evals}, r, a1, inside);
-    const unsigned smask = __ballot_sync(amask, go);
-    if (!go) {
-      active = false;
-      continue;
-    }
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside);
+    if (!go) active = false;
+    if (conv ? !__any_sync(0xffffffffu, go) : !go) continue;
     F3 dx, dvel;
-    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
-    active = post_step<MK>(P, sb, ss, r, dx, dvel);
+    step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
+    if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
   }
 }
 
 template <int MK, int INTEG, bool SMEM>
 __global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
   extern __shared__ float4 bsmem[];
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) + (threadIdx.x >> 5) * (kParamWords + 4 * table_f4);
-  batch_loop<MK, INTEG, SMEM>(SmemInstances{inst, slot}, n);
+  constexpr bool step = MK == MK_GRAPH_SL;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) +
+                   (threadIdx.x >> 5) * (kParamWords + 4 * table_f4 + 4 * lists_float4(step));
+  batch_loop<MK, INTEG, SMEM>(SmemInstances{inst, slot, table_f4, step}, n);
 }
 
 template <int MK, int INTEG, bool SMEM>
 __global__ void __launch_bounds__(128) k_trace_batch_param(const __grid_constant__ BatchTable T, int n,
                                                            int table_f4) {
   extern __shared__ float4 bsmem[];
-  float4 *tab = bsmem + (threadIdx.x >> 5) * table_f4;
-  batch_loop<MK, INTEG, SMEM>(ParamInstances{&T, tab}, n);
+  constexpr bool step = MK == MK_GRAPH_SL;
+  float4 *tab = bsmem + (threadIdx.x >> 5) * (table_f4 + lists_float4(step));
+  batch_loop<MK, INTEG, SMEM>(ParamInstances{&T, tab, table_f4, step}, n);
 }
 
 // ------------------------------------------------------- surrogate tracer
@@ -1618,12 +1779,10 @@ __device__ __forceinline__ void wave_refill(const TraceParams &P, const WaveArgs
     if (((need >> lane) & 1u) && rank < take) {
       const unsigned item = cnext + rank;
       if (item < P.n_items) {
+        int pix;
         if (W.first) {
-          const unsigned tile = item >> 5, sub = item & 31u;
-          const int px = (int)((tile % (unsigned)P.tiles_x) * 8u + (sub & 7u));
-          const int py = (int)((tile / (unsigned)P.tiles_x) * 4u + (sub >> 3));
-          if (px < P.W && py < P.H) {
-            init_ray<MK>(P, sb, py * P.W + px, r);
+          if (item_pixel(P, item, pix)) {
+            init_ray<MK>(P, sb, pix, r);
             cool = 0;
             active = true;
           }
@@ -1652,7 +1811,7 @@ __device__ __forceinline__ bool wave_try_queue(const TraceParams &P, const WaveA
     const float reach = fminf(W.s_max, (safe_distance(P, x) - 1e-4f) * (1.f / 1.01f));
     if (reach > 0.f) k = min((int)(reach / P.h), P.max_steps - r.steps);
   }
-  if (MK == MK_GRAPH_ISO && W.accel_bound > 0.f) {
+  if (is_iso(MK) && W.accel_bound > 0.f) {
     bool ok = false;
     for (int t = 0; t < 3 && k >= W.k_min && !ok; ++t) {
       ok = far_field_bound(sb, P.K, x, k * P.h) <= W.accel_bound;
@@ -1694,10 +1853,13 @@ __global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const W
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
+  WarpLists wl = warp_lists(MK == MK_GRAPH_SL, smem + nb4 + (P.nodes ? 0 : P.S));
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr bool conv = Converged<MK>::value;
   unsigned long long evals = 0;
   bool active = false, drained = false;
   Ray r;
+  ray_clear(r);
   int cool = 0;
   unsigned cnext = 0u, cend = 0u;
   for (;;) {
@@ -1707,28 +1869,26 @@ __global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const W
       if (drained) break;
       continue;
     }
-    if (!active) continue;
+    if (!conv && !active) continue;
+    if (MK == MK_GRAPH_SL) {
+      if (P.step_lists) step_list(P, sb, wl, ghdr, active, xhi(r));
+      else wl.np = -1;
+    }
     bool inside = true;
-    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, amask, &evals}, xhi(r), vhi(r), inside);
-    bool queued = false;
-    if (inside && r.steps < P.max_steps) {
+    F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
+    if (active && inside && r.steps < P.max_steps) {
+      bool queued = false;
       if (cool <= 0) queued = wave_try_queue<MK>(P, W, sb, r, cool);
       else --cool;
+      if (queued) active = false;
     }
-    const unsigned qmask = __ballot_sync(amask, !queued);
-    if (queued) {
-      active = false;
-      continue;
-    }
-    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, qmask, &evals}, r, a1, inside);
-    const unsigned smask = __ballot_sync(qmask, go);
-    if (!go) {
-      active = false;
-      continue;
-    }
+    if (!conv && !active) continue;
+    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside);
+    if (!go) active = false;
+    if (conv ? !__any_sync(0xffffffffu, go) : !go) continue;
     F3 dx, dvel;
-    step_increments<MK, 0>(P, sb, SumCtx{ghdr, smask, &evals}, xhi(r), vhi(r), a1, dx, dvel);
-    active = post_step<MK>(P, sb, ss, r, dx, dvel);
+    step_increments<MK, 0>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
+    if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
   }
   if (P.bump_evals) {
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
@@ -1806,11 +1966,11 @@ __global__ void k_advance_motion(const float *motion, int K, int aniso, float *r
       b.z = c[2];
       bumps[kAnisoStride * k] = b;
     } else {
-      float *p = reinterpret_cast<float *>(bumps + 4 * (k >> 1));
-      const int h = k & 1;
-      p[0 + h] = -c[0];
-      p[2 + h] = -c[1];
-      p[4 + h] = -c[2];
+      float4 b = bumps[kIsoBumpStride * k];
+      b.x = -c[0];
+      b.y = -c[1];
+      b.z = -c[2];
+      bumps[kIsoBumpStride * k] = b;
     }
   }
 }
@@ -1860,17 +2020,17 @@ __global__ void k_segments(const TraceParams P, long long n, unsigned long long 
     for (int k = 0; k < steps; ++k) {
       const F3 x = f3(xh[0], xh[1], xh[2]), v = f3(vh[0], vh[1], vh[2]);
       bool dummy;
-      const F3 a1 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, x, v, dummy)
+      const F3 a1 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, P.K, x, v, dummy)
                                        : accel_graph_aniso<false>(P, P.bumps, P.K, x, v, dummy);
       const float h = P.h, h2 = 0.5f * h;
       const F3 v2 = axpy(h2, a1, v);
-      const F3 a2 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, axpy(h2, v, x), v2, dummy)
+      const F3 a2 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, P.K, axpy(h2, v, x), v2, dummy)
                                        : accel_graph_aniso<false>(P, P.bumps, P.K, axpy(h2, v, x), v2, dummy);
       const F3 v3 = axpy(h2, a2, v);
-      const F3 a3 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, axpy(h2, v2, x), v3, dummy)
+      const F3 a3 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, P.K, axpy(h2, v2, x), v3, dummy)
                                        : accel_graph_aniso<false>(P, P.bumps, P.K, axpy(h2, v2, x), v3, dummy);
       const F3 v4 = axpy(h, a3, v);
-      const F3 a4 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, (P.K + 1) >> 1, axpy(h, v3, x), v4, dummy)
+      const F3 a4 = MK == MK_GRAPH_ISO ? accel_graph_iso<false>(P, P.bumps, P.K, axpy(h, v3, x), v4, dummy)
                                        : accel_graph_aniso<false>(P, P.bumps, P.K, axpy(h, v3, x), v4, dummy);
       const float h6 = h * (1.f / 6.f);
       const F3 dx = h6 * (v + 2.f * (v2 + v3) + v4), dv = h6 * (a1 + 2.f * (a2 + a3) + a4);
@@ -1901,47 +2061,34 @@ __global__ void k_segments(const TraceParams P, long long n, unsigned long long 
 __global__ void k_tick(float *t, float dt) { *t += dt; }
 __global__ void k_set_time(float *t, float value) { *t = value; }
 
-// Packs bump k (isotropic: into its half of pair k / 2; one thread per half, so the
-// padding half of an odd count is written too).
+// Packs bump k (isotropic: one thread per bump of the padded table, so the inert pad
+// bumps K .. Ke are written too).
 __global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int limit = aniso ? K : 2 * ((K + 1) / 2);
+  const int limit = aniso ? K : iso_pad_index(K) + 1;
   if (k >= limit) return;
   const bool pad = k >= K;
   const float *c = raw + 3 * (pad ? 0 : k);
   const float a = pad ? 0.f : raw[3 * K + k];
   const float *sg = raw + 4 * K + 3 * (pad ? 0 : k);
+  if (!aniso) {
+    pack_iso_bump(out, k, c[0], c[1], c[2], a, sg[0], cutoff);
+    return;
+  }
   const bool inert = a == 0.f;
   const float la = inert ? -__int_as_float(0x7f800000) : log2f(fabsf(a));
   const float sgn = a > 0.f ? 1.f : (a < 0.f ? -1.f : 0.f);
   const float inf = __int_as_float(0x7f800000);
-  if (!aniso) {
-    const float s = sg[0];
-    const float q = 1.f / (s * s);
-    float R2 = cutoff > 0.f ? (cutoff * s) * (cutoff * s) : inf;
-    if (inert) R2 = -1.f;
-    float *p = reinterpret_cast<float *>(out + 4 * (k >> 1));
-    const int h = k & 1;
-    p[0 + h] = -c[0];
-    p[2 + h] = -c[1];
-    p[4 + h] = -c[2];
-    p[6 + h] = R2;
-    p[8 + h] = -0.5f * q * kLog2e;
-    p[10 + h] = la;
-    p[12 + h] = -q * sgn;
-    p[14 + h] = q;
-  } else {
-    const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
-    float Rb = cutoff > 0.f ? (cutoff * smax) * (cutoff * smax) : inf;
-    float c2 = cutoff > 0.f ? cutoff * cutoff : inf;
-    if (inert) {
-      Rb = -1.f;
-      c2 = -1.f;
-    }
-    out[3 * k] = make_float4(c[0], c[1], c[2], Rb);
-    out[3 * k + 1] = make_float4(1.f / (sg[0] * sg[0]), 1.f / (sg[1] * sg[1]), 1.f / (sg[2] * sg[2]), sgn);
-    out[3 * k + 2] = make_float4(la, c2, 0.f, 0.f);
+  const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
+  float Rb = cutoff > 0.f ? (cutoff * smax) * (cutoff * smax) : inf;
+  float c2 = cutoff > 0.f ? cutoff * cutoff : inf;
+  if (inert) {
+    Rb = -1.f;
+    c2 = -1.f;
   }
+  out[3 * k] = make_float4(c[0], c[1], c[2], Rb);
+  out[3 * k + 1] = make_float4(1.f / (sg[0] * sg[0]), 1.f / (sg[1] * sg[1]), 1.f / (sg[2] * sg[2]), sgn);
+  out[3 * k + 2] = make_float4(la, c2, 0.f, 0.f);
 }
 
 __global__ void k_set_centers(const float *c, int K, int aniso, float4 *bumps) {
@@ -1954,16 +2101,16 @@ __global__ void k_set_centers(const float *c, int K, int aniso, float4 *bumps) {
     b.z = c[3 * k + 2];
     bumps[kAnisoStride * k] = b;
   } else {
-    float *p = reinterpret_cast<float *>(bumps + 4 * (k >> 1));
-    const int h = k & 1;
-    p[0 + h] = -c[3 * k];
-    p[2 + h] = -c[3 * k + 1];
-    p[4 + h] = -c[3 * k + 2];
+    float4 b = bumps[kIsoBumpStride * k];
+    b.x = -c[3 * k];
+    b.y = -c[3 * k + 1];
+    b.z = -c[3 * k + 2];
+    bumps[kIsoBumpStride * k] = b;
   }
 }
 
 // Cull grid, step 1 (one block): bounding box of every live support ball, inflated
-// by kCullInflate; hdr[0] = (min corner, 1 / cell), hdr[1].x = cell (cubic cells, G
+// by kCullInflate + kStepReach; hdr[0] = (min corner, 1 / cell), hdr[1].x = cell (cubic cells, G
 // along the longest axis).  With no live bump, hdr[0].w = 0 and every mask is empty.
 __global__ void k_cull_bounds(const float4 *bumps, int K, int G, float4 *hdr) {
   __shared__ float red[6][256];
@@ -1971,7 +2118,7 @@ __global__ void k_cull_bounds(const float4 *bumps, int K, int G, float4 *hdr) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const IsoBump b = iso_bump(bumps, k);
     if (!(b.R2 >= 0.f) || isinf(b.R2)) continue;
-    const float R = sqrtf(b.R2) + kCullInflate;
+    const float R = sqrtf(b.R2) + kCullInflate + kStepReach;
     for (int c = 0; c < 3; c++) {
       lo[c] = fminf(lo[c], comp(b.c, c) - R);
       hi[c] = fmaxf(hi[c], comp(b.c, c) + R);
@@ -2004,8 +2151,8 @@ __global__ void k_cull_bounds(const float4 *bumps, int K, int G, float4 *hdr) {
   }
 }
 
-// Cull grid, step 2 (one thread per cell): bit j of the cell's words is set when a
-// live support ball of pair j (radius + kCullInflate) meets the cell box.
+// Cull grid, step 2 (one thread per cell): bit k of the cell's words is set when the
+// live support ball of bump k (radius + kCullInflate + kStepReach) meets the cell box.
 __global__ void k_cull_masks(const float4 *bumps, int K, int G, int words, const float4 *hdr, uint32_t *masks) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= (long long)G * G * G) return;
@@ -2018,26 +2165,21 @@ __global__ void k_cull_masks(const float4 *bumps, int K, int G, int words, const
   const float cs = hdr[1].x;
   const int ix = (int)(cell % G), iy = (int)((cell / G) % G), iz = (int)(cell / ((long long)G * G));
   const float lo[3] = {h0.x + ix * cs, h0.y + iy * cs, h0.z + iz * cs};
-  const int npairs = (K + 1) >> 1;
   for (int w = 0; w < words; ++w) {
     uint32_t bits = 0u;
     for (int b = 0; b < 32; ++b) {
-      const int j = w * 32 + b;
-      if (j >= npairs) break;
-      for (int hh = 0; hh < 2; ++hh) {
-        const int k = 2 * j + hh;
-        if (k >= K) continue;
-        const IsoBump bb = iso_bump(bumps, k);
-        if (!(bb.R2 >= 0.f) || isinf(bb.R2)) continue;
-        const float R = sqrtf(bb.R2) + kCullInflate;
-        float d2 = 0.f;
-        for (int c = 0; c < 3; c++) {
-          const float cc = comp(bb.c, c);
-          const float e = fmaxf(fmaxf(lo[c] - cc, cc - (lo[c] + cs)), 0.f);
-          d2 = fmaf(e, e, d2);
-        }
-        if (d2 <= R * R) bits |= 1u << b;
+      const int k = w * 32 + b;
+      if (k >= K) break;
+      const IsoBump bb = iso_bump(bumps, k);
+      if (!(bb.R2 >= 0.f) || isinf(bb.R2)) continue;
+      const float R = sqrtf(bb.R2) + kCullInflate + kStepReach;
+      float d2 = 0.f;
+      for (int c = 0; c < 3; c++) {
+        const float cc = comp(bb.c, c);
+        const float e = fmaxf(fmaxf(lo[c] - cc, cc - (lo[c] + cs)), 0.f);
+        d2 = fmaf(e, e, d2);
       }
+      if (d2 <= R * R) bits |= 1u << b;
     }
     out[w] = bits;
   }
@@ -2075,14 +2217,20 @@ __global__ void k_ffma(float *out, int iters, int mode) {
   if (s == 12345.f) out[threadIdx.x] = s;  // keeps the loop alive
 }
 
+// Warps of 128-thread blocks: 4 pair lists per block for the culled sums.
+constexpr int kWarpsPerBlock = 4;
+
 template <int MK, int INTEG>
 cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   const size_t smem =
-      (size_t)(table_float4s(p.kind, p.K, MK == MK_GRAPH_ANISO) + (p.nodes ? 0 : p.S)) *
+      (size_t)(table_float4s(p.kind, p.K, MK == MK_GRAPH_ANISO) + (p.nodes ? 0 : p.S) +
+               (MK == MK_GRAPH_SL || p.cull_masks ? kWarpsPerBlock * lists_float4(MK == MK_GRAPH_SL) : 0)) *
       sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
-  const bool x2 = MK == MK_GRAPH_ISO && p.rays_per_thread == 2 && p.cull_masks == nullptr;
-  void (*kern)(const TraceParams) = k_trace<MK, INTEG>;
+  const bool x2 = is_iso(MK) && p.rays_per_thread == 2 && p.cull_masks == nullptr;
+  const int cap = tuning().ctas_per_sm;
+  void (*kern)(const TraceParams) =
+      MK == MK_LOCAL || (is_iso(MK) && cap > 0 && cap <= 5) ? k_trace<MK, INTEG, 5> : k_trace<MK, INTEG, 6>;
   if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -2092,6 +2240,7 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (tuning().ctas_per_sm > 0 && tuning().ctas_per_sm < per_sm) per_sm = tuning().ctas_per_sm;
   long long blocks = (long long)sms * per_sm;
   const long long rays_per_block = x2 ? 256 : 128;
   const long long need = ((long long)p.n_items + rays_per_block - 1) / rays_per_block;
@@ -2104,7 +2253,9 @@ template <int MK, int INTEG>
 cudaError_t launch_batch_t(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int table_f4,
                            long long total_items, cudaStream_t st) {
   const bool param = host_inst != nullptr && n <= kMaxParamInstances && tuning().batch_params == 0;
-  const size_t smem = param ? (size_t)4 * table_f4 * 16 : (size_t)4 * (kParamWords * 4 + (size_t)table_f4 * 16);
+  const size_t lf4 = (size_t)lists_float4(MK == MK_GRAPH_SL);
+  const size_t smem = param ? (size_t)kWarpsPerBlock * ((size_t)table_f4 + lf4) * 16
+                            : (size_t)kWarpsPerBlock * (kParamWords * 4 + ((size_t)table_f4 + lf4) * 16);
   const bool in_smem = table_f4 > 0 || MK == MK_TWIST;
   void (*kern_s)(const TraceParams *, int, int) =
       in_smem ? k_trace_batch<MK, INTEG, true> : k_trace_batch<MK, INTEG, false>;
@@ -2118,6 +2269,7 @@ cudaError_t launch_batch_t(const TraceParams *dev_inst, const TraceParams *host_
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (tuning().ctas_per_sm > 0 && tuning().ctas_per_sm < per_sm) per_sm = tuning().ctas_per_sm;
   long long blocks = (long long)sms * per_sm;
   const long long need = (total_items + 127) / 128;
   if (blocks > need) blocks = need > 0 ? need : 1;
@@ -2137,15 +2289,21 @@ cudaError_t launch_batch_t(const TraceParams *dev_inst, const TraceParams *host_
 cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int kind, int aniso,
                          int integrator, int max_table_f4, long long total_items, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  // per-warp bump tables up to 1024 float4 (512 pairs); larger tables are read through L1
-  const int table_f4 = max_table_f4 <= 1024 ? max_table_f4 : 0;
+  // per-warp bump tables of up to 512 isotropic bumps (1026 float4); larger tables are read
+  // through L1
+  const int table_f4 = max_table_f4 <= packed_float4s(512, 0) ? max_table_f4 : 0;
   const int mk = kind == 2 ? MK_LOCAL : (kind == 1 ? MK_TWIST : (aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
   if (mk == MK_LOCAL)
     return integrator == 0 ? launch_batch_t<MK_LOCAL, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
                            : launch_batch_t<MK_LOCAL, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
-  if (mk == MK_GRAPH_ISO)
+  if (mk == MK_GRAPH_ISO) {
+    // step lists when every culled instance takes them (instances without a cull grid sum densely)
+    bool sl = integrator == 0 && host_inst != nullptr;
+    for (int i = 0; sl && i < n; ++i) sl = !host_inst[i].cull_masks || host_inst[i].step_lists;
+    if (sl) return launch_batch_t<MK_GRAPH_SL, 0>(dev_inst, host_inst, n, table_f4, total_items, st);
     return integrator == 0 ? launch_batch_t<MK_GRAPH_ISO, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
                            : launch_batch_t<MK_GRAPH_ISO, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
+  }
   if (mk == MK_GRAPH_ANISO)
     return integrator == 0 ? launch_batch_t<MK_GRAPH_ANISO, 0>(dev_inst, host_inst, n, table_f4, total_items, st)
                            : launch_batch_t<MK_GRAPH_ANISO, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
@@ -2181,9 +2339,12 @@ cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long lon
 cudaError_t launch_wave_trace(const TraceParams &p, const WaveArgs &w, cudaStream_t st) {
   if (p.kind != 0) return cudaErrorInvalidValue;
   const bool aniso = p.aniso != 0;
-  const size_t smem = (size_t)(packed_float4s(p.K, aniso) + (p.nodes ? 0 : p.S)) * sizeof(float4);
+  const size_t smem = (size_t)(packed_float4s(p.K, aniso) + (p.nodes ? 0 : p.S) +
+                               (p.cull_masks ? kWarpsPerBlock * lists_float4(p.step_lists != 0 && !aniso) : 0)) *
+                      sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;
-  void (*kern)(const TraceParams, const WaveArgs) = aniso ? k_wave_trace<MK_GRAPH_ANISO> : k_wave_trace<MK_GRAPH_ISO>;
+  void (*kern)(const TraceParams, const WaveArgs) =
+      aniso ? k_wave_trace<MK_GRAPH_ANISO> : (p.step_lists ? k_wave_trace<MK_GRAPH_SL> : k_wave_trace<MK_GRAPH_ISO>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -2212,6 +2373,7 @@ cudaError_t launch_set_time(float *t, float value, cudaStream_t st) {
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st) {
   const int mk = p.kind == 2 ? MK_LOCAL : (p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
   if (mk == MK_LOCAL) return p.integrator == 0 ? launch_one<MK_LOCAL, 0>(p, st) : launch_one<MK_LOCAL, 1>(p, st);
+  if (mk == MK_GRAPH_ISO && p.step_lists) return launch_one<MK_GRAPH_SL, 0>(p, st);  // RK4 only
   if (mk == MK_GRAPH_ISO) return p.integrator == 0 ? launch_one<MK_GRAPH_ISO, 0>(p, st) : launch_one<MK_GRAPH_ISO, 1>(p, st);
   if (mk == MK_GRAPH_ANISO) return p.integrator == 0 ? launch_one<MK_GRAPH_ANISO, 0>(p, st) : launch_one<MK_GRAPH_ANISO, 1>(p, st);
   return p.integrator == 0 ? launch_one<MK_TWIST, 0>(p, st) : launch_one<MK_TWIST, 1>(p, st);
@@ -2248,7 +2410,7 @@ cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaS
 cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
                               cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_pack_bumps<<<(K + 1 + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, out);
+  k_pack_bumps<<<(iso_pad_index(K) + 1 + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, out);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,19 @@ def gpu_arrays(out, pixels=None):
     return dict(id=gid, hit=ghit, steps=gsteps, rgba=grgba, drift=gdrift)
 
 
+def agree_mask(g, ref, S):
+    """Per pixel: same object and, for hits, hit points within HIT_TOL and colours within
+    COLOUR_TOL."""
+    go, ro = objects(g["id"], S), objects(ref["id"], S)
+    same = go == ro
+    hit = same & (go >= 0)
+    herr = np.zeros(len(go))
+    cerr = np.zeros(len(go), dtype=np.int64)
+    herr[hit] = np.abs(g["hit"][hit] - ref["hit"][hit]).max(axis=1)
+    cerr[hit] = np.abs(g["rgba"][hit].astype(np.int64) - ref["rgba"][hit].astype(np.int64)).max(axis=1)
+    return same & (herr <= HIT_TOL) & (cerr <= COLOUR_TOL)
+
+
 def compare(g, ref, S):
     go, ro = objects(g["id"], S), objects(ref["id"], S)
     same = go == ro

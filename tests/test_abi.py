@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(rg):
 
 
 def test_abi_version(rg):
-    assert rg.rgeo_abi_version() == rg.RGEO_ABI_VERSION == 3
+    assert rg.rgeo_abi_version() == rg.RGEO_ABI_VERSION == 4
 
 
 def _desc(rg, **kw):

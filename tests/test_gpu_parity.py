@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_2005_05386_gb300 import scenes
-from parity import assert_parity, compare, gpu_arrays
+from parity import AGREE_MIN, HIT_TOL, agree_mask, assert_parity, compare, gpu_arrays
 
 pytestmark = pytest.mark.gpu
 
@@ -178,27 +178,30 @@ def test_cull_grid_with_many_bumps_matches_oracle(rg):
 
 def test_parity_4k_1024_full_size_sample(rg):
     """3840x2160, 1024 bumps, 128 spheres + 100k-triangle mesh, <= 4000 steps: the full frame in
-    the benchmark's launch configuration against the oracle on a seeded sample of ~2000 pixels.
+    the benchmark's launch configuration against the oracle on a seeded sample of ~2000 pixels,
+    at the bar of every other workload (>= 99.9 % agree at 1e-4).
 
-    Every pixel sees the same object.  Hit points: rays that end within 2000 steps (the 1080p
-    budget) meet the 1e-4 bar; longer rays through this dense field drift apart from the FP64
-    integration (float32 rounding amplified along the path, about x6 per 1000 steps), so the
-    bar for all hits is 1e-4 on >= 98.5 % (measured: 1,509 of 1,526) and 5e-3 at worst."""
+    A float32 path cannot be held to an answer that float32 cannot resolve: a pixel is
+    ill-conditioned when its FP64 oracle answer itself changes object or moves by more than
+    1e-4 when the ray's initial direction turns by one float32 ulp (oracle.conditioning, four
+    tilts).  Such pixels -- only those, established on the oracle's side -- count as agreeing;
+    they are long rays through the dense field (about 2 % of hits in this sample)."""
     w = scenes.config_4k_1024()
     px = scenes.pixel_sample(w.n_pixels, 21, 2.4e-4)
     assert 1500 <= len(px) <= 2500
     g = _run(rg, w, 0, px)
     ref = oracle.trace(w, px)
-    st = compare(g, ref, w.scene.n_spheres)
-    assert st["same_object"] >= 0.999, st
     S = w.scene.n_spheres
-    go, ro = np.where(g["id"] >= S, S, g["id"]), np.where(ref["id"] >= S, S, ref["id"])
-    hit = (go == ro) & (go >= 0)
-    err = np.abs(g["hit"][hit] - ref["hit"][hit]).max(axis=1)
-    short = ref["steps"][hit] <= 2000
-    assert hit.sum() > 1000 and short.sum() > 1000
-    assert (err[short] <= 1e-4).mean() >= 0.998, (err[short] > 1e-4).sum()
-    assert (err <= 1e-4).mean() >= 0.985 and err.max() < 5e-3, ((err > 1e-4).sum(), err.max())
+    agree = agree_mask(g, ref, S)
+    bad = np.nonzero(~agree)[0]
+    excused = np.zeros(len(px), bool)
+    if len(bad):
+        same, move = oracle.conditioning(w, px[bad])
+        excused[bad] = ~same | (move > HIT_TOL)
+    print("4K parity", compare(g, ref, S), "disagree", len(bad), "ill-conditioned", int(excused.sum()))
+    assert (agree | excused).mean() >= AGREE_MIN, (len(bad), int(excused.sum()))
+    assert excused.mean() <= 0.03
+    assert (ref["id"] >= 0).sum() > 1000
 
 
 def test_one_and_two_rays_per_thread_agree(rg):
@@ -393,3 +396,38 @@ def test_trace_captured_in_a_graph_replays_exactly(rg):
         got = gpu_arrays(out)
         for k in ("id", "steps", "rgba", "hit"):
             assert np.array_equal(got[k], ref[k]), k
+
+
+def test_frame_parts_and_tuning_reproduce_the_frame_bit_for_bit(rg):
+    """Every lane sums its own bumps in the order of the dense sums whatever shares its warp,
+    so the frame is the same bit for bit when it is split into interleaved tile parts
+    (rgeo_trace_tiles, the multi-GPU split) and under every launch tuning: tile shape, CTAs per
+    SM (with the 96-register build), lists per step or per right-hand side."""
+    w = scenes.config_1080p_64(width=320, height=180)
+    ref = _run(rg, w)
+    N = w.n_pixels
+
+    def same(g):
+        for k in ("id", "steps", "rgba", "hit"):
+            assert np.array_equal(g[k], ref[k]), k
+
+    for n_parts in (2, 3):
+        out = rg.alloc_outputs(N)
+        for k in ("id", "hit", "steps", "rgba"):
+            out[k].fill_(7)
+        for part in range(n_parts):
+            rg.trace(w, out=out, tiles=(part, -1, n_parts))
+        rg.rgeo_sync()
+        same(gpu_arrays(out))
+    out = rg.alloc_outputs(N)
+    rg.trace(w, out=out, tiles=(0, 0, 1))  # an empty part writes nothing and is not an error
+    with pytest.raises(rg.RgeoError):
+        rg.trace(w, out=out, tiles=(0, -1, 0))
+    for kw in (dict(tile_shape=2), dict(tile_shape=3), dict(ctas_per_sm=5), dict(ctas_per_sm=3),
+               dict(sum_lists=1), dict(sum_lists=1, ctas_per_sm=5)):
+        try:
+            rg.rgeo_set_tuning(**kw)
+            g = _run(rg, w)
+        finally:
+            rg.rgeo_set_tuning()
+        same(g)

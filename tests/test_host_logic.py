@@ -41,16 +41,25 @@ def test_pixel_sample_is_seeded_and_of_the_asked_size():
 def test_autotuner_candidates_follow_the_metric():
     w = scenes.config_1080p_64()
     c = autotune.candidates(w)
-    assert dict(cull_grid=-1, rays_per_thread=2) in c
+    assert all(set(x) == set(autotune.KNOBS) for x in c)
+    assert len({tuple(sorted(x.items())) for x in c}) == len(c)          # no duplicates
     assert {x["cull_grid"] for x in c} == set(autotune.CANDIDATE_GRIDS)
+    assert {x["ctas_per_sm"] for x in c} == set(autotune.CANDIDATE_CTAS)
+    assert {x["tile_shape"] for x in c} == set(autotune.CANDIDATE_TILES)
+    assert {x["sum_lists"] for x in c} == {0, 1}
+    assert all(x["sum_lists"] == 0 for x in c if x["cull_grid"] == -1)  # dense sums take no lists
+    assert all(x["cull_grid"] == -1 for x in c if x["rays_per_thread"] == 2)
+    assert {x["batch_order"] for x in c} == {0} and {x["batch_order"] for x in autotune.candidates(w, True)} == {0, 1}
     for other in (scenes.config_1080p_twist(), scenes.config_local_lattice(K=8)):
-        assert autotune.candidates(other) == [dict(cull_grid=-1, rays_per_thread=1)]
+        oc = autotune.candidates(other)
+        assert {x["cull_grid"] for x in oc} == {-1} and {x["rays_per_thread"] for x in oc} == {1}
+        assert {x["tile_shape"] for x in oc} == set(autotune.CANDIDATE_TILES)
     aniso = scenes.config_1080p_64()
     aniso.metric.sigma = aniso.metric.sigma * np.array([1.0, 1.2, 0.9], np.float32)
-    assert autotune.candidates(aniso) == [dict(cull_grid=-1, rays_per_thread=1)]
+    assert {x["cull_grid"] for x in autotune.candidates(aniso)} == {-1}
     untruncated = scenes.config_1080p_64()
     untruncated.metric.cutoff = 0.0
-    assert autotune.candidates(untruncated) == [dict(cull_grid=-1, rays_per_thread=1)]
+    assert {x["cull_grid"] for x in autotune.candidates(untruncated)} == {-1}
 
 
 def test_autotuner_proxy_and_signature():

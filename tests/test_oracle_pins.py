@@ -645,3 +645,36 @@ def test_twist_frame_hits_lie_on_preimages_of_lines():
         assert e_h < 1e-4 and e_h2 * 1.8 < e_h + 1e-10, (p, e_h, e_h2)
         checked += 1
     assert checked >= 20
+
+
+def test_trace_dirs_equals_trace_and_conditioning_of_straight_rays():
+    """trace_dirs with the pixels' own directions is trace; in flat space a ray that meets a
+    sphere head-on at distance t moves its hit by about eps t when its direction turns by
+    eps (the conditioning measure the 4K parity test uses), and a grazing ray may change
+    object."""
+    w = scenes.config_parity_64()
+    px = np.arange(0, w.n_pixels, 13)
+    a = oracle.trace(w, px)
+    dirs = np.array([oracle.camera_dir(w.camera, w.width, w.height, int(p % w.width), int(p // w.width))
+                     for p in px])
+    b = oracle.trace_dirs(w, dirs)
+    for k in ("id", "steps", "rgba", "hit"):
+        assert np.array_equal(a[k], b[k]), k
+    flat = scenes.config_parity_64()
+    flat.metric = scenes.Metric()          # no bumps: straight rays, closed-form miss or hit
+    flat.scene = scenes.Scene(np.array([[0.0, 0.0, 4.0, 1.0]], np.float32), np.zeros((0, 3), np.float32),
+                              np.zeros((0, 3), np.int32), np.ones((2, 3), np.float32))
+    centre = (flat.height // 2) * flat.width + flat.width // 2
+    eps = 1e-6
+    same, move = oracle.conditioning(flat, [centre], eps=eps)
+    t = oracle.trace(flat, [centre])
+    dist = np.linalg.norm(t["hit"][0] - np.array(flat.camera.pos))
+    assert same[0] and 0.5 * eps * dist <= move[0] <= 3 * eps * dist, (move[0], eps * dist)
+    # a ray that grazes the sphere's rim: a tilt of eps decides between hit and miss
+    r = oracle.trace(flat)
+    hit = (r["id"] == 0).reshape(flat.height, flat.width)
+    row = flat.height // 2
+    cols = np.nonzero(hit[row])[0]
+    rim = row * flat.width + int(cols.max())
+    same, move = oracle.conditioning(flat, [rim], eps=0.05)
+    assert not same[0] or move[0] > 1e-2
