@@ -311,7 +311,7 @@ def bench_gpu(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    flags = rg.RGEO_FLAG_DENSE if args.dense else 0
+    flags = (rg.RGEO_FLAG_DENSE if args.dense else 0) | (rg.RGEO_FLAG_BUNDLE if args.bundle else 0)
     split = args.split == "frame" and world > 1
     part = {k: out[k] for k in ("id", "hit", "steps", "rgba")}
 
@@ -337,6 +337,7 @@ def bench_gpu(args):
             cout[k].zero_()
         frame(fl, rg.outputs_struct(cout))
         rg.rgeo_sync(stream.cuda_stream)
+        counted.slots = int(cout["bump_slots"].item())
         return (int(cout["steps"].to(torch.int64).sum().item()), int(cout["bump_evals"].item()),
                 cout["id"].cpu().numpy())
 
@@ -345,6 +346,7 @@ def bench_gpu(args):
             frame()
         rg.rgeo_sync(stream.cuda_stream)
         steps_total, evals_total, ids = counted(flags)
+        slots_total = counted.slots
 
         clocks = ClockSampler(local)
         barrier(world)
@@ -484,9 +486,12 @@ def bench_gpu(args):
                      "ffma2_probe_tflops": ffma2_tflops,
                      "flops_per_launch": flops, "bump_terms_per_launch": evals_total,
                      "bump_terms_per_rhs": evals_total / max(1, 4 * steps_total),
+                     "bump_slots_per_launch": slots_total,
+                     "bump_loop_simd_efficiency": evals_total / slots_total if slots_total else None,
                      "rk4_steps_per_launch": steps_total, "kernel_ms": mean_ms,
                      "sums": ("jet through the composed local maps" if w.metric.kind == scenes.METRIC_DIFFEO_LOCAL
-                              else ("dense" if args.dense else "cull grid"))},
+                              else ("dense" if args.dense else "cull grid")),
+                     "segment_tests": "bundles of four chords" if args.bundle else "one chord per query"},
         "dense_kernel": dense,
         "clocks": clk,
         "gpu_launches": args.steps,
@@ -934,6 +939,7 @@ def main():
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dense", action="store_true", help="time the dense sums (no cull grid) as the step")
+    ap.add_argument("--bundle", action="store_true", help="segment tests four chords per scene query")
     ap.add_argument("--no-dense-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="",

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define RGEO_ABI_VERSION 4 /* 4: rgeo_trace_tiles, tuning knobs; 3: rgeo_trace_lit; 2: composed local maps */
+#define RGEO_ABI_VERSION 4 /* 4: rgeo_trace_tiles, tuning knobs, bundles, bump_slots; 3: rgeo_trace_lit; 2: local maps */
 
 typedef enum {
   RGEO_OK = 0,
@@ -66,6 +66,10 @@ typedef enum { RGEO_SHADE_LAMBERT = 0, RGEO_SHADE_PSEUDO = 1 } rgeo_shading;
 #define RGEO_FLAG_ENERGY_DIAG 1u /* write drift[p] = g(v_end, v_end) / g(v_0, v_0) - 1 (FP64) */
 #define RGEO_FLAG_NO_SAFE_SKIP 2u /* test every segment (disables the exact safe-distance skip) */
 #define RGEO_FLAG_DENSE 4u        /* sum over every bump even when the metric has a cull grid */
+#define RGEO_FLAG_BUNDLE 8u       /* test the segments that need a test in bundles of four chords per
+                                     scene query (Section 4.1: many segments per query); same results;
+                                     rgeo_trace and rgeo_trace_tiles with RK4 only, ignored with
+                                     RGEO_FLAG_ENERGY_DIAG */
 
 /* Object ids written to rgeo_outputs.id */
 #define RGEO_ID_MISS (-1)   /* the geodesic left every bump support and met nothing */
@@ -140,7 +144,7 @@ typedef struct {
  *   steps [W*H] int32: integration steps taken (closed-form flat advances not counted)
  *   rgba  [4*W*H] uint8: shaded colour, alpha 255 on a hit, all zero otherwise
  *   drift [W*H] double, may be NULL: energy drift when RGEO_FLAG_ENERGY_DIAG is set
- *   bump_evals: optional work counter (below) */
+ *   bump_evals, bump_slots: optional work counters (below) */
 typedef struct {
   int32_t *id;
   float *hit;
@@ -151,6 +155,10 @@ typedef struct {
                                      its current value) the number of bump terms summed, over
                                      all rays and RHS stages: K per stage for dense sums, the
                                      bumps of the ray's cull-grid cell otherwise */
+  unsigned long long *bump_slots; /* DEVICE, may be NULL: as bump_evals, the bump terms the
+                                     lanes evaluated (every lane of a warp evaluates the pairs
+                                     of the warp's list, pads and other lanes' bumps included);
+                                     bump_evals / bump_slots is the bump loop's SIMD efficiency */
 } rgeo_outputs;
 
 /* Library version and device capability check.  Returns RGEO_ABI_VERSION. */

@@ -29,6 +29,7 @@ RGEO_SHADE_LAMBERT, RGEO_SHADE_PSEUDO = 0, 1
 RGEO_FLAG_ENERGY_DIAG = 1
 RGEO_FLAG_NO_SAFE_SKIP = 2
 RGEO_FLAG_DENSE = 4
+RGEO_FLAG_BUNDLE = 8
 RGEO_ID_MISS, RGEO_ID_BUDGET = -1, -2
 RGEO_MAX_BUMPS = 4096
 
@@ -85,7 +86,8 @@ TUNING_FIELDS = ("rays_per_thread", "batch_params", "wait_limit", "ctas_per_sm",
 
 class rgeo_outputs(ctypes.Structure):
     _fields_ = [("id", ctypes.c_void_p), ("hit", ctypes.c_void_p), ("steps", ctypes.c_void_p),
-                ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p), ("bump_evals", ctypes.c_void_p)]
+                ("rgba", ctypes.c_void_p), ("drift", ctypes.c_void_p), ("bump_evals", ctypes.c_void_p),
+                ("bump_slots", ctypes.c_void_p)]
 
 
 class rgeo_train_cfg(ctypes.Structure):
@@ -580,6 +582,7 @@ def alloc_outputs(n_pixels: int, device="cuda", drift: bool = False, pin: bool =
                rgba=torch.empty(n_pixels, 4, dtype=torch.uint8, **kw))
     out["drift"] = torch.empty(n_pixels, dtype=torch.float64, **kw) if drift else None
     out["bump_evals"] = torch.zeros(1, dtype=torch.int64, device=device) if count and not pin else None
+    out["bump_slots"] = torch.zeros(1, dtype=torch.int64, device=device) if count and not pin else None
     return out
 
 
@@ -588,7 +591,7 @@ def outputs_struct(out) -> rgeo_outputs:
         t = out.get(k)
         return t.data_ptr() if t is not None else None
     return rgeo_outputs(out["id"].data_ptr(), out["hit"].data_ptr(), out["steps"].data_ptr(),
-                        out["rgba"].data_ptr(), ptr("drift"), ptr("bump_evals"))
+                        out["rgba"].data_ptr(), ptr("drift"), ptr("bump_evals"), ptr("bump_slots"))
 
 
 def instance(work: scenes.Workload, metric: Metric, scene: Scene, out, flags: int = 0) -> rgeo_instance:

@@ -18,7 +18,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "librgeo")
 LIB = os.path.join(HERE, "librgeo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["rgeo_api.cu", "rgeo_trace.cu", "rgeo_noalloc.cu", "rgeo_mlp.cu", "rgeo_scene_build.cpp"]
+# (source, object name, extra flags): rgeo_trace.cu is compiled in three parts
+SOURCES = [("rgeo_api.cu", "rgeo_api", []), ("rgeo_trace.cu", "rgeo_trace_p1", ["-DRGEO_TRACE_PART=1", "-diag-suppress=177"]),
+           ("rgeo_trace.cu", "rgeo_trace_p2", ["-DRGEO_TRACE_PART=2", "-diag-suppress=177"]),
+           ("rgeo_trace.cu", "rgeo_trace_p3", ["-DRGEO_TRACE_PART=3", "-diag-suppress=177"]), ("rgeo_noalloc.cu", "rgeo_noalloc", []),
+           ("rgeo_mlp.cu", "rgeo_mlp", []), ("rgeo_scene_build.cpp", "rgeo_scene_build", [])]
 
 
 def nvcc() -> str:
@@ -28,10 +32,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build librgeo")
 
 
-def _compile(src: str, extra=()) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(unit, extra=()) -> str:
+    src, name, defs = unit
+    obj = os.path.join(BUILD, name + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-           "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
+           "-I", INCLUDE, "-I", CSRC, *defs, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     if src.endswith(".cpp"):
         cmd[cmd.index("-c")] = "-x=c++"
         cmd.insert(cmd.index("-x=c++") + 1, "-c")

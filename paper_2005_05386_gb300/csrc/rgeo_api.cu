@@ -96,7 +96,7 @@ rgeo_status validate_trace(const rgeo_metric *metric, const rgeo_scene *scene, c
     return fail(RGEO_EINVAL, "rgeo_trace: unknown integrator");
   if (shading != RGEO_SHADE_LAMBERT && shading != RGEO_SHADE_PSEUDO)
     return fail(RGEO_EINVAL, "rgeo_trace: unknown shading mode");
-  if (flags & ~(RGEO_FLAG_ENERGY_DIAG | RGEO_FLAG_NO_SAFE_SKIP | RGEO_FLAG_DENSE))
+  if (flags & ~(RGEO_FLAG_ENERGY_DIAG | RGEO_FLAG_NO_SAFE_SKIP | RGEO_FLAG_DENSE | RGEO_FLAG_BUNDLE))
     return fail(RGEO_EINVAL, "rgeo_trace: unknown flag bits");
   if (!out->id || !out->hit || !out->steps || !out->rgba)
     return fail(RGEO_EINVAL, "rgeo_trace: id, hit, steps and rgba outputs are required");
@@ -175,12 +175,14 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   p.integrator = integrator;
   p.shading = shading;
   p.energy = (flags & RGEO_FLAG_ENERGY_DIAG) ? 1 : 0;
+  p.bundle = (flags & RGEO_FLAG_BUNDLE) && !p.energy && integrator == RGEO_RK4 ? 1 : 0;
   p.id = out->id;
   p.hit = out->hit;
   p.steps = out->steps;
   p.rgba = reinterpret_cast<uchar4 *>(out->rgba);
   p.drift = out->drift;
   p.bump_evals = out->bump_evals;
+  p.bump_slots = out->bump_slots;
   p.rays_per_thread = rgeo::tuning().rays_per_thread;
   return p;
 }
@@ -570,6 +572,7 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene, 
   RGEO_CUDA(cudaMallocAsync((void **)&buf, bytes, st), "rgeo_trace_host: staging");
   rgeo_outputs d;
   d.bump_evals = nullptr;
+  d.bump_slots = nullptr;
   d.drift = drift ? (double *)buf : nullptr;
   char *q = buf + (drift ? N * 8 : 0);
   d.hit = (float *)q;
@@ -678,6 +681,7 @@ rgeo_status rgeo_batch_create(int32_t n, const rgeo_instance *inst, rgeo_batch *
     table[i] = make_params(q.metric, q.scene, &q.camera, q.width, q.height, q.h, q.max_steps, q.integrator,
                            q.shading, q.flags, &q.out);
     table[i].rays_per_thread = 1;
+    table[i].bundle = 0;  // the batch kernel tests every chord alone
     total += table[i].n_items;
     max_f4 = std::max(max_f4, rgeo::table_float4s(q.metric->d.kind, q.metric->d.K, q.metric->d.aniso));
   }

@@ -134,6 +134,7 @@ struct TraceParams {
   const float4 *cull_hdr;
   int cull_G, cull_words;
   int step_lists;              // culled sums from one list per step (the step's reach <= kStepReach)
+  int bundle;                  // segment tests in bundles of several chords (one query each)
   float b[3];
   float A[9];
   int has_affine, has_quad;
@@ -169,7 +170,8 @@ struct TraceParams {
   int32_t *steps;
   uchar4 *rgba;
   double *drift;
-  unsigned long long *bump_evals;  // optional work counter
+  unsigned long long *bump_evals;  // optional work counter: bump terms of the rays' own cells
+  unsigned long long *bump_slots;  // optional work counter: bump terms the lanes evaluated
   float *hit_nrm;                  // optional [3][N]: unit normal of each hit, facing the incoming segment
   uint32_t *counter;
   // launch shape
@@ -284,7 +286,10 @@ cudaError_t launch_gather_batch(const float *X, const float *T, long long n, int
                                 long long step, float *Xb, float *Tb, cudaStream_t st);
 // Surrogate forward pass over n rows of 7 inputs into n rows of 7 outputs (stream-ordered).
 cudaError_t expmap_infer(const rgeo_expmap *x, const float *X, long long n, float *Y, cudaStream_t st);
-cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);
+cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st);  // all three parts
+cudaError_t read_and_clear_trace_error_1(unsigned *word, cudaStream_t st);
+cudaError_t read_and_clear_trace_error_2(unsigned *word, cudaStream_t st);
+cudaError_t read_and_clear_trace_error_3(unsigned *word, cudaStream_t st);
 cudaError_t run_ffma_probe(int mode, float *tflops, float *ms);
 
 }  // namespace rgeo

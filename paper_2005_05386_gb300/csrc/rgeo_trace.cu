@@ -19,11 +19,23 @@
 
 #include "rgeo_internal.h"
 
+// This file is compiled three times (RGEO_TRACE_PART = 1, 2, 3), each time emitting one group
+// of launchers and the kernels they instantiate, so that the parts compile in parallel:
+//   1  single traces (k_trace and its variants) and the metric's table and grid kernels
+//   2  batches (k_trace_batch)
+//   3  the surrogate tracer, training segments and Riemannian illumination
+#ifndef RGEO_TRACE_PART
+#error "compile rgeo_trace.cu with -DRGEO_TRACE_PART=1, 2 or 3"
+#endif
+#define RGEO_PART(n) (RGEO_TRACE_PART == (n))
+#define RGEO_PART_NAME_(base, n) base##n
+#define RGEO_PART_NAME(base, n) RGEO_PART_NAME_(base, n)
+
 namespace rgeo {
 
-__device__ unsigned int g_rgeo_error;  // sticky per-device error word
-
 namespace {
+
+__device__ unsigned int g_rgeo_error;  // sticky per-device error word of this part's kernels
 
 constexpr int MK_GRAPH_ISO = 0;
 constexpr int MK_GRAPH_ANISO = 1;
@@ -91,6 +103,26 @@ __device__ __forceinline__ void poly_terms(const TraceParams &P, F3 x, F3 v, flo
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Per-lane work counters: evals, the bump terms of the cells of the lane's own rays (the
+// counter bump_evals); slots, the bump terms the lane evaluated, every pair of its warp's
+// lists included (bump_slots).  flush adds the warp's sums to the requested counters.
+struct WorkCount {
+  unsigned long long evals = 0ull, slots = 0ull;
+  __device__ __forceinline__ void flush(const TraceParams &P) {
+    if (P.bump_evals) {
+      unsigned long long e = evals;
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+      if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, e);
+    }
+    if (P.bump_slots) {
+      unsigned long long e = slots;
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+      if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_slots, e);
+    }
+    evals = slots = 0ull;
+  }
+};
 
 // Position and velocity of one ray, and its paired accumulators: the .x halves sum the
 // even-numbered bumps, the .y halves the odd-numbered ones, each in increasing order.
@@ -300,7 +332,7 @@ __device__ __forceinline__ F3 accel_step_list(const TraceParams &P, const WarpLi
 template <bool INSIDE>
 __device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const float4 *__restrict__ sb,
                                                      int2 *lst, float4 ghdr, bool part, F3 x, F3 v,
-                                                     bool &inside, unsigned long long &evals) {
+                                                     bool &inside, WorkCount &wc) {
   PairAcc a;
   pair_acc_init(a, x, v);
   const int words = P.cull_words;
@@ -314,9 +346,10 @@ __device__ __forceinline__ F3 accel_graph_iso_culled(const TraceParams &P, const
   for (int wi = 0; wi < words; ++wi) {
     const unsigned m = mnext;
     if (wi + 1 < words) mnext = cell >= 0 ? __ldg(cm + wi + 1) : 0u;
-    evals += list_word(lst, m, wi, ne, no);  // the bumps of this lane's own cell
+    wc.evals += list_word(lst, m, wi, ne, no);  // the bumps of this lane's own cell
     if (max(ne, no) > kListPairs - 16 || wi + 1 == words) {  // full (a word adds up to 16 a column) or done
       const int np = list_pad(lst, ne, no, pad);
+      wc.slots += 2u * (unsigned)np;
       __syncwarp();
       for (int i = 0; i < np; ++i) {
         const int2 e = lst[i];
@@ -521,7 +554,7 @@ struct SumCtx {
   float4 ghdr;                // cull-grid header (culled sums)
   WarpLists *wl;              // the warp's lists in shared memory (culled sums)
   bool part;                  // this lane's ray needs the sums
-  unsigned long long *evals;  // per-lane count of bump terms summed
+  WorkCount *evals;           // per-lane work counters
 };
 
 template <int MK>
@@ -534,20 +567,24 @@ __device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, cons
                                     bool &inside) {
   if (MK == MK_GRAPH_SL) {  // the warp's step list; the dense sums where there is none
     if (cx.wl->np >= 0) {
-      if (cx.part) *cx.evals += cx.wl->own;
+      if (cx.part) cx.evals->evals += cx.wl->own;
+      cx.evals->slots += 2u * (unsigned)cx.wl->np;
       return accel_step_list<INSIDE>(P, *cx.wl, x, v, inside);
     }
-    if (cx.part) *cx.evals += (unsigned)P.K;
+    if (cx.part) cx.evals->evals += (unsigned)P.K;
+    cx.evals->slots += (unsigned)iso_pad_index(P.K);
     return accel_graph_iso<INSIDE>(P, sb, P.K, x, v, inside);
   }
   if (MK == MK_GRAPH_ISO) {
     if (P.cull_masks)
       return accel_graph_iso_culled<INSIDE>(P, sb, cx.wl->idx, cx.ghdr, cx.part, x, v, inside, *cx.evals);
-    if (cx.part) *cx.evals += (unsigned)P.K;
+    if (cx.part) cx.evals->evals += (unsigned)P.K;
+    cx.evals->slots += (unsigned)iso_pad_index(P.K);
     return accel_graph_iso<INSIDE>(P, sb, P.K, x, v, inside);
   }
   if (MK == MK_GRAPH_ANISO) {
-    *cx.evals += (unsigned)P.K;
+    cx.evals->evals += (unsigned)P.K;
+    cx.evals->slots += (unsigned)P.K;
     return accel_graph_aniso<INSIDE>(P, sb, P.K, x, v, inside);
   }
   if (MK == MK_LOCAL) return accel_local(sb, P.K, x, v);
@@ -758,6 +795,97 @@ __device__ bool scene_hit(const TraceParams &P, const float4 *ss, F3 O, F3 D, fl
   return hr.id >= 0;
 }
 
+// Earliest hit of the polygon's chords [p_j, p_j+1], j = 0 .. n - 1 (n <= NB), in one
+// query (Section 4.1: many segments per intersection query): the BVH is walked once with
+// the bounding box of all the chords, and every primitive of a leaf it reaches is tested
+// against each chord up to the best hit so far.  Each chord-primitive test is the one
+// scene_hit makes, so the result -- the first chord with a hit, its earliest s and then
+// lowest id -- is the one the chords tested one by one give.  pts[i * stride] holds p_i.
+template <int NB>
+__device__ bool scene_hit_bundle(const TraceParams &P, const float4 *ss, const float4 *pts, int stride, int n,
+                                 HitRec &hr, int &jbest) {
+  F3 p[NB + 1];
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) {
+    const float4 q = pts[(i <= n ? i : n) * stride];
+    p[i] = f3(q.x, q.y, q.z);
+  }
+  F3 lo = p[0], hi = p[0];
+#pragma unroll
+  for (int i = 1; i <= NB; ++i) {
+    lo = f3(fminf(lo.x, p[i].x), fminf(lo.y, p[i].y), fminf(lo.z, p[i].z));
+    hi = f3(fmaxf(hi.x, p[i].x), fmaxf(hi.y, p[i].y), fmaxf(hi.z, p[i].z));
+  }
+  hr.id = -1;
+  hr.tq = -1;
+  hr.s = 1.f;
+  jbest = NB;
+  // chord j against one primitive (sphere: sp; triangle: a4, b4, c4 at BVH slot q)
+  auto consider = [&](int j, int id, int q, float s) {
+    if (j < jbest || (j == jbest && (s < hr.s || (s == hr.s && id < hr.id)))) {
+      jbest = j;
+      hr.s = s;
+      hr.id = id;
+      hr.tq = q;
+    }
+  };
+  if (P.nodes == nullptr) {
+    for (int k = 0; k < P.S; ++k) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (j >= n || j > jbest) break;
+        const F3 D = p[j + 1] - p[j];
+        float s;
+        if (hit_sphere(p[j], D, dot(D, D), ss[k], s) && s < 1.f) consider(j, k, -1, s);
+      }
+    }
+    return hr.id >= 0;
+  }
+  int stack[kTraversalStack];
+  int sp = 0;
+  int node = 0;
+  for (;;) {
+    const float4 n0 = __ldg(&P.nodes[2 * node]);
+    const float4 n1 = __ldg(&P.nodes[2 * node + 1]);
+    if (n0.x <= hi.x && n0.y <= hi.y && n0.z <= hi.z && lo.x <= n1.x && lo.y <= n1.y && lo.z <= n1.z) {
+      const int first = __float_as_int(n0.w);
+      const int cnt = __float_as_int(n1.w);
+      if (cnt > 0) {
+        for (int q = first; q < first + cnt; ++q) {
+          const float4 a4 = __ldg(&P.prims[3 * q]);
+          const float4 b4 = __ldg(&P.prims[3 * q + 1]);
+          const int id = __float_as_int(a4.w);
+          const float4 c4 = id < P.S ? a4 : __ldg(&P.prims[3 * q + 2]);
+#pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            if (j >= n || j > jbest) break;
+            const F3 D = p[j + 1] - p[j];
+            if (id < P.S) {
+              float s;
+              if (hit_sphere(p[j], D, dot(D, D), make_float4(a4.x, a4.y, a4.z, b4.x), s) && s < 1.f)
+                consider(j, id, -1, s);
+            } else {
+              const float s = hit_triangle(make_frame(D), p[j], 1.f, a4, b4, c4);
+              if (s >= 0.f) consider(j, id, q, s);
+            }
+          }
+        }
+      } else {
+        if (sp >= kTraversalStack) {
+          atomicOr(&g_rgeo_error, kErrStackOverflow);
+          break;
+        }
+        stack[sp++] = first + 1;
+        node = first;
+        continue;
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  return hr.id >= 0;
+}
+
 // Lower bound of the distance from x to the scene.
 __device__ __forceinline__ float safe_distance(const TraceParams &P, F3 x) {
   const float fx = (x.x - P.gmin[0]) * P.ginv, fy = (x.y - P.gmin[1]) * P.ginv,
@@ -869,6 +997,7 @@ struct Ray {
   float dleft;
   float e0m1;
   float arc;  // arc length travelled: h per step, the parameter length of straight advances
+  int nb;     // chords of the open bundle (segment tests deferred to one query), 0: none
 };
 
 __device__ __forceinline__ F3 xhi(const Ray &r) { return f3(r.xh[0], r.xh[1], r.xh[2]); }
@@ -886,6 +1015,7 @@ __device__ __forceinline__ void ray_clear(Ray &r) {
   r.steps = 0;
   r.pix = 0;
   r.dleft = r.e0m1 = r.arc = 0.f;
+  r.nb = 0;
 }
 
 template <int MK>
@@ -930,6 +1060,7 @@ __device__ void init_ray(const TraceParams &P, const float4 *sb, int pix, Ray &r
   r.dleft = 0.f;
   r.e0m1 = 0.f;
   r.arc = 0.f;
+  r.nb = 0;
   if (P.energy) r.e0m1 = (float)(energy<MK>(P, sb, x, v) - 1.0);
 }
 
@@ -1028,19 +1159,46 @@ __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *
   }
 }
 
+// Tests the open bundle of r (its chords' end points and arc lengths in the thread's slots
+// bs[i * blockDim.x], i = 0 .. r.nb) in one query; on a hit the ray finishes as the chord
+// that hit would have finished it tested alone (its step count, hit point and arc length).
+// Returns true on a hit.  The bundle is closed either way.
+template <int MK, int NB>
+__device__ __noinline__ bool bundle_flush(const TraceParams &P, const float4 *sb, const float4 *ss, Ray &r,
+                                          const float4 *bs) {
+  HitRec hr;
+  int j;
+  const int stride = (int)blockDim.x;
+  const bool hit = scene_hit_bundle<NB>(P, ss, bs, stride, r.nb, hr, j);
+  if (hit) {
+    const float4 a = bs[j * stride], b = bs[(j + 1) * stride];
+    const F3 A = f3(a.x, a.y, a.z), D = f3(b.x - a.x, b.y - a.y, b.z - a.z);
+    r.steps -= r.nb - 1 - j;
+    finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, A), D, fmaf(hr.s - 1.f, P.h, b.w));
+  }
+  r.nb = 0;
+  r.dleft = 0.f;
+  return hit;
+}
+
 // Before a step: closed-form advance through flat space when x lies outside every
-// truncated support (exact: Hess f = 0 there, Eq. 5.4), then the step budget.
-// a1 is the stage-1 acceleration at x; it is recomputed if x moves.  Returns false
-// when the ray finished (its pixel is written) or the lane holds no ray (cx.part false;
-// such lanes call only when CONV, to join the warp's sums; with CONV every lane of the
-// warp calls together).
-template <int MK, bool CONV = Converged<MK>::value>
+// truncated support (exact: Hess f = 0 there, Eq. 5.4), then the step budget.  An open
+// bundle of chords (NB > 1) is tested first, since the flat advance and the budget end
+// come after its chords.  a1 is the stage-1 acceleration at x; it is recomputed if x
+// moves.  Returns false when the ray finished (its pixel is written) or the lane holds no
+// ray (cx.part false; such lanes call only when CONV, to join the warp's sums; with CONV
+// every lane of the warp calls together).
+template <int MK, bool CONV = Converged<MK>::value, int NB = 1>
 __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb, const float4 *ss,
-                                         const SumCtx &cx, Ray &r, F3 &a1, bool inside) {
+                                         const SumCtx &cx, Ray &r, F3 &a1, bool inside,
+                                         const float4 *bs = nullptr) {
   F3 x = xhi(r);
   const F3 v = vhi(r);
   bool moved = false, finished = false;
-  if (cx.part && MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
+  const bool flat = MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside;
+  if (NB > 1 && cx.part && r.nb > 0 && (flat || r.steps >= P.max_steps))
+    finished = bundle_flush<MK, NB>(P, sb, ss, r, bs);
+  if (cx.part && !finished && flat) {
     const float t = support_entry<MK>(sb, P.K, x, v);
     HitRec hr;
     if (scene_hit(P, ss, x, v, t, hr)) {
@@ -1081,10 +1239,13 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
 
 // After a step: compensated update of (x, v), then the new polygon segment
 // [x_i, x_{i+1}] against the scene (Section 4.1), skipped exactly while the polygon
-// cannot have left a ball that holds no scene point.  Returns false on a hit.
-template <int MK>
+// cannot have left a ball that holds no scene point.  With NB > 1 a segment that needs a
+// test opens a bundle instead; the next NB - 1 chords join it, and the bundle is tested
+// in one query (Section 4.1, many segments per query) once it holds NB chords (or before
+// a flat advance or the budget end, in pre_step).  Returns false on a hit.
+template <int MK, int NB = 1>
 __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb, const float4 *ss,
-                                          Ray &r, F3 dx, F3 dvel) {
+                                          Ray &r, F3 dx, F3 dvel, float4 *bs = nullptr) {
   const F3 x = xhi(r);
   for (int c = 0; c < 3; c++) {
     comp_add(r.xh[c], r.xl[c], comp(dx, c));
@@ -1092,7 +1253,14 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
   }
   r.steps++;
   r.arc += P.h;
-  const F3 D = xhi(r) - x;
+  const F3 xn = xhi(r);
+  const F3 D = xn - x;
+  const int stride = (int)blockDim.x;
+  if (NB > 1 && r.nb > 0) {  // an open bundle: this chord joins it
+    bs[(r.nb + 1) * stride] = make_float4(xn.x, xn.y, xn.z, r.arc);
+    if (++r.nb == NB) return !bundle_flush<MK, NB>(P, sb, ss, r, bs);
+    return true;
+  }
   if (P.safe_skip) {
     const float L = sqrtf(dot(D, D)) * (1.f + 1e-6f);
     if (L < r.dleft) {
@@ -1105,6 +1273,12 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
       return true;
     }
     r.dleft = 0.f;
+  }
+  if (NB > 1) {  // open a bundle with this chord
+    bs[0] = make_float4(x.x, x.y, x.z, 0.f);
+    bs[stride] = make_float4(xn.x, xn.y, xn.z, r.arc);
+    r.nb = 1;
+    return true;
   }
   HitRec hr;
   if (scene_hit(P, ss, x, D, 1.f, hr)) {
@@ -1147,21 +1321,35 @@ __device__ __forceinline__ WarpLists warp_lists(bool step, float4 *lists) {
   return WarpLists{reinterpret_cast<int2 *>(base), step ? base + kListFloat4 : nullptr, -1, 0u};
 }
 
+// Warps of the 128-thread trace blocks.
+constexpr int kWarpsPerBlock = 4;
+// Chords per bundle when segment tests are bundled (RGEO_FLAG_BUNDLE).
+constexpr int kBundle = 4;
+
+// float4s of a trace block's warp lists: index lists for the culled sums, packed pairs too
+// for step lists.
+__host__ __device__ inline int trace_lists_float4(int mk, const TraceParams &P) {
+  return (mk == MK_GRAPH_SL || P.cull_masks) ? kWarpsPerBlock * lists_float4(mk == MK_GRAPH_SL) : 0;
+}
+
 // One ray per thread (every metric kind).  MINB 128-thread CTAs per SM at least: six (80
 // registers) for the graph and twist metrics by default, five (102 registers) for the
 // local-map jet and, on request (rgeo_tuning.ctas_per_sm <= 5), for the isotropic graph metric.  For the
 // isotropic graph metric every lane runs every evaluation of the bump sums (a lane without
 // a ray joins with empty masks), so that the warp can build its pair list together.
-template <int MK, int INTEG, int MINB>
+template <int MK, int INTEG, int MINB, int NB>
 __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
-  WarpLists wl = warp_lists(MK == MK_GRAPH_SL, smem + nb4 + (P.nodes ? 0 : P.S));
+  float4 *const lists = smem + nb4 + (P.nodes ? 0 : P.S);
+  WarpLists wl = warp_lists(MK == MK_GRAPH_SL, lists);
+  // the threads' bundle slots (NB > 1), after the warps' lists: slot i of thread t at i * 128 + t
+  float4 *const bs = lists + trace_lists_float4(MK, P) + threadIdx.x;
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
   constexpr bool conv = Converged<MK>::value;
-  unsigned long long evals = 0;
+  WorkCount evals;
   bool active = false, drained = false;
   Ray r;
   ray_clear(r);
@@ -1180,17 +1368,15 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
     }
     bool inside = true;
     F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
-    const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside);
+    const bool go =
+        pre_step<MK, Converged<MK>::value, NB>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside, bs);
     if (!go) active = false;
     if (conv ? !__any_sync(0xffffffffu, go) : !go) continue;
     F3 dx, dvel;
     step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
-    if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
+    if (go) active = post_step<MK, NB>(P, sb, ss, r, dx, dvel, bs);
   }
-  if (P.bump_evals) {
-    for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
-    if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
-  }
+  evals.flush(P);
 }
 
 // ------------------------------------------------------ Riemannian illumination
@@ -1202,7 +1388,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
 // metric kinds, and metrics without a cull grid, take the dense sums.
 template <int MK, bool INSIDE>
 __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside,
-                                         unsigned long long &evals) {
+                                         WorkCount &evals) {
   if (MK != MK_GRAPH_ISO || !P.cull_masks) {
     WarpLists nolists{nullptr, nullptr, -1, 0u};
     const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), &nolists, true, &evals};
@@ -1219,13 +1405,13 @@ __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb,
     const uint32_t *cm = P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
     // two cursors walk the cell's even-numbered and odd-numbered bumps in increasing order
     const unsigned w0 = __ldg(cm);
-    evals += (unsigned)__popc(w0);
+    evals.evals += (unsigned)__popc(w0);
     unsigned me = w0 & 0x55555555u, mo = w0 & 0xaaaaaaaau;
     int we = 0, wo = 0;
     for (;;) {
       while (!me && we + 1 < P.cull_words) {  // every word passes the even cursor once
         const unsigned t = __ldg(cm + ++we);
-        evals += (unsigned)__popc(t);
+        evals.evals += (unsigned)__popc(t);
         me = t & 0x55555555u;
       }
       while (!mo && wo + 1 < P.cull_words) mo = __ldg(cm + ++wo) & 0xaaaaaaaau;
@@ -1240,6 +1426,7 @@ __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb,
         mo &= mo - 1u;
       }
       pair_eval<INSIDE>(a, sb, ie, io);
+      evals.slots += 2u;
     }
   }
   if (INSIDE) inside = a.in;
@@ -1249,7 +1436,7 @@ __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb,
 // One RK4 (or Euler) step's increments with per-lane sums (the light geodesics).
 template <int MK, int INTEG>
 __device__ __forceinline__ void step_increments_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, F3 a1,
-                                                     F3 &dx, F3 &dvel, unsigned long long &evals) {
+                                                     F3 &dx, F3 &dvel, WorkCount &evals) {
   const float h = P.h;
   if (INTEG == 0) {
     bool dummy;
@@ -1330,7 +1517,7 @@ __device__ float metric_inv_nn(const TraceParams &P, const float4 *sb, F3 x, F3 
 // blocked.  u: the initial g-unit tangent.
 template <int MK, int INTEG, bool SHADOW>
 __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, F3 L, F3 q, F3 d, F3 &e, F3 &u,
-                      bool &blocked, unsigned long long &evals) {
+                      bool &blocked, WorkCount &evals) {
   u = rsqrtf(metric_dd<MK>(P, sb, q, d)) * d;
   float xh[3] = {q.x, q.y, q.z}, xl[3] = {0.f, 0.f, 0.f}, vh[3] = {u.x, u.y, u.z}, vl[3] = {0.f, 0.f, 0.f};
   blocked = false;
@@ -1393,6 +1580,7 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
   }
 }
 
+#if RGEO_PART(3)
 // Riemannian illumination of every hit of a finished trace (Section 4): the geodesic from
 // q = hit + 1e-3 n to the light is found by shooting (Gauss-Newton on the initial
 // direction d0 + alpha e1 + beta e2, forward-difference Jacobian), and the hit is lit
@@ -1429,7 +1617,7 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
   float al = 0.f, be = 0.f;
   bool lit = false, blocked;
   F3 u = d0;
-  unsigned long long evals = 0;  // bump terms summed (work counter)
+  WorkCount evals;  // work counters
   for (int k = 0;; k++) {
     const F3 d = normalize(axpy(be, b2, axpy(al, b1, d0)));
     F3 e;
@@ -1477,9 +1665,13 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
   P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
                           to_u8(P.albedo[3 * obj + 2] * inten), 255);
   if (LP.lit) LP.lit[p] = lit ? 1 : 0;
-  if (P.bump_evals) atomicAdd(P.bump_evals, evals);
+  if (P.bump_evals) atomicAdd(P.bump_evals, evals.evals);
+  if (P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
 }
 
+#endif
+
+#if RGEO_PART(1)
 // Eq. 5.4 for two rays against the same isotropic bumps (dense sums): each pair of
 // bumps loaded from shared memory serves both rays, halving shared-memory traffic per ray.
 template <bool INSIDE>
@@ -1513,7 +1705,7 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
   bool act0 = false, act1 = false, drained = false;
-  unsigned long long evals = 0;
+  WorkCount evals;
   Ray r0, r1;
   for (int c = 0; c < 3; c++) {
     r0.xh[c] = r0.vh[c] = r1.xh[c] = r1.vh[c] = 0.f;
@@ -1534,7 +1726,8 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     accel_graph_iso_x2<true>(P, sb, P.K, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);  // this kernel sums densely (no cull grid)
     WarpLists nolists{nullptr, nullptr, -1, 0u};
-    evals += 2ull * (unsigned)P.K;
+    evals.evals += 2ull * (unsigned)P.K;
+    evals.slots += 2ull * (unsigned)iso_pad_index(P.K);
     if (act0) act0 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r0, a10, in0);
     if (act1) act1 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r1, a11, in1);
     if (!act0 && !act1) continue;
@@ -1555,7 +1748,8 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
       F3 a40, a41;
       accel_graph_iso_x2<false>(P, sb, P.K, axpy(h, v30, x0), v40, axpy(h, v31, x1), v41, a40, a41, dummy0,
                                 dummy1);
-      evals += 6ull * (unsigned)P.K;
+      evals.evals += 6ull * (unsigned)P.K;
+      evals.slots += 6ull * (unsigned)iso_pad_index(P.K);
       const float h6 = h * (1.f / 6.f);
       dx0 = h6 * (v0 + 2.f * (v20 + v30) + v40);
       dv0 = h6 * (a10 + 2.f * (a20 + a30) + a40);
@@ -1570,11 +1764,10 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     if (act0) act0 = post_step<MK_GRAPH_ISO>(P, sb, ss, r0, dx0, dv0);
     if (act1) act1 = post_step<MK_GRAPH_ISO>(P, sb, ss, r1, dx1, dv1);
   }
-  if (P.bump_evals) {
-    for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
-    if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
-  }
+  evals.flush(P);
 }
+
+#endif
 
 // Many instances (frames, views or metrics of uneven size) in one persistent launch.
 // Each warp serves one instance at a time: its lanes refill from that instance's
@@ -1653,7 +1846,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
   constexpr bool conv = Converged<MK>::value;
   int i = 0;
   int visited = 0;
-  unsigned long long evals = 0;
+  WorkCount evals;
   bool active = false, drained = false;
   Ray r;
   ray_clear(r);
@@ -1669,11 +1862,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
       if (drained) {
-        if (P.bump_evals) {
-          for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
-          if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
-        }
-        evals = 0;
+        evals.flush(P);
         if (++visited >= n) break;
         i = (i + 1) % n;
         drained = false;
@@ -1751,6 +1940,7 @@ __device__ __forceinline__ void wave_load(const WaveArgs &W, int pix, Ray &r, in
   r.arc = W.st[14 * N + p];
   r.steps = W.steps[p];
   r.pix = pix;
+  r.nb = 0;
   cool = W.cool[p];
 }
 
@@ -1856,7 +2046,7 @@ __global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const W
   WarpLists wl = warp_lists(MK == MK_GRAPH_SL, smem + nb4 + (P.nodes ? 0 : P.S));
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
   constexpr bool conv = Converged<MK>::value;
-  unsigned long long evals = 0;
+  WorkCount evals;
   bool active = false, drained = false;
   Ray r;
   ray_clear(r);
@@ -1890,12 +2080,10 @@ __global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const W
     step_increments<MK, 0>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
     if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
   }
-  if (P.bump_evals) {
-    for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
-    if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, evals);
-  }
+  evals.flush(P);
 }
 
+#if RGEO_PART(3)
 // The network's jump for queue slot i: x_s = x + s v + s^2 r_x, v_s = v + s r_v
 // (scaled residuals of Eq. 3.5's exp map), taken when the predicted log squared
 // error (output 6) is at most log tau^2; otherwise the ray integrates the segment.
@@ -1944,6 +2132,9 @@ __global__ void k_wave_apply(const WaveArgs W, unsigned n, float h) {
   }
 }
 
+#endif
+
+#if RGEO_PART(1)
 // Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
 // table; t is read from and advanced in device memory so that a captured graph
 // animates without host input.  motion = [K*3 c0 | K*3 A | K f | K phi].
@@ -1975,6 +2166,9 @@ __global__ void k_advance_motion(const float *motion, int K, int aniso, float *r
   }
 }
 
+#endif
+
+#if RGEO_PART(3)
 // Counter-based uniform in [0, 1): SplitMix64 (Steele, Lea, Flood 2014) output for the
 // state seed + (i + 1) golden, top 24 bits.
 __device__ __forceinline__ float u01(unsigned long long seed, unsigned long long i) {
@@ -2058,6 +2252,9 @@ __global__ void k_segments(const TraceParams P, long long n, unsigned long long 
   }
 }
 
+#endif
+
+#if RGEO_PART(1)
 __global__ void k_tick(float *t, float dt) { *t += dt; }
 __global__ void k_set_time(float *t, float value) { *t = value; }
 
@@ -2217,20 +2414,21 @@ __global__ void k_ffma(float *out, int iters, int mode) {
   if (s == 12345.f) out[threadIdx.x] = s;  // keeps the loop alive
 }
 
-// Warps of 128-thread blocks: 4 pair lists per block for the culled sums.
-constexpr int kWarpsPerBlock = 4;
+#endif
 
+#if RGEO_PART(1)
 template <int MK, int INTEG>
 cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
-  const size_t smem =
-      (size_t)(table_float4s(p.kind, p.K, MK == MK_GRAPH_ANISO) + (p.nodes ? 0 : p.S) +
-               (MK == MK_GRAPH_SL || p.cull_masks ? kWarpsPerBlock * lists_float4(MK == MK_GRAPH_SL) : 0)) *
-      sizeof(float4);
-  if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
-  const bool x2 = is_iso(MK) && p.rays_per_thread == 2 && p.cull_masks == nullptr;
   const int cap = tuning().ctas_per_sm;
-  void (*kern)(const TraceParams) =
-      MK == MK_LOCAL || (is_iso(MK) && cap > 0 && cap <= 5) ? k_trace<MK, INTEG, 5> : k_trace<MK, INTEG, 6>;
+  const bool five = MK == MK_LOCAL || (is_iso(MK) && cap > 0 && cap <= 5);
+  const bool bundle = INTEG == 0 && p.bundle;
+  const size_t smem = (size_t)(table_float4s(p.kind, p.K, MK == MK_GRAPH_ANISO) + (p.nodes ? 0 : p.S) +
+                               trace_lists_float4(MK, p) + (bundle ? (kBundle + 1) * 128 : 0)) *
+                      sizeof(float4);
+  if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
+  const bool x2 = is_iso(MK) && p.rays_per_thread == 2 && p.cull_masks == nullptr && !bundle;
+  void (*kern)(const TraceParams) = bundle ? (five ? k_trace<MK, 0, 5, kBundle> : k_trace<MK, 0, 6, kBundle>)
+                                           : (five ? k_trace<MK, INTEG, 5, 1> : k_trace<MK, INTEG, 6, 1>);
   if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -2240,7 +2438,7 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (tuning().ctas_per_sm > 0 && tuning().ctas_per_sm < per_sm) per_sm = tuning().ctas_per_sm;
+  if (cap > 0 && cap < per_sm) per_sm = cap;
   long long blocks = (long long)sms * per_sm;
   const long long rays_per_block = x2 ? 256 : 128;
   const long long need = ((long long)p.n_items + rays_per_block - 1) / rays_per_block;
@@ -2249,6 +2447,9 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+#endif
+
+#if RGEO_PART(2)
 template <int MK, int INTEG>
 cudaError_t launch_batch_t(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int table_f4,
                            long long total_items, cudaStream_t st) {
@@ -2284,8 +2485,11 @@ cudaError_t launch_batch_t(const TraceParams *dev_inst, const TraceParams *host_
   return cudaGetLastError();
 }
 
+#endif
+
 }  // namespace
 
+#if RGEO_PART(2)
 cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int kind, int aniso,
                          int integrator, int max_table_f4, long long total_items, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -2311,6 +2515,9 @@ cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_in
                          : launch_batch_t<MK_TWIST, 1>(dev_inst, host_inst, n, table_f4, total_items, st);
 }
 
+#endif
+
+#if RGEO_PART(1)
 cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
                                   float dt, cudaStream_t st) {
   if (K > 0) {
@@ -2322,6 +2529,9 @@ cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *
   return cudaGetLastError();
 }
 
+#endif
+
+#if RGEO_PART(3)
 cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long long seed, float box, float s_max,
                             float accel_bound, float *X, float *T, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -2365,6 +2575,9 @@ cudaError_t launch_wave_apply(const WaveArgs &w, unsigned n, float h, cudaStream
   return cudaGetLastError();
 }
 
+#endif
+
+#if RGEO_PART(1)
 cudaError_t launch_set_time(float *t, float value, cudaStream_t st) {
   k_set_time<<<1, 1, 0, st>>>(t, value);
   return cudaGetLastError();
@@ -2379,6 +2592,9 @@ cudaError_t launch_trace(const TraceParams &p, cudaStream_t st) {
   return p.integrator == 0 ? launch_one<MK_TWIST, 0>(p, st) : launch_one<MK_TWIST, 1>(p, st);
 }
 
+#endif
+
+#if RGEO_PART(3)
 template <int MK, int INTEG>
 cudaError_t launch_illuminate_t(const TraceParams &p, const LightParams &l, cudaStream_t st) {
   const size_t smem =
@@ -2407,6 +2623,9 @@ cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaS
   return rk4 ? launch_illuminate_t<MK_GRAPH_ISO, 0>(p, l, st) : launch_illuminate_t<MK_GRAPH_ISO, 1>(p, l, st);
 }
 
+#endif
+
+#if RGEO_PART(1)
 cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
                               cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
@@ -2431,7 +2650,10 @@ cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, 
   return cudaGetLastError();
 }
 
-cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st) {
+#endif
+
+// This part's error word, read and cleared.
+cudaError_t RGEO_PART_NAME(read_and_clear_trace_error_, RGEO_TRACE_PART)(unsigned *word, cudaStream_t st) {
   cudaError_t e = cudaMemcpyFromSymbolAsync(word, g_rgeo_error, sizeof(unsigned), 0,
                                             cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
@@ -2440,6 +2662,16 @@ cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st) {
   e = cudaMemcpyToSymbolAsync(g_rgeo_error, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
+}
+
+#if RGEO_PART(1)
+cudaError_t read_and_clear_device_error(unsigned *word, cudaStream_t st) {
+  unsigned w[3] = {0u, 0u, 0u};
+  cudaError_t e = read_and_clear_trace_error_1(&w[0], st);
+  if (e == cudaSuccess) e = read_and_clear_trace_error_2(&w[1], st);
+  if (e == cudaSuccess) e = read_and_clear_trace_error_3(&w[2], st);
+  *word = w[0] | w[1] | w[2];
+  return e;
 }
 
 cudaError_t run_ffma_probe(int mode, float *tflops, float *ms) {
@@ -2469,5 +2701,7 @@ cudaError_t run_ffma_probe(int mode, float *tflops, float *ms) {
   *tflops = (float)(flops / (t * 1e-3) / 1e12);
   return cudaGetLastError();
 }
+
+#endif  // RGEO_PART(1)
 
 }  // namespace rgeo

@@ -431,3 +431,19 @@ def test_frame_parts_and_tuning_reproduce_the_frame_bit_for_bit(rg):
         finally:
             rg.rgeo_set_tuning()
         same(g)
+
+
+@pytest.mark.parametrize("config", ["1080p_64", "twist", "quad_lattice", "local8"])
+def test_bundled_segment_tests_are_exact(rg, config):
+    """Segments tested four chords per scene query (RGEO_FLAG_BUNDLE, Section 4.1's many
+    segments per query) give the frame of one query per segment bit for bit: the first chord
+    with a hit, its hit point, step count, arc length and colour."""
+    w = {"1080p_64": lambda: scenes.config_1080p_64(width=320, height=180),
+         "twist": lambda: scenes.scaled(scenes.config_1080p_twist(), 320, 180),
+         "quad_lattice": lambda: scenes.scaled(scenes.config_quad_lattice(), 320, 180),
+         "local8": lambda: scenes.scaled(scenes.config_local_lattice(K=8), 240, 135)}[config]()
+    a = _run(rg, w)
+    b = _run(rg, w, rg.RGEO_FLAG_BUNDLE)
+    for k in ("id", "steps", "rgba", "hit"):
+        assert np.array_equal(a[k], b[k]), k
+    assert (a["id"] >= 0).sum() > 100

@@ -65,11 +65,11 @@ def test_autotuner_candidates_follow_the_metric():
 def test_autotuner_proxy_and_signature():
     w = scenes.config_1080p_64()
     p = autotune.proxy(w)
-    assert 0.9 * 2 ** 18 <= p.width * p.height <= 2 ** 18
+    assert 0.9 * 2 ** 20 <= p.width * p.height <= 2 ** 20
     assert abs(p.width / p.height - 16 / 9) < 0.02
     assert p.metric is w.metric and p.h == w.h and p.max_steps == w.max_steps
     small = scenes.config_parity_64()
-    assert autotune.proxy(small) is small
+    assert autotune.proxy(small) is small and autotune.proxy(scenes.config_1080p_64(width=960, height=540)).width == 960
     s = autotune.signature(w)
     assert s == autotune.signature(scenes.scaled(w, 1900, 1080))  # same power-of-two size bucket
     assert s != autotune.signature(scenes.scaled(w, 960, 540))
