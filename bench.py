@@ -302,6 +302,8 @@ def bench_gpu(args):
     import paper_2005_05386_gb300 as rg
     torch.cuda.set_device(local)
     w = workload(args.workload, args.resolution)
+    if args.cull_grid is not None:
+        w.metric.cull_grid = args.cull_grid
     K = w.metric.n_bumps
     N = w.n_pixels
     metric, scene = rg.Metric(w.metric), rg.Scene(w.scene)
@@ -474,6 +476,7 @@ def bench_gpu(args):
                    "spheres": w.scene.n_spheres, "triangles": w.scene.n_tris, "h": w.h,
                    "max_steps": w.max_steps, "integrator": "rk4", "camera": "(0,0,-6) +z, 60 deg",
                    "l2": "flushed between timed frames (256 MiB write)",
+                   "cull_grid": w.metric.cull_grid,
                    "per_rank": ("interleaved tiles r, r + N, ... of one shared frame, summed onto rank 0"
                                 if split else "one full frame per rank per step"),
                    "tuning": rg.rgeo_get_tuning()},
@@ -940,6 +943,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dense", action="store_true", help="time the dense sums (no cull grid) as the step")
     ap.add_argument("--bundle", action="store_true", help="segment tests four chords per scene query")
+    ap.add_argument("--cull-grid", type=int, default=None, help="G of the metric's cull grid (0 automatic, -1 none)")
     ap.add_argument("--no-dense-reference", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="",

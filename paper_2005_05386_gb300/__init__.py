@@ -18,7 +18,8 @@ import os
 from . import scenes
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librgeo.so")
+# the in-tree build; RGEO_LIBRARY names another build of the same sources to load instead
+LIB_PATH = os.environ.get("RGEO_LIBRARY") or os.path.join(_HERE, "librgeo.so")
 
 RGEO_OK, RGEO_EINVAL, RGEO_ENOMEM, RGEO_ECUDA, RGEO_ETIMEOUT, RGEO_EUNSUPPORTED, RGEO_EDEVICE = range(7)
 RGEO_METRIC_GRAPH_BUMPS, RGEO_METRIC_DIFFEO_TWIST, RGEO_METRIC_DIFFEO_LOCAL = 0, 1, 2

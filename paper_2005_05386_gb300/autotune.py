@@ -9,8 +9,8 @@ warp, so every candidate gives the same image bit for bit.
 
   cull_grid        G of the bump-support cull grid (-1: dense sums over all bumps)
   rays_per_thread  1, or 2 (two rays share each bump pair; dense sums only)
-  ctas_per_sm      persistent CTAs per SM (0: as many as fit; 5 or fewer take the
-                   96-register build of the kernel)
+  ctas_per_sm      persistent CTAs per SM (0: as many as fit, seven for the isotropic
+                   graph metric; 5 or fewer take the 96-register build of the kernel)
   tile_shape       the refill tile a warp takes from the queue: 1 (8 x 4) or 2 (4 x 8)
                    pixels (16 x 2 was measured slower at 1080p and is left out)
   sum_lists        culled bump sums from one list per RK4 step (0) or per right-hand
@@ -33,7 +33,7 @@ import os
 from . import scenes
 
 CANDIDATE_GRIDS = (-1, 64, 96, 128)
-CANDIDATE_CTAS = (0, 5)
+CANDIDATE_CTAS = (0, 6, 5)
 CANDIDATE_TILES = (1, 2)
 CANDIDATE_LISTS = (0, 1)
 KNOBS = ("cull_grid", "rays_per_thread", "ctas_per_sm", "tile_shape", "sum_lists", "batch_order")

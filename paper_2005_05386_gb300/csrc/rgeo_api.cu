@@ -282,8 +282,8 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
   if (K < 0 || K > RGEO_MAX_BUMPS) return fail(RGEO_EINVAL, "rgeo_metric_create: n_bumps out of range");
   for (int i = 0; i < 3; i++)
     if (desc->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_metric_create: reserved fields must be zero");
-  if (desc->cull_grid != 0 && desc->cull_grid != -1 && (desc->cull_grid < 4 || desc->cull_grid > 128))
-    return fail(RGEO_EINVAL, "rgeo_metric_create: cull_grid must be 0, -1 or in [4, 128]");
+  if (desc->cull_grid != 0 && desc->cull_grid != -1 && (desc->cull_grid < 4 || desc->cull_grid > 256))
+    return fail(RGEO_EINVAL, "rgeo_metric_create: cull_grid must be 0, -1 or in [4, 256]");
   if (desc->kind == RGEO_METRIC_DIFFEO_TWIST && K != 0)
     return fail(RGEO_EINVAL, "rgeo_metric_create: the twist metric takes no bumps");
   if (!finite_all(desc->affine_b, 3) || !finite_all(desc->quad_A, 9) || !std::isfinite(desc->cutoff_sigmas) ||

@@ -108,7 +108,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // counter bump_evals); slots, the bump terms the lane evaluated, every pair of its warp's
 // lists included (bump_slots).  flush adds the warp's sums to the requested counters.
 struct WorkCount {
-  unsigned long long evals = 0ull, slots = 0ull;
+  unsigned long long evals = 0ull;
+  unsigned slots = 0u;  // per lane: well below 2^32 at every frame size here
   __device__ __forceinline__ void flush(const TraceParams &P) {
     if (P.bump_evals) {
       unsigned long long e = evals;
@@ -116,11 +117,12 @@ struct WorkCount {
       if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_evals, e);
     }
     if (P.bump_slots) {
-      unsigned long long e = slots;
+      unsigned long long e = slots;  // summed in 64 bits
       for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
       if ((threadIdx.x & 31u) == 0) atomicAdd(P.bump_slots, e);
     }
-    evals = slots = 0ull;
+    evals = 0ull;
+    slots = 0u;
   }
 };
 
@@ -1332,9 +1334,10 @@ __host__ __device__ inline int trace_lists_float4(int mk, const TraceParams &P) 
   return (mk == MK_GRAPH_SL || P.cull_masks) ? kWarpsPerBlock * lists_float4(mk == MK_GRAPH_SL) : 0;
 }
 
-// One ray per thread (every metric kind).  MINB 128-thread CTAs per SM at least: six (80
-// registers) for the graph and twist metrics by default, five (102 registers) for the
-// local-map jet and, on request (rgeo_tuning.ctas_per_sm <= 5), for the isotropic graph metric.  For the
+// One ray per thread (every metric kind).  MINB 128-thread CTAs per SM at least: seven (72
+// registers) for the isotropic graph metric and six (80) for the twist and anisotropic bumps
+// by default, five (102 registers) for the local-map jet and, on request
+// (rgeo_tuning.ctas_per_sm <= 5), for the isotropic graph metric.  For the
 // isotropic graph metric every lane runs every evaluation of the bump sums (a lane without
 // a ray joins with empty masks), so that the warp can build its pair list together.
 template <int MK, int INTEG, int MINB, int NB>
@@ -1727,7 +1730,7 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);  // this kernel sums densely (no cull grid)
     WarpLists nolists{nullptr, nullptr, -1, 0u};
     evals.evals += 2ull * (unsigned)P.K;
-    evals.slots += 2ull * (unsigned)iso_pad_index(P.K);
+    evals.slots += 2u * (unsigned)iso_pad_index(P.K);
     if (act0) act0 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r0, a10, in0);
     if (act1) act1 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r1, a11, in1);
     if (!act0 && !act1) continue;
@@ -1749,7 +1752,7 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
       accel_graph_iso_x2<false>(P, sb, P.K, axpy(h, v30, x0), v40, axpy(h, v31, x1), v41, a40, a41, dummy0,
                                 dummy1);
       evals.evals += 6ull * (unsigned)P.K;
-      evals.slots += 6ull * (unsigned)iso_pad_index(P.K);
+      evals.slots += 6u * (unsigned)iso_pad_index(P.K);
       const float h6 = h * (1.f / 6.f);
       dx0 = h6 * (v0 + 2.f * (v20 + v30) + v40);
       dv0 = h6 * (a10 + 2.f * (a20 + a30) + a40);
@@ -1888,7 +1891,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
 }
 
 template <int MK, int INTEG, bool SMEM>
-__global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
+__global__ void __launch_bounds__(128, 6) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
   extern __shared__ float4 bsmem[];
   constexpr bool step = MK == MK_GRAPH_SL;
   uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) +
@@ -1897,7 +1900,7 @@ __global__ void __launch_bounds__(128) k_trace_batch(const TraceParams *__restri
 }
 
 template <int MK, int INTEG, bool SMEM>
-__global__ void __launch_bounds__(128) k_trace_batch_param(const __grid_constant__ BatchTable T, int n,
+__global__ void __launch_bounds__(128, 6) k_trace_batch_param(const __grid_constant__ BatchTable T, int n,
                                                            int table_f4) {
   extern __shared__ float4 bsmem[];
   constexpr bool step = MK == MK_GRAPH_SL;
@@ -2038,7 +2041,7 @@ __device__ __forceinline__ bool wave_try_queue(const TraceParams &P, const WaveA
 
 // One round of the surrogate tracer (graph metrics, RK4).
 template <int MK>
-__global__ void __launch_bounds__(128) k_wave_trace(const TraceParams P, const WaveArgs W) {
+__global__ void __launch_bounds__(128, 5) k_wave_trace(const TraceParams P, const WaveArgs W) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
@@ -2427,8 +2430,12 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
                       sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;  // bump table + spheres must fit on chip
   const bool x2 = is_iso(MK) && p.rays_per_thread == 2 && p.cull_masks == nullptr && !bundle;
-  void (*kern)(const TraceParams) = bundle ? (five ? k_trace<MK, 0, 5, kBundle> : k_trace<MK, 0, 6, kBundle>)
-                                           : (five ? k_trace<MK, INTEG, 5, 1> : k_trace<MK, INTEG, 6, 1>);
+  // CTAs per SM at least (the register budget): 7 (72 registers) for the isotropic graph metric,
+  // measured 3 % faster at 1080p than 6 and 8; 5 (102) for the local-map jet and on request
+  constexpr int kDefaultMinb = is_iso(MK) ? 7 : 6;
+  void (*kern)(const TraceParams) =
+      bundle ? (five ? k_trace<MK, 0, 5, kBundle> : k_trace<MK, 0, kDefaultMinb, kBundle>)
+             : (five ? k_trace<MK, INTEG, 5, 1> : k_trace<MK, INTEG, kDefaultMinb, 1>);
   if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -70,10 +70,12 @@ def test_far_field_generator_matches_oracle(rg):
     assert np.abs(Ug - Ur).max() * eps < 2e-6, np.abs(Ug - Ur).max() * eps
 
 
-def test_trained_surrogate_gains_work_within_1e3_of_oracle(rg):
-    """The gain of the learned map: jumps replace RK4 bump-term work while the image stays
-    within 1e-3 of the FP64 oracle.  (On this field the certified far field is small, so
-    the gain is small; the benchmark reports its size and the wall-clock cost.)"""
+def test_trained_surrogate_removes_rk4_work_within_1e3_of_oracle(rg):
+    """What the learned map does on this field: its jumps replace RK4 bump-term work while the
+    image stays within 1e-3 of the FP64 oracle.  The certified far field is small here, so the
+    work removed is small (about 1-2 % of the bump terms); the benchmark reports it with the
+    wall-clock cost, and plain RK4 at its own largest step meeting the same bar is faster
+    than the surrogate frame."""
     import torch
     w = _work(240, 135)
     dm, ds = rg.Metric(w.metric), rg.Scene(w.scene)
@@ -92,7 +94,8 @@ def test_trained_surrogate_gains_work_within_1e3_of_oracle(rg):
                                  out=rg.alloc_outputs(w.n_pixels, count=True))
     rg.rgeo_sync()
     assert st["accepted"] > 0, st
-    assert out["bump_evals"].item() < plain["bump_evals"].item()
+    assert out["bump_evals"].item() < 0.998 * plain["bump_evals"].item(), (out["bump_evals"].item(),
+                                                                         plain["bump_evals"].item())
     ref = oracle.trace(w)
     g = gpu_arrays(out)
     S = w.scene.n_spheres
