@@ -113,7 +113,7 @@ typedef struct {
   float cutoff_sigmas;     /* c; 4 is the default used by the workloads */
   float twist_rate;        /* k (twist only) */
   int32_t cull_grid;       /* bump-support cull grid of G^3 cells: 0 = automatic (for >= 16
-                              isotropic truncated bumps, G = 128 up to 1024 bumps, else 64; the
+                              isotropic truncated bumps, G = 192 up to 64 bumps, 128 up to 1024, else 64; the
                               masks take G^3 x ceil(K / 32) x 4 bytes), -1 = none, 4..256 = that G */
   int32_t reserved[3];     /* must be zero */
   const float *direction;  /* HOST [K*3] v_k (local maps only; else ignored) */

@@ -32,7 +32,7 @@ import os
 
 from . import scenes
 
-CANDIDATE_GRIDS = (-1, 64, 96, 128)
+CANDIDATE_GRIDS = (-1, 96, 128, 192)
 CANDIDATE_CTAS = (0, 6, 5)
 CANDIDATE_TILES = (1, 2)
 CANDIDATE_LISTS = (0, 1)

@@ -80,7 +80,8 @@ struct MetricDev {
   int aniso;           // 1: anisotropic layout
   int skippable;       // graph, truncated, A == 0: flat space outside the supports
   float4 *bumps;       // packed table (device)
-  float *raw;          // raw centres/amplitudes/sigmas (device) [K*7]
+  float *raw;          // raw centres/amplitudes/sigmas (device) [K*7], in the caller's bump order
+  int32_t *perm;       // (device) bump of table slot k, or null: slot k is bump k
   float b[3];
   float A[9];
   int has_affine, has_quad;
@@ -257,19 +258,19 @@ constexpr unsigned kErrStackOverflow = 1u;
 constexpr unsigned kErrTimeout = 2u;
 
 // Kernel launchers (rgeo_trace.cu).
-cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
+cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, const int32_t *perm, float4 *out,
                               cudaStream_t st);
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
 // Illumination pass over the hits of a finished trace p (p.hit_nrm filled by it).
 cudaError_t launch_illuminate(const TraceParams &p, const LightParams &l, cudaStream_t st);
-cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st);
+cudaError_t launch_set_centers(const float *c, int K, int aniso, const int32_t *perm, float4 *bumps, cudaStream_t st);
 cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
                               cudaStream_t st);
 cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int kind, int aniso,
                          int integrator,
                          int max_table_f4, long long total_items, cudaStream_t st);
-cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
-                                  float dt, cudaStream_t st);
+cudaError_t launch_advance_motion(const float *motion, int K, int aniso, const int32_t *perm, float *raw,
+                                  float4 *bumps, float *t, float dt, cudaStream_t st);
 cudaError_t launch_set_time(float *t, float value, cudaStream_t st);
 cudaError_t launch_segments(const TraceParams &p, long long n, unsigned long long seed, float box, float s_max,
                             float accel_bound, float *X, float *T, cudaStream_t st);

@@ -1891,7 +1891,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
 }
 
 template <int MK, int INTEG, bool SMEM>
-__global__ void __launch_bounds__(128, 6) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
+__global__ void __launch_bounds__(128, 5) k_trace_batch(const TraceParams *__restrict__ inst, int n, int table_f4) {
   extern __shared__ float4 bsmem[];
   constexpr bool step = MK == MK_GRAPH_SL;
   uint32_t *slot = reinterpret_cast<uint32_t *>(bsmem) +
@@ -1900,7 +1900,7 @@ __global__ void __launch_bounds__(128, 6) k_trace_batch(const TraceParams *__res
 }
 
 template <int MK, int INTEG, bool SMEM>
-__global__ void __launch_bounds__(128, 6) k_trace_batch_param(const __grid_constant__ BatchTable T, int n,
+__global__ void __launch_bounds__(128, 5) k_trace_batch_param(const __grid_constant__ BatchTable T, int n,
                                                            int table_f4) {
   extern __shared__ float4 bsmem[];
   constexpr bool step = MK == MK_GRAPH_SL;
@@ -2141,17 +2141,18 @@ __global__ void k_wave_apply(const WaveArgs W, unsigned n, float h) {
 // Bump motion c_k(t) = c0_k + A_k sin(2 pi f_k t + phi_k) (per axis), then the packed
 // table; t is read from and advanced in device memory so that a captured graph
 // animates without host input.  motion = [K*3 c0 | K*3 A | K f | K phi].
-__global__ void k_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
-                                 float dt) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_advance_motion(const float *motion, int K, int aniso, const int32_t *perm, float *raw,
+                                 float4 *bumps, float *t, float dt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // table slot k holds bump u
   const float tt = *t;
   if (k < K) {
-    const float f = motion[6 * K + k], ph = motion[7 * K + k];
+    const int u = perm ? perm[k] : k;
+    const float f = motion[6 * K + u], ph = motion[7 * K + u];
     const float s = sinf(6.283185307179586f * f * tt + ph);
     float c[3];
     for (int a = 0; a < 3; a++) {
-      c[a] = motion[3 * k + a] + motion[3 * K + 3 * k + a] * s;
-      raw[3 * k + a] = c[a];
+      c[a] = motion[3 * u + a] + motion[3 * K + 3 * u + a] * s;
+      raw[3 * u + a] = c[a];
     }
     if (aniso) {
       float4 b = bumps[kAnisoStride * k];
@@ -2261,16 +2262,17 @@ __global__ void k_segments(const TraceParams P, long long n, unsigned long long 
 __global__ void k_tick(float *t, float dt) { *t += dt; }
 __global__ void k_set_time(float *t, float value) { *t = value; }
 
-// Packs bump k (isotropic: one thread per bump of the padded table, so the inert pad
-// bumps K .. Ke are written too).
-__global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out) {
+// Packs table slot k (isotropic: one thread per slot of the padded table, so the inert pad
+// bumps K .. Ke are written too) from bump perm[k] (k without a permutation).
+__global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, const int32_t *perm, float4 *out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int limit = aniso ? K : iso_pad_index(K) + 1;
   if (k >= limit) return;
   const bool pad = k >= K;
-  const float *c = raw + 3 * (pad ? 0 : k);
-  const float a = pad ? 0.f : raw[3 * K + k];
-  const float *sg = raw + 4 * K + 3 * (pad ? 0 : k);
+  const int u = pad ? 0 : (perm ? perm[k] : k);
+  const float *c = raw + 3 * u;
+  const float a = pad ? 0.f : raw[3 * K + u];
+  const float *sg = raw + 4 * K + 3 * u;
   if (!aniso) {
     pack_iso_bump(out, k, c[0], c[1], c[2], a, sg[0], cutoff);
     return;
@@ -2291,20 +2293,22 @@ __global__ void k_pack_bumps(const float *raw, int K, float cutoff, int aniso, f
   out[3 * k + 2] = make_float4(la, c2, 0.f, 0.f);
 }
 
-__global__ void k_set_centers(const float *c, int K, int aniso, float4 *bumps) {
+// Table slot k takes the centre of bump perm[k] (k without a permutation) from c [K*3].
+__global__ void k_set_centers(const float *c, int K, int aniso, const int32_t *perm, float4 *bumps) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
+  const float *cu = c + 3 * (perm ? perm[k] : k);
   if (aniso) {
     float4 b = bumps[kAnisoStride * k];
-    b.x = c[3 * k];
-    b.y = c[3 * k + 1];
-    b.z = c[3 * k + 2];
+    b.x = cu[0];
+    b.y = cu[1];
+    b.z = cu[2];
     bumps[kAnisoStride * k] = b;
   } else {
     float4 b = bumps[kIsoBumpStride * k];
-    b.x = -c[3 * k];
-    b.y = -c[3 * k + 1];
-    b.z = -c[3 * k + 2];
+    b.x = -cu[0];
+    b.y = -cu[1];
+    b.z = -cu[2];
     bumps[kIsoBumpStride * k] = b;
   }
 }
@@ -2525,10 +2529,10 @@ cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_in
 #endif
 
 #if RGEO_PART(1)
-cudaError_t launch_advance_motion(const float *motion, int K, int aniso, float *raw, float4 *bumps, float *t,
-                                  float dt, cudaStream_t st) {
+cudaError_t launch_advance_motion(const float *motion, int K, int aniso, const int32_t *perm, float *raw,
+                                  float4 *bumps, float *t, float dt, cudaStream_t st) {
   if (K > 0) {
-    k_advance_motion<<<(K + 127) / 128, 128, 0, st>>>(motion, K, aniso, raw, bumps, t, dt);
+    k_advance_motion<<<(K + 127) / 128, 128, 0, st>>>(motion, K, aniso, perm, raw, bumps, t, dt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -2633,10 +2637,10 @@ cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaS
 #endif
 
 #if RGEO_PART(1)
-cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, float4 *out,
+cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, const int32_t *perm, float4 *out,
                               cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_pack_bumps<<<(iso_pad_index(K) + 1 + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, out);
+  k_pack_bumps<<<(iso_pad_index(K) + 1 + 127) / 128, 128, 0, st>>>(raw, K, cutoff, aniso, perm, out);
   return cudaGetLastError();
 }
 
@@ -2651,9 +2655,9 @@ cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_centers(const float *c, int K, int aniso, float4 *bumps, cudaStream_t st) {
+cudaError_t launch_set_centers(const float *c, int K, int aniso, const int32_t *perm, float4 *bumps, cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_set_centers<<<(K + 127) / 128, 128, 0, st>>>(c, K, aniso, bumps);
+  k_set_centers<<<(K + 127) / 128, 128, 0, st>>>(c, K, aniso, perm, bumps);
   return cudaGetLastError();
 }
 
