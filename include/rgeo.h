@@ -555,9 +555,10 @@ rgeo_status rgeo_trace_noalloc(const float *center, const float *amplitude, cons
  *                    rgeo_frame_tiles and every trace.
  *   batch_order      rgeo_batch_create's instance order: 0 (default) by
  *                    decreasing cost (pixels x bumps), 1 as given.
- *   sum_lists        culled bump sums of a warp: 0 (default) one list of bumps per
- *                    RK4 step where the step's reach allows it (up to 512 bumps),
- *                    else per right-hand side; 1 always per right-hand side.
+ *   sum_lists        culled bump sums of a warp: 0 (default) one list of bumps for
+ *                    as many RK4 steps as stay within its reach (up to 512 bumps),
+ *                    else a list per right-hand side; 1 always per right-hand side;
+ *                    2 one list per RK4 step.
  * A setting is read when a trace or batch is enqueued or created (a captured
  * graph keeps the choice made at capture); it is not synchronised between host
  * threads.  Errors: RGEO_EINVAL (NULL, bad value, nonzero reserved fields). */

@@ -13,8 +13,8 @@ warp, so every candidate gives the same image bit for bit.
                    graph metric; 5 or fewer take the 96-register build of the kernel)
   tile_shape       the refill tile a warp takes from the queue: 1 (8 x 4) or 2 (4 x 8)
                    pixels (16 x 2 was measured slower at 1080p and is left out)
-  sum_lists        culled bump sums from one list per RK4 step (0) or per right-hand
-                   side (1)
+  sum_lists        culled bump sums from one list for as many RK4 steps as its reach
+                   covers (0) or from one per right-hand side (1)
   batch_order      batches: instances by decreasing cost (0) or as given (1)
 
 The candidate set is the product of the knobs that apply to the workload's metric

@@ -129,8 +129,11 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
     // start: |v| <= 1 for a g-unit tangent (g >= I; 1% for its float32 drift) and
     // |x_stage - x| <= h (|v| + h |x''| / 2)
     const double reach = (double)h * (1.01 + 0.5 * (double)h * m.accel_max) * 1.001 + 1e-5;
-    p.step_lists = integrator == RGEO_RK4 && rgeo::tuning().sum_lists == 0 && reach <= rgeo::kStepReach &&
-                   m.K <= 512;
+    const int mode = rgeo::tuning().sum_lists;
+    p.step_lists = integrator == RGEO_RK4 && mode != 1 && reach <= rgeo::kStepReach && m.K <= 512;
+    // a list serves the steps whose stage points all stay within kStepReach of its positions
+    // (mode 2: one step each)
+    p.list_steps = !p.step_lists ? 0 : (mode == 2 ? 1 : std::max(1, std::min(8, (int)std::floor(rgeo::kStepReach / reach))));
   }
   p.K = m.kind == RGEO_METRIC_DIFFEO_TWIST ? 0 : m.K;
   p.kind = m.kind;
@@ -710,7 +713,7 @@ rgeo_status rgeo_set_tuning(const rgeo_tuning *t) {
     return fail(RGEO_EINVAL, "rgeo_set_tuning: tile_shape must be 0 (default), 1 (8x4), 2 (4x8) or 3 (16x2)");
   if (t->batch_order != 0 && t->batch_order != 1)
     return fail(RGEO_EINVAL, "rgeo_set_tuning: batch_order must be 0 or 1");
-  if (t->sum_lists != 0 && t->sum_lists != 1) return fail(RGEO_EINVAL, "rgeo_set_tuning: sum_lists must be 0 or 1");
+  if (t->sum_lists < 0 || t->sum_lists > 2) return fail(RGEO_EINVAL, "rgeo_set_tuning: sum_lists must be 0, 1 or 2");
   rgeo::Tuning &g = rgeo::tuning();
   const rgeo::Tuning d;
   g.rays_per_thread = t->rays_per_thread == 0 ? d.rays_per_thread : t->rays_per_thread;

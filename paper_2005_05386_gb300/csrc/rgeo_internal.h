@@ -135,6 +135,7 @@ struct TraceParams {
   const float4 *cull_hdr;
   int cull_G, cull_words;
   int step_lists;              // culled sums from one list per step (the step's reach <= kStepReach)
+  int list_steps;              // steps one list serves (their reach together <= kStepReach)
   int bundle;                  // segment tests in bundles of several chords (one query each)
   float b[3];
   float A[9];

@@ -231,12 +231,14 @@ __device__ __forceinline__ F3 accel_graph_iso(const TraceParams &P, const float4
 //   (qs_e, qs_o, q_e, q_o)
 // for the even bump e and the odd bump o of the pair.  np (the same on every lane) is the
 // number of packed pairs of the current step, or -1 when each right-hand side looks up
-// its own cells; own (per lane) counts the bumps of the lane's own cell in the step list.
+// its own cells; own (per lane) counts the bumps of the lane's own cell in the step list;
+// age (the same on every lane) counts the steps the list has served since it was built.
 struct WarpLists {
   int2 *idx;   // [kListPairs]
   float4 *pk;  // [4 * kListPairs], or null: no step lists
   int np;
   unsigned own;
+  int age;
 };
 
 // Lists the union of the participating lanes' cell masks, even-numbered bumps in idx[.].x
@@ -278,8 +280,9 @@ __device__ __forceinline__ long long cull_cell(const TraceParams &P, float4 ghdr
 // The step list (all 32 lanes together): the union of the cells of the participating
 // lanes' positions x, listed and packed into the warp's pk.  The cull grid's supports are
 // inflated by kStepReach, which bounds the distance from x to every RK4 stage point of the
-// step (the launcher checks that), so the list holds every bump that can be nonzero at any
-// stage.  A union beyond the list's capacity leaves np = -1 (per right-hand-side lists).
+// next P.list_steps steps (the launcher checks that), so the list holds every bump that can
+// be nonzero at any of their stages.  A union beyond the list's capacity leaves np = -1
+// (the dense sums).
 __device__ __forceinline__ void step_list(const TraceParams &P, const float4 *__restrict__ sb, WarpLists &wl,
                                           float4 ghdr, bool part, F3 x) {
   const long long cell = part ? cull_cell(P, ghdr, x) : -1;
@@ -299,6 +302,7 @@ __device__ __forceinline__ void step_list(const TraceParams &P, const float4 *__
     }
   }
   wl.own = own;
+  wl.age = 0;
   if (full) {
     wl.np = -1;
     return;
@@ -313,6 +317,18 @@ __device__ __forceinline__ void step_list(const TraceParams &P, const float4 *__
   }
   __syncwarp();
   wl.np = np;
+}
+
+// Keeps the warp's step list while it still covers every lane (it has served fewer than
+// P.list_steps steps and no lane took a new ray, fresh), else lists afresh at the lanes' x.
+__device__ __forceinline__ void step_list_refresh(const TraceParams &P, const float4 *__restrict__ sb,
+                                                  WarpLists &wl, float4 ghdr, bool part, bool fresh, F3 x) {
+  if (!P.step_lists) {
+    wl.np = -1;
+    return;
+  }
+  if (wl.np >= 0 && wl.age < P.list_steps && !__any_sync(0xffffffffu, fresh)) return;
+  step_list(P, sb, wl, ghdr, part, x);
 }
 
 // Eq. 5.4 over the packed pairs of the warp's step list (every lane together or not: no
@@ -1320,7 +1336,7 @@ constexpr int kPackFloat4 = 4 * kListPairs;                                     
 __host__ __device__ inline int lists_float4(bool step) { return kListFloat4 + (step ? kPackFloat4 : 0); }
 __device__ __forceinline__ WarpLists warp_lists(bool step, float4 *lists) {
   float4 *base = lists + (threadIdx.x >> 5) * lists_float4(step);
-  return WarpLists{reinterpret_cast<int2 *>(base), step ? base + kListFloat4 : nullptr, -1, 0u};
+  return WarpLists{reinterpret_cast<int2 *>(base), step ? base + kListFloat4 : nullptr, -1, 0u, 0};
 }
 
 // Warps of the 128-thread trace blocks.
@@ -1358,6 +1374,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   ray_clear(r);
   unsigned cnext = 0u, cend = 0u;
   for (;;) {
+    const bool held = active;
     refill_tile<MK>(P, sb, active, drained, r, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
@@ -1365,10 +1382,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
       continue;
     }
     if (!conv && !active) continue;
-    if (MK == MK_GRAPH_SL) {
-      if (P.step_lists) step_list(P, sb, wl, ghdr, active, xhi(r));
-      else wl.np = -1;
-    }
+    if (MK == MK_GRAPH_SL) step_list_refresh(P, sb, wl, ghdr, active, active && !held, xhi(r));
     bool inside = true;
     F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
     const bool go =
@@ -1378,6 +1392,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
     F3 dx, dvel;
     step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
     if (go) active = post_step<MK, NB>(P, sb, ss, r, dx, dvel, bs);
+    ++wl.age;
   }
   evals.flush(P);
 }
@@ -1393,7 +1408,7 @@ template <int MK, bool INSIDE>
 __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside,
                                          WorkCount &evals) {
   if (MK != MK_GRAPH_ISO || !P.cull_masks) {
-    WarpLists nolists{nullptr, nullptr, -1, 0u};
+    WarpLists nolists{nullptr, nullptr, -1, 0u, 0};
     const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), &nolists, true, &evals};
     return accel<MK, INSIDE>(P, sb, cx, x, v, inside);
   }
@@ -1728,7 +1743,7 @@ __global__ void __launch_bounds__(128) k_trace_x2(const TraceParams P) {
     F3 a10, a11;
     accel_graph_iso_x2<true>(P, sb, P.K, xhi(r0), vhi(r0), xhi(r1), vhi(r1), a10, a11, in0, in1);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);  // this kernel sums densely (no cull grid)
-    WarpLists nolists{nullptr, nullptr, -1, 0u};
+    WarpLists nolists{nullptr, nullptr, -1, 0u, 0};
     evals.evals += 2ull * (unsigned)P.K;
     evals.slots += 2u * (unsigned)iso_pad_index(P.K);
     if (act0) act0 = pre_step<MK_GRAPH_ISO, false>(P, sb, ss, SumCtx{z4, &nolists, true, &evals}, r0, a10, in0);
@@ -1812,7 +1827,7 @@ struct SmemInstances {
   __device__ __forceinline__ float4 *table() const { return reinterpret_cast<float4 *>(slot + kParamWords); }
   __device__ __forceinline__ WarpLists lists() const {
     float4 *b = table() + table_f4;
-    return WarpLists{reinterpret_cast<int2 *>(b), step ? b + kListFloat4 : nullptr, -1, 0u};
+    return WarpLists{reinterpret_cast<int2 *>(b), step ? b + kListFloat4 : nullptr, -1, 0u, 0};
   }
   __device__ __forceinline__ void load(int i) const {
     const unsigned lane = threadIdx.x & 31u;
@@ -1835,7 +1850,7 @@ struct ParamInstances {
   __device__ __forceinline__ float4 *table() const { return tab; }
   __device__ __forceinline__ WarpLists lists() const {
     float4 *b = tab + table_f4;
-    return WarpLists{reinterpret_cast<int2 *>(b), step ? b + kListFloat4 : nullptr, -1, 0u};
+    return WarpLists{reinterpret_cast<int2 *>(b), step ? b + kListFloat4 : nullptr, -1, 0u, 0};
   }
   __device__ __forceinline__ void load(int) const {}
 };
@@ -1861,6 +1876,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
   for (;;) {
     const TraceParams &P = src.get(i);
     const float4 *ss = P.spheres;
+    const bool held = active;
     refill_tile<MK>(P, sb, active, drained, r, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
@@ -1870,6 +1886,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
         i = (i + 1) % n;
         drained = false;
         cnext = cend = 0u;
+        wl.np = -1;  // the next instance's lists start afresh
         src.load(i);
         warp_load_table<SMEM>(src.get(i), src.table(), sb);
       }
@@ -1877,8 +1894,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
     }
     if (!conv && !active) continue;
     const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
-    wl.np = -1;
-    if (MK == MK_GRAPH_SL && P.step_lists) step_list(P, sb, wl, ghdr, active, xhi(r));
+    if (MK == MK_GRAPH_SL) step_list_refresh(P, sb, wl, ghdr, active, active && !held, xhi(r));
     bool inside = true;
     F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
     const bool go = pre_step<MK>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside);
@@ -1887,6 +1903,7 @@ __device__ __forceinline__ void batch_loop(const Src &src, int n) {
     F3 dx, dvel;
     step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
     if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
+    ++wl.age;
   }
 }
 
@@ -2056,6 +2073,7 @@ __global__ void __launch_bounds__(128, 5) k_wave_trace(const TraceParams P, cons
   int cool = 0;
   unsigned cnext = 0u, cend = 0u;
   for (;;) {
+    const bool held = active;
     wave_refill<MK>(P, W, sb, active, drained, r, cool, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
@@ -2063,10 +2081,7 @@ __global__ void __launch_bounds__(128, 5) k_wave_trace(const TraceParams P, cons
       continue;
     }
     if (!conv && !active) continue;
-    if (MK == MK_GRAPH_SL) {
-      if (P.step_lists) step_list(P, sb, wl, ghdr, active, xhi(r));
-      else wl.np = -1;
-    }
+    if (MK == MK_GRAPH_SL) step_list_refresh(P, sb, wl, ghdr, active, active && !held, xhi(r));
     bool inside = true;
     F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
     if (active && inside && r.steps < P.max_steps) {
@@ -2082,6 +2097,7 @@ __global__ void __launch_bounds__(128, 5) k_wave_trace(const TraceParams P, cons
     F3 dx, dvel;
     step_increments<MK, 0>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
     if (go) active = post_step<MK>(P, sb, ss, r, dx, dvel);
+    ++wl.age;
   }
   evals.flush(P);
 }

@@ -424,7 +424,7 @@ def test_frame_parts_and_tuning_reproduce_the_frame_bit_for_bit(rg):
     with pytest.raises(rg.RgeoError):
         rg.trace(w, out=out, tiles=(0, -1, 0))
     for kw in (dict(tile_shape=2), dict(tile_shape=3), dict(ctas_per_sm=5), dict(ctas_per_sm=3),
-               dict(sum_lists=1), dict(sum_lists=1, ctas_per_sm=5)):
+               dict(sum_lists=1), dict(sum_lists=2), dict(sum_lists=1, ctas_per_sm=5)):
         try:
             rg.rgeo_set_tuning(**kw)
             g = _run(rg, w)
