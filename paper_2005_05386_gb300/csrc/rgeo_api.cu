@@ -113,6 +113,20 @@ rgeo_status validate_trace(const rgeo_metric *metric, const rgeo_scene *scene, c
   return RGEO_OK;
 }
 
+// Steps one culled-sum list serves at step h, 0 when a single step can leave its reach (the
+// sums then look up each right-hand side's own cell).  A list built at x holds every bump
+// whose support, inflated by kCullInflate + kStepReach, meets x's cell, so it serves every
+// point within kStepReach of x: a step's stage points stay within h (|v| + h |x''| / 2) of
+// its start, with |v| <= 1 for a g-unit tangent (g >= I; 1 % for its float32 drift) and
+// |x''| <= accel_max, and n steps within n times that.  Tuning: sum_lists 1 takes no lists,
+// 2 one list per step.
+int list_steps_for(const rgeo::MetricDev &m, float h) {
+  const double reach = (double)h * (1.01 + 0.5 * (double)h * m.accel_max) * 1.001 + 1e-5;
+  const int mode = rgeo::tuning().sum_lists;
+  if (mode == 1 || reach > rgeo::kStepReach) return 0;
+  return mode == 2 ? 1 : std::max(1, std::min(8, (int)std::floor(rgeo::kStepReach / reach)));
+}
+
 rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *cam,
                               int32_t W, int32_t H, float h, int32_t max_steps, int32_t integrator,
                               int32_t shading, uint32_t flags, const rgeo_outputs *out) {
@@ -125,15 +139,10 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
     p.cull_hdr = m.cull_hdr;
     p.cull_G = m.cull_G;
     p.cull_words = m.cull_words;
-    // one list per RK4 step when every stage point of a step stays within kStepReach of its
-    // start: |v| <= 1 for a g-unit tangent (g >= I; 1% for its float32 drift) and
-    // |x_stage - x| <= h (|v| + h |x''| / 2)
-    const double reach = (double)h * (1.01 + 0.5 * (double)h * m.accel_max) * 1.001 + 1e-5;
-    const int mode = rgeo::tuning().sum_lists;
-    p.step_lists = integrator == RGEO_RK4 && mode != 1 && reach <= rgeo::kStepReach && m.K <= 512;
-    // a list serves the steps whose stage points all stay within kStepReach of its positions
-    // (mode 2: one step each)
-    p.list_steps = !p.step_lists ? 0 : (mode == 2 ? 1 : std::max(1, std::min(8, (int)std::floor(rgeo::kStepReach / reach))));
+    // warp step lists (RK4, up to 512 bumps: the warp's packed pairs in shared memory)
+    const int n = list_steps_for(m, h);
+    p.step_lists = integrator == RGEO_RK4 && n > 0 && m.K <= 512;
+    p.list_steps = p.step_lists ? n : 0;
   }
   p.K = m.kind == RGEO_METRIC_DIFFEO_TWIST ? 0 : m.K;
   p.kind = m.kind;
@@ -219,11 +228,16 @@ namespace {
 // grid cell form a list; bumps are taken by decreasing support radius, and each joins the
 // parity (even or odd table slots, ceil(K/2) and floor(K/2) of them) that lowers the summed
 // imbalance of its lists (greedy discrepancy balancing).  Returns perm, the bump of each
-// table slot; the numbering changes the summation order only.
-std::vector<int32_t> balanced_parity_order(const float *center, const float *sigma, int K, float cutoff, int G) {
+// table slot; the numbering changes the summation order only.  The sample cells are those
+// of a fixed 192^3 grid over the supports whatever grid the metric is culled on (or none),
+// so the numbering, and with it every result bit, is a function of the bumps alone: dense
+// sums and culled sums on any grid give the same frame.
+constexpr int kParityCells = 192;
+
+std::vector<int32_t> balanced_parity_order(const float *center, const float *sigma, int K, float cutoff) {
   std::vector<int32_t> perm(K);
   for (int k = 0; k < K; k++) perm[k] = k;
-  if (K < 2 || G <= 0 || !(cutoff > 0.f)) return perm;
+  if (K < 2 || !(cutoff > 0.f)) return perm;
   std::vector<double> R(K);
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int k = 0; k < K; k++) {
@@ -234,7 +248,7 @@ std::vector<int32_t> balanced_parity_order(const float *center, const float *sig
     }
   }
   const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
-  const double cell = ext / G;
+  const double cell = ext / kParityCells;
   uint64_t state = 0x5EEDBA5Eull + (uint64_t)K;
   auto u01 = [&state]() {  // SplitMix64 (Steele, Lea and Flood 2014)
     uint64_t z = (state += 0x9E3779B97F4A7C15ull);
@@ -428,8 +442,8 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
       G = desc->cull_grid == 0 ? (K >= 16 ? (K <= 64 ? 192 : (K <= 1024 ? 128 : 64)) : 0)
                                : (desc->cull_grid < 0 ? 0 : desc->cull_grid);
     cudaError_t e = upload(&m->d.raw, raw.data(), raw.size());
-    if (e == cudaSuccess && G > 0) {
-      const std::vector<int32_t> perm = balanced_parity_order(desc->center, desc->sigma, K, desc->cutoff_sigmas, G);
+    if (e == cudaSuccess && desc->kind == RGEO_METRIC_GRAPH_BUMPS && !aniso && desc->cutoff_sigmas > 0.f) {
+      const std::vector<int32_t> perm = balanced_parity_order(desc->center, desc->sigma, K, desc->cutoff_sigmas);
       e = upload(&m->d.perm, perm.data(), perm.size());
     }
     if (e == cudaSuccess) e = cudaMalloc(&m->d.bumps, sizeof(float4) * (size_t)rgeo::packed_float4s(K, aniso));
@@ -634,6 +648,7 @@ rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, c
   l.tol = light->tol;
   l.delta = light->delta;
   l.lit = lit;
+  l.list_steps = p.cull_masks ? list_steps_for(metric->d, light->h) : 0;
   cudaError_t e = cudaMemsetAsync(buf, 0, 16, st);
   if (e == cudaSuccess) e = rgeo::launch_trace(p, st);
   if (e == cudaSuccess) e = rgeo::launch_illuminate(p, l, st);

@@ -207,7 +207,8 @@ struct LightParams {
   float h;
   int max_steps, iters;
   float tol, delta;
-  int32_t *lit;  // optional [N]
+  int32_t *lit;    // optional [N]
+  int list_steps;  // steps a lane's culled-sum list serves at step h (0: a cell per right-hand side)
 };
 
 // Instance table of a batch passed by value in the kernel's parameter space (CUDA

@@ -1399,14 +1399,27 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
 
 // ------------------------------------------------------ Riemannian illumination
 
-// Eq. 5.4 over the bumps of the lane's own cull cell only, with no warp collective: for
-// lanes that follow their own paths (the light geodesics), each walks its own list and
-// SIMT serialises the differences.  The cell's even-numbered bumps are paired with its
-// odd-numbered ones as in the warp-wide form, so the sums equal the dense sums.  Other
-// metric kinds, and metrics without a cull grid, take the dense sums.
+// The cull cell of x for the per-lane sums: its mask words, or null when x lies outside the
+// grid (which covers every bump's support inflated by kCullInflate + kStepReach, so no bump
+// reaches within kStepReach of x either).
+__device__ __forceinline__ const uint32_t *lane_cell(const TraceParams &P, F3 x) {
+  const float4 ghdr = __ldg(P.cull_hdr);
+  const int G = P.cull_G;
+  const float fx = (x.x - ghdr.x) * ghdr.w, fy = (x.y - ghdr.y) * ghdr.w, fz = (x.z - ghdr.z) * ghdr.w;
+  if (!(fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G)) return nullptr;
+  return P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
+}
+
+// Eq. 5.4 over the bumps of one cull cell's list, with no warp collective: for lanes that
+// follow their own paths (the light geodesics), each walks its own list and SIMT serialises
+// the differences.  cm is the cell of a position within kStepReach of x (a lane's list
+// serves the steps its reach covers, as the warps' step lists do), or null: no bumps.  The
+// list's even-numbered bumps are paired with its odd-numbered ones as in the warp-wide
+// form, so the sums equal the dense sums.  Other metric kinds, and metrics without a cull
+// grid, take the dense sums (cm unused).
 template <int MK, bool INSIDE>
-__device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, bool &inside,
-                                         WorkCount &evals) {
+__device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb, const uint32_t *cm, F3 x, F3 v,
+                                         bool &inside, WorkCount &evals) {
   if (MK != MK_GRAPH_ISO || !P.cull_masks) {
     WarpLists nolists{nullptr, nullptr, -1, 0u, 0};
     const SumCtx cx{make_float4(0.f, 0.f, 0.f, 0.f), &nolists, true, &evals};
@@ -1414,13 +1427,8 @@ __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb,
   }
   PairAcc a;
   pair_acc_init(a, x, v);
-  const float4 ghdr = __ldg(P.cull_hdr);
-  const int G = P.cull_G;
   const int pad = kIsoBumpStride * iso_pad_index(P.K);
-  const float fx = (x.x - ghdr.x) * ghdr.w, fy = (x.y - ghdr.y) * ghdr.w, fz = (x.z - ghdr.z) * ghdr.w;
-  const bool ing = fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)G && fy < (float)G && fz < (float)G;
-  if (ing) {
-    const uint32_t *cm = P.cull_masks + ((size_t)(((int)fz * G + (int)fy) * G + (int)fx)) * (size_t)P.cull_words;
+  if (cm) {
     // two cursors walk the cell's even-numbered and odd-numbered bumps in increasing order
     const unsigned w0 = __ldg(cm);
     evals.evals += (unsigned)__popc(w0);
@@ -1451,20 +1459,29 @@ __device__ __forceinline__ F3 accel_lane(const TraceParams &P, const float4 *sb,
   return pair_acc_finish(P, a, x, v);
 }
 
+// The list a light geodesic's sums at x take: the cell kept from the step that built it
+// while it serves (P.list_steps > 0), else x's own cell.
+__device__ __forceinline__ const uint32_t *lane_list(const TraceParams &P, const uint32_t *kept, F3 x) {
+  return (P.list_steps > 0 || !P.cull_masks) ? kept : lane_cell(P, x);
+}
+
 // One RK4 (or Euler) step's increments with per-lane sums (the light geodesics).
 template <int MK, int INTEG>
-__device__ __forceinline__ void step_increments_lane(const TraceParams &P, const float4 *sb, F3 x, F3 v, F3 a1,
-                                                     F3 &dx, F3 &dvel, WorkCount &evals) {
+__device__ __forceinline__ void step_increments_lane(const TraceParams &P, const float4 *sb, const uint32_t *kept,
+                                                     F3 x, F3 v, F3 a1, F3 &dx, F3 &dvel, WorkCount &evals) {
   const float h = P.h;
   if (INTEG == 0) {
     bool dummy;
     const float h2 = 0.5f * h;
     const F3 v2 = axpy(h2, a1, v);
-    const F3 a2 = accel_lane<MK, false>(P, sb, axpy(h2, v, x), v2, dummy, evals);
+    const F3 x2 = axpy(h2, v, x);
+    const F3 a2 = accel_lane<MK, false>(P, sb, lane_list(P, kept, x2), x2, v2, dummy, evals);
     const F3 v3 = axpy(h2, a2, v);
-    const F3 a3 = accel_lane<MK, false>(P, sb, axpy(h2, v2, x), v3, dummy, evals);
+    const F3 x3 = axpy(h2, v2, x);
+    const F3 a3 = accel_lane<MK, false>(P, sb, lane_list(P, kept, x3), x3, v3, dummy, evals);
     const F3 v4 = axpy(h, a3, v);
-    const F3 a4 = accel_lane<MK, false>(P, sb, axpy(h, v3, x), v4, dummy, evals);
+    const F3 x4 = axpy(h, v3, x);
+    const F3 a4 = accel_lane<MK, false>(P, sb, lane_list(P, kept, x4), x4, v4, dummy, evals);
     const float h6 = h * (1.f / 6.f);
     dx = h6 * (v + 2.f * (v2 + v3) + v4);
     dvel = h6 * (a1 + 2.f * (a2 + a3) + a4);
@@ -1539,11 +1556,18 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
   u = rsqrtf(metric_dd<MK>(P, sb, q, d)) * d;
   float xh[3] = {q.x, q.y, q.z}, xl[3] = {0.f, 0.f, 0.f}, vh[3] = {u.x, u.y, u.z}, vl[3] = {0.f, 0.f, 0.f};
   blocked = false;
+  const bool keep = MK == MK_GRAPH_ISO && P.cull_masks && P.list_steps > 0;
+  const uint32_t *kept = nullptr;  // the lane's list: the cell of the step that built it
+  int age = P.list_steps;          // steps it has served
   for (int steps = 0;;) {
     F3 x = f3(xh[0], xh[1], xh[2]);
     const F3 v = f3(vh[0], vh[1], vh[2]);
+    if (keep && age >= P.list_steps) {
+      kept = lane_cell(P, x);
+      age = 0;
+    }
     bool inside = true;
-    F3 a1 = accel_lane<MK, true>(P, sb, x, v, inside, evals);
+    F3 a1 = accel_lane<MK, true>(P, sb, lane_list(P, kept, x), x, v, inside, evals);
     if (MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside) {
       // straight line x + t v: closest approach to L at tL, next support ball at te
       const float te = support_entry<MK>(sb, P.K, x, v);
@@ -1563,17 +1587,22 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
       }
       for (int c = 0; c < 3; c++) comp_add(xh[c], xl[c], te * comp(v, c));
       x = f3(xh[0], xh[1], xh[2]);
+      if (keep) {  // the advance left the list's reach: list afresh
+        kept = lane_cell(P, x);
+        age = 0;
+      }
       bool dummy;
-      a1 = accel_lane<MK, false>(P, sb, x, v, dummy, evals);
+      a1 = accel_lane<MK, false>(P, sb, lane_list(P, kept, x), x, v, dummy, evals);
     }
     if (steps >= P.max_steps) return false;
     F3 dx, dvel;
-    step_increments_lane<MK, INTEG>(P, sb, x, v, a1, dx, dvel, evals);
+    step_increments_lane<MK, INTEG>(P, sb, kept, x, v, a1, dx, dvel, evals);
     for (int c = 0; c < 3; c++) {
       comp_add(xh[c], xl[c], comp(dx, c));
       comp_add(vh[c], vl[c], comp(dvel, c));
     }
     ++steps;
+    ++age;
     const F3 D = f3(xh[0], xh[1], xh[2]) - x;
     const float t = dot(L - x, D) / dot(D, D);
     if (t < 1.f) {  // the closest approach lies on this segment (or the distance grows)
@@ -2641,6 +2670,8 @@ cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaS
   p.h = l.h;
   p.max_steps = l.max_steps;
   p.energy = 0;
+  p.step_lists = 0;  // the light geodesics keep per-lane lists (shoot), for l.list_steps steps
+  p.list_steps = l.list_steps;
   const int mk = p.kind == 2 ? MK_LOCAL : (p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
   const bool rk4 = p.integrator == 0;
   if (mk == MK_LOCAL) return rk4 ? launch_illuminate_t<MK_LOCAL, 0>(p, l, st) : launch_illuminate_t<MK_LOCAL, 1>(p, l, st);
