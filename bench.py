@@ -794,6 +794,8 @@ def bench_lit(args):
     import paper_2005_05386_gb300 as rg
     torch.cuda.set_device(0)
     w = workload("1080p_64", args.resolution)
+    if args.cull_grid is not None:
+        w.metric.cull_grid = args.cull_grid
     light = scenes.Light()
     N = w.n_pixels
     metric, scene = rg.Metric(w.metric), rg.Scene(w.scene)
@@ -869,7 +871,8 @@ def bench_lit(args):
         "data": "synthetic (seeded SplitMix64 bumps, spheres and displaced-sphere mesh)",
         "config": {"workload": "1080p_64bumps_lit", "width": w.width, "height": w.height, "light": light.pos,
                    "light_h": light.h, "light_max_steps": light.max_steps, "gauss_newton_iters": light.iters,
-                   "tol": light.tol, "l2": "flushed between timed frames (256 MiB write)"},
+                   "tol": light.tol, "cull_grid": w.metric.cull_grid,
+                   "l2": "flushed between timed frames (256 MiB write)"},
         "plain_ms": ms_plain, "illumination_ms": ms_illum,
         "hits_lit_unlit": [int(((ids >= 0) & (lit == 1)).sum()), int(((ids >= 0) & (lit == 0)).sum())],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -928,6 +931,56 @@ def bench_infer(args):
     return 0
 
 
+def bench_train(args):
+    """Adam steps of the learned exponential map at batch 8192 on far-field segments that the
+    device integrator generated from the 1080p / 64-bump field (``rgeo_expmap_train_step`` on
+    consecutive batches of the generated set), with the roofline of the tensor-core products:
+    per row, layers 2 and 3 forward (one product each) and backward (two products each)."""
+    import torch
+    import paper_2005_05386_gb300 as rg
+    torch.cuda.set_device(0)
+    w = workload("1080p_64", None)
+    dm = rg.Metric(w.metric)
+    B, steps = 8192, args.steps
+    n = B * (args.warmup + steps)
+    X, T = rg.Expmap.generate(dm, n, seed=11, accel_bound=0.03)
+    net = rg.Expmap(max_batch=B, seed=7)
+    loss = torch.zeros(1, device="cuda")
+    for i in range(args.warmup):
+        net.train_step(X[i * B:(i + 1) * B], T[i * B:(i + 1) * B], 1e-3, loss=loss)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.warmup, args.warmup + steps):
+        net.train_step(X[i * B:(i + 1) * B], T[i * B:(i + 1) * B], 1e-3, loss=loss)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rg.rgeo_sync()
+    ms = e0.elapsed_time(e1) / steps
+    flops = B * 3 * 2 * 2 * 256 * 256
+    peak = measured_peaks().get("bf16_tflops")
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "Adam steps/s of the learned exponential map (batch 8192)", "value": 1e3 / ms,
+        "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
+        "data": "synthetic (segments generated by the device integrator on the seeded 64-bump field)",
+        "config": {"workload": "expmap_train_b8192", "batch": B, "segments": n,
+                   "l2": "weights and one batch's activations stay in L2 (the step's working set)"},
+        "loss_last": float(loss.item()),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_basis": "burst BF16 GEMM (MEASURED_PEAKS.json)",
+                     "algorithmic": "3 x 2 x 2 x 256 x 256 flops per row (layers 2 and 3, forward and backward)"},
+        "clocks": clk, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -937,7 +990,7 @@ def main():
     ap.add_argument("--workload", default="1080p_64",
                     choices=["1080p_64", "1080p_twist", "parity_64", "quad_lattice", "paraboloid_lattice",
                              "local8_lattice", "4k_1024", "batch16",
-                             "anim120", "surrogate", "infer", "lit"])
+                             "anim120", "surrogate", "infer", "lit", "train"])
     ap.add_argument("--rows", type=int, default=1 << 23, help="rows for --workload infer")
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -962,6 +1015,8 @@ def main():
         return bench_surrogate(args)
     if args.workload == "infer":
         return bench_infer(args)
+    if args.workload == "train":
+        return bench_train(args)
     if args.workload == "lit":
         return bench_lit(args)
     return bench_gpu(args)

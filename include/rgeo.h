@@ -392,11 +392,15 @@ rgeo_status rgeo_expmap_forward(const rgeo_expmap *expmap, const float *inputs, 
 
 /* Loss and its gradient w.r.t. every parameter for one batch (a multiple of 128,
  * at most max_batch): grads (DEVICE [param_count], may be NULL) and loss (DEVICE
- * [1], may be NULL).  Asynchronous. */
+ * [1], may be NULL).  One persistent kernel runs the forward and backward pass of
+ * every 128-row tile (the 256-wide layers' products on the tensor cores); its CTAs'
+ * partial gradients are summed in a fixed order, so the same inputs give the same
+ * bits on every call on a given device.  Asynchronous. */
 rgeo_status rgeo_expmap_gradients(rgeo_expmap *expmap, const float *inputs, const float *targets, int32_t batch,
                                   float *grads, float *loss, void *cuda_stream);
 
-/* One Adam step (beta 0.9, 0.999, eps 1e-8) at learning rate lr. Asynchronous. */
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) at learning rate lr (finite, > 0) on the
+ * gradient of rgeo_expmap_gradients: two kernel launches.  Asynchronous. */
 rgeo_status rgeo_expmap_train_step(rgeo_expmap *expmap, const float *inputs, const float *targets,
                                    int32_t batch, float lr, float *loss, void *cuda_stream);
 

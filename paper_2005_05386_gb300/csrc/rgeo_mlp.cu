@@ -7,14 +7,18 @@
 //   * tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulation) issued by one thread,
 //   * accumulators in tensor memory (TMEM), read back with tcgen05.ld,
 //   * operands in shared memory in the canonical K-major layout without swizzle
-//     (8-row x 16-byte core matrices): staged with cp.async by the training GEMM,
-//     bulk-copied (cp.async.bulk) by the persistent inference kernel,
+//     (8-row x 16-byte core matrices): staged with cp.async by the GEMM and the
+//     training kernel, bulk-copied (cp.async.bulk) by the persistent inference kernel,
 //   * completion signalled through mbarriers by tcgen05.commit.
 // Inference runs all four layers in one persistent, warp-specialised kernel
-// (k_mlp_infer_ws).  Every wait is bounded: a wait that runs out records kErrTimeout
+// (k_mlp_infer_ws); a training step is one persistent kernel over the batch's 128-row
+// tiles (k_train_tile) and one kernel that sums its partial gradients and takes the Adam
+// step (k_reduce_adam).  Every wait is bounded: a wait that runs out records kErrTimeout
 // in the error word and the kernel returns after releasing its tensor memory.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -253,150 +257,7 @@ constexpr int kIn = 7, kOut = 7, kWid = 256;
 constexpr int oW1 = 0, ob1 = oW1 + kWid * kIn, oW2 = ob1 + kWid, ob2 = oW2 + kWid * kWid, oW3 = ob2 + kWid,
               ob3 = oW3 + kWid * kWid, oW4 = ob3 + kWid, ob4 = oW4 + kOut * kWid, kParams = ob4 + kOut;
 
-// Layer 1 in FP32 (K = 7 is too small for the tensor cores): H1 = relu(X W1^T + b1),
-// written as bf16 rows and (when H1t is set) as the transposed bf16 copy used by the
-// weight gradient.
-__global__ void k_layer_in(const float *__restrict__ X, int B, const float *__restrict__ P,
-                           __nv_bfloat16 *H1, __nv_bfloat16 *H1t) {
-  const int b = blockIdx.x;
-  const int j = threadIdx.x;  // 256 threads: one output unit each
-  __shared__ float xs[kIn];
-  if (j < kIn) xs[j] = X[(size_t)b * kIn + j];
-  __syncthreads();
-  float z = P[ob1 + j];
-  for (int k = 0; k < kIn; ++k) z = fmaf(P[oW1 + j * kIn + k], xs[k], z);
-  const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(z, 0.f));
-  H1[(size_t)b * kWid + j] = h;
-  if (H1t) H1t[(size_t)j * B + b] = h;
-}
-
-// Layer 4 in FP32 (N = 7): Y = H3 W4^T + b4.  One warp per row.
-__global__ void k_layer_out(const __nv_bfloat16 *__restrict__ H3, int B, const float *__restrict__ P, float *Y) {
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (b >= B) return;
-  float acc[kOut];
-  for (int o = 0; o < kOut; ++o) acc[o] = 0.f;
-  for (int k = lane; k < kWid; k += 32) {
-    const float h = __bfloat162float(H3[(size_t)b * kWid + k]);
-    for (int o = 0; o < kOut; ++o) acc[o] = fmaf(P[oW4 + o * kWid + k], h, acc[o]);
-  }
-  for (int o = 0; o < kOut; ++o)
-    for (int off = 16; off > 0; off >>= 1) acc[o] += __shfl_down_sync(0xffffffffu, acc[o], off);
-  if (lane == 0)
-    for (int o = 0; o < kOut; ++o) Y[(size_t)b * kOut + o] = acc[o] + P[ob4 + o];
-}
-
-// Loss and its gradient.  Outputs 0..5 regress the scaled residuals T (mean squared
-// error); output 6 regresses e = log(sum_i (Y_i - T_i)^2 + 1e-6), the log squared
-// error of the same sample (a target that is not differentiated), weighted by lam.
-__global__ void k_loss_grad(const float *__restrict__ Y, const float *__restrict__ T, int B, float lam, float *dY,
-                            float *loss) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  float l = 0.f;
-  if (b < B) {
-    float se = 0.f;
-    for (int o = 0; o < 6; ++o) {
-      const float d = Y[(size_t)b * kOut + o] - T[(size_t)b * 6 + o];
-      se = fmaf(d, d, se);
-      dY[(size_t)b * kOut + o] = 2.f * d / (6.f * B);
-    }
-    const float e = logf(se + 1e-6f);
-    const float d6 = Y[(size_t)b * kOut + 6] - e;
-    dY[(size_t)b * kOut + 6] = 2.f * lam * d6 / B;
-    l = se / (6.f * B) + lam * d6 * d6 / B;
-  }
-  for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
-  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
-}
-
-// Gradient of layer 4 and the error into layer 3:
-//   dW4[o, k] += sum_b dY[b, o] H3[b, k], db4[o] += sum_b dY[b, o]  (atomics per block)
-//   dZ3[b, k] = (sum_o dY[b, o] W4[o, k]) [H3[b, k] > 0], as bf16 rows and transposed.
-__global__ void k_back_out(const float *__restrict__ dY, const __nv_bfloat16 *__restrict__ H3, int B,
-                           const float *__restrict__ P, float *G, __nv_bfloat16 *dZ3, __nv_bfloat16 *dZ3t) {
-  const int k = threadIdx.x;  // 256 threads: one hidden unit each
-  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
-  float gw[kOut];
-  for (int o = 0; o < kOut; ++o) gw[o] = 0.f;
-  float w4[kOut];
-  for (int o = 0; o < kOut; ++o) w4[o] = P[oW4 + o * kWid + k];
-  for (int b = b0; b < b1; ++b) {
-    const float h = __bfloat162float(H3[(size_t)b * kWid + k]);
-    float dh = 0.f;
-    for (int o = 0; o < kOut; ++o) {
-      const float dy = dY[(size_t)b * kOut + o];
-      gw[o] = fmaf(dy, h, gw[o]);
-      dh = fmaf(dy, w4[o], dh);
-    }
-    const __nv_bfloat16 dz = __float2bfloat16_rn(h > 0.f ? dh : 0.f);
-    dZ3[(size_t)b * kWid + k] = dz;
-    dZ3t[(size_t)k * B + b] = dz;
-  }
-  for (int o = 0; o < kOut; ++o) atomicAdd(&G[oW4 + o * kWid + k], gw[o]);
-  if (k < kOut) {
-    float s = 0.f;
-    for (int b = b0; b < b1; ++b) s += dY[(size_t)b * kOut + k];
-    atomicAdd(&G[ob4 + k], s);
-  }
-}
-
-// dZ = dH [H > 0] for a hidden layer: bf16 rows + transposed copy (layers 2, 3), or
-// FP32 rows (layer 1).  Also the bias gradient db[k] += sum_b dZ[b, k].
-__global__ void k_relu_back(const float *__restrict__ dH, const __nv_bfloat16 *__restrict__ H, int B, float *db,
-                            __nv_bfloat16 *dZ, __nv_bfloat16 *dZt, float *dZf) {
-  const int k = threadIdx.x;
-  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
-  float s = 0.f;
-  for (int b = b0; b < b1; ++b) {
-    const float g = __bfloat162float(H[(size_t)b * kWid + k]) > 0.f ? dH[(size_t)b * kWid + k] : 0.f;
-    s += g;
-    if (dZ) {
-      const __nv_bfloat16 gb = __float2bfloat16_rn(g);
-      dZ[(size_t)b * kWid + k] = gb;
-      dZt[(size_t)k * B + b] = gb;
-    }
-    if (dZf) dZf[(size_t)b * kWid + k] = g;
-  }
-  atomicAdd(&db[k], s);
-}
-
-// Bias gradient of a layer whose dZ exists only in bf16 (layer 3): db[k] += sum_b dZ[b, k].
-__global__ void k_bias_back(const __nv_bfloat16 *__restrict__ dZ, int B, float *db) {
-  const int k = threadIdx.x;
-  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
-  float s = 0.f;
-  for (int b = b0; b < b1; ++b) s += __bfloat162float(dZ[(size_t)b * kWid + k]);
-  atomicAdd(&db[k], s);
-}
-
-// Layer-1 weight gradient: dW1[j, i] += sum_b dZ1[b, j] X[b, i].
-__global__ void k_back_in(const float *__restrict__ dZ1, const float *__restrict__ X, int B, float *G) {
-  const int j = threadIdx.x;
-  const int b0 = blockIdx.x * 32, b1 = min(B, b0 + 32);
-  float g[kIn];
-  for (int i = 0; i < kIn; ++i) g[i] = 0.f;
-  for (int b = b0; b < b1; ++b) {
-    const float dz = dZ1[(size_t)b * kWid + j];
-    for (int i = 0; i < kIn; ++i) g[i] = fmaf(dz, X[(size_t)b * kIn + i], g[i]);
-  }
-  for (int i = 0; i < kIn; ++i) atomicAdd(&G[oW1 + j * kIn + i], g[i]);
-}
-
-// Adam (Kingma and Ba 2015) on the FP32 master parameters; then the bf16 copies of
-// W2 and W3 (row-major, and transposed for the backward products).
-__global__ void k_adam(float *P, const float *G, float *m, float *v, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float g = G[i];
-  const float mi = b1 * m[i] + (1.f - b1) * g;
-  const float vi = b2 * v[i] + (1.f - b2) * g * g;
-  m[i] = mi;
-  v[i] = vi;
-  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-}
-
+// The BF16 copies of W2 and W3 (row-major, and transposed for the backward products).
 __global__ void k_refresh_bf16(const float *P, __nv_bfloat16 *W2b, __nv_bfloat16 *W3b, __nv_bfloat16 *W2t,
                                __nv_bfloat16 *W3t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -896,6 +757,477 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWid) : "memory");
 }
+
+// ------------------------------------------------------------ fused training step
+// One training step's forward and backward pass in one persistent kernel: CTA c takes the
+// 128-row tiles c, c + grid, ... of the batch.  Per tile, the six products of the 256-wide
+// layers run on the tensor core (Z2 = H1 W2^T, Z3 = H2 W3^T, the tile's dW3 = dZ3^T H2,
+// dH2 = dZ3 W3, its dW2 = dZ2^T H1 and dH1 = dZ2 W2), each into TMEM (the two 128-row halves
+// of a weight gradient side by side: 512 columns).  Their epilogues run the rest on the CUDA
+// cores, one tile row per thread: layer 1 before them, then layer 4, the loss and dY, the
+// ReLU masks, and the gradients of the biases and of the 7-wide layers, whose sums over the
+// tile's rows are taken across the warp's lanes by a fixed shuffle tree and across its four
+// row quarters in order.  The operands of the next product go through the training state's
+// scratch rows (L2-resident: H1, H2, dZ and their transposes), from which they are staged by
+// cp.async.  Each CTA sums its tiles' gradients in tile order into its own slot of part
+// (kPartStride floats: the parameters in the order of P, then the loss); k_reduce_adam sums
+// the slots in CTA order, so a step's gradient does not depend on timing.  The roundings are
+// those of the training arithmetic: H1, H2, H3, dZ3 and dZ2 are BF16 operands, everything
+// else FP32.
+constexpr int kTrThreads = 256;
+constexpr int kTrStageA = kTileM * kTileK * 2;     // 16 KB
+constexpr int kTrStageB = kMaxTileN * kTileK * 2;  // 32 KB
+constexpr int kTrFloats = kOut * kWid + 2 * kWid + 3 * kTileM * 8;
+constexpr int kTrSmem = 2 * (kTrStageA + kTrStageB) + kTrFloats * 4;  // 117 KB: one CTA per SM
+constexpr int kPartStride = (kParams + 1 + 3) & ~3;                   // floats per slot, 16-byte aligned
+constexpr int kRedQty = 8;  // column sums reduced at once (in the stage buffers, free in an epilogue)
+static_assert(kTrSmem <= 227 * 1024 && 2 * kTrSmem > 228 * 1024, "one training CTA per SM (it takes all of TMEM)");
+static_assert(kRedQty * 4 * kWid * 4 <= 2 * (kTrStageA + kTrStageB), "column-sum buffer in the stage buffers");
+static_assert(oW2 % 4 == 0 && oW3 % 4 == 0, "vector access to the weight-gradient slots");
+
+struct TrainArgs {
+  const float *X, *T;
+  int B;
+  float lam;
+  const float *P;
+  const __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
+  float *part;
+  __nv_bfloat16 *H1, *H2, *H1t, *H2t, *dZ, *dZt;
+  long long polls;
+};
+
+__device__ __forceinline__ uint4 pack8_bf16(const __nv_bfloat16 (&h)[8]) {
+  uint32_t w[4];
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 p = __halves2bfloat162(h[2 * i], h[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t *>(&p);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+// element j (0 or 1) of a packed BF16 pair as FP32, and as BF16
+__device__ __forceinline__ float bf16_of(uint32_t pair, int j) {
+  return __uint_as_float(j ? (pair & 0xFFFF0000u) : (pair << 16));
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_at(uint32_t pair, int j) {
+  return __ushort_as_bfloat16((unsigned short)(j ? (pair >> 16) : (pair & 0xFFFFu)));
+}
+
+// For every j, the sum of v[j] over the warp's 32 lanes; lane l returns the sum for j = l.  A
+// fixed tree (halves exchanged at distance 16, 8, 4, 2, 1), so the result does not depend on
+// timing.  v is clobbered.
+__device__ __forceinline__ float lane_sums(float (&v)[32]) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = (lane & (unsigned)w) != 0u;
+#pragma unroll
+    for (int j = 0; j < w; ++j) {
+      const float send = up ? v[j] : v[j + w];
+      const float keep = up ? v[j + w] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// All threads of the CTA: TMEM columns acc.. (128 lanes x N) = A[arow0 + 0..127][ak0 + 0..K-1] x
+// B[brow0 + 0..N-1][bk0 + 0..K-1]^T for row-major BF16 A and B (leading dimensions lda, ldb;
+// K a multiple of 64), the K stages double-buffered in sA / sB and signalled on bar[2], whose
+// phases ph tracks.  Returns with every MMA complete, or false once a wait ran out (abort
+// raised; the caller leaves, and the kernel's drain waits for what is in flight).
+__device__ bool tile_gemm(uint8_t *sA0, uint8_t *sA1, uint8_t *sB0, uint8_t *sB1, const __nv_bfloat16 *A, int lda,
+                          int arow0, int ak0, const __nv_bfloat16 *B, int ldb, int brow0, int bk0, int N, int K,
+                          uint32_t acc, uint64_t *bar, uint32_t (&ph)[2], volatile int *abort, long long polls) {
+  uint8_t *sA[2] = {sA0, sA1}, *sB[2] = {sB0, sB1};
+  const int nst = K / kTileK;
+  const uint32_t idesc = idesc_bf16(kTileM, N);
+  stage_tile(sA[0], A, lda, arow0, kTileM, arow0 + kTileM, ak0);
+  stage_tile(sB[0], B, ldb, brow0, N, brow0 + N, bk0);
+  cp_async_commit();
+  for (int s = 0; s < nst; ++s) {
+    const int buf = s & 1;
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA[buf]), b0 = smem_u32(sB[buf]);
+      for (int kk = 0; kk < kTileK / 16; ++kk)
+        mma_bf16(acc, smem_desc(a0 + kk * 256, 128, 1024), smem_desc(b0 + kk * 256, 128, 1024), idesc,
+                 (s > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&bar[buf]);
+    }
+    if (s + 1 < nst) {
+      const int nb = buf ^ 1;
+      if (s >= 1) {  // the MMAs of stage s - 1 read buffer nb
+        if (!mbar_wait(&bar[nb], ph[nb], polls)) *abort = 1;
+        ph[nb] ^= 1u;
+      }
+      __syncthreads();
+      if (*abort) return false;
+      stage_tile(sA[nb], A, lda, arow0, kTileM, arow0 + kTileM, ak0 + (s + 1) * kTileK);
+      stage_tile(sB[nb], B, ldb, brow0, N, brow0 + N, bk0 + (s + 1) * kTileK);
+      cp_async_commit();
+    }
+  }
+  // the commits of the last two stages (or the only one) have not been waited for yet
+  for (int s = nst >= 2 ? nst - 2 : 0; s < nst; ++s) {
+    if (!mbar_wait(&bar[s & 1], ph[s & 1], polls)) *abort = 1;
+    ph[s & 1] ^= 1u;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return !*abort;
+}
+
+// Writes 32 consecutive BF16 columns c0.. of one row: row-major (dst + c0) and transposed
+// (column c at dstT + c * ld).
+__device__ __forceinline__ void store_row32(__nv_bfloat16 *dst, __nv_bfloat16 *dstT, size_t ld, int c0,
+                                            const uint32_t (&pk)[16]) {
+  uint4 *d = reinterpret_cast<uint4 *>(dst + c0);
+  for (int u = 0; u < 4; ++u) d[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+  for (int j = 0; j < 32; ++j) dstT[(size_t)(c0 + j) * ld] = bf16_at(pk[j >> 1], j & 1);
+}
+
+// The tile's dW (two 128-row halves in TMEM columns 0..255 and 256..511) into the slot's W
+// (added to what the CTA's earlier tiles left there).
+__device__ __forceinline__ void add_weight_grad(uint32_t tl, int half, int row, float *Wslot, bool first) {
+  for (int mh = 0; mh < 2; ++mh)
+    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32_nowait(tl + (uint32_t)(mh * kWid + c0), v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float4 *g = reinterpret_cast<float4 *>(Wslot + (size_t)(mh * kTileM + row) * kWid + c0);
+      for (int u = 0; u < 8; ++u) {
+        float4 s = make_float4(__uint_as_float(v[4 * u]), __uint_as_float(v[4 * u + 1]),
+                               __uint_as_float(v[4 * u + 2]), __uint_as_float(v[4 * u + 3]));
+        if (!first) {
+          const float4 o = g[u];
+          s = make_float4(o.x + s.x, o.y + s.y, o.z + s.z, o.w + s.w);
+        }
+        g[u] = s;
+      }
+    }
+}
+
+__global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  uint8_t *sA0 = tsm, *sA1 = tsm + kTrStageA, *sB0 = tsm + 2 * kTrStageA, *sB1 = sB0 + kTrStageB;
+  float *red = reinterpret_cast<float *>(tsm);  // [kRedQty][4 row quarters][256 columns], in an epilogue
+  float *w4s = reinterpret_cast<float *>(tsm + 2 * (kTrStageA + kTrStageB));  // [7][256]
+  float *b2s = w4s + kOut * kWid, *b3s = b2s + kWid;
+  float *xs = b3s + kWid, *dys = xs + kTileM * 8, *part4 = dys + kTileM * 8;  // [128][8] each
+  __shared__ uint64_t bar[2], drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ float loss_w[kTrThreads / 32];
+  volatile int *abortp = &abort_flag;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  // epilogues: warp w reads TMEM lanes 32 (w % 4) .. (its row quarter q) and the column half w / 4
+  const int q = warp & 3, half = warp >> 2, row = q * 32 + lane;
+  const int Bn = a.B, ntiles = Bn / kTileM;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(2 * kWid)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int i = t; i < kOut * kWid; i += kTrThreads) w4s[i] = a.P[oW4 + i];
+  b2s[t] = a.P[ob2 + t];
+  b3s[t] = a.P[ob3 + t];
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+  uint32_t ph[2] = {0u, 0u};
+  float *slot = a.part + (size_t)blockIdx.x * kPartStride;
+  // this thread's share of the small gradients, summed over the CTA's tiles: column t of
+  // layers 1 (dW1 row, db1), 2 (db2), 3 (db3) and 4 (dW4 column; db4 for t < 7)
+  float gw1[kIn], gw4[kOut], gb1 = 0.f, gb2 = 0.f, gb3 = 0.f, gb4 = 0.f, lsum = 0.f;
+  for (int i = 0; i < kIn; ++i) gw1[i] = 0.f;
+  for (int o = 0; o < kOut; ++o) gw4[o] = 0.f;
+  // column t's sum of quantity k over the four row quarters of red, in order
+  auto red_sum = [&](int k) {
+    float s = 0.f;
+    for (int qq = 0; qq < 4; ++qq) s += red[(k * 4 + qq) * kWid + t];
+    return s;
+  };
+  bool first = true;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, first = false) {
+    const int m0 = tile * kTileM;
+    for (int i = t; i < kTileM * 8; i += kTrThreads) {
+      const int r = i >> 3, k = i & 7;
+      xs[i] = k < kIn ? a.X[(size_t)(m0 + r) * kIn + k] : 0.f;
+    }
+    __syncthreads();
+    // ---- layer 1 (FP32, K = 7): H1 = relu(X W1^T + b1), BF16 rows and transposed; unit j = t
+    {
+      float w1[kIn];
+      for (int k = 0; k < kIn; ++k) w1[k] = a.P[oW1 + t * kIn + k];
+      const float b1 = a.P[ob1 + t];
+      for (int r0 = 0; r0 < kTileM; r0 += 8) {
+        __nv_bfloat16 hv[8];
+        for (int u = 0; u < 8; ++u) {
+          float z = b1;
+          for (int k = 0; k < kIn; ++k) z = fmaf(w1[k], xs[(r0 + u) * 8 + k], z);
+          hv[u] = __float2bfloat16_rn(fmaxf(z, 0.f));
+          a.H1[(size_t)(m0 + r0 + u) * kWid + t] = hv[u];
+        }
+        *reinterpret_cast<uint4 *>(a.H1t + (size_t)t * Bn + m0 + r0) = pack8_bf16(hv);
+      }
+    }
+    __syncthreads();
+    // ---- Z2 = H1 W2^T; H2 = relu(Z2 + b2), BF16 rows and transposed
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.H1, kWid, m0, 0, a.W2b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
+                   a.polls))
+      break;
+    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+      uint32_t v[32], pk[16];
+      tmem_ld32_nowait(tl + (uint32_t)c0, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int j = 0; j < 16; ++j)
+        pk[j] = pack_bf16_relu(__uint_as_float(v[2 * j]) + b2s[c0 + 2 * j],
+                               __uint_as_float(v[2 * j + 1]) + b2s[c0 + 2 * j + 1]);
+      store_row32(a.H2 + (size_t)(m0 + row) * kWid, a.H2t + m0 + row, Bn, c0, pk);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // ---- Z3 = H2 W3^T; H3 = relu(Z3 + b3) (BF16); layer 4 (FP32) from the BF16 H3
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.H2, kWid, m0, 0, a.W3b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
+                   a.polls))
+      break;
+    {
+      float y[kOut];
+      for (int o = 0; o < kOut; ++o) y[o] = 0.f;
+      for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32_nowait(tl + (uint32_t)c0, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int j = 0; j < 32; j += 2) {
+          const uint32_t pk = pack_bf16_relu(__uint_as_float(v[j]) + b3s[c0 + j],
+                                             __uint_as_float(v[j + 1]) + b3s[c0 + j + 1]);
+          for (int u = 0; u < 2; ++u)
+            for (int o = 0; o < kOut; ++o) y[o] = fmaf(w4s[o * kWid + c0 + j + u], bf16_of(pk, u), y[o]);
+        }
+      }
+      if (half == 1)
+        for (int o = 0; o < kOut; ++o) part4[row * 8 + o] = y[o];
+      __syncthreads();
+      // the loss and its gradient dY (outputs 0..5: mean squared error against T; output 6: the
+      // log squared error of the same row, weighted by lam), by the column-half-0 thread of each row
+      if (half == 0) {
+        float Y[kOut];
+        for (int o = 0; o < kOut; ++o) Y[o] = (y[o] + part4[row * 8 + o]) + a.P[ob4 + o];
+        const float *Tr = a.T + (size_t)(m0 + row) * 6;
+        float se = 0.f;
+        for (int o = 0; o < 6; ++o) {
+          const float d = Y[o] - Tr[o];
+          se = fmaf(d, d, se);
+          dys[row * 8 + o] = 2.f * d / (6.f * Bn);
+        }
+        const float e = logf(se + 1e-6f);
+        const float d6 = Y[6] - e;
+        dys[row * 8 + 6] = 2.f * a.lam * d6 / Bn;
+        lsum += se / (6.f * Bn) + a.lam * d6 * d6 / Bn;
+      }
+      __syncthreads();
+    }
+    // ---- layer 4 backward from the same accumulator: dZ3 = bf16(dH3 [H3 > 0]) with dH3 = dY W4 (rows
+    // and transposed); the tile's dW4 = dY^T H3 and db3 = sum of dZ3 as column sums
+    {
+      float dy[kOut];
+      for (int o = 0; o < kOut; ++o) dy[o] = dys[row * 8 + o];
+      for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+        uint32_t v[32], pz[16];
+        tmem_ld32_nowait(tl + (uint32_t)c0, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float h[32], z[32], w[32];
+        for (int j = 0; j < 32; j += 2) {
+          const uint32_t pk = pack_bf16_relu(__uint_as_float(v[j]) + b3s[c0 + j],
+                                             __uint_as_float(v[j + 1]) + b3s[c0 + j + 1]);
+          h[j] = bf16_of(pk, 0);
+          h[j + 1] = bf16_of(pk, 1);
+        }
+        for (int j = 0; j < 32; j += 2) {
+          __nv_bfloat16 zb[2];
+          for (int u = 0; u < 2; ++u) {
+            float dh = 0.f;
+            for (int o = 0; o < kOut; ++o) dh = fmaf(dy[o], w4s[o * kWid + c0 + j + u], dh);
+            zb[u] = __float2bfloat16_rn(h[j + u] > 0.f ? dh : 0.f);
+            z[j + u] = __bfloat162float(zb[u]);
+          }
+          const __nv_bfloat162 p2 = __halves2bfloat162(zb[0], zb[1]);
+          pz[j >> 1] = *reinterpret_cast<const uint32_t *>(&p2);
+        }
+        store_row32(a.dZ + (size_t)(m0 + row) * kWid, a.dZt + m0 + row, Bn, c0, pz);
+        for (int o = 0; o < kOut; ++o) {
+          for (int j = 0; j < 32; ++j) w[j] = dy[o] * h[j];
+          red[(o * 4 + q) * kWid + c0 + lane] = lane_sums(w);
+        }
+        red[(7 * 4 + q) * kWid + c0 + lane] = lane_sums(z);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      for (int o = 0; o < kOut; ++o) gw4[o] += red_sum(o);
+      gb3 += red_sum(7);
+      if (t < kOut)
+        for (int r = 0; r < kTileM; ++r) gb4 += dys[r * 8 + t];
+      __syncthreads();
+    }
+    // ---- the tile's dW3 = dZ3^T H2 (K = its 128 rows), added into the CTA's slot
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, 0, m0, a.H2t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp,
+                   a.polls))
+      break;
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, kTileM, m0, a.H2t, Bn, 0, m0, kWid, kTileM, tmem + kWid, bar, ph,
+                   abortp, a.polls))
+      break;
+    add_weight_grad(tl, half, row, slot + oW3, first);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // ---- dH2 = dZ3 W3; dZ2 = bf16(dH2 [H2 > 0]) (rows and transposed); db2 = column sums of the FP32 values
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZ, kWid, m0, 0, a.W3t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
+                   a.polls))
+      break;
+    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+      uint32_t v[32], pz[16];
+      tmem_ld32_nowait(tl + (uint32_t)c0, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const uint4 *hr = reinterpret_cast<const uint4 *>(a.H2 + (size_t)(m0 + row) * kWid + c0);
+      float g[32];
+      for (int u = 0; u < 4; ++u) {
+        const uint4 hb = hr[u];
+        const uint32_t hw[4] = {hb.x, hb.y, hb.z, hb.w};
+        for (int j = 0; j < 8; ++j)
+          g[8 * u + j] = bf16_of(hw[j >> 1], j & 1) > 0.f ? __uint_as_float(v[8 * u + j]) : 0.f;
+      }
+      for (int j = 0; j < 32; j += 2) {
+        const __nv_bfloat162 p2 = __halves2bfloat162(__float2bfloat16_rn(g[j]), __float2bfloat16_rn(g[j + 1]));
+        pz[j >> 1] = *reinterpret_cast<const uint32_t *>(&p2);
+      }
+      store_row32(a.dZ + (size_t)(m0 + row) * kWid, a.dZt + m0 + row, Bn, c0, pz);
+      red[q * kWid + c0 + lane] = lane_sums(g);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    gb2 += red_sum(0);
+    __syncthreads();
+    // ---- the tile's dW2 = dZ2^T H1, as dW3
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, 0, m0, a.H1t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp,
+                   a.polls))
+      break;
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, kTileM, m0, a.H1t, Bn, 0, m0, kWid, kTileM, tmem + kWid, bar, ph,
+                   abortp, a.polls))
+      break;
+    add_weight_grad(tl, half, row, slot + oW2, first);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // ---- dH1 = dZ2 W2; dZ1 = dH1 [H1 > 0] (FP32); db1 and dW1 = dZ1^T X as column sums
+    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZ, kWid, m0, 0, a.W2t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
+                   a.polls))
+      break;
+    {
+      float xr[kIn];
+      for (int i = 0; i < kIn; ++i) xr[i] = xs[row * 8 + i];
+      for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32_nowait(tl + (uint32_t)c0, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const uint4 *hr = reinterpret_cast<const uint4 *>(a.H1 + (size_t)(m0 + row) * kWid + c0);
+        float g[32], w[32];
+        for (int u = 0; u < 4; ++u) {
+          const uint4 hb = hr[u];
+          const uint32_t hw[4] = {hb.x, hb.y, hb.z, hb.w};
+          for (int j = 0; j < 8; ++j)
+            g[8 * u + j] = bf16_of(hw[j >> 1], j & 1) > 0.f ? __uint_as_float(v[8 * u + j]) : 0.f;
+        }
+        for (int i = 0; i < kIn; ++i) {
+          for (int j = 0; j < 32; ++j) w[j] = g[j] * xr[i];
+          red[((1 + i) * 4 + q) * kWid + c0 + lane] = lane_sums(w);
+        }
+        red[q * kWid + c0 + lane] = lane_sums(g);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      gb1 += red_sum(0);
+      for (int i = 0; i < kIn; ++i) gw1[i] += red_sum(1 + i);
+      __syncthreads();
+    }
+  }
+  if (!*abortp && blockIdx.x < ntiles) {
+    // the CTA's small gradients and loss into its slot
+    for (int i = 0; i < kIn; ++i) slot[oW1 + t * kIn + i] = gw1[i];
+    slot[ob1 + t] = gb1;
+    slot[ob2 + t] = gb2;
+    slot[ob3 + t] = gb3;
+    for (int o = 0; o < kOut; ++o) slot[oW4 + o * kWid + t] = gw4[o];
+    if (t < kOut) slot[ob4 + t] = gb4;
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+    if (lane == 0) loss_w[warp] = lsum;
+    __syncthreads();
+    if (t == 0) {
+      float s = 0.f;
+      for (int w = 0; w < kTrThreads / 32; ++w) s += loss_w[w];
+      slot[kParams] = s;
+    }
+  }
+  // every MMA issued has completed before the tensor memory is released
+  cp_async_wait_all();
+  if (t == 0) mma_commit(&drain);
+  if (!mbar_wait(&drain, 0u)) *abortp = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (t == 0 && *abortp) atomicOr(&g_mlp_error, kErrTimeout);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kWid) : "memory");
+}
+
+// The step's gradient and loss: each parameter's slots summed in CTA order (so the result does
+// not depend on timing), into G and *loss when set.  With lr > 0, an Adam step (Kingma and Ba
+// 2015) on the FP32 master parameters, and the BF16 copies of W2 and W3 (row-major and
+// transposed) that the next step's products read.  Nothing is written while the error word
+// is set: the slots of a training kernel that gave up are incomplete.
+__global__ void k_reduce_adam(const float *__restrict__ part, int nparts, float *G, float *loss, float *P, float *m,
+                              float *v, float lr, float b1, float b2, float eps, float c1, float c2,
+                              __nv_bfloat16 *W2b, __nv_bfloat16 *W3b, __nv_bfloat16 *W2t, __nv_bfloat16 *W3t) {
+  if (*(volatile unsigned *)&g_mlp_error) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && loss) {
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += part[(size_t)c * kPartStride + kParams];
+    *loss = s;
+  }
+  if (i >= kParams) return;
+  float g = 0.f;
+  for (int c = 0; c < nparts; ++c) g += part[(size_t)c * kPartStride + i];
+  if (G) G[i] = g;
+  if (!(lr > 0.f)) return;
+  const float mi = b1 * m[i] + (1.f - b1) * g;
+  const float vi = b2 * v[i] + (1.f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  const float p = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  P[i] = p;
+  if (i >= oW2 && i < ob2) {
+    const int e = i - oW2, r = e / kWid, c = e % kWid;
+    const __nv_bfloat16 w = __float2bfloat16_rn(p);
+    W2b[e] = w;
+    W2t[c * kWid + r] = w;
+  } else if (i >= oW3 && i < ob3) {
+    const int e = i - oW3, r = e / kWid, c = e % kWid;
+    const __nv_bfloat16 w = __float2bfloat16_rn(p);
+    W3b[e] = w;
+    W3t[c * kWid + r] = w;
+  }
+}
 }  // namespace
 
 // Polls of the work's own barrier waits for a launch: the kernel's default, or the
@@ -962,12 +1294,14 @@ namespace {
 
 struct ExpmapDev {
   int bmax;
+  int sms;     // CTAs of the training kernel at most (one per SM)
   long long step;
-  float *P, *G, *m, *v;
+  float *P, *m, *v;
   __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
   __nv_bfloat16 *Wp;  // the operands of the persistent inference kernel, packed by k_pack_chunks
-  __nv_bfloat16 *H1, *H2, *H3, *H1t, *H2t, *H3t, *dZ, *dZt;
-  float *Y, *dY, *dH, *dZ1, *loss;
+  bool wp_stale;      // P has changed since Wp was packed
+  __nv_bfloat16 *H1, *H2, *H1t, *H2t, *dZ, *dZt;  // scratch rows of the training step
+  float *part;  // the training CTAs' gradient slots, kPartStride floats each
 };
 
 template <typename T>
@@ -976,55 +1310,57 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_all(ExpmapDev &d) {
-  void *ptrs[] = {d.P, d.G, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.Wp, d.H1, d.H2, d.H3, d.H1t, d.H2t, d.H3t,
-                  d.dZ, d.dZt, d.Y, d.dY, d.dH, d.dZ1, d.loss};
+  void *ptrs[] = {d.P, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.Wp, d.H1, d.H2, d.H1t, d.H2t, d.dZ,
+                  d.dZt, d.part};
   for (void *q : ptrs) cudaFree(q);
 }
 
-// Training forward pass over B rows: keeps H1..H3 and their transposes for back-propagation.
-cudaError_t forward(const ExpmapDev &d, const float *X, int B, float *Y, cudaStream_t st) {
-  k_layer_in<<<B, kWid, 0, st>>>(X, B, d.P, d.H1, d.H1t);
-  cudaError_t e = cudaGetLastError();
+// Forward and backward pass over B rows (B a multiple of 128): the CTAs' gradient slots; the
+// grid (one CTA per SM, at most one per tile) depends only on B and the device, so the
+// slots' sum is the same on every call.
+cudaError_t train_pass(ExpmapDev &d, const float *X, const float *T, int B, float lam, cudaStream_t st,
+                       int *nparts) {
+  const int tiles = B / kTileM, grid = tiles < d.sms ? tiles : d.sms;
+  cudaError_t e = cudaFuncSetAttribute(k_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmem);
   if (e != cudaSuccess) return e;
-  e = launch_gemm_bf16(d.H1, d.W2b, B, kWid, kWid, 1, d.P + ob2, 1, d.H2, kWid, d.H2t, B, st);
-  if (e != cudaSuccess) return e;
-  e = launch_gemm_bf16(d.H2, d.W3b, B, kWid, kWid, 1, d.P + ob3, 1, d.H3, kWid, d.H3t, B, st);
-  if (e != cudaSuccess) return e;
-  k_layer_out<<<(B + 7) / 8, 256, 0, st>>>(d.H3, B, d.P, Y);
+  TrainArgs a;
+  a.X = X;
+  a.T = T;
+  a.B = B;
+  a.lam = lam;
+  a.P = d.P;
+  a.W2b = d.W2b;
+  a.W3b = d.W3b;
+  a.W2t = d.W2t;
+  a.W3t = d.W3t;
+  a.part = d.part;
+  a.H1 = d.H1;
+  a.H2 = d.H2;
+  a.H1t = d.H1t;
+  a.H2t = d.H2t;
+  a.dZ = d.dZ;
+  a.dZt = d.dZt;
+  a.polls = wait_polls(kSpinLimit);
+  k_train_tile<<<grid, kTrThreads, kTrSmem, st>>>(a);
+  *nparts = grid;
   return cudaGetLastError();
 }
 
-// Gradients of the loss w.r.t. every parameter into d.G (zeroed first); loss into d.loss.
-cudaError_t gradients(ExpmapDev &d, const float *X, const float *T, int B, float lam, cudaStream_t st) {
-  cudaError_t e = forward(d, X, B, d.Y, st);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(d.G, 0, sizeof(float) * kParams, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(d.loss, 0, sizeof(float), st)) != cudaSuccess) return e;
-  k_loss_grad<<<(B + 255) / 256, 256, 0, st>>>(d.Y, T, B, lam, d.dY, d.loss);
-  const unsigned rb = (unsigned)((B + 31) / 32);
-  k_back_out<<<rb, kWid, 0, st>>>(d.dY, d.H3, B, d.P, d.G, d.dZ, d.dZt);
-  k_bias_back<<<rb, kWid, 0, st>>>(d.dZ, B, d.G + ob3);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int splits = B >= 2048 ? 16 : 1;
-  // dW3 = dZ3^T H2, dH2 = dZ3 W3
-  e = launch_gemm_bf16(d.dZt, d.H2t, kWid, kWid, B, splits, nullptr, 2, d.G + oW3, kWid, nullptr, 0, st);
-  if (e != cudaSuccess) return e;
-  e = launch_gemm_bf16(d.dZ, d.W3t, B, kWid, kWid, 1, nullptr, 0, d.dH, kWid, nullptr, 0, st);
-  if (e != cudaSuccess) return e;
-  k_relu_back<<<rb, kWid, 0, st>>>(d.dH, d.H2, B, d.G + ob2, d.dZ, d.dZt, nullptr);
-  // dW2 = dZ2^T H1, dH1 = dZ2 W2
-  e = launch_gemm_bf16(d.dZt, d.H1t, kWid, kWid, B, splits, nullptr, 2, d.G + oW2, kWid, nullptr, 0, st);
-  if (e != cudaSuccess) return e;
-  e = launch_gemm_bf16(d.dZ, d.W2t, B, kWid, kWid, 1, nullptr, 0, d.dH, kWid, nullptr, 0, st);
-  if (e != cudaSuccess) return e;
-  k_relu_back<<<rb, kWid, 0, st>>>(d.dH, d.H1, B, d.G + ob1, nullptr, nullptr, d.dZ1);
-  k_back_in<<<rb, kWid, 0, st>>>(d.dZ1, X, B, d.G);
+// The slots' sum into G and loss (device pointers, each may be null); with lr > 0 also the
+// Adam step of step count d.step and the refreshed BF16 weight copies.
+cudaError_t reduce_adam(ExpmapDev &d, int nparts, float *G, float *loss, float lr, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = lr > 0.f ? 1.f - powf(b1, (float)d.step) : 1.f, c2 = lr > 0.f ? 1.f - powf(b2, (float)d.step) : 1.f;
+  k_reduce_adam<<<(kParams + 255) / 256, 256, 0, st>>>(d.part, nparts, G, loss, d.P, d.m, d.v, lr, b1, b2, 1e-8f,
+                                                      c1, c2, d.W2b, d.W3b, d.W2t, d.W3t);
+  if (lr > 0.f) d.wp_stale = true;
   return cudaGetLastError();
 }
 
 cudaError_t refresh(ExpmapDev &d, cudaStream_t st) {
   k_refresh_bf16<<<(kWid * kWid + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.W2t, d.W3t);
   k_pack_chunks<<<(kPackedElems + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.Wp);
+  d.wp_stale = false;
   return cudaGetLastError();
 }
 
@@ -1052,8 +1388,17 @@ struct rgeo_expmap {
 
 namespace rgeo {
 // Inference over n rows: the persistent fused kernel (no host sync).
+// The packed operands are brought up to date first when training steps have changed P since
+// (stream-ordered, like the steps themselves).
 cudaError_t expmap_infer(const rgeo_expmap *x, const float *X, long long n, float *Y, cudaStream_t st) {
-  return launch_mlp_infer_ws(X, n, x->d.P, x->d.Wp, Y, st);
+  ExpmapDev &d = const_cast<rgeo_expmap *>(x)->d;
+  if (d.wp_stale) {
+    k_pack_chunks<<<(kPackedElems + 255) / 256, 256, 0, st>>>(d.P, d.W2b, d.W3b, d.Wp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    d.wp_stale = false;
+  }
+  return launch_mlp_infer_ws(X, n, d.P, d.Wp, Y, st);
 }
 }  // namespace rgeo
 
@@ -1074,7 +1419,6 @@ rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **o
   d.bmax = max_batch;
   const size_t B = (size_t)max_batch, HW = B * kWid;
   cudaError_t e = dalloc(&d.P, kParams);
-  if (e == cudaSuccess) e = dalloc(&d.G, kParams);
   if (e == cudaSuccess) e = dalloc(&d.m, kParams);
   if (e == cudaSuccess) e = dalloc(&d.v, kParams);
   if (e == cudaSuccess) e = dalloc(&d.W2b, (size_t)kWid * kWid);
@@ -1082,14 +1426,16 @@ rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **o
   if (e == cudaSuccess) e = dalloc(&d.W2t, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.W3t, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.Wp, (size_t)kPackedElems);
-  __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H3, &d.H1t, &d.H2t, &d.H3t, &d.dZ, &d.dZt};
+  __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H1t, &d.H2t, &d.dZ, &d.dZt};
   for (auto b : bufs)
     if (e == cudaSuccess) e = dalloc(b, HW);
-  if (e == cudaSuccess) e = dalloc(&d.Y, B * kOut);
-  if (e == cudaSuccess) e = dalloc(&d.dY, B * kOut);
-  if (e == cudaSuccess) e = dalloc(&d.dH, HW);
-  if (e == cudaSuccess) e = dalloc(&d.dZ1, HW);
-  if (e == cudaSuccess) e = dalloc(&d.loss, 1);
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    const int slots = std::min(max_batch / kTileM, d.sms);
+    e = dalloc(&d.part, (size_t)slots * kPartStride);
+  }
   if (e == cudaSuccess) {
     k_init<<<(kParams + 255) / 256, 256>>>(d.P, (unsigned long long)seed);
     e = cudaGetLastError();
@@ -1129,29 +1475,26 @@ rgeo_status rgeo_expmap_gradients(rgeo_expmap *x, const float *inputs, const flo
   if (batch < 128 || batch % 128 != 0 || batch > x->d.bmax)
     return mlp_fail(RGEO_EINVAL, "rgeo_expmap_gradients: batch must be a multiple of 128, at most max_batch");
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  rgeo_status s = mlp_cuda(gradients(x->d, inputs, targets, batch, kErrWeight, st), "rgeo_expmap_gradients");
-  if (s != RGEO_OK) return s;
-  if (grads) s = mlp_cuda(cudaMemcpyAsync(grads, x->d.G, sizeof(float) * kParams, cudaMemcpyDeviceToDevice, st),
-                          "rgeo_expmap_gradients: copy");
-  if (s == RGEO_OK && loss)
-    s = mlp_cuda(cudaMemcpyAsync(loss, x->d.loss, sizeof(float), cudaMemcpyDeviceToDevice, st), "rgeo_expmap_gradients");
+  int nparts = 0;
+  rgeo_status s = mlp_cuda(train_pass(x->d, inputs, targets, batch, kErrWeight, st, &nparts), "rgeo_expmap_gradients");
+  if (s == RGEO_OK) s = mlp_cuda(reduce_adam(x->d, nparts, grads, loss, 0.f, st), "rgeo_expmap_gradients: sum");
   return s;
 }
 
 rgeo_status rgeo_expmap_train_step(rgeo_expmap *x, const float *inputs, const float *targets, int32_t batch,
                                    float lr, float *loss, void *cuda_stream) {
   using namespace rgeo;
-  rgeo_status s = rgeo_expmap_gradients(x, inputs, targets, batch, nullptr, loss, cuda_stream);
-  if (s != RGEO_OK) return s;
-  if (!(lr > 0.f)) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_train_step: lr must be > 0");
+  set_last_error("");
+  if (!x || !inputs || !targets) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_train_step: NULL argument");
+  if (batch < 128 || batch % 128 != 0 || batch > x->d.bmax)
+    return mlp_fail(RGEO_EINVAL, "rgeo_expmap_train_step: batch must be a multiple of 128, at most max_batch");
+  if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(RGEO_EINVAL, "rgeo_expmap_train_step: lr must be > 0");
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  int nparts = 0;
+  rgeo_status s = mlp_cuda(train_pass(x->d, inputs, targets, batch, kErrWeight, st, &nparts), "rgeo_expmap_train_step");
+  if (s != RGEO_OK) return s;
   x->d.step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - powf(b1, (float)x->d.step), c2 = 1.f - powf(b2, (float)x->d.step);
-  k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(x->d.P, x->d.G, x->d.m, x->d.v, kParams, lr, b1, b2, 1e-8f, c1, c2);
-  s = mlp_cuda(cudaGetLastError(), "rgeo_expmap_train_step: adam");
-  if (s == RGEO_OK) s = mlp_cuda(refresh(x->d, st), "rgeo_expmap_train_step: refresh");
-  return s;
+  return mlp_cuda(reduce_adam(x->d, nparts, nullptr, loss, lr, st), "rgeo_expmap_train_step: adam");
 }
 
 rgeo_status rgeo_expmap_get_params(const rgeo_expmap *x, float *host, int64_t n) {

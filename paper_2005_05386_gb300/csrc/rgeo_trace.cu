@@ -1633,21 +1633,32 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
 // direction d0 + alpha e1 + beta e2, forward-difference Jacobian), and the hit is lit
 // when it converged, the Riemannian cosine n.u / sqrt(n^T g^-1 n) is positive and the
 // geodesic meets no object on the way; colour albedo (0.1 + 0.9 cos) lit, albedo 0.1 not.
-// One thread per pixel, pixels in 8 x 4 tiles; each lane sums the bumps of its own cull
-// cell (no warp collective), so lanes may follow their own geodesics.
+// Each hit takes a group of three lanes (ten hits per warp, hits in 8 x 4 pixel tiles): in
+// every Gauss-Newton step, lane 0 of the group marches the light geodesic of the current
+// direction while lanes 1 and 2 march those of its two difference directions, so a step
+// takes the time of one march rather than three (the slowest solves set the kernel's time).
+// The lanes then exchange their miss vectors and take the same decision and update, those of
+// the solve with its marches one after another, so the result is that solve's bit for bit;
+// the difference marches of the step that converges are made and not used.  Each lane sums
+// the bumps of its own cull cell (no warp collective): lanes follow their own geodesics.
+constexpr unsigned kIllumGroups = 10;  // groups of three lanes per warp
+
 template <int MK, int INTEG>
 __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const LightParams LP) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
   const float4 *sb = smem;
   const float4 *ss = smem + nb4;
-  const unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u, grp = lane / 3u, role = lane - 3u * grp;
+  if (grp >= kIllumGroups) return;
+  const unsigned item = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kIllumGroups + grp;
   int p;
   if (item >= P.n_items || !item_pixel(P, item, p)) return;
+  const unsigned gmask = 7u << (3u * grp), base = 3u * grp;  // the group's lanes, its lane 0
   const size_t N = (size_t)P.W * P.H;
   const int id = P.id[p];
   if (id < 0) {
-    if (LP.lit) LP.lit[p] = 0;
+    if (role == 0 && LP.lit) LP.lit[p] = 0;
     return;
   }
   const F3 Ph = f3(P.hit[p], P.hit[N + p], P.hit[2 * N + p]);
@@ -1666,26 +1677,38 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
   F3 u = d0;
   WorkCount evals;  // work counters
   for (int k = 0;; k++) {
-    const F3 d = normalize(axpy(be, b2, axpy(al, b1, d0)));
-    F3 e;
-    if (!shoot<MK, INTEG, false>(P, sb, ss, L, q, d, e, u, blocked, evals)) break;
-    if (sqrtf(dot(e, e)) <= LP.tol) {
+    // this lane's march: the current direction (role 0) or its difference in alpha (1) or beta (2)
+    const float aa = role == 1u ? al + LP.delta : al, bb = role == 2u ? be + LP.delta : be;
+    F3 e, ud;
+    WorkCount w;  // this march's work: counted when the solve uses the march
+    const bool ok = shoot<MK, INTEG, false>(P, sb, ss, L, q, normalize(axpy(bb, b2, axpy(aa, b1, d0))), e, ud,
+                                            blocked, w);
+    F3 eg[3];
+    bool okg[3];
+    for (unsigned j = 0; j < 3u; ++j) {
+      eg[j] = f3(__shfl_sync(gmask, e.x, base + j), __shfl_sync(gmask, e.y, base + j),
+                 __shfl_sync(gmask, e.z, base + j));
+      okg[j] = __shfl_sync(gmask, ok ? 1 : 0, base + j) != 0;
+    }
+    const bool conv = okg[0] && sqrtf(dot(eg[0], eg[0])) <= LP.tol;
+    const bool more = okg[0] && !conv && k != LP.iters;  // the step goes on to the differences
+    if (role == 0u || (more && (role == 1u || okg[1]))) {
+      evals.evals += w.evals;
+      evals.slots += w.slots;
+    }
+    if (!okg[0]) break;
+    u = ud;  // role 0: the g-unit tangent of the current direction
+    if (conv) {
       lit = true;
       break;
     }
-    if (k == LP.iters) break;
-    F3 J0, J1, ud, ee;
-    if (!shoot<MK, INTEG, false>(P, sb, ss, L, q, normalize(axpy(be, b2, axpy(al + LP.delta, b1, d0))), ee, ud,
-                                 blocked, evals))
-      break;
-    J0 = (1.f / LP.delta) * (ee - e);
-    if (!shoot<MK, INTEG, false>(P, sb, ss, L, q, normalize(axpy(be + LP.delta, b2, axpy(al, b1, d0))), ee, ud,
-                                 blocked, evals))
-      break;
-    J1 = (1.f / LP.delta) * (ee - e);
+    if (!more || !okg[1]) break;
+    const F3 J0 = (1.f / LP.delta) * (eg[1] - eg[0]);
+    if (!okg[2]) break;
+    const F3 J1 = (1.f / LP.delta) * (eg[2] - eg[0]);
     // Gauss-Newton: (J^T J) step = -J^T e, by Cramer's rule
     const float A00 = dot(J0, J0), A01 = dot(J0, J1), A11 = dot(J1, J1);
-    const float r0 = -dot(J0, e), r1 = -dot(J1, e);
+    const float r0 = -dot(J0, eg[0]), r1 = -dot(J1, eg[0]);
     const float det = A00 * A11 - A01 * A01;
     if (!(det > 1e-12f * (A00 * A11))) break;
     float s0 = (r0 * A11 - r1 * A01) / det, s1 = (A00 * r1 - A01 * r0) / det;
@@ -1697,21 +1720,23 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
     al += s0;
     be += s1;
   }
-  float cosg = 0.f;
-  if (lit) {
-    cosg = dot(n, u) * rsqrtf(metric_inv_nn<MK>(P, sb, q, n));
-    if (!(cosg > 0.f)) lit = false;
+  if (role == 0u) {
+    float cosg = 0.f;
+    if (lit) {
+      cosg = dot(n, u) * rsqrtf(metric_inv_nn<MK>(P, sb, q, n));
+      if (!(cosg > 0.f)) lit = false;
+    }
+    if (lit) {
+      F3 e, uu;
+      shoot<MK, INTEG, true>(P, sb, ss, L, q, normalize(axpy(be, b2, axpy(al, b1, d0))), e, uu, blocked, evals);
+      if (blocked) lit = false;
+    }
+    const int obj = id < P.S ? id : P.S;
+    const float inten = lit ? fmaf(0.9f, cosg, 0.1f) : 0.1f;
+    P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
+                            to_u8(P.albedo[3 * obj + 2] * inten), 255);
+    if (LP.lit) LP.lit[p] = lit ? 1 : 0;
   }
-  if (lit) {
-    F3 e, uu;
-    shoot<MK, INTEG, true>(P, sb, ss, L, q, normalize(axpy(be, b2, axpy(al, b1, d0))), e, uu, blocked, evals);
-    if (blocked) lit = false;
-  }
-  const int obj = id < P.S ? id : P.S;
-  const float inten = lit ? fmaf(0.9f, cosg, 0.1f) : 0.1f;
-  P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
-                          to_u8(P.albedo[3 * obj + 2] * inten), 255);
-  if (LP.lit) LP.lit[p] = lit ? 1 : 0;
   if (P.bump_evals) atomicAdd(P.bump_evals, evals.evals);
   if (P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
 }
@@ -2658,7 +2683,8 @@ cudaError_t launch_illuminate_t(const TraceParams &p, const LightParams &l, cuda
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_illuminate<MK, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (p.n_items + 127u) / 128u;
+  const unsigned per_block = 4u * kIllumGroups;  // hits per 128-thread block
+  const unsigned blocks = (p.n_items + per_block - 1u) / per_block;
   if (blocks == 0) return cudaSuccess;
   k_illuminate<MK, INTEG><<<blocks, 128, smem, st>>>(p, l);
   return cudaGetLastError();

@@ -188,15 +188,16 @@ def test_forward_rows_independent_of_tile_and_slot(rg):
     assert not bad.any(), (bad.sum(), np.argwhere(bad)[:5])
 
 
-@pytest.mark.parametrize("batch", [256, 2048])
+@pytest.mark.parametrize("batch", [256, 2048, 20480])
 def test_gradients_match_oracle_element_by_element(rg, batch):
-    """Back-propagation on the tensor cores against the oracle's FP64 back-propagation, every
-    gradient element within its bound (batch 2048 takes the split-K weight-gradient
-    products).  The same comparison with one W2 gradient entry or one bias gradient entry
-    planted wrong in a copy of the GPU result must fail at exactly that element."""
+    """Back-propagation on the tensor cores (one persistent kernel over 128-row tiles)
+    against the oracle's FP64 back-propagation, every gradient element within its bound;
+    at batch 20480 (160 tiles) some CTAs take two tiles.  The same comparison with one W2
+    gradient entry or one bias gradient entry planted wrong in a copy of the GPU result
+    must fail at exactly that element."""
     dm = rg.Metric(_field_metric())
     X, T = rg.Expmap.generate(dm, batch, seed=23)
-    x, params = _net(rg, 9, 2048)
+    x, params = _net(rg, 9, max(batch, 2048))
     G, L = x.gradients(X, T)
     rg.rgeo_sync()
     Xn, Tn = X.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64)
@@ -255,19 +256,40 @@ def test_training_reduces_loss_and_checkpoint_roundtrip(rg, tmp_path):
     Yx, Yy = x.forward(Xv), y.forward(Xv)
     rg.rgeo_sync()
     assert torch.equal(Yx, Yy)
-    # The Adam moments and step count travel too: one more step on the same batch moves
-    # both copies alike.  (Gradient sums use atomics, so the two steps differ in rounding
-    # only; with fresh moments every coordinate would instead move by about lr.)
-    p0 = x.get_params().astype(np.float64)
+    # The Adam moments and step count travel too: one more step on the same batch moves both
+    # copies to the same parameters, bit for bit (the gradient sums have a fixed order; with
+    # fresh moments every coordinate would instead move by about lr).
     x.train_step(X[:4096], T[:4096], 1e-3)
     y.train_step(X[:4096], T[:4096], 1e-3)
     rg.rgeo_sync()
-    dx, dy = x.get_params() - p0, y.get_params() - p0
-    assert np.linalg.norm(dx - dy) <= 1e-2 * np.linalg.norm(dx), (np.linalg.norm(dx - dy), np.linalg.norm(dx))
+    assert np.array_equal(x.get_params(), y.get_params())
     bad = tmp_path / "bad.ckpt"
     bad.write_bytes(b"not a checkpoint")
     with pytest.raises(rg.RgeoError):
         y.load(str(bad))
+
+
+def test_gradients_and_training_are_deterministic(rg):
+    """Each CTA of the training kernel sums its tiles in order and the CTAs' partials are summed
+    in CTA order: the same batch gives the same gradient bits on every call, also when CTAs
+    take several tiles, and training from the same start on the same batches reaches the same
+    parameters bit for bit."""
+    import torch
+    dm = rg.Metric(_field_metric())
+    X, T = rg.Expmap.generate(dm, 40960, seed=41)
+    x, _ = _net(rg, 3, 40960)
+    for b in (128, 40960):
+        G1, L1 = x.gradients(X[:b], T[:b])
+        G2, L2 = x.gradients(X[:b], T[:b])
+        rg.rgeo_sync()
+        assert torch.equal(G1, G2) and torch.equal(L1, L2), b
+    nets = [_net(rg, 4, 8192)[0] for _ in range(2)]
+    for net in nets:
+        for i in range(5):
+            net.train_step(X[i * 8192:(i + 1) * 8192], T[i * 8192:(i + 1) * 8192], 1e-3)
+    rg.rgeo_sync()
+    assert np.array_equal(nets[0].get_params(), nets[1].get_params())
+    assert not np.array_equal(nets[0].get_params(), _cpu_params(4))
 
 
 def test_train_in_one_call(rg):

@@ -131,21 +131,26 @@ def test_surrogate_rejects_bad_arguments(rg):
 
 
 def test_surrogate_full_1080p_sample_within_1e3_of_oracle(rg):
-    """The benchmark's surrogate frame (1920x1080, far-field bound 0.03, tau 0.03, network
-    trained in one call) against the oracle on a seeded pixel sample at the 1e-3 bar.  The
-    sample is 1 % of the frame (about 20,700 pixels), so that the 0.999 bar tolerates about
-    20 misses; silhouette pixels miss at a rate of a few 1e-4, and a 0.2 % sample (4
-    tolerated misses) left the outcome to chance."""
+    """The benchmark's surrogate frame (1920x1080, far-field bound 0.03, tau 0.03, the network
+    trained in one call exactly as the benchmark trains it) against the oracle on a seeded
+    pixel sample at the 1e-3 bar, and the work its jumps remove against the plain frame.  The
+    training step sums its gradients in a fixed order, so this network is the benchmark's, bit
+    for bit, on a device with the same SM count.  The sample is 1 % of the frame (about 20,700
+    pixels), so that the 0.999 bar tolerates about 20 misses; silhouette pixels miss at a rate
+    of a few 1e-4, and a 0.2 % sample (4 tolerated misses) left the outcome to chance."""
     w = scenes.config_1080p_64()
     dm, ds = rg.Metric(w.metric), rg.Scene(w.scene)
-    net = rg.Expmap(max_batch=1 << 16, seed=7)
-    net.train(dm, n_segments=1 << 21, steps=3000, batch=8192, accel_bound=0.03, seed=11)
-    out, st = rg.trace_surrogate(w, net, 0.03, accel_bound=0.03, metric=dm, scene=ds)
+    net = rg.Expmap(max_batch=1 << 18, seed=7)
+    net.train(dm, n_segments=1 << 22, steps=8000, batch=8192, lr_max=2e-3, lr_min=1e-4, seed=11, accel_bound=0.03)
+    plain = rg.alloc_outputs(w.n_pixels, count=True)
+    rg.trace(w, dm, ds, out=plain)
+    out, st = rg.trace_surrogate(w, net, 0.03, accel_bound=0.03, metric=dm, scene=ds,
+                                 out=rg.alloc_outputs(w.n_pixels, count=True))
     rg.rgeo_sync()
-    # the network's gradients are summed with float atomics, so each training run ends at a
-    # slightly different network and the number of accepted jumps varies between runs (8,885
-    # in one, above 10,000 in others): the bar only asks for thousands of jumps
-    assert st["accepted"] > 4000, st
+    # jumps replace RK4 work on many rays, and the bump terms they save are a measurable
+    # share of the frame's (the certified far field of this field is small: about 1.6 %)
+    ratio = out["bump_evals"].item() / plain["bump_evals"].item()
+    assert st["accepted"] > 200_000 and ratio < 0.995, (st, ratio)
     px = scenes.pixel_sample(w.n_pixels, 1234, 0.01)
     ref = oracle.trace(w, px)
     g = gpu_arrays(out, px)

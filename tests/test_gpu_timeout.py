@@ -32,6 +32,8 @@ def test_waits_that_run_out_report_timeout_and_leave_the_context_usable(rg):
     C = torch.zeros((128, 256), device="cuda")
     ex = rg.Expmap(max_batch=256, seed=5)
     X = torch.rand((128, 7), generator=g, device="cuda") * 2 - 1
+    T = torch.rand((128, 6), generator=g, device="cuda") - 0.5
+    p0 = ex.get_params()
     rg.rgeo_sync()
     try:
         rg.rgeo_set_tuning(wait_limit=-1)
@@ -44,6 +46,13 @@ def test_waits_that_run_out_report_timeout_and_leave_the_context_usable(rg):
         with pytest.raises(rg.RgeoError) as e:
             rg.rgeo_sync()
         assert e.value.status == rg.RGEO_ETIMEOUT, e.value
+        # fused training step: the first product's stage wait gives up; the Adam kernel then
+        # leaves the parameters alone
+        ex.train_step(X, T, 1e-3)
+        with pytest.raises(rg.RgeoError) as e:
+            rg.rgeo_sync()
+        assert e.value.status == rg.RGEO_ETIMEOUT, e.value
+        assert np.array_equal(ex.get_params(), p0)
     finally:
         rg.rgeo_set_tuning()
     assert rg.rgeo_get_tuning()["wait_limit"] == 0
@@ -51,6 +60,8 @@ def test_waits_that_run_out_report_timeout_and_leave_the_context_usable(rg):
     C.zero_()
     _gemm(rg, A, B, C)
     Y = ex.forward(X)
+    G, L = ex.gradients(X, T)
     rg.rgeo_sync()
     torch.testing.assert_close(C, A.float() @ B.float().T, rtol=1e-5, atol=1e-4 * 512 ** 0.5)
     assert np.isfinite(Y.cpu().numpy()).all()
+    assert np.isfinite(G.cpu().numpy()).all() and L.item() > 0
