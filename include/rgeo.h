@@ -555,14 +555,15 @@ rgeo_status rgeo_trace_noalloc(const float *center, const float *amplitude, cons
  *   ctas_per_sm      persistent trace launches: 0 (default) as many 128-thread
  *                    CTAs per SM as fit, else at most this many (1 .. 32).
  *   tile_shape       pixels a warp takes from the queue at a time (32 per tile):
- *                    0 default (8 x 4), 1 8 x 4, 2 4 x 8, 3 16 x 2; read by
+ *                    0 default (4 x 8), 1 8 x 4, 2 4 x 8, 3 16 x 2; read by
  *                    rgeo_frame_tiles and every trace.
  *   batch_order      rgeo_batch_create's instance order: 0 (default) by
  *                    decreasing cost (pixels x bumps), 1 as given.
  *   sum_lists        culled bump sums of a warp: 0 (default) one list of bumps for
- *                    as many RK4 steps as stay within its reach (up to 512 bumps),
- *                    else a list per right-hand side; 1 always per right-hand side;
- *                    2 one list per RK4 step.
+ *                    as many RK4 steps (up to 8) as stay within 0.04 of where it
+ *                    was made (metrics of up to 512 bumps, whose cull masks carry
+ *                    that margin), else a list per right-hand side; 1 always per
+ *                    right-hand side; 2 one list per RK4 step.
  * A setting is read when a trace or batch is enqueued or created (a captured
  * graph keeps the choice made at capture); it is not synchronised between host
  * threads.  Errors: RGEO_EINVAL (NULL, bad value, nonzero reserved fields). */

@@ -11,7 +11,7 @@ warp, so every candidate gives the same image bit for bit.
   rays_per_thread  1, or 2 (two rays share each bump pair; dense sums only)
   ctas_per_sm      persistent CTAs per SM (0: as many as fit, seven for the isotropic
                    graph metric; 5 or fewer take the 96-register build of the kernel)
-  tile_shape       the refill tile a warp takes from the queue: 1 (8 x 4) or 2 (4 x 8)
+  tile_shape       the refill tile a warp takes from the queue: 1 (8 x 4) or 2 (4 x 8, the default)
                    pixels (16 x 2 was measured slower at 1080p and is left out)
   sum_lists        culled bump sums from one list for as many RK4 steps as its reach
                    covers (0) or from one per right-hand side (1)

@@ -115,16 +115,16 @@ rgeo_status validate_trace(const rgeo_metric *metric, const rgeo_scene *scene, c
 
 // Steps one culled-sum list serves at step h, 0 when a single step can leave its reach (the
 // sums then look up each right-hand side's own cell).  A list built at x holds every bump
-// whose support, inflated by kCullInflate + kStepReach, meets x's cell, so it serves every
-// point within kStepReach of x: a step's stage points stay within h (|v| + h |x''| / 2) of
-// its start, with |v| <= 1 for a g-unit tangent (g >= I; 1 % for its float32 drift) and
-// |x''| <= accel_max, and n steps within n times that.  Tuning: sum_lists 1 takes no lists,
-// 2 one list per step.
+// whose support, inflated by kCullInflate + the masks' reach margin m.cull_reach, meets x's
+// cell, so it serves every point within m.cull_reach of x: a step's stage points stay within
+// h (|v| + h |x''| / 2) of its start, with |v| <= 1 for a g-unit tangent (g >= I; 1 % for its
+// float32 drift) and |x''| <= accel_max, and n steps within n times that.  Tuning: sum_lists
+// 1 takes no lists, 2 one list per step.
 int list_steps_for(const rgeo::MetricDev &m, float h) {
   const double reach = (double)h * (1.01 + 0.5 * (double)h * m.accel_max) * 1.001 + 1e-5;
   const int mode = rgeo::tuning().sum_lists;
-  if (mode == 1 || reach > rgeo::kStepReach) return 0;
-  return mode == 2 ? 1 : std::max(1, std::min(8, (int)std::floor(rgeo::kStepReach / reach)));
+  if (mode == 1 || !(m.cull_reach > 0.f) || reach > m.cull_reach) return 0;
+  return mode == 2 ? 1 : std::max(1, std::min(8, (int)std::floor(m.cull_reach / reach)));
 }
 
 rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *cam,
@@ -139,9 +139,9 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
     p.cull_hdr = m.cull_hdr;
     p.cull_G = m.cull_G;
     p.cull_words = m.cull_words;
-    // warp step lists (RK4, up to 512 bumps: the warp's packed pairs in shared memory)
+    // warp step lists (RK4, up to kStepListBumps bumps: the warp's packed pairs in shared memory)
     const int n = list_steps_for(m, h);
-    p.step_lists = integrator == RGEO_RK4 && n > 0 && m.K <= 512;
+    p.step_lists = integrator == RGEO_RK4 && n > 0 && m.K <= rgeo::kStepListBumps;
     p.list_steps = p.step_lists ? n : 0;
   }
   p.K = m.kind == RGEO_METRIC_DIFFEO_TWIST ? 0 : m.K;
@@ -241,7 +241,7 @@ std::vector<int32_t> balanced_parity_order(const float *center, const float *sig
   std::vector<double> R(K);
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int k = 0; k < K; k++) {
-    R[k] = (double)cutoff * sigma[3 * k] + rgeo::kCullInflate + rgeo::kStepReach;
+    R[k] = (double)cutoff * sigma[3 * k] + rgeo::kCullInflate + rgeo::cull_reach_for(K);
     for (int c = 0; c < 3; c++) {
       lo[c] = std::min(lo[c], (double)center[3 * k + c] - R[k]);
       hi[c] = std::max(hi[c], (double)center[3 * k + c] + R[k]);
@@ -453,9 +453,11 @@ rgeo_status rgeo_metric_create(const rgeo_metric_desc *desc, rgeo_metric **out) 
       const int words = rgeo::cull_words_for(K);
       m->d.cull_G = G;
       m->d.cull_words = words;
+      m->d.cull_reach = rgeo::cull_reach_for(K);
       e = cudaMalloc(&m->d.cull_masks, sizeof(uint32_t) * (size_t)G * G * G * words);
       if (e == cudaSuccess) e = cudaMalloc(&m->d.cull_hdr, sizeof(float4) * 2);
-      if (e == cudaSuccess) e = rgeo::launch_build_cull(m->d.bumps, K, G, words, m->d.cull_hdr, m->d.cull_masks, 0);
+      if (e == cudaSuccess)
+        e = rgeo::launch_build_cull(m->d.bumps, K, G, words, m->d.cull_reach, m->d.cull_hdr, m->d.cull_masks, 0);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
@@ -481,8 +483,8 @@ rgeo_status rgeo_metric_set_centers(rgeo_metric *metric, const float *center, vo
   RGEO_CUDA(rgeo::launch_set_centers(metric->d.raw, K, metric->d.aniso, metric->d.perm, metric->d.bumps, st),
             "rgeo_metric_set_centers: launch");
   if (metric->d.cull_G > 0)
-    RGEO_CUDA(rgeo::launch_build_cull(metric->d.bumps, K, metric->d.cull_G, metric->d.cull_words, metric->d.cull_hdr,
-                                      metric->d.cull_masks, st),
+    RGEO_CUDA(rgeo::launch_build_cull(metric->d.bumps, K, metric->d.cull_G, metric->d.cull_words, metric->d.cull_reach,
+                                      metric->d.cull_hdr, metric->d.cull_masks, st),
               "rgeo_metric_set_centers: cull grid");
   return RGEO_OK;
 }
@@ -878,7 +880,7 @@ rgeo_status rgeo_metric_advance(rgeo_metric *m, float dt, void *cuda_stream) {
                                         dt, st),
             "rgeo_metric_advance: motion");
   if (m->d.cull_G > 0)
-    RGEO_CUDA(rgeo::launch_build_cull(m->d.bumps, m->d.K, m->d.cull_G, m->d.cull_words, m->d.cull_hdr,
+    RGEO_CUDA(rgeo::launch_build_cull(m->d.bumps, m->d.K, m->d.cull_G, m->d.cull_words, m->d.cull_reach, m->d.cull_hdr,
                                       m->d.cull_masks, st),
               "rgeo_metric_advance: cull grid");
   return RGEO_OK;

@@ -91,6 +91,7 @@ struct MetricDev {
   int cull_G, cull_words;
   uint32_t *cull_masks;  // [G^3 * words]
   float4 *cull_hdr;      // (gmin.xyz, 1 / cell)
+  float cull_reach;      // the masks' reach margin beyond kCullInflate: cull_reach_for(K)
   // bound on |x''| over the whole space for a g-unit tangent: (sum_k |a_k| / sigma_k^2 +
   // ||A||_F) / 2 (Eq. 5.4 with |grad f| / (1 + |grad f|^2) <= 1/2, ||Hess f_k|| <= |a_k| q_k)
   float accel_max;
@@ -99,13 +100,16 @@ struct MetricDev {
   float *time;
 };
 
-// Cull grid: inflation of every support radius (absolute): kCullInflate covers float32
-// rounding of the cell look-up, kStepReach the distance from a step's start to its RK4
-// stage points, so that the cell of a step's start lists every bump whose support can
-// meet any stage point of the step (step lists, below) when that distance is at most
-// kStepReach.
+// Cull grid: inflation of every support radius (absolute).  kCullInflate covers float32
+// rounding of the cell look-up.  A metric that may take step lists (at most kStepListBumps
+// bumps) adds its reach margin kStepReach: the cell of a step's start then lists every bump
+// whose support can meet any RK4 stage point of the steps whose stage points stay within
+// kStepReach of it (step lists, below).  Larger metrics add none, so that their per-RHS
+// lists stay as short as the supports allow.
 constexpr float kCullInflate = 1e-3f;
-constexpr float kStepReach = 0.02f;
+constexpr float kStepReach = 0.04f;
+constexpr int kStepListBumps = 512;
+__host__ __device__ constexpr float cull_reach_for(int K) { return K <= kStepListBumps ? kStepReach : 0.f; }
 
 // BVH node: two float4.  n0 = (lo.xyz, int first_or_left), n1 = (hi.xyz, int count);
 // count > 0: leaf over primitives [first, first + count); count == 0: children at
@@ -224,7 +228,7 @@ struct Tuning {
   int batch_params = 0;     // 0: parameter space when n <= kMaxParamInstances; 1: shared-memory copies
   int wait_limit = 0;       // tensor-core kernels' work waits: 0 default, n > 0 polls, -1 none (give up at once)
   int ctas_per_sm = 0;      // persistent trace grids: 0 as many as fit, else at most this many per SM
-  int tile_lw = 3;          // refill tile width log2: 3 (8 x 4, default), 2 (4 x 8), 4 (16 x 2)
+  int tile_lw = 2;          // refill tile width log2: 2 (4 x 8, default), 3 (8 x 4), 4 (16 x 2)
   int batch_order = 0;      // batch instances: 0 by decreasing cost, 1 as given
   int sum_lists = 0;        // culled sums: 0 one list per RK4 step where it applies, 1 one per right-hand side
 };
@@ -266,7 +270,7 @@ cudaError_t launch_trace(const TraceParams &p, cudaStream_t st);
 // Illumination pass over the hits of a finished trace p (p.hit_nrm filled by it).
 cudaError_t launch_illuminate(const TraceParams &p, const LightParams &l, cudaStream_t st);
 cudaError_t launch_set_centers(const float *c, int K, int aniso, const int32_t *perm, float4 *bumps, cudaStream_t st);
-cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
+cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float reach, float4 *hdr, uint32_t *masks,
                               cudaStream_t st);
 cudaError_t launch_batch(const TraceParams *dev_inst, const TraceParams *host_inst, int n, int kind, int aniso,
                          int integrator,

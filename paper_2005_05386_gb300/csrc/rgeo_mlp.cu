@@ -767,22 +767,24 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 // cores, one tile row per thread: layer 1 before them, then layer 4, the loss and dY, the
 // ReLU masks, and the gradients of the biases and of the 7-wide layers, whose sums over the
 // tile's rows are taken across the warp's lanes by a fixed shuffle tree and across its four
-// row quarters in order.  The operands of the next product go through the training state's
-// scratch rows (L2-resident: H1, H2, dZ and their transposes), from which they are staged by
-// cp.async.  Each CTA sums its tiles' gradients in tile order into its own slot of part
-// (kPartStride floats: the parameters in the order of P, then the loss); k_reduce_adam sums
-// the slots in CTA order, so a step's gradient does not depend on timing.  The roundings are
-// those of the training arithmetic: H1, H2, H3, dZ3 and dZ2 are BF16 operands, everything
-// else FP32.
+// row quarters in order.  Each epilogue writes the next product's activation operand straight
+// into shared memory in the canonical layout (the rows H1, H2, dZ3, dZ2 in sAct; dZ3^T and
+// dZ2^T in sTr), so only the weights and the transposed activations H2^T and H1^T that the
+// weight gradients take are staged, by cp.async from L2.  Each CTA sums its tiles' gradients in
+// tile order into its own slot of part (kPartStride floats: the parameters in the order of P,
+// then the loss); k_reduce_adam sums the slots in CTA order, so a step's gradient does not
+// depend on timing.  The roundings are those of the training arithmetic: H1, H2, H3, dZ3 and
+// dZ2 are BF16 operands, everything else FP32.
 constexpr int kTrThreads = 256;
-constexpr int kTrStageA = kTileM * kTileK * 2;     // 16 KB
-constexpr int kTrStageB = kMaxTileN * kTileK * 2;  // 32 KB
+constexpr int kTrAct = kTileM * kWid * 2;          // 64 KB: 128 rows x K = 256 (core matrices, SBO 4096 B)
+constexpr int kTrTr = kWid * kTileM * 2;           // 64 KB: M = 256 x K = 128 (two 128-row halves, SBO 2048 B)
+constexpr int kTrStageB = kMaxTileN * kTileK * 2;  // 32 KB: 256 x 64 (SBO 1024 B)
 constexpr int kTrFloats = kOut * kWid + 2 * kWid + 3 * kTileM * 8;
-constexpr int kTrSmem = 2 * (kTrStageA + kTrStageB) + kTrFloats * 4;  // 117 KB: one CTA per SM
-constexpr int kPartStride = (kParams + 1 + 3) & ~3;                   // floats per slot, 16-byte aligned
+constexpr int kTrSmem = kTrAct + kTrTr + 2 * kTrStageB + kTrFloats * 4;  // 213 KB: one CTA per SM
+constexpr int kPartStride = (kParams + 1 + 3) & ~3;                      // floats per slot, 16-byte aligned
 constexpr int kRedQty = 8;  // column sums reduced at once (in the stage buffers, free in an epilogue)
-static_assert(kTrSmem <= 227 * 1024 && 2 * kTrSmem > 228 * 1024, "one training CTA per SM (it takes all of TMEM)");
-static_assert(kRedQty * 4 * kWid * 4 <= 2 * (kTrStageA + kTrStageB), "column-sum buffer in the stage buffers");
+static_assert(kTrSmem <= 227 * 1024, "shared memory of the training kernel (one CTA per SM: it takes all of TMEM)");
+static_assert(kRedQty * 4 * kWid * 4 <= 2 * kTrStageB, "column-sum buffer in the stage buffers");
 static_assert(oW2 % 4 == 0 && oW3 % 4 == 0, "vector access to the weight-gradient slots");
 
 struct TrainArgs {
@@ -792,7 +794,7 @@ struct TrainArgs {
   const float *P;
   const __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
   float *part;
-  __nv_bfloat16 *H1, *H2, *H1t, *H2t, *dZ, *dZt;
+  __nv_bfloat16 *H1, *H2, *H1t, *H2t;
   long long polls;
 };
 
@@ -810,6 +812,12 @@ __device__ __forceinline__ float bf16_of(uint32_t pair, int j) {
 }
 __device__ __forceinline__ __nv_bfloat16 bf16_at(uint32_t pair, int j) {
   return __ushort_as_bfloat16((unsigned short)(j ? (pair >> 16) : (pair & 0xFFFFu)));
+}
+
+// Byte offset of element (m, k) of a K-major canonical operand whose row groups are sbo bytes
+// apart: core matrix (m / 8, k / 8) of 8 rows x 16 bytes, row m % 8 at 16 (m % 8).
+__device__ __forceinline__ uint32_t canon_off(int m, int k, uint32_t sbo) {
+  return (uint32_t)(m >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(m & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
 // For every j, the sum of v[j] over the warp's 32 lanes; lane l returns the sum for j = l.  A
@@ -830,31 +838,44 @@ __device__ __forceinline__ float lane_sums(float (&v)[32]) {
   return v[0];
 }
 
-// All threads of the CTA: TMEM columns acc.. (128 lanes x N) = A[arow0 + 0..127][ak0 + 0..K-1] x
-// B[brow0 + 0..N-1][bk0 + 0..K-1]^T for row-major BF16 A and B (leading dimensions lda, ldb;
-// K a multiple of 64), the K stages double-buffered in sA / sB and signalled on bar[2], whose
-// phases ph tracks.  Returns with every MMA complete, or false once a wait ran out (abort
-// raised; the caller leaves, and the kernel's drain waits for what is in flight).
-__device__ bool tile_gemm(uint8_t *sA0, uint8_t *sA1, uint8_t *sB0, uint8_t *sB1, const __nv_bfloat16 *A, int lda,
-                          int arow0, int ak0, const __nv_bfloat16 *B, int ldb, int brow0, int bk0, int N, int K,
-                          uint32_t acc, uint64_t *bar, uint32_t (&ph)[2], volatile int *abort, long long polls) {
-  uint8_t *sA[2] = {sA0, sA1}, *sB[2] = {sB0, sB1};
+// Stage 0 of a product's B (rows brow0 .. brow0 + N - 1, K columns bk0 .. bk0 + 63) into sB,
+// ahead of the product: issued by all threads while the previous product's epilogue runs.
+__device__ __forceinline__ void prefetch_b(uint8_t *sB, const __nv_bfloat16 *B, int ldb, int brow0, int bk0, int N) {
+  stage_tile(sB, B, ldb, brow0, N, brow0 + N, bk0);
+  cp_async_commit();
+}
+
+// All threads of the CTA: TMEM columns acc.. (128 lanes x N) = A x B[brow0 + 0..N-1][bk0 + 0..K-1]^T,
+// A the 128 x K canonical operand in shared memory at a_base (row groups a_sbo bytes apart), B
+// row-major BF16 (leading dimension ldb) staged in 64-wide K stages double-buffered in sB, stage
+// s in sB[(fb + s) % 2] and signalled on bar of that buffer, whose phases ph tracks (K a
+// multiple of 64).  With pre, stage 0 is already in flight (prefetch_b into sB[fb]).  With
+// a_off2 > 0, a second 128-row A at a_base + a_off2 is multiplied by the same staged B into
+// columns acc2.. (the two halves of a weight gradient).  Returns with every MMA complete, or
+// false once a wait ran out (abort raised; the caller leaves, and the kernel's drain waits for
+// what is in flight).
+__device__ bool tile_gemm(uint32_t a_base, uint32_t a_sbo, uint8_t *sB0, uint8_t *sB1, const __nv_bfloat16 *B,
+                          int ldb, int brow0, int bk0, int N, int K, uint32_t acc, uint64_t *bar, uint32_t (&ph)[2],
+                          volatile int *abort, long long polls, int fb, bool pre, uint32_t a_off2 = 0u,
+                          uint32_t acc2 = 0u) {
+  uint8_t *sB[2] = {sB0, sB1};
   const int nst = K / kTileK;
   const uint32_t idesc = idesc_bf16(kTileM, N);
-  stage_tile(sA[0], A, lda, arow0, kTileM, arow0 + kTileM, ak0);
-  stage_tile(sB[0], B, ldb, brow0, N, brow0 + N, bk0);
-  cp_async_commit();
+  if (!pre) prefetch_b(sB[fb], B, ldb, brow0, bk0, N);
   for (int s = 0; s < nst; ++s) {
-    const int buf = s & 1;
+    const int buf = (fb + s) & 1;
     cp_async_wait_all();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // also orders the epilogue's operand writes
     __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA[buf]), b0 = smem_u32(sB[buf]);
-      for (int kk = 0; kk < kTileK / 16; ++kk)
-        mma_bf16(acc, smem_desc(a0 + kk * 256, 128, 1024), smem_desc(b0 + kk * 256, 128, 1024), idesc,
-                 (s > 0 || kk > 0) ? 1u : 0u);
+      const uint32_t b0 = smem_u32(sB[buf]);
+      for (int kk = 0; kk < kTileK / 16; ++kk) {
+        const uint32_t ao = (uint32_t)(s * 1024 + kk * 256), accum = (s > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+        mma_bf16(acc, smem_desc(a_base + ao, 128, a_sbo), bd, idesc, accum);
+        if (a_off2) mma_bf16(acc2, smem_desc(a_base + a_off2 + ao, 128, a_sbo), bd, idesc, accum);
+      }
       mma_commit(&bar[buf]);
     }
     if (s + 1 < nst) {
@@ -865,19 +886,31 @@ __device__ bool tile_gemm(uint8_t *sA0, uint8_t *sA1, uint8_t *sB0, uint8_t *sB1
       }
       __syncthreads();
       if (*abort) return false;
-      stage_tile(sA[nb], A, lda, arow0, kTileM, arow0 + kTileM, ak0 + (s + 1) * kTileK);
       stage_tile(sB[nb], B, ldb, brow0, N, brow0 + N, bk0 + (s + 1) * kTileK);
       cp_async_commit();
     }
   }
   // the commits of the last two stages (or the only one) have not been waited for yet
   for (int s = nst >= 2 ? nst - 2 : 0; s < nst; ++s) {
-    if (!mbar_wait(&bar[s & 1], ph[s & 1], polls)) *abort = 1;
-    ph[s & 1] ^= 1u;
+    const int b = (fb + s) & 1;
+    if (!mbar_wait(&bar[b], ph[b], polls)) *abort = 1;
+    ph[b] ^= 1u;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   return !*abort;
+}
+
+// 32 consecutive BF16 columns c0.. of tile row `row` (packed pairs pk) into the canonical
+// row operand sAct (four 16-byte stores) and, when sTr is set, as column `row` of the
+// canonical transposed operand sTr (one element per column).
+__device__ __forceinline__ void put_operand32(uint8_t *sAct, uint8_t *sTr, int row, int c0, const uint32_t (&pk)[16]) {
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<uint4 *>(sAct + canon_off(row, c0 + 8 * u, 4096)) =
+        make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+  if (sTr)
+    for (int j = 0; j < 32; ++j)
+      *reinterpret_cast<__nv_bfloat16 *>(sTr + canon_off(c0 + j, row, 2048)) = bf16_at(pk[j >> 1], j & 1);
 }
 
 // Writes 32 consecutive BF16 columns c0.. of one row: row-major (dst + c0) and transposed
@@ -912,11 +945,12 @@ __device__ __forceinline__ void add_weight_grad(uint32_t tl, int half, int row, 
 
 __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a) {
   extern __shared__ __align__(1024) uint8_t tsm[];
-  uint8_t *sA0 = tsm, *sA1 = tsm + kTrStageA, *sB0 = tsm + 2 * kTrStageA, *sB1 = sB0 + kTrStageB;
-  float *red = reinterpret_cast<float *>(tsm);  // [kRedQty][4 row quarters][256 columns], in an epilogue
-  float *w4s = reinterpret_cast<float *>(tsm + 2 * (kTrStageA + kTrStageB));  // [7][256]
+  uint8_t *sAct = tsm, *sTr = tsm + kTrAct, *sB0 = sTr + kTrTr, *sB1 = sB0 + kTrStageB;
+  float *red = reinterpret_cast<float *>(sB0);  // [kRedQty][4 row quarters][256 columns], in an epilogue
+  float *w4s = reinterpret_cast<float *>(sB1 + kTrStageB);  // [7][256]
   float *b2s = w4s + kOut * kWid, *b3s = b2s + kWid;
   float *xs = b3s + kWid, *dys = xs + kTileM * 8, *part4 = dys + kTileM * 8;  // [128][8] each
+  const uint32_t aAct = smem_u32(sAct), aTr = smem_u32(sTr);
   __shared__ uint64_t bar[2], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -968,7 +1002,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
       xs[i] = k < kIn ? a.X[(size_t)(m0 + r) * kIn + k] : 0.f;
     }
     __syncthreads();
-    // ---- layer 1 (FP32, K = 7): H1 = relu(X W1^T + b1), BF16 rows and transposed; unit j = t
+    // ---- layer 1 (FP32, K = 7): H1 = relu(X W1^T + b1) into sAct, and as BF16 rows and
+    // transposed rows in L2 (the ReLU mask of dH1, the operand of dW2); unit j = t
     {
       float w1[kIn];
       for (int k = 0; k < kIn; ++k) w1[k] = a.P[oW1 + t * kIn + k];
@@ -980,15 +1015,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
           for (int k = 0; k < kIn; ++k) z = fmaf(w1[k], xs[(r0 + u) * 8 + k], z);
           hv[u] = __float2bfloat16_rn(fmaxf(z, 0.f));
           a.H1[(size_t)(m0 + r0 + u) * kWid + t] = hv[u];
+          *reinterpret_cast<__nv_bfloat16 *>(sAct + canon_off(r0 + u, t, 4096)) = hv[u];
         }
         *reinterpret_cast<uint4 *>(a.H1t + (size_t)t * Bn + m0 + r0) = pack8_bf16(hv);
       }
     }
-    __syncthreads();
-    // ---- Z2 = H1 W2^T; H2 = relu(Z2 + b2), BF16 rows and transposed
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.H1, kWid, m0, 0, a.W2b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
-                   a.polls))
+    // ---- Z2 = H1 W2^T; H2 = relu(Z2 + b2) into sAct, and as BF16 rows and transposed in L2
+    // (stage 0 of W2 was prefetched into sB1 during the previous tile's last epilogue)
+    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W2b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 1, !first))
       break;
+    prefetch_b(sB0, a.W3b, kWid, 0, 0, kWid);
     for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
       uint32_t v[32], pk[16];
       tmem_ld32_nowait(tl + (uint32_t)c0, v);
@@ -996,14 +1032,14 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
       for (int j = 0; j < 16; ++j)
         pk[j] = pack_bf16_relu(__uint_as_float(v[2 * j]) + b2s[c0 + 2 * j],
                                __uint_as_float(v[2 * j + 1]) + b2s[c0 + 2 * j + 1]);
+      put_operand32(sAct, nullptr, row, c0, pk);
       store_row32(a.H2 + (size_t)(m0 + row) * kWid, a.H2t + m0 + row, Bn, c0, pk);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
     // ---- Z3 = H2 W3^T; H3 = relu(Z3 + b3) (BF16); layer 4 (FP32) from the BF16 H3
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.H2, kWid, m0, 0, a.W3b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
-                   a.polls))
+    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W3b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
       break;
+    prefetch_b(sB1, a.H2t, Bn, 0, m0, kWid);  // the epilogue's column sums use sB0
     {
       float y[kOut];
       for (int o = 0; o < kOut; ++o) y[o] = 0.f;
@@ -1040,8 +1076,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
       }
       __syncthreads();
     }
-    // ---- layer 4 backward from the same accumulator: dZ3 = bf16(dH3 [H3 > 0]) with dH3 = dY W4 (rows
-    // and transposed); the tile's dW4 = dY^T H3 and db3 = sum of dZ3 as column sums
+    // ---- layer 4 backward from the same accumulator: dZ3 = bf16(dH3 [H3 > 0]) with dH3 = dY W4, into
+    // sAct (rows) and sTr (transposed); the tile's dW4 = dY^T H3 and db3 = sum of dZ3 as column sums
     {
       float dy[kOut];
       for (int o = 0; o < kOut; ++o) dy[o] = dys[row * 8 + o];
@@ -1067,7 +1103,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
           const __nv_bfloat162 p2 = __halves2bfloat162(zb[0], zb[1]);
           pz[j >> 1] = *reinterpret_cast<const uint32_t *>(&p2);
         }
-        store_row32(a.dZ + (size_t)(m0 + row) * kWid, a.dZt + m0 + row, Bn, c0, pz);
+        put_operand32(sAct, sTr, row, c0, pz);
         for (int o = 0; o < kOut; ++o) {
           for (int j = 0; j < 32; ++j) w[j] = dy[o] * h[j];
           red[(o * 4 + q) * kWid + c0 + lane] = lane_sums(w);
@@ -1082,20 +1118,18 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
         for (int r = 0; r < kTileM; ++r) gb4 += dys[r * 8 + t];
       __syncthreads();
     }
-    // ---- the tile's dW3 = dZ3^T H2 (K = its 128 rows), added into the CTA's slot
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, 0, m0, a.H2t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp,
-                   a.polls))
+    // ---- the tile's dW3 = dZ3^T H2 (K = its 128 rows; both 128-row halves of dW3 per staged H2^T
+    // stage), added into the CTA's slot
+    if (!tile_gemm(aTr, 2048, sB0, sB1, a.H2t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp, a.polls, 1, true,
+                   16u * 2048u, tmem + kWid))
       break;
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, kTileM, m0, a.H2t, Bn, 0, m0, kWid, kTileM, tmem + kWid, bar, ph,
-                   abortp, a.polls))
-      break;
+    prefetch_b(sB0, a.W3t, kWid, 0, 0, kWid);
     add_weight_grad(tl, half, row, slot + oW3, first);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    // ---- dH2 = dZ3 W3; dZ2 = bf16(dH2 [H2 > 0]) (rows and transposed); db2 = column sums of the FP32 values
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZ, kWid, m0, 0, a.W3t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
-                   a.polls))
+    // ---- dH2 = dZ3 W3; dZ2 = bf16(dH2 [H2 > 0]) into sAct and sTr; db2 = column sums of the FP32 values
+    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W3t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
       break;
+    prefetch_b(sB1, a.H1t, Bn, 0, m0, kWid);  // the epilogue's column sums use sB0
     for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
       uint32_t v[32], pz[16];
       tmem_ld32_nowait(tl + (uint32_t)c0, v);
@@ -1112,27 +1146,25 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
         const __nv_bfloat162 p2 = __halves2bfloat162(__float2bfloat16_rn(g[j]), __float2bfloat16_rn(g[j + 1]));
         pz[j >> 1] = *reinterpret_cast<const uint32_t *>(&p2);
       }
-      store_row32(a.dZ + (size_t)(m0 + row) * kWid, a.dZt + m0 + row, Bn, c0, pz);
+      put_operand32(sAct, sTr, row, c0, pz);
       red[q * kWid + c0 + lane] = lane_sums(g);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     gb2 += red_sum(0);
+    // (the next product's first stage overwrites red: tile_gemm synchronises before it stages)
     __syncthreads();
     // ---- the tile's dW2 = dZ2^T H1, as dW3
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, 0, m0, a.H1t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp,
-                   a.polls))
+    if (!tile_gemm(aTr, 2048, sB0, sB1, a.H1t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp, a.polls, 1, true,
+                   16u * 2048u, tmem + kWid))
       break;
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZt, Bn, kTileM, m0, a.H1t, Bn, 0, m0, kWid, kTileM, tmem + kWid, bar, ph,
-                   abortp, a.polls))
-      break;
+    prefetch_b(sB0, a.W2t, kWid, 0, 0, kWid);
     add_weight_grad(tl, half, row, slot + oW2, first);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
     // ---- dH1 = dZ2 W2; dZ1 = dH1 [H1 > 0] (FP32); db1 and dW1 = dZ1^T X as column sums
-    if (!tile_gemm(sA0, sA1, sB0, sB1, a.dZ, kWid, m0, 0, a.W2t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp,
-                   a.polls))
+    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W2t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
       break;
+    if (tile + (int)gridDim.x < ntiles) prefetch_b(sB1, a.W2b, kWid, 0, 0, kWid);  // the next tile's Z2
     {
       float xr[kIn];
       for (int i = 0; i < kIn; ++i) xr[i] = xs[row * 8 + i];
@@ -1300,7 +1332,7 @@ struct ExpmapDev {
   __nv_bfloat16 *W2b, *W3b, *W2t, *W3t;
   __nv_bfloat16 *Wp;  // the operands of the persistent inference kernel, packed by k_pack_chunks
   bool wp_stale;      // P has changed since Wp was packed
-  __nv_bfloat16 *H1, *H2, *H1t, *H2t, *dZ, *dZt;  // scratch rows of the training step
+  __nv_bfloat16 *H1, *H2, *H1t, *H2t;  // scratch rows of the training step (row-major and transposed)
   float *part;  // the training CTAs' gradient slots, kPartStride floats each
 };
 
@@ -1310,8 +1342,7 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_all(ExpmapDev &d) {
-  void *ptrs[] = {d.P, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.Wp, d.H1, d.H2, d.H1t, d.H2t, d.dZ,
-                  d.dZt, d.part};
+  void *ptrs[] = {d.P, d.m, d.v, d.W2b, d.W3b, d.W2t, d.W3t, d.Wp, d.H1, d.H2, d.H1t, d.H2t, d.part};
   for (void *q : ptrs) cudaFree(q);
 }
 
@@ -1338,8 +1369,6 @@ cudaError_t train_pass(ExpmapDev &d, const float *X, const float *T, int B, floa
   a.H2 = d.H2;
   a.H1t = d.H1t;
   a.H2t = d.H2t;
-  a.dZ = d.dZ;
-  a.dZt = d.dZt;
   a.polls = wait_polls(kSpinLimit);
   k_train_tile<<<grid, kTrThreads, kTrSmem, st>>>(a);
   *nparts = grid;
@@ -1426,7 +1455,7 @@ rgeo_status rgeo_expmap_create(int32_t max_batch, uint64_t seed, rgeo_expmap **o
   if (e == cudaSuccess) e = dalloc(&d.W2t, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.W3t, (size_t)kWid * kWid);
   if (e == cudaSuccess) e = dalloc(&d.Wp, (size_t)kPackedElems);
-  __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H1t, &d.H2t, &d.dZ, &d.dZt};
+  __nv_bfloat16 **bufs[] = {&d.H1, &d.H2, &d.H1t, &d.H2t};
   for (auto b : bufs)
     if (e == cudaSuccess) e = dalloc(b, HW);
   int dev = 0;

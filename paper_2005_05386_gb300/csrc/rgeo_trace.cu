@@ -1118,7 +1118,7 @@ __device__ __forceinline__ int stage_shared(const TraceParams &P, float4 *smem) 
 }
 
 // Warp-synchronous refill: every lane calls this; lanes whose slot is empty take
-// the next queue items (one atomic per warp).  Items walk 8 x 4 pixel tiles so that
+// the next queue items (one atomic per warp).  Items walk 32-pixel tiles so that
 // a warp's rays start close together.
 template <int MK>
 __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, bool &active,
@@ -1141,8 +1141,8 @@ __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, b
   }
 }
 
-// Warp-synchronous refill from a warp-private chunk of 32 consecutive items (one 8 x 4 pixel
-// tile) taken from the queue one chunk at a time: the rays a warp starts come from the same
+// Warp-synchronous refill from a warp-private chunk of 32 consecutive items (one 32-pixel
+// tile, 4 x 8 by default) taken from the queue one chunk at a time: the rays a warp starts come from the same
 // tile, so its lanes stay closer together and the union of their cull cells stays smaller.
 // cnext / cend (the chunk's next and end item) are the same on every lane.
 template <int MK>
@@ -1633,7 +1633,7 @@ __device__ bool shoot(const TraceParams &P, const float4 *sb, const float4 *ss, 
 // direction d0 + alpha e1 + beta e2, forward-difference Jacobian), and the hit is lit
 // when it converged, the Riemannian cosine n.u / sqrt(n^T g^-1 n) is positive and the
 // geodesic meets no object on the way; colour albedo (0.1 + 0.9 cos) lit, albedo 0.1 not.
-// Each hit takes a group of three lanes (ten hits per warp, hits in 8 x 4 pixel tiles): in
+// Each hit takes a group of three lanes (ten hits per warp, hits in 32-pixel tiles): in
 // every Gauss-Newton step, lane 0 of the group marches the light geodesic of the current
 // direction while lanes 1 and 2 march those of its two difference directions, so a step
 // takes the time of one march rather than three (the slowest solves set the kernel's time).
@@ -2384,15 +2384,15 @@ __global__ void k_set_centers(const float *c, int K, int aniso, const int32_t *p
 }
 
 // Cull grid, step 1 (one block): bounding box of every live support ball, inflated
-// by kCullInflate + kStepReach; hdr[0] = (min corner, 1 / cell), hdr[1].x = cell (cubic cells, G
+// by kCullInflate + reach; hdr[0] = (min corner, 1 / cell), hdr[1].x = cell (cubic cells, G
 // along the longest axis).  With no live bump, hdr[0].w = 0 and every mask is empty.
-__global__ void k_cull_bounds(const float4 *bumps, int K, int G, float4 *hdr) {
+__global__ void k_cull_bounds(const float4 *bumps, int K, int G, float reach, float4 *hdr) {
   __shared__ float red[6][256];
   float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const IsoBump b = iso_bump(bumps, k);
     if (!(b.R2 >= 0.f) || isinf(b.R2)) continue;
-    const float R = sqrtf(b.R2) + kCullInflate + kStepReach;
+    const float R = sqrtf(b.R2) + kCullInflate + reach;
     for (int c = 0; c < 3; c++) {
       lo[c] = fminf(lo[c], comp(b.c, c) - R);
       hi[c] = fmaxf(hi[c], comp(b.c, c) + R);
@@ -2426,8 +2426,9 @@ __global__ void k_cull_bounds(const float4 *bumps, int K, int G, float4 *hdr) {
 }
 
 // Cull grid, step 2 (one thread per cell): bit k of the cell's words is set when the
-// live support ball of bump k (radius + kCullInflate + kStepReach) meets the cell box.
-__global__ void k_cull_masks(const float4 *bumps, int K, int G, int words, const float4 *hdr, uint32_t *masks) {
+// live support ball of bump k (radius + kCullInflate + reach) meets the cell box.
+__global__ void k_cull_masks(const float4 *bumps, int K, int G, int words, float reach, const float4 *hdr,
+                             uint32_t *masks) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= (long long)G * G * G) return;
   uint32_t *out = masks + cell * words;
@@ -2446,7 +2447,7 @@ __global__ void k_cull_masks(const float4 *bumps, int K, int G, int words, const
       if (k >= K) break;
       const IsoBump bb = iso_bump(bumps, k);
       if (!(bb.R2 >= 0.f) || isinf(bb.R2)) continue;
-      const float R = sqrtf(bb.R2) + kCullInflate + kStepReach;
+      const float R = sqrtf(bb.R2) + kCullInflate + reach;
       float d2 = 0.f;
       for (int c = 0; c < 3; c++) {
         const float cc = comp(bb.c, c);
@@ -2717,14 +2718,14 @@ cudaError_t launch_pack_bumps(const float *raw, int K, float cutoff, int aniso, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float4 *hdr, uint32_t *masks,
-                              cudaStream_t st) {
+cudaError_t launch_build_cull(const float4 *bumps, int K, int G, int words, float reach, float4 *hdr,
+                              uint32_t *masks, cudaStream_t st) {
   if (K <= 0 || G <= 0) return cudaSuccess;
-  k_cull_bounds<<<1, 256, 0, st>>>(bumps, K, G, hdr);
+  k_cull_bounds<<<1, 256, 0, st>>>(bumps, K, G, reach, hdr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long cells = (long long)G * G * G;
-  k_cull_masks<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(bumps, K, G, words, hdr, masks);
+  k_cull_masks<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(bumps, K, G, words, reach, hdr, masks);
   return cudaGetLastError();
 }
 

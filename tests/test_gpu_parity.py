@@ -169,6 +169,18 @@ def test_bump_term_counter(rg):
     assert 0 < counts["culled"] < counts["dense"] / 2
 
 
+def test_cull_grid_above_512_bumps_matches_dense_sums(rg):
+    """1024 bumps: no step lists, masks without the step lists' reach margin, lists per
+    right-hand side in parts; still the dense sums' frame bit for bit."""
+    w = scenes.scaled(scenes.config_4k_1024(), 160, 90)
+    w.max_steps = 600
+    culled = _run(rg, w)
+    dense = _run(rg, w, rg.RGEO_FLAG_DENSE)
+    for k in ("id", "steps", "rgba", "hit"):
+        assert np.array_equal(culled[k], dense[k]), k
+    assert (dense["id"] >= 0).sum() > 500
+
+
 def test_cull_grid_with_many_bumps_matches_oracle(rg):
     """1024 bumps (several mask words per cell) against the oracle on a sample."""
     w = scenes.config_4k_1024()
