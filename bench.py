@@ -932,16 +932,17 @@ def bench_infer(args):
 
 
 def bench_train(args):
-    """Adam steps of the learned exponential map at batch 8192 on far-field segments that the
-    device integrator generated from the 1080p / 64-bump field (``rgeo_expmap_train_step`` on
-    consecutive batches of the generated set), with the roofline of the tensor-core products:
-    per row, layers 2 and 3 forward (one product each) and backward (two products each)."""
+    """Adam steps of the learned exponential map at batch ``--batch`` (8192, the surrogate's
+    training batch) on far-field segments that the device integrator generated from the
+    1080p / 64-bump field (``rgeo_expmap_train_step`` on consecutive batches of the generated
+    set), with the roofline of the tensor-core products: per row, layers 2 and 3 forward (one
+    product each) and backward (two products each)."""
     import torch
     import paper_2005_05386_gb300 as rg
     torch.cuda.set_device(0)
     w = workload("1080p_64", None)
     dm = rg.Metric(w.metric)
-    B, steps = 8192, args.steps
+    B, steps = args.batch, args.steps
     n = B * (args.warmup + steps)
     X, T = rg.Expmap.generate(dm, n, seed=11, accel_bound=0.03)
     net = rg.Expmap(max_batch=B, seed=7)
@@ -964,11 +965,11 @@ def bench_train(args):
     peak = measured_peaks().get("bf16_tflops")
     achieved = flops / (ms * 1e-3) / 1e12
     line = {
-        "metric": "Adam steps/s of the learned exponential map (batch 8192)", "value": 1e3 / ms,
+        "metric": f"Adam steps/s of the learned exponential map (batch {B})", "value": 1e3 / ms,
         "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
         "data": "synthetic (segments generated by the device integrator on the seeded 64-bump field)",
-        "config": {"workload": "expmap_train_b8192", "batch": B, "segments": n,
+        "config": {"workload": f"expmap_train_b{B}", "batch": B, "segments": n,
                    "l2": "weights and one batch's activations stay in L2 (the step's working set)"},
         "loss_last": float(loss.item()),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -992,6 +993,7 @@ def main():
                              "local8_lattice", "4k_1024", "batch16",
                              "anim120", "surrogate", "infer", "lit", "train"])
     ap.add_argument("--rows", type=int, default=1 << 23, help="rows for --workload infer")
+    ap.add_argument("--batch", type=int, default=8192, help="batch for --workload train (a multiple of 128)")
     ap.add_argument("--resolution", default=None, help="WxH override (small cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dense", action="store_true", help="time the dense sums (no cull grid) as the step")

@@ -138,8 +138,8 @@ struct TraceParams {
   const uint32_t *cull_masks;  // null: dense sums over all bumps
   const float4 *cull_hdr;
   int cull_G, cull_words;
-  int step_lists;              // culled sums from one list per step (the step's reach <= kStepReach)
-  int list_steps;              // steps one list serves (their reach together <= kStepReach)
+  int step_lists;              // culled sums from step lists (the step's reach <= the masks' reach margin)
+  int list_steps;              // steps one list serves (their reach together <= the margin)
   int bundle;                  // segment tests in bundles of several chords (one query each)
   float b[3];
   float A[9];

@@ -279,9 +279,9 @@ __device__ __forceinline__ long long cull_cell(const TraceParams &P, float4 ghdr
 
 // The step list (all 32 lanes together): the union of the cells of the participating
 // lanes' positions x, listed and packed into the warp's pk.  The cull grid's supports are
-// inflated by kStepReach, which bounds the distance from x to every RK4 stage point of the
-// next P.list_steps steps (the launcher checks that), so the list holds every bump that can
-// be nonzero at any of their stages.  A union beyond the list's capacity leaves np = -1
+// inflated by the metric's reach margin, which bounds the distance from x to every RK4 stage
+// point of the next P.list_steps steps (the launcher checks that), so the list holds every
+// bump that can be nonzero at any of their stages.  A union beyond the list's capacity leaves np = -1
 // (the dense sums).
 __device__ __forceinline__ void step_list(const TraceParams &P, const float4 *__restrict__ sb, WarpLists &wl,
                                           float4 ghdr, bool part, F3 x) {
@@ -1400,8 +1400,8 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
 // ------------------------------------------------------ Riemannian illumination
 
 // The cull cell of x for the per-lane sums: its mask words, or null when x lies outside the
-// grid (which covers every bump's support inflated by kCullInflate + kStepReach, so no bump
-// reaches within kStepReach of x either).
+// grid (which covers every bump's support inflated by kCullInflate + the metric's reach
+// margin, so no bump reaches within that margin of x either).
 __device__ __forceinline__ const uint32_t *lane_cell(const TraceParams &P, F3 x) {
   const float4 ghdr = __ldg(P.cull_hdr);
   const int G = P.cull_G;
@@ -1412,8 +1412,9 @@ __device__ __forceinline__ const uint32_t *lane_cell(const TraceParams &P, F3 x)
 
 // Eq. 5.4 over the bumps of one cull cell's list, with no warp collective: for lanes that
 // follow their own paths (the light geodesics), each walks its own list and SIMT serialises
-// the differences.  cm is the cell of a position within kStepReach of x (a lane's list
-// serves the steps its reach covers, as the warps' step lists do), or null: no bumps.  The
+// the differences.  cm is the cell of x, or of a position within the metric's reach margin
+// of x (a lane's list serves the steps its reach covers, as the warps' step lists do), or
+// null: no bumps.  The
 // list's even-numbered bumps are paired with its odd-numbered ones as in the warp-wide
 // form, so the sums equal the dense sums.  Other metric kinds, and metrics without a cull
 // grid, take the dense sums (cm unused).
