@@ -751,6 +751,7 @@ def bench_surrogate(args):
                       "hit_err_p999_vs_oracle": p999})
     ok = [r for r in sweep if r["agree_1e-3_vs_oracle"] >= 0.999]
     best_plain = max(ok, key=lambda r: r["h"]) if ok else None
+    fastest_plain = min(ok, key=lambda r: r["ms_per_frame"]) if ok else None  # the equal-error baseline
     sur_agree, sur_p999 = err_vs_oracle(out)
     line = {
         "metric": "Mrays/s at 1080p/64 bumps traced with surrogate jumps (hit error <= 1e-3); plain RK4 alongside",
@@ -771,6 +772,8 @@ def bench_surrogate(args):
         "plain_step_sweep": sweep,
         "plain_at_own_largest_h": best_plain,
         "speed_ratio_vs_plain_at_own_h": (best_plain["ms_per_frame"] / (ms * 1e3)) if best_plain else None,
+        "plain_fastest_within_bar": fastest_plain,
+        "speed_ratio_vs_fastest_plain": (fastest_plain["ms_per_frame"] / (ms * 1e3)) if fastest_plain else None,
         "training": {"generate_s": gen_s, "train_s": train_s, "steps_per_s": steps / train_s,
                      "final_loss": train_loss,
                      "tensor_tflops": steps * B * 3 * mma_flops_row / train_s / 1e12},
