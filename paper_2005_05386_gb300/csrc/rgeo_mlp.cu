@@ -778,13 +778,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 constexpr int kTrThreads = 256;
 constexpr int kTrAct = kTileM * kWid * 2;          // 64 KB: 128 rows x K = 256 (core matrices, SBO 4096 B)
 constexpr int kTrTr = kWid * kTileM * 2;           // 64 KB: M = 256 x K = 128 (two 128-row halves, SBO 2048 B)
-constexpr int kTrStageB = kMaxTileN * kTileK * 2;  // 32 KB: 256 x 64 (SBO 1024 B)
+constexpr int kTrKStep = 32;                         // K columns per staged step of B
+constexpr int kTrNBuf = 4;                           // B stages in the ring: three loads in flight
+constexpr int kTrStageB = kMaxTileN * kTrKStep * 2;  // 16 KB: 256 x 32 (SBO 512 B)
 constexpr int kTrFloats = kOut * kWid + 2 * kWid + 3 * kTileM * 8;
-constexpr int kTrSmem = kTrAct + kTrTr + 2 * kTrStageB + kTrFloats * 4;  // 213 KB: one CTA per SM
+constexpr int kTrSmem = kTrAct + kTrTr + kTrNBuf * kTrStageB + kTrFloats * 4;  // 213 KB: one CTA per SM
 constexpr int kPartStride = (kParams + 1 + 3) & ~3;                      // floats per slot, 16-byte aligned
 constexpr int kRedQty = 8;  // column sums reduced at once (in the stage buffers, free in an epilogue)
 static_assert(kTrSmem <= 227 * 1024, "shared memory of the training kernel (one CTA per SM: it takes all of TMEM)");
-static_assert(kRedQty * 4 * kWid * 4 <= 2 * kTrStageB, "column-sum buffer in the stage buffers");
+static_assert(kRedQty * 4 * kWid * 4 <= 2 * kTrStageB, "column-sum buffer in stage buffers 0 and 1");
 static_assert(oW2 % 4 == 0 && oW3 % 4 == 0, "vector access to the weight-gradient slots");
 
 struct TrainArgs {
@@ -838,61 +840,83 @@ __device__ __forceinline__ float lane_sums(float (&v)[32]) {
   return v[0];
 }
 
-// Stage 0 of a product's B (rows brow0 .. brow0 + N - 1, K columns bk0 .. bk0 + 63) into sB,
-// ahead of the product: issued by all threads while the previous product's epilogue runs.
+// K columns k0 .. k0 + 31 of rows row0 .. row0 + rows - 1 of the row-major BF16 src (leading
+// dimension ld) into the canonical K-major layout of one B stage: core matrix (row group g, K
+// chunk c) at (4 g + c) * 128, row r at 16 (r % 8) within it (LBO 128, SBO 512).
+__device__ __forceinline__ void stage_b32(uint8_t *dst, const __nv_bfloat16 *src, int ld, int row0, int rows, int k0) {
+  for (int q = threadIdx.x; q < rows * 4; q += blockDim.x) {
+    const int r = q >> 2, c = q & 3;
+    cp_async16(dst + ((r >> 3) * 4 + c) * 128 + (r & 7) * 16, src + (size_t)(row0 + r) * ld + k0 + c * 8);
+  }
+}
+
+// One K step of a product's B (rows brow0 .. brow0 + N - 1, K columns bk0 .. bk0 + 31) into sB as
+// one cp.async group; issued by all threads, also ahead of the product while the previous
+// product's epilogue runs.
 __device__ __forceinline__ void prefetch_b(uint8_t *sB, const __nv_bfloat16 *B, int ldb, int brow0, int bk0, int N) {
-  stage_tile(sB, B, ldb, brow0, N, brow0 + N, bk0);
+  stage_b32(sB, B, ldb, brow0, N, bk0);
   cp_async_commit();
+}
+
+// Waits until at most n (0, 1 or 2) of this thread's most recent cp.async groups are pending.
+__device__ __forceinline__ void cp_async_wait_upto(int n) {
+  if (n >= 2)
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+  else if (n == 1)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // All threads of the CTA: TMEM columns acc.. (128 lanes x N) = A x B[brow0 + 0..N-1][bk0 + 0..K-1]^T,
 // A the 128 x K canonical operand in shared memory at a_base (row groups a_sbo bytes apart), B
-// row-major BF16 (leading dimension ldb) staged in 64-wide K stages double-buffered in sB, stage
-// s in sB[(fb + s) % 2] and signalled on bar of that buffer, whose phases ph tracks (K a
-// multiple of 64).  With pre, stage 0 is already in flight (prefetch_b into sB[fb]).  With
-// a_off2 > 0, a second 128-row A at a_base + a_off2 is multiplied by the same staged B into
-// columns acc2.. (the two halves of a weight gradient).  Returns with every MMA complete, or
-// false once a wait ran out (abort raised; the caller leaves, and the kernel's drain waits for
-// what is in flight).
-__device__ bool tile_gemm(uint32_t a_base, uint32_t a_sbo, uint8_t *sB0, uint8_t *sB1, const __nv_bfloat16 *B,
-                          int ldb, int brow0, int bk0, int N, int K, uint32_t acc, uint64_t *bar, uint32_t (&ph)[2],
+// row-major BF16 (leading dimension ldb) staged in 32-wide K steps through the ring sB of
+// kTrNBuf buffers, step s in sB[(fb + s) % kTrNBuf] and signalled on that buffer's bar, whose
+// phases ph tracks (K a multiple of 32): up to three steps load while the MMAs of an earlier one
+// run.  With pre, step 0 is already in flight (prefetch_b into sB[fb]).  With a_off2 > 0, a
+// second 128-row A at a_base + a_off2 is multiplied by the same staged B into columns acc2..
+// (the two halves of a weight gradient).  Returns with every MMA complete, or false once a wait
+// ran out (abort raised; the caller leaves, and the kernel's drain waits for what is in flight).
+__device__ bool tile_gemm(uint32_t a_base, uint32_t a_sbo, uint8_t *const *sB, const __nv_bfloat16 *B, int ldb,
+                          int brow0, int bk0, int N, int K, uint32_t acc, uint64_t *bar, uint32_t (&ph)[kTrNBuf],
                           volatile int *abort, long long polls, int fb, bool pre, uint32_t a_off2 = 0u,
                           uint32_t acc2 = 0u) {
-  uint8_t *sB[2] = {sB0, sB1};
-  const int nst = K / kTileK;
+  const int nst = K / kTrKStep;
+  const int ahead = nst < kTrNBuf - 1 ? nst : kTrNBuf - 1;  // steps loaded ahead of the MMAs
   const uint32_t idesc = idesc_bf16(kTileM, N);
-  if (!pre) prefetch_b(sB[fb], B, ldb, brow0, bk0, N);
+  for (int i = pre ? 1 : 0; i < ahead; ++i) prefetch_b(sB[(fb + i) % kTrNBuf], B, ldb, brow0, bk0 + i * kTrKStep, N);
   for (int s = 0; s < nst; ++s) {
-    const int buf = (fb + s) & 1;
-    cp_async_wait_all();
+    const int buf = (fb + s) % kTrNBuf;
+    const int committed = s + ahead < nst ? s + ahead : nst;  // steps 0 .. committed - 1 are in flight or landed
+    cp_async_wait_upto(committed - s - 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // also orders the epilogue's operand writes
     __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t b0 = smem_u32(sB[buf]);
-      for (int kk = 0; kk < kTileK / 16; ++kk) {
-        const uint32_t ao = (uint32_t)(s * 1024 + kk * 256), accum = (s > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 1024);
+      for (int kk = 0; kk < kTrKStep / 16; ++kk) {
+        const uint32_t ao = (uint32_t)(s * 512 + kk * 256), accum = (s > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t bd = smem_desc(b0 + kk * 256, 128, 512);
         mma_bf16(acc, smem_desc(a_base + ao, 128, a_sbo), bd, idesc, accum);
         if (a_off2) mma_bf16(acc2, smem_desc(a_base + a_off2 + ao, 128, a_sbo), bd, idesc, accum);
       }
       mma_commit(&bar[buf]);
     }
-    if (s + 1 < nst) {
-      const int nb = buf ^ 1;
-      if (s >= 1) {  // the MMAs of stage s - 1 read buffer nb
-        if (!mbar_wait(&bar[nb], ph[nb], polls)) *abort = 1;
-        ph[nb] ^= 1u;
+    const int nxt = s + ahead;  // the step loaded now, into the buffer of step s - 1
+    if (nxt < nst) {
+      if (s >= 1) {  // the MMAs of step s - 1 read that buffer
+        const int pb = (fb + s - 1) % kTrNBuf;
+        if (!mbar_wait(&bar[pb], ph[pb], polls)) *abort = 1;
+        ph[pb] ^= 1u;
       }
       __syncthreads();
       if (*abort) return false;
-      stage_tile(sB[nb], B, ldb, brow0, N, brow0 + N, bk0 + (s + 1) * kTileK);
-      cp_async_commit();
+      prefetch_b(sB[(fb + nxt) % kTrNBuf], B, ldb, brow0, bk0 + nxt * kTrKStep, N);
     }
   }
-  // the commits of the last two stages (or the only one) have not been waited for yet
-  for (int s = nst >= 2 ? nst - 2 : 0; s < nst; ++s) {
-    const int b = (fb + s) & 1;
+  // the steps whose MMAs have not been waited for: the in-loop waits took steps 0 .. nst - ahead - 2
+  for (int s = nst - ahead - 1 > 0 ? nst - ahead - 1 : 0; s < nst; ++s) {
+    const int b = (fb + s) % kTrNBuf;
     if (!mbar_wait(&bar[b], ph[b], polls)) *abort = 1;
     ph[b] ^= 1u;
   }
@@ -945,13 +969,17 @@ __device__ __forceinline__ void add_weight_grad(uint32_t tl, int half, int row, 
 
 __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a) {
   extern __shared__ __align__(1024) uint8_t tsm[];
-  uint8_t *sAct = tsm, *sTr = tsm + kTrAct, *sB0 = sTr + kTrTr, *sB1 = sB0 + kTrStageB;
-  float *red = reinterpret_cast<float *>(sB0);  // [kRedQty][4 row quarters][256 columns], in an epilogue
-  float *w4s = reinterpret_cast<float *>(sB1 + kTrStageB);  // [7][256]
+  uint8_t *sAct = tsm, *sTr = tsm + kTrAct;
+  uint8_t *const sB[kTrNBuf] = {sTr + kTrTr, sTr + kTrTr + kTrStageB, sTr + kTrTr + 2 * kTrStageB,
+                                sTr + kTrTr + 3 * kTrStageB};
+  // [kRedQty][4 row quarters][256 columns] in an epilogue, over stage buffers 0 and 1 (an epilogue
+  // that uses it prefetches the next product's first step into buffer 2)
+  float *red = reinterpret_cast<float *>(sB[0]);
+  float *w4s = reinterpret_cast<float *>(sB[kTrNBuf - 1] + kTrStageB);  // [7][256]
   float *b2s = w4s + kOut * kWid, *b3s = b2s + kWid;
   float *xs = b3s + kWid, *dys = xs + kTileM * 8, *part4 = dys + kTileM * 8;  // [128][8] each
   const uint32_t aAct = smem_u32(sAct), aTr = smem_u32(sTr);
-  __shared__ uint64_t bar[2], drain;
+  __shared__ uint64_t bar[kTrNBuf], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ float loss_w[kTrThreads / 32];
@@ -961,8 +989,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
   const int q = warp & 3, half = warp >> 2, row = q * 32 + lane;
   const int Bn = a.B, ntiles = Bn / kTileM;
   if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < kTrNBuf; ++b) mbar_init(&bar[b], 1);
     mbar_init(&drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -981,7 +1008,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-  uint32_t ph[2] = {0u, 0u};
+  uint32_t ph[kTrNBuf] = {0u, 0u, 0u, 0u};
   float *slot = a.part + (size_t)blockIdx.x * kPartStride;
   // this thread's share of the small gradients, summed over the CTA's tiles: column t of
   // layers 1 (dW1 row, db1), 2 (db2), 3 (db3) and 4 (dW4 column; db4 for t < 7)
@@ -1021,10 +1048,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
       }
     }
     // ---- Z2 = H1 W2^T; H2 = relu(Z2 + b2) into sAct, and as BF16 rows and transposed in L2
-    // (stage 0 of W2 was prefetched into sB1 during the previous tile's last epilogue)
-    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W2b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 1, !first))
+    // (step 0 of W2 was prefetched into buffer 2 during the previous tile's last epilogue)
+    if (!tile_gemm(aAct, 4096, sB, a.W2b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 2, !first))
       break;
-    prefetch_b(sB0, a.W3b, kWid, 0, 0, kWid);
+    prefetch_b(sB[0], a.W3b, kWid, 0, 0, kWid);
     for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
       uint32_t v[32], pk[16];
       tmem_ld32_nowait(tl + (uint32_t)c0, v);
@@ -1037,9 +1064,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     // ---- Z3 = H2 W3^T; H3 = relu(Z3 + b3) (BF16); layer 4 (FP32) from the BF16 H3
-    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W3b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
+    if (!tile_gemm(aAct, 4096, sB, a.W3b, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
       break;
-    prefetch_b(sB1, a.H2t, Bn, 0, m0, kWid);  // the epilogue's column sums use sB0
+    prefetch_b(sB[2], a.H2t, Bn, 0, m0, kWid);  // the epilogue's column sums use buffers 0 and 1
     {
       float y[kOut];
       for (int o = 0; o < kOut; ++o) y[o] = 0.f;
@@ -1120,16 +1147,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
     }
     // ---- the tile's dW3 = dZ3^T H2 (K = its 128 rows; both 128-row halves of dW3 per staged H2^T
     // stage), added into the CTA's slot
-    if (!tile_gemm(aTr, 2048, sB0, sB1, a.H2t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp, a.polls, 1, true,
+    if (!tile_gemm(aTr, 2048, sB, a.H2t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp, a.polls, 2, true,
                    16u * 2048u, tmem + kWid))
       break;
-    prefetch_b(sB0, a.W3t, kWid, 0, 0, kWid);
+    prefetch_b(sB[0], a.W3t, kWid, 0, 0, kWid);
     add_weight_grad(tl, half, row, slot + oW3, first);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     // ---- dH2 = dZ3 W3; dZ2 = bf16(dH2 [H2 > 0]) into sAct and sTr; db2 = column sums of the FP32 values
-    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W3t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
+    if (!tile_gemm(aAct, 4096, sB, a.W3t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
       break;
-    prefetch_b(sB1, a.H1t, Bn, 0, m0, kWid);  // the epilogue's column sums use sB0
+    prefetch_b(sB[2], a.H1t, Bn, 0, m0, kWid);  // the epilogue's column sums use buffers 0 and 1
     for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
       uint32_t v[32], pz[16];
       tmem_ld32_nowait(tl + (uint32_t)c0, v);
@@ -1155,16 +1182,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_train_tile(const TrainArgs a)
     // (the next product's first stage overwrites red: tile_gemm synchronises before it stages)
     __syncthreads();
     // ---- the tile's dW2 = dZ2^T H1, as dW3
-    if (!tile_gemm(aTr, 2048, sB0, sB1, a.H1t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp, a.polls, 1, true,
+    if (!tile_gemm(aTr, 2048, sB, a.H1t, Bn, 0, m0, kWid, kTileM, tmem, bar, ph, abortp, a.polls, 2, true,
                    16u * 2048u, tmem + kWid))
       break;
-    prefetch_b(sB0, a.W2t, kWid, 0, 0, kWid);
+    prefetch_b(sB[0], a.W2t, kWid, 0, 0, kWid);
     add_weight_grad(tl, half, row, slot + oW2, first);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     // ---- dH1 = dZ2 W2; dZ1 = dH1 [H1 > 0] (FP32); db1 and dW1 = dZ1^T X as column sums
-    if (!tile_gemm(aAct, 4096, sB0, sB1, a.W2t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
+    if (!tile_gemm(aAct, 4096, sB, a.W2t, kWid, 0, 0, kWid, kWid, tmem, bar, ph, abortp, a.polls, 0, true))
       break;
-    if (tile + (int)gridDim.x < ntiles) prefetch_b(sB1, a.W2b, kWid, 0, 0, kWid);  // the next tile's Z2
+    if (tile + (int)gridDim.x < ntiles) prefetch_b(sB[2], a.W2b, kWid, 0, 0, kWid);  // the next tile's Z2
     {
       float xr[kIn];
       for (int i = 0; i < kIn; ++i) xr[i] = xs[row * 8 + i];
