@@ -598,6 +598,8 @@ __device__ __forceinline__ F3 accel(const TraceParams &P, const float4 *sb, cons
       return accel_graph_iso_culled<INSIDE>(P, sb, cx.wl->idx, cx.ghdr, cx.part, x, v, inside, *cx.evals);
     if (cx.part) cx.evals->evals += (unsigned)P.K;
     cx.evals->slots += (unsigned)iso_pad_index(P.K);
+    // the block's packed table (k_trace) or the table itself: the same sums in the same order
+    if (cx.wl->pk) return accel_step_list<INSIDE>(P, *cx.wl, x, v, inside);
     return accel_graph_iso<INSIDE>(P, sb, P.K, x, v, inside);
   }
   if (MK == MK_GRAPH_ANISO) {
@@ -1344,10 +1346,31 @@ constexpr int kWarpsPerBlock = 4;
 // Chords per bundle when segment tests are bundled (RGEO_FLAG_BUNDLE).
 constexpr int kBundle = 4;
 
+// Dense sums of the isotropic graph metric from the bump table packed in pairs (up to this many
+// bumps: two float4 per bump more in shared memory).
+constexpr int kDensePackBumps = 512;
+__host__ __device__ inline bool dense_packed(int mk, const TraceParams &P) {
+  return mk == MK_GRAPH_ISO && !P.cull_masks && P.K > 0 && P.K <= kDensePackBumps;
+}
+
 // float4s of a trace block's warp lists: index lists for the culled sums, packed pairs too
-// for step lists.
+// for step lists; for packed dense sums, the block's one packed copy of the table.
 __host__ __device__ inline int trace_lists_float4(int mk, const TraceParams &P) {
+  if (dense_packed(mk, P)) return 2 * iso_pad_index(P.K);
   return (mk == MK_GRAPH_SL || P.cull_masks) ? kWarpsPerBlock * lists_float4(mk == MK_GRAPH_SL) : 0;
+}
+
+// The bump table staged in sb, packed in pairs (2 j, 2 j + 1) into pk in the layout of the step
+// lists (WarpLists), for the dense sums: every pair read by one paired-FP32 instruction per
+// operation.  All threads of the block, then a barrier.
+__device__ __forceinline__ void pack_dense_pairs(const float4 *sb, int K, float4 *pk) {
+  const int np = iso_pad_index(K) / 2;
+  for (int t = threadIdx.x; t < 4 * np; t += blockDim.x) {
+    const int j = t >> 2, half = (t >> 1) & 1;  // float4 0, 1 from A, 2, 3 from B
+    const float4 a = sb[kIsoBumpStride * (2 * j) + half], b = sb[kIsoBumpStride * (2 * j + 1) + half];
+    pk[t] = (t & 1) == 0 ? make_float4(a.x, b.x, a.y, b.y) : make_float4(a.z, b.z, a.w, b.w);
+  }
+  __syncthreads();
 }
 
 // One ray per thread (every metric kind).  MINB 128-thread CTAs per SM at least: seven (72
@@ -1364,6 +1387,10 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   const float4 *ss = smem + nb4;
   float4 *const lists = smem + nb4 + (P.nodes ? 0 : P.S);
   WarpLists wl = warp_lists(MK == MK_GRAPH_SL, lists);
+  if (dense_packed(MK, P)) {  // the dense sums take the block's packed copy of the table
+    pack_dense_pairs(sb, P.K, lists);
+    wl = WarpLists{nullptr, lists, iso_pad_index(P.K) / 2, 0u, 0};
+  }
   // the threads' bundle slots (NB > 1), after the warps' lists: slot i of thread t at i * 128 + t
   float4 *const bs = lists + trace_lists_float4(MK, P) + threadIdx.x;
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
