@@ -524,7 +524,7 @@ def bench_batch(args):
     dt = 1.0 / 30.0
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     frames = 120 if anim else args.steps
-    default = dict(cull_grid=0, rays_per_thread=1, ctas_per_sm=0, tile_shape=0, sum_lists=0, batch_order=0)
+    default = dict(cull_grid=0, rays_per_thread=1, ctas_per_sm=0, tile_shape=0, sum_lists=0, batch_order=0, refill=0)
 
     def timed(schedule, modes=(0, 1), orders=(0,)):
         """Frames of the batch under a schedule; the instance-table source and the instance

@@ -564,6 +564,12 @@ rgeo_status rgeo_trace_noalloc(const float *center, const float *amplitude, cons
  *                    was made (metrics of up to 512 bumps, whose cull masks carry
  *                    that margin), else a list per right-hand side; 1 always per
  *                    right-hand side; 2 one list per RK4 step.
+ *   refill           when the lanes of a trace warp take new rays from the queue:
+ *                    0 (default) in generations, the warp taking the next 32
+ *                    items once all of its rays have finished: its rays start
+ *                    from one tile together and stay close, so the bump lists
+ *                    its lanes share stay short, and its lanes take the same
+ *                    branches longer; 1 each lane as soon as its ray has finished.
  * A setting is read when a trace or batch is enqueued or created (a captured
  * graph keeps the choice made at capture); it is not synchronised between host
  * threads.  Errors: RGEO_EINVAL (NULL, bad value, nonzero reserved fields). */
@@ -575,6 +581,7 @@ typedef struct {
   int32_t tile_shape;
   int32_t batch_order;
   int32_t sum_lists;
+  int32_t refill;
   int32_t reserved[1]; /* must be zero */
 } rgeo_tuning;
 

@@ -78,11 +78,11 @@ class rgeo_tuning(ctypes.Structure):
     _fields_ = [("rays_per_thread", ctypes.c_int32), ("batch_params", ctypes.c_int32),
                 ("wait_limit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("tile_shape", ctypes.c_int32), ("batch_order", ctypes.c_int32), ("sum_lists", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("refill", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 TUNING_FIELDS = ("rays_per_thread", "batch_params", "wait_limit", "ctas_per_sm", "tile_shape", "batch_order",
-                 "sum_lists")
+                 "sum_lists", "refill")
 
 
 class rgeo_outputs(ctypes.Structure):
@@ -482,10 +482,11 @@ def rgeo_sync(stream=None):
 
 
 def rgeo_set_tuning(rays_per_thread: int = 0, batch_params: int = 0, wait_limit: int = 0, ctas_per_sm: int = 0,
-                    tile_shape: int = 0, batch_order: int = 0, sum_lists: int = 0):
+                    tile_shape: int = 0, batch_order: int = 0, sum_lists: int = 0, refill: int = 0):
     t = rgeo_tuning()
     t.rays_per_thread, t.batch_params, t.wait_limit = rays_per_thread, batch_params, wait_limit
     t.ctas_per_sm, t.tile_shape, t.batch_order, t.sum_lists = ctas_per_sm, tile_shape, batch_order, sum_lists
+    t.refill = refill
     _check(library().rgeo_set_tuning(ctypes.byref(t)), "rgeo_set_tuning")
 
 

@@ -17,6 +17,9 @@ warp, so every candidate gives the same image bit for bit.
   sum_lists        culled bump sums from one list for as many RK4 steps as its reach
                    covers (0) or from one per right-hand side (1)
   batch_order      batches: instances by decreasing cost (0) or as given (1)
+  refill           a warp takes new rays in generations of 32, once all of its rays have
+                   finished (0, the default), or each lane as soon as its ray has finished (1);
+                   the second is timed with the default CTAs per SM only
 
 The candidate set is the product of the knobs that apply to the workload's metric
 (the grid, list and thread knobs only to isotropic truncated bumps).  The winner is
@@ -37,7 +40,8 @@ CANDIDATE_GRIDS = (-1, 96, 128, 192)
 CANDIDATE_CTAS = (0, 6, 5)
 CANDIDATE_TILES = (1, 2)
 CANDIDATE_LISTS = (0, 1)
-KNOBS = ("cull_grid", "rays_per_thread", "ctas_per_sm", "tile_shape", "sum_lists", "batch_order")
+CANDIDATE_REFILL = (0, 1)
+KNOBS = ("cull_grid", "rays_per_thread", "ctas_per_sm", "tile_shape", "sum_lists", "batch_order", "refill")
 
 
 def cache_path() -> str:
@@ -83,18 +87,20 @@ def candidates(work: scenes.Workload, batch: bool = False):
     orders = (0, 1) if batch else (0,)
     out = []
     if culled:
-        for g, c, t, s, b in itertools.product(CANDIDATE_GRIDS, CANDIDATE_CTAS, CANDIDATE_TILES, CANDIDATE_LISTS,
-                                               orders):
-            if g == -1 and s == 1:
-                continue  # dense sums take no lists
+        for g, c, t, s, b, f in itertools.product(CANDIDATE_GRIDS, CANDIDATE_CTAS, CANDIDATE_TILES, CANDIDATE_LISTS,
+                                                  orders, CANDIDATE_REFILL):
+            if (g == -1 and s == 1) or (f == 1 and c != 0):
+                continue  # dense sums take no lists; per-lane refill with the default CTAs only
             out.append(dict(cull_grid=g, rays_per_thread=1, ctas_per_sm=c, tile_shape=t, sum_lists=s,
-                            batch_order=b))
-        out += [dict(cull_grid=-1, rays_per_thread=2, ctas_per_sm=0, tile_shape=t, sum_lists=0, batch_order=b)
-                for t, b in itertools.product(CANDIDATE_TILES, orders)]
+                            batch_order=b, refill=f))
+        out += [dict(cull_grid=-1, rays_per_thread=2, ctas_per_sm=0, tile_shape=t, sum_lists=0, batch_order=b,
+                     refill=0) for t, b in itertools.product(CANDIDATE_TILES, orders)]
     else:
-        for c, t, b in itertools.product(CANDIDATE_CTAS, CANDIDATE_TILES, orders):
+        for c, t, b, f in itertools.product(CANDIDATE_CTAS, CANDIDATE_TILES, orders, CANDIDATE_REFILL):
+            if f == 1 and c != 0:
+                continue
             out.append(dict(cull_grid=-1, rays_per_thread=1, ctas_per_sm=c, tile_shape=t, sum_lists=0,
-                            batch_order=b))
+                            batch_order=b, refill=f))
     return out
 
 
@@ -103,7 +109,8 @@ def set_schedule(choice: dict, batch_params: int = 0):
     from . import rgeo_set_tuning
     rgeo_set_tuning(rays_per_thread=int(choice["rays_per_thread"]), batch_params=batch_params,
                     ctas_per_sm=int(choice["ctas_per_sm"]), tile_shape=int(choice["tile_shape"]),
-                    batch_order=int(choice.get("batch_order", 0)), sum_lists=int(choice["sum_lists"]))
+                    batch_order=int(choice.get("batch_order", 0)), sum_lists=int(choice["sum_lists"]),
+                    refill=int(choice.get("refill", 0)))
 
 
 def tune(work: scenes.Workload, repeats: int = 2, use_cache: bool = True, verbose: bool = False,

@@ -197,6 +197,7 @@ rgeo::TraceParams make_params(const rgeo_metric *metric, const rgeo_scene *scene
   p.bump_evals = out->bump_evals;
   p.bump_slots = out->bump_slots;
   p.rays_per_thread = rgeo::tuning().rays_per_thread;
+  p.refill_lanes = rgeo::tuning().refill;
   return p;
 }
 
@@ -731,6 +732,7 @@ rgeo_status rgeo_set_tuning(const rgeo_tuning *t) {
   if (t->batch_order != 0 && t->batch_order != 1)
     return fail(RGEO_EINVAL, "rgeo_set_tuning: batch_order must be 0 or 1");
   if (t->sum_lists < 0 || t->sum_lists > 2) return fail(RGEO_EINVAL, "rgeo_set_tuning: sum_lists must be 0, 1 or 2");
+  if (t->refill != 0 && t->refill != 1) return fail(RGEO_EINVAL, "rgeo_set_tuning: refill must be 0 or 1");
   rgeo::Tuning &g = rgeo::tuning();
   const rgeo::Tuning d;
   g.rays_per_thread = t->rays_per_thread == 0 ? d.rays_per_thread : t->rays_per_thread;
@@ -740,6 +742,7 @@ rgeo_status rgeo_set_tuning(const rgeo_tuning *t) {
   g.tile_lw = t->tile_shape == 0 ? d.tile_lw : (t->tile_shape == 1 ? 3 : (t->tile_shape == 2 ? 2 : 4));
   g.batch_order = t->batch_order;
   g.sum_lists = t->sum_lists;
+  g.refill = t->refill;
   return RGEO_OK;
 }
 
@@ -755,6 +758,7 @@ rgeo_status rgeo_get_tuning(rgeo_tuning *t) {
   t->tile_shape = g.tile_lw == 3 ? 1 : (g.tile_lw == 2 ? 2 : 3);
   t->batch_order = g.batch_order;
   t->sum_lists = g.sum_lists;
+  t->refill = g.refill;
   return RGEO_OK;
 }
 

@@ -182,6 +182,7 @@ struct TraceParams {
   uint32_t *counter;
   // launch shape
   int rays_per_thread;  // 1, or 2 (isotropic graph metric only)
+  int refill_lanes;     // 0: a warp takes new rays once all of its rays have finished; 1: each lane as its ray finishes
 };
 
 // State of the surrogate tracer: per-ray SoA over the N = W * H pixels, the queue of
@@ -231,6 +232,7 @@ struct Tuning {
   int tile_lw = 2;          // refill tile width log2: 2 (4 x 8, default), 3 (8 x 4), 4 (16 x 2)
   int batch_order = 0;      // batch instances: 0 by decreasing cost, 1 as given
   int sum_lists = 0;        // culled sums: 0 one list per RK4 step where it applies, 1 one per right-hand side
+  int refill = 0;           // 0: a warp takes new rays in generations of 32; 1: each lane as soon as it is free
 };
 Tuning &tuning();
 

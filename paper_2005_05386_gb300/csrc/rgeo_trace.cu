@@ -1146,11 +1146,16 @@ __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, b
 // Warp-synchronous refill from a warp-private chunk of 32 consecutive items (one 32-pixel
 // tile, 4 x 8 by default) taken from the queue one chunk at a time: the rays a warp starts come from the same
 // tile, so its lanes stay closer together and the union of their cull cells stays smaller.
-// cnext / cend (the chunk's next and end item) are the same on every lane.
+// By default (P.refill_lanes == 0) the warp takes rays in generations: only once every ray
+// it holds has finished, so that the 32 rays of a tile march side by side from the camera
+// (most of them run to the step budget together) instead of a fresh ray starting next to
+// rays far along their paths, which widens the warp's bump lists.  cnext / cend (the chunk's
+// next and end item) are the same on every lane.
 template <int MK>
 __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *sb, bool &active, bool &drained,
                                             Ray &r, unsigned &cnext, unsigned &cend) {
   const unsigned lane = threadIdx.x & 31u;
+  if (!P.refill_lanes && __any_sync(0xffffffffu, active)) return;
   for (int pass = 0; pass < 2; ++pass) {
     const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
     if (!need) return;
@@ -1379,7 +1384,9 @@ __device__ __forceinline__ void pack_dense_pairs(const float4 *sb, int K, float4
 // (rgeo_tuning.ctas_per_sm <= 5), for the isotropic graph metric.  For the
 // isotropic graph metric every lane runs every evaluation of the bump sums (a lane without
 // a ray joins with empty masks), so that the warp can build its pair list together.
-template <int MK, int INTEG, int MINB, int NB>
+// COUNT false (a launch without work counters) leaves the per-lane counts unread, so the
+// compiler drops them.
+template <int MK, int INTEG, int MINB, int NB, bool COUNT = true>
 __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
@@ -1421,7 +1428,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
     if (go) active = post_step<MK, NB>(P, sb, ss, r, dx, dvel, bs);
     ++wl.age;
   }
-  evals.flush(P);
+  if (COUNT) evals.flush(P);
 }
 
 // ------------------------------------------------------ Riemannian illumination
@@ -2536,9 +2543,12 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   // CTAs per SM at least (the register budget): 7 (72 registers) for the isotropic graph metric,
   // measured 3 % faster at 1080p than 6 and 8; 5 (102) for the local-map jet and on request
   constexpr int kDefaultMinb = is_iso(MK) ? 7 : 6;
+  // the step-list kernel without work counters when the launch asks for none (1 % faster at 1080p)
+  const bool count = p.bump_evals != nullptr || p.bump_slots != nullptr;
   void (*kern)(const TraceParams) =
       bundle ? (five ? k_trace<MK, 0, 5, kBundle> : k_trace<MK, 0, kDefaultMinb, kBundle>)
-             : (five ? k_trace<MK, INTEG, 5, 1> : k_trace<MK, INTEG, kDefaultMinb, 1>);
+             : (five ? k_trace<MK, INTEG, 5, 1>
+                     : (count ? k_trace<MK, INTEG, kDefaultMinb, 1> : k_trace<MK, INTEG, kDefaultMinb, 1, MK != MK_GRAPH_SL>));
   if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

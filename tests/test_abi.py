@@ -171,3 +171,26 @@ def test_trace_lit_validation(rg):
     with pytest.raises(rg.RgeoError) as e:
         rg.rgeo_trace_lit(fake, fake, cam, 4, 4, 0.01, 10, 0, lt, out, 0, stream=0)
     assert "reserved" in str(e.value)
+
+
+def test_tuning_round_trip_and_validation(rg):
+    """The launch tuning is host state: set and read back, defaults restored, bad values and
+    nonzero reserved fields rejected (no device call)."""
+    try:
+        rg.rgeo_set_tuning(refill=1, tile_shape=1, sum_lists=2)
+        t = rg.rgeo_get_tuning()
+        assert (t["refill"], t["tile_shape"], t["sum_lists"]) == (1, 1, 2)
+        rg.rgeo_set_tuning()
+        t = rg.rgeo_get_tuning()
+        assert (t["refill"], t["tile_shape"], t["sum_lists"], t["rays_per_thread"]) == (0, 2, 0, 1)
+        for kw in (dict(refill=2), dict(refill=-1), dict(sum_lists=3), dict(tile_shape=4), dict(ctas_per_sm=33),
+                   dict(wait_limit=-2), dict(rays_per_thread=3), dict(batch_order=2)):
+            with pytest.raises(rg.RgeoError) as e:
+                rg.rgeo_set_tuning(**kw)
+            assert e.value.status == rg.RGEO_EINVAL, kw
+        bad = rg.rgeo_tuning()
+        bad.reserved[0] = 1
+        assert rg.library().rgeo_set_tuning(ctypes.byref(bad)) == rg.RGEO_EINVAL
+        assert "reserved" in rg.rgeo_last_error()
+    finally:
+        rg.rgeo_set_tuning()

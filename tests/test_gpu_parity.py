@@ -420,7 +420,8 @@ def test_frame_parts_and_tuning_reproduce_the_frame_bit_for_bit(rg):
     """Every lane sums its own bumps in the order of the dense sums whatever shares its warp,
     so the frame is the same bit for bit when it is split into interleaved tile parts
     (rgeo_trace_tiles, the multi-GPU split) and under every launch tuning: tile shape, CTAs per
-    SM (with the 96-register build), lists per step or per right-hand side."""
+    SM (with the 96-register build), lists per step or per right-hand side, rays taken by
+    whole warps or lane by lane."""
     w = scenes.config_1080p_64(width=320, height=180)
     ref = _run(rg, w)
     N = w.n_pixels
@@ -442,13 +443,35 @@ def test_frame_parts_and_tuning_reproduce_the_frame_bit_for_bit(rg):
     with pytest.raises(rg.RgeoError):
         rg.trace(w, out=out, tiles=(0, -1, 0))
     for kw in (dict(tile_shape=2), dict(tile_shape=3), dict(ctas_per_sm=5), dict(ctas_per_sm=3),
-               dict(sum_lists=1), dict(sum_lists=2), dict(sum_lists=1, ctas_per_sm=5)):
+               dict(sum_lists=1), dict(sum_lists=2), dict(sum_lists=1, ctas_per_sm=5), dict(refill=1),
+               dict(refill=1, sum_lists=1)):
         try:
             rg.rgeo_set_tuning(**kw)
             g = _run(rg, w)
         finally:
             rg.rgeo_set_tuning()
         same(g)
+
+
+@pytest.mark.parametrize("config", ["twist", "local8", "aniso"])
+def test_refill_policies_give_the_same_frame(rg, config):
+    """The metrics whose lanes march independently give the same frame bit for bit whether a
+    warp takes its rays in generations (the default) or lane by lane (rgeo_tuning.refill = 1)."""
+    if config == "aniso":
+        w = scenes.config_1080p_64(width=160, height=90)
+        w.metric.sigma = w.metric.sigma * np.array([1.0, 1.2, 0.9], np.float32)
+    else:
+        w = {"twist": lambda: scenes.scaled(scenes.config_1080p_twist(), 160, 90),
+             "local8": lambda: scenes.scaled(scenes.config_local_lattice(K=8), 120, 68)}[config]()
+    ref = _run(rg, w)
+    for refill in (1,):
+        try:
+            rg.rgeo_set_tuning(refill=refill)
+            g = _run(rg, w)
+        finally:
+            rg.rgeo_set_tuning()
+        for k in ("id", "steps", "rgba", "hit"):
+            assert np.array_equal(g[k], ref[k]), (refill, k)
 
 
 @pytest.mark.parametrize("config", ["1080p_64", "twist", "quad_lattice", "local8"])

@@ -47,6 +47,7 @@ def test_autotuner_candidates_follow_the_metric():
     assert {x["ctas_per_sm"] for x in c} == set(autotune.CANDIDATE_CTAS)
     assert {x["tile_shape"] for x in c} == set(autotune.CANDIDATE_TILES)
     assert {x["sum_lists"] for x in c} == {0, 1}
+    assert {x["refill"] for x in c} == {0, 1} and all(x["ctas_per_sm"] == 0 for x in c if x["refill"] == 1)
     assert all(x["sum_lists"] == 0 for x in c if x["cull_grid"] == -1)  # dense sums take no lists
     assert all(x["cull_grid"] == -1 for x in c if x["rays_per_thread"] == 2)
     assert {x["batch_order"] for x in c} == {0} and {x["batch_order"] for x in autotune.candidates(w, True)} == {0, 1}
@@ -54,6 +55,7 @@ def test_autotuner_candidates_follow_the_metric():
         oc = autotune.candidates(other)
         assert {x["cull_grid"] for x in oc} == {-1} and {x["rays_per_thread"] for x in oc} == {1}
         assert {x["tile_shape"] for x in oc} == set(autotune.CANDIDATE_TILES)
+        assert {x["refill"] for x in oc} == {0, 1} and all(x["ctas_per_sm"] == 0 for x in oc if x["refill"] == 1)
     aniso = scenes.config_1080p_64()
     aniso.metric.sigma = aniso.metric.sigma * np.array([1.0, 1.2, 0.9], np.float32)
     assert {x["cull_grid"] for x in autotune.candidates(aniso)} == {-1}
