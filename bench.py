@@ -879,7 +879,7 @@ def bench_lit(args):
         "plain_ms": ms_plain, "illumination_ms": ms_illum,
         "hits_lit_unlit": [int(((ids >= 0) & (lit == 1)).sum()), int(((ids >= 0) & (lit == 0)).sum())],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_illuminate (per-lane culled bump sums)",
+                     "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_illuminate_sl (lockstep light geodesics, shared culled bump lists)",
                      "flops_per_launch": flops, "bump_terms_per_launch": terms_illum,
                      "kernel_ms": ms_illum, "timing": "lit frame minus plain frame, CUDA events"},
         "clocks": clk, "gpu_launches": args.steps * 3,

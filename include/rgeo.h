@@ -273,14 +273,18 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
  *     segment of the light geodesic up to its closest approach meets the scene;
  *   - colour albedo * (0.1 + 0.9 cos) when lit, albedo * 0.1 otherwise (no fog).
  * The light geodesics sum, at each point, the bumps of its cull-grid cell (every bump
- * when the metric has no cull grid), each lane on its own; out->bump_evals, when given,
- * receives the bump terms of the view rays and of the light geodesics together.
+ * when the metric has no cull grid).  For isotropic truncated bumps with a cull grid (up
+ * to 512 bumps) a warp's 30 light geodesics advance in lockstep by default and sum one
+ * shared list of bumps, the union of their cells; schedule = 1, and every other metric,
+ * has each lane walk its own cell's list.  Both give the same image bit for bit.
+ * out->bump_evals, when given, receives the bump terms of the view rays and of the light
+ * geodesics together.
  * `lit` (DEVICE [W*H] int32, may be NULL) receives 1 for lit hits, else 0.
  * Allocates a work counter and a 12-byte-per-pixel normal buffer with
  * cudaMallocAsync on the stream.  Asynchronous on the stream.
  * Errors: those of rgeo_trace, and RGEO_EINVAL for a NULL light, a non-finite
- * light position, h or tol or delta not finite or <= 0, max_steps < 1, iters < 0
- * or nonzero reserved fields. */
+ * light position, h or tol or delta not finite or <= 0, max_steps < 1, iters < 0,
+ * a schedule other than 0 or 1, or nonzero reserved fields. */
 typedef struct {
   float pos[3];      /* the point light L */
   float h;           /* step of the light geodesics */
@@ -288,7 +292,8 @@ typedef struct {
   int32_t iters;     /* Gauss-Newton steps at most */
   float tol;         /* miss distance that counts as reaching the light */
   float delta;       /* forward-difference step of the Jacobian */
-  int32_t reserved[4]; /* must be zero */
+  int32_t schedule;  /* 0 (default): lockstep marches where they apply; 1: each lane on its own */
+  int32_t reserved[3]; /* must be zero */
 } rgeo_light;
 
 rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, const rgeo_camera *camera,

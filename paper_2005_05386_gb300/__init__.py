@@ -71,7 +71,7 @@ class rgeo_camera(ctypes.Structure):
 class rgeo_light(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_float * 3), ("h", ctypes.c_float), ("max_steps", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("tol", ctypes.c_float), ("delta", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class rgeo_tuning(ctypes.Structure):
@@ -641,7 +641,7 @@ def trace(work: scenes.Workload, metric: Metric = None, scene: Scene = None, out
 
 def light_struct(light: scenes.Light) -> rgeo_light:
     return rgeo_light((ctypes.c_float * 3)(*light.pos), light.h, light.max_steps, light.iters, light.tol,
-                      light.delta, (ctypes.c_int32 * 4)())
+                      light.delta, light.schedule, (ctypes.c_int32 * 3)())
 
 
 def trace_lit(work: scenes.Workload, light: scenes.Light, metric: Metric = None, scene: Scene = None, out=None,

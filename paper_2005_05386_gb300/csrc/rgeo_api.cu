@@ -632,7 +632,8 @@ rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, c
       !(light->delta > 0.f))
     return fail(RGEO_EINVAL, "rgeo_trace_lit: light position, h, tol and delta must be finite, h, tol, delta > 0, "
                              "max_steps >= 1, iters >= 0");
-  for (int i = 0; i < 4; i++)
+  if (light->schedule != 0 && light->schedule != 1) return fail(RGEO_EINVAL, "rgeo_trace_lit: schedule must be 0 or 1");
+  for (int i = 0; i < 3; i++)
     if (light->reserved[i] != 0) return fail(RGEO_EINVAL, "rgeo_trace_lit: reserved fields must be zero");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   rgeo::TraceParams p = make_params(metric, scene, camera, width, height, h, max_steps, integrator,
@@ -652,6 +653,7 @@ rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, c
   l.delta = light->delta;
   l.lit = lit;
   l.list_steps = p.cull_masks ? list_steps_for(metric->d, light->h) : 0;
+  l.per_lane = light->schedule;
   cudaError_t e = cudaMemsetAsync(buf, 0, 16, st);
   if (e == cudaSuccess) e = rgeo::launch_trace(p, st);
   if (e == cudaSuccess) e = rgeo::launch_illuminate(p, l, st);

@@ -214,6 +214,7 @@ struct LightParams {
   float tol, delta;
   int32_t *lit;    // optional [N]
   int list_steps;  // steps a lane's culled-sum list serves at step h (0: a cell per right-hand side)
+  int per_lane;    // 1: each lane walks its own cell's list (no lockstep marches)
 };
 
 // Instance table of a batch passed by value in the kernel's parameter space (CUDA

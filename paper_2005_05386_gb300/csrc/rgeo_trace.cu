@@ -1108,6 +1108,40 @@ __device__ void finish_ray(const TraceParams &P, const float4 *sb, const float4 
   }
 }
 
+// The rare paths of a ray (its start and end, the search for the next support ball of a flat
+// advance), called out of line with OOL: k_trace does so for the isotropic graph metric, whose
+// hot loop's code and registers then stay small (4 % faster at 1080p / 64 bumps); the other
+// kinds and kernels take them inline (3 % faster for the twist metric).
+template <int MK>
+__device__ __noinline__ void init_ray_ool(const TraceParams &P, const float4 *sb, int pix, Ray &r) {
+  init_ray<MK>(P, sb, pix, r);
+}
+template <int MK>
+__device__ __noinline__ void finish_ray_ool(const TraceParams &P, const float4 *sb, const float4 *ss, const Ray &r,
+                                            int id, const HitRec &hr, F3 Ph, F3 D, float arc) {
+  finish_ray<MK>(P, sb, ss, r, id, hr, Ph, D, arc);
+}
+template <int MK>
+__device__ __noinline__ float support_entry_ool(const float4 *sb, int K, F3 x, F3 v) {
+  return support_entry<MK>(sb, K, x, v);
+}
+template <int MK, bool OOL>
+__device__ __forceinline__ void start_ray(const TraceParams &P, const float4 *sb, int pix, Ray &r) {
+  if constexpr (OOL) init_ray_ool<MK>(P, sb, pix, r);
+  else init_ray<MK>(P, sb, pix, r);
+}
+template <int MK, bool OOL>
+__device__ __forceinline__ void end_ray(const TraceParams &P, const float4 *sb, const float4 *ss, const Ray &r,
+                                        int id, const HitRec &hr, F3 Ph, F3 D, float arc = 0.f) {
+  if constexpr (OOL) finish_ray_ool<MK>(P, sb, ss, r, id, hr, Ph, D, arc);
+  else finish_ray<MK>(P, sb, ss, r, id, hr, Ph, D, arc);
+}
+template <int MK, bool OOL>
+__device__ __forceinline__ float next_support(const float4 *sb, int K, F3 x, F3 v) {
+  if constexpr (OOL) return support_entry_ool<MK>(sb, K, x, v);
+  else return support_entry<MK>(sb, K, x, v);
+}
+
 // Stage the bump table and the spheres in shared memory; returns the bump part size.
 template <int MK>
 __device__ __forceinline__ int stage_shared(const TraceParams &P, float4 *smem) {
@@ -1151,7 +1185,7 @@ __device__ __forceinline__ void refill(const TraceParams &P, const float4 *sb, b
 // (most of them run to the step budget together) instead of a fresh ray starting next to
 // rays far along their paths, which widens the warp's bump lists.  cnext / cend (the chunk's
 // next and end item) are the same on every lane.
-template <int MK>
+template <int MK, bool OOL = false>
 __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *sb, bool &active, bool &drained,
                                             Ray &r, unsigned &cnext, unsigned &cend) {
   const unsigned lane = threadIdx.x & 31u;
@@ -1176,7 +1210,7 @@ __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *
       const unsigned item = cnext + rank;
       int pix;
       if (item < P.n_items && item_pixel(P, item, pix)) {
-        init_ray<MK>(P, sb, pix, r);
+        start_ray<MK, OOL>(P, sb, pix, r);
         active = true;
       }
     }
@@ -1188,7 +1222,7 @@ __device__ __forceinline__ void refill_tile(const TraceParams &P, const float4 *
 // bs[i * blockDim.x], i = 0 .. r.nb) in one query; on a hit the ray finishes as the chord
 // that hit would have finished it tested alone (its step count, hit point and arc length).
 // Returns true on a hit.  The bundle is closed either way.
-template <int MK, int NB>
+template <int MK, int NB, bool OOL = false>
 __device__ __noinline__ bool bundle_flush(const TraceParams &P, const float4 *sb, const float4 *ss, Ray &r,
                                           const float4 *bs) {
   HitRec hr;
@@ -1199,7 +1233,7 @@ __device__ __noinline__ bool bundle_flush(const TraceParams &P, const float4 *sb
     const float4 a = bs[j * stride], b = bs[(j + 1) * stride];
     const F3 A = f3(a.x, a.y, a.z), D = f3(b.x - a.x, b.y - a.y, b.z - a.z);
     r.steps -= r.nb - 1 - j;
-    finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, A), D, fmaf(hr.s - 1.f, P.h, b.w));
+    end_ray<MK, OOL>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, A), D, fmaf(hr.s - 1.f, P.h, b.w));
   }
   r.nb = 0;
   r.dleft = 0.f;
@@ -1213,7 +1247,7 @@ __device__ __noinline__ bool bundle_flush(const TraceParams &P, const float4 *sb
 // moves.  Returns false when the ray finished (its pixel is written) or the lane holds no
 // ray (cx.part false; such lanes call only when CONV, to join the warp's sums; with CONV
 // every lane of the warp calls together).
-template <int MK, bool CONV = Converged<MK>::value, int NB = 1>
+template <int MK, bool CONV = Converged<MK>::value, int NB = 1, bool OOL = false>
 __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb, const float4 *ss,
                                          const SumCtx &cx, Ray &r, F3 &a1, bool inside,
                                          const float4 *bs = nullptr) {
@@ -1222,15 +1256,15 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
   bool moved = false, finished = false;
   const bool flat = MK != MK_TWIST && MK != MK_LOCAL && P.skippable && !inside;
   if (NB > 1 && cx.part && r.nb > 0 && (flat || r.steps >= P.max_steps))
-    finished = bundle_flush<MK, NB>(P, sb, ss, r, bs);
+    finished = bundle_flush<MK, NB, OOL>(P, sb, ss, r, bs);
   if (cx.part && !finished && flat) {
-    const float t = support_entry<MK>(sb, P.K, x, v);
+    const float t = next_support<MK, OOL>(sb, P.K, x, v);
     HitRec hr;
     if (scene_hit(P, ss, x, v, t, hr)) {
-      finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v, r.arc + hr.s);
+      end_ray<MK, OOL>(P, sb, ss, r, hr.id, hr, axpy(hr.s, v, x), v, r.arc + hr.s);
       finished = true;
     } else if (isinf(t)) {
-      finish_ray<MK>(P, sb, ss, r, RGEO_ID_MISS, hr, x, v);
+      end_ray<MK, OOL>(P, sb, ss, r, RGEO_ID_MISS, hr, x, v);
       finished = true;
     } else {
       for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], t * comp(v, c));
@@ -1256,7 +1290,7 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
   if (r.steps >= P.max_steps) {
     HitRec hr;
     hr.id = -1;
-    finish_ray<MK>(P, sb, ss, r, RGEO_ID_BUDGET, hr, x, v);
+    end_ray<MK, OOL>(P, sb, ss, r, RGEO_ID_BUDGET, hr, x, v);
     return false;
   }
   return true;
@@ -1268,7 +1302,7 @@ __device__ __forceinline__ bool pre_step(const TraceParams &P, const float4 *sb,
 // test opens a bundle instead; the next NB - 1 chords join it, and the bundle is tested
 // in one query (Section 4.1, many segments per query) once it holds NB chords (or before
 // a flat advance or the budget end, in pre_step).  Returns false on a hit.
-template <int MK, int NB = 1>
+template <int MK, int NB = 1, bool OOL = false>
 __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb, const float4 *ss,
                                           Ray &r, F3 dx, F3 dvel, float4 *bs = nullptr) {
   const F3 x = xhi(r);
@@ -1283,7 +1317,7 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
   const int stride = (int)blockDim.x;
   if (NB > 1 && r.nb > 0) {  // an open bundle: this chord joins it
     bs[(r.nb + 1) * stride] = make_float4(xn.x, xn.y, xn.z, r.arc);
-    if (++r.nb == NB) return !bundle_flush<MK, NB>(P, sb, ss, r, bs);
+    if (++r.nb == NB) return !bundle_flush<MK, NB, OOL>(P, sb, ss, r, bs);
     return true;
   }
   if (P.safe_skip) {
@@ -1307,7 +1341,7 @@ __device__ __forceinline__ bool post_step(const TraceParams &P, const float4 *sb
   }
   HitRec hr;
   if (scene_hit(P, ss, x, D, 1.f, hr)) {
-    finish_ray<MK>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, x), D, fmaf(hr.s - 1.f, P.h, r.arc));
+    end_ray<MK, OOL>(P, sb, ss, r, hr.id, hr, axpy(hr.s, D, x), D, fmaf(hr.s - 1.f, P.h, r.arc));
     return false;
   }
   return true;
@@ -1385,8 +1419,8 @@ __device__ __forceinline__ void pack_dense_pairs(const float4 *sb, int K, float4
 // isotropic graph metric every lane runs every evaluation of the bump sums (a lane without
 // a ray joins with empty masks), so that the warp can build its pair list together.
 // COUNT false (a launch without work counters) leaves the per-lane counts unread, so the
-// compiler drops them.
-template <int MK, int INTEG, int MINB, int NB, bool COUNT = true>
+// compiler drops them.  OOL takes a ray's rare paths out of line (start_ray).
+template <int MK, int INTEG, int MINB, int NB, bool COUNT = true, bool OOL = is_iso(MK)>
 __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK>(P, smem);
@@ -1402,6 +1436,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   float4 *const bs = lists + trace_lists_float4(MK, P) + threadIdx.x;
   const float4 ghdr = P.cull_masks ? __ldg(P.cull_hdr) : make_float4(0.f, 0.f, 0.f, 0.f);
   constexpr bool conv = Converged<MK>::value;
+  constexpr bool ool = OOL;
   WorkCount evals;
   bool active = false, drained = false;
   Ray r;
@@ -1409,7 +1444,7 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
   unsigned cnext = 0u, cend = 0u;
   for (;;) {
     const bool held = active;
-    refill_tile<MK>(P, sb, active, drained, r, cnext, cend);
+    refill_tile<MK, ool>(P, sb, active, drained, r, cnext, cend);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     if (!amask) {
       if (drained) break;
@@ -1420,12 +1455,12 @@ __global__ void __launch_bounds__(128, MINB) k_trace(const TraceParams P) {
     bool inside = true;
     F3 a1 = accel<MK, true>(P, sb, SumCtx{ghdr, &wl, active, &evals}, xhi(r), vhi(r), inside);
     const bool go =
-        pre_step<MK, Converged<MK>::value, NB>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside, bs);
+        pre_step<MK, Converged<MK>::value, NB, ool>(P, sb, ss, SumCtx{ghdr, &wl, active, &evals}, r, a1, inside, bs);
     if (!go) active = false;
     if (conv ? !__any_sync(0xffffffffu, go) : !go) continue;
     F3 dx, dvel;
     step_increments<MK, INTEG>(P, sb, SumCtx{ghdr, &wl, go, &evals}, xhi(r), vhi(r), a1, dx, dvel);
-    if (go) active = post_step<MK, NB>(P, sb, ss, r, dx, dvel, bs);
+    if (go) active = post_step<MK, NB, ool>(P, sb, ss, r, dx, dvel, bs);
     ++wl.age;
   }
   if (COUNT) evals.flush(P);
@@ -1771,6 +1806,223 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
     P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
                             to_u8(P.albedo[3 * obj + 2] * inten), 255);
     if (LP.lit) LP.lit[p] = lit ? 1 : 0;
+  }
+  if (P.bump_evals) atomicAdd(P.bump_evals, evals.evals);
+  if (P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
+}
+
+// The same illumination with the warp's light geodesics marched in lockstep, for isotropic
+// truncated bumps with a cull grid: every iteration advances each lane's current march by one
+// step, and the warp sums the bumps of one list together (the union of the marching lanes' cull
+// cells, packed in pairs and kept for LP.list_steps steps, as k_trace does), so the lanes read
+// each pair once by broadcast instead of walking their own cells apart.  A lane whose march has
+// ended waits for the other two of its group; the group then takes the decision and update of
+// k_illuminate and starts its next three marches, or ends its solve (lane 0 then marches the
+// shadow geodesic).  Each march takes the steps of shoot: the lists hold every bump that is
+// nonzero at a lane's stage points, in the order of the dense sums, so every pixel is the same
+// bit for bit as with k_illuminate.
+template <int INTEG>
+__global__ void __launch_bounds__(128, 4) k_illuminate_sl(const TraceParams P, const LightParams LP) {
+  extern __shared__ float4 smem[];
+  const int nb4 = stage_shared<MK_GRAPH_SL>(P, smem);
+  const float4 *sb = smem;
+  const float4 *ss = smem + nb4;
+  WarpLists wl = warp_lists(true, smem + nb4 + (P.nodes ? 0 : P.S));
+  const float4 ghdr = __ldg(P.cull_hdr);
+  const unsigned lane = threadIdx.x & 31u, grp = lane / 3u, role = lane - 3u * grp;
+  const unsigned base = 3u * min(grp, kIllumGroups - 1u);  // the group's lane 0 (lanes 30, 31: none)
+  const unsigned item = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kIllumGroups + grp;
+  const size_t N = (size_t)P.W * P.H;
+  int p = 0, id = -1;
+  if (grp < kIllumGroups && item < P.n_items && item_pixel(P, item, p)) {
+    id = P.id[p];
+    if (id < 0 && role == 0 && LP.lit) LP.lit[p] = 0;
+  }
+  constexpr int kMarch = 0, kWait = 1, kDone = 2;
+  int phase = id >= 0 ? kMarch : kDone;
+  const F3 L = f3(LP.L[0], LP.L[1], LP.L[2]);
+  F3 n = f3(0.f, 0.f, 1.f), q = f3(0.f, 0.f, 0.f), d0 = f3(0.f, 0.f, 1.f), b1 = d0, b2 = d0;
+  if (phase == kMarch) {
+    const F3 Ph = f3(P.hit[p], P.hit[N + p], P.hit[2 * N + p]);
+    n = f3(P.hit_nrm[p], P.hit_nrm[N + p], P.hit_nrm[2 * N + p]);
+    q = axpy(1e-3f, n, Ph);
+    d0 = normalize(L - q);
+    int ax = 0;  // e1 across the axis least aligned with d0 (lowest index on ties), e2 = d0 x e1
+    if (fabsf(d0.y) < fabsf(d0.x)) ax = 1;
+    if (fabsf(d0.z) < fabsf(ax == 0 ? d0.x : d0.y)) ax = 2;
+    b1 = normalize(cross(f3(ax == 0 ? 1.f : 0.f, ax == 1 ? 1.f : 0.f, ax == 2 ? 1.f : 0.f), d0));
+    b2 = cross(d0, b1);
+  }
+  float al = 0.f, be = 0.f;
+  int k = 0;
+  bool lit = false, shadow = false, ok = false, blocked = false, fresh = false;
+  F3 u = d0, ud = d0, e = f3(0.f, 0.f, 0.f);
+  Ray r;
+  ray_clear(r);
+  WorkCount evals, w;  // the lane's counts; those of its current march (counted if the solve uses it)
+  // starts this lane's march from q in the Euclidean direction d (shoot's first lines)
+  auto start = [&](F3 d) {
+    ud = rsqrtf(metric_dd<MK_GRAPH_SL>(P, sb, q, d)) * d;
+    for (int c = 0; c < 3; c++) {
+      r.xh[c] = comp(q, c);
+      r.xl[c] = 0.f;
+      r.vh[c] = comp(ud, c);
+      r.vl[c] = 0.f;
+    }
+    r.steps = 0;
+    blocked = false;
+    fresh = true;
+    phase = kMarch;
+  };
+  // the shaded colour of the hit (lane 0 of its group)
+  auto finish = [&](float cosg) {
+    const int obj = id < P.S ? id : P.S;
+    const float inten = lit ? fmaf(0.9f, cosg, 0.1f) : 0.1f;
+    P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
+                            to_u8(P.albedo[3 * obj + 2] * inten), 255);
+    if (LP.lit) LP.lit[p] = lit ? 1 : 0;
+    phase = kDone;
+  };
+  if (phase == kMarch) start(normalize(axpy(role == 2u ? LP.delta : 0.f, b2, axpy(role == 1u ? LP.delta : 0.f, b1, d0))));
+  float cosg = 0.f;
+  for (;;) {
+    // the decision of every group whose three marches have ended (k_illuminate's, in its order)
+    const unsigned waiting = __ballot_sync(0xffffffffu, phase == kWait);
+    const bool ready = phase == kWait && ((waiting >> base) & 7u) == 7u;
+    if (__any_sync(0xffffffffu, ready)) {
+      F3 eg[3];
+      bool okg[3];
+      for (unsigned j = 0; j < 3u; ++j) {
+        eg[j] = f3(__shfl_sync(0xffffffffu, e.x, base + j), __shfl_sync(0xffffffffu, e.y, base + j),
+                   __shfl_sync(0xffffffffu, e.z, base + j));
+        okg[j] = __shfl_sync(0xffffffffu, ok ? 1 : 0, base + j) != 0;
+      }
+      if (ready) {
+        const bool conv = okg[0] && sqrtf(dot(eg[0], eg[0])) <= LP.tol;
+        const bool more = okg[0] && !conv && k != LP.iters;
+        if (role == 0u || (more && (role == 1u || okg[1]))) {
+          evals.evals += w.evals;
+          evals.slots += w.slots;
+        }
+        w = WorkCount{};
+        bool next = false;
+        if (okg[0]) {
+          u = ud;
+          if (conv) {
+            lit = true;
+          } else if (more && okg[1] && okg[2]) {
+            const F3 J0 = (1.f / LP.delta) * (eg[1] - eg[0]);
+            const F3 J1 = (1.f / LP.delta) * (eg[2] - eg[0]);
+            const float A00 = dot(J0, J0), A01 = dot(J0, J1), A11 = dot(J1, J1);
+            const float r0 = -dot(J0, eg[0]), r1 = -dot(J1, eg[0]);
+            const float det = A00 * A11 - A01 * A01;
+            if (det > 1e-12f * (A00 * A11)) {
+              float s0 = (r0 * A11 - r1 * A01) / det, s1 = (A00 * r1 - A01 * r0) / det;
+              const float sn = sqrtf(s0 * s0 + s1 * s1);
+              if (sn > 0.25f) {
+                s0 *= 0.25f / sn;
+                s1 *= 0.25f / sn;
+              }
+              al += s0;
+              be += s1;
+              next = true;
+            }
+          }
+        }
+        if (next) {
+          ++k;
+          const float aa = role == 1u ? al + LP.delta : al, bb = role == 2u ? be + LP.delta : be;
+          start(normalize(axpy(bb, b2, axpy(aa, b1, d0))));
+        } else if (role != 0u) {
+          phase = kDone;
+        } else {
+          if (lit) {
+            cosg = dot(n, u) * rsqrtf(metric_inv_nn<MK_GRAPH_SL>(P, sb, q, n));
+            if (!(cosg > 0.f)) lit = false;
+          }
+          if (lit) {
+            shadow = true;
+            start(normalize(axpy(be, b2, axpy(al, b1, d0))));
+          } else {
+            finish(cosg);
+          }
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, phase == kDone)) break;
+    // one step of every lane's march, the warp's sums together
+    const bool marching = phase == kMarch;
+    WorkCount *wc = marching && !shadow ? &w : &evals;
+    step_list_refresh(P, sb, wl, ghdr, marching, fresh, xhi(r));
+    fresh = false;
+    bool inside = true;
+    F3 x = xhi(r);
+    const F3 v = vhi(r);
+    F3 a1 = accel<MK_GRAPH_SL, true>(P, sb, SumCtx{ghdr, &wl, marching, wc}, x, v, inside);
+    bool ended = false, moved = false;
+    if (marching && P.skippable && !inside) {
+      // straight line x + t v: closest approach to L at tL, next support ball at te
+      const float te = support_entry<MK_GRAPH_SL>(sb, P.K, x, v);
+      const F3 wv = L - x;
+      const float tL = fmaxf(dot(wv, v) / dot(v, v), 0.f);
+      const float tend = fminf(tL, te);
+      HitRec hr;
+      if (shadow && tend > 0.f && scene_hit(P, ss, x, v, tend, hr)) {
+        blocked = true;
+        ok = ended = true;
+      } else if (tL <= te) {
+        e = axpy(tL, v, x) - L;
+        ok = ended = true;
+      } else {
+        for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], te * comp(v, c));
+        x = xhi(r);
+        moved = true;
+      }
+    }
+    if (__any_sync(0xffffffffu, moved)) {
+      // the advance left the list's reach: list afresh at every marching lane's position
+      if (wl.np >= 0) step_list(P, sb, wl, ghdr, marching && !ended, x);
+      bool dummy;
+      const F3 am = accel<MK_GRAPH_SL, false>(P, sb, SumCtx{ghdr, &wl, moved, wc}, x, v, dummy);
+      if (moved) a1 = am;
+    }
+    if (marching && !ended && r.steps >= P.max_steps) {
+      ok = false;
+      ended = true;
+    }
+    const bool go = marching && !ended;
+    if (__any_sync(0xffffffffu, go)) {
+      F3 dx, dvel;
+      step_increments<MK_GRAPH_SL, INTEG>(P, sb, SumCtx{ghdr, &wl, go, wc}, x, v, a1, dx, dvel);
+      if (go) {
+        for (int c = 0; c < 3; c++) {
+          comp_add(r.xh[c], r.xl[c], comp(dx, c));
+          comp_add(r.vh[c], r.vl[c], comp(dvel, c));
+        }
+        ++r.steps;
+        const F3 D = xhi(r) - x;
+        const float t = dot(L - x, D) / dot(D, D);
+        HitRec hr;
+        if (t < 1.f) {  // the closest approach lies on this segment (or the distance grows)
+          const float tc = fmaxf(t, 0.f);
+          if (shadow && tc > 0.f && scene_hit(P, ss, x, D, tc, hr)) blocked = true;
+          else e = axpy(tc, D, x) - L;
+          ok = ended = true;
+        } else if (shadow && scene_hit(P, ss, x, D, 1.f, hr)) {
+          blocked = true;
+          ok = ended = true;
+        }
+      }
+    }
+    ++wl.age;
+    if (ended) {
+      if (shadow) {  // lane 0's shadow geodesic
+        if (blocked) lit = false;
+        finish(cosg);
+      } else {
+        phase = kWait;
+      }
+    }
   }
   if (P.bump_evals) atomicAdd(P.bump_evals, evals.evals);
   if (P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
@@ -2543,12 +2795,23 @@ cudaError_t launch_one(const TraceParams &p, cudaStream_t st) {
   // CTAs per SM at least (the register budget): 7 (72 registers) for the isotropic graph metric,
   // measured 3 % faster at 1080p than 6 and 8; 5 (102) for the local-map jet and on request
   constexpr int kDefaultMinb = is_iso(MK) ? 7 : 6;
-  // the step-list kernel without work counters when the launch asks for none (1 % faster at 1080p)
+  // The step-list kernel without work counters when the launch asks for none (1 % faster at
+  // 1080p).  The isotropic graph metric with an affine or quadratic part (the lattice
+  // showcases) takes its rays' rare paths inline in RK4: 6 % faster there, where out of line
+  // is 4 % faster at 1080p / 64 bumps.
   const bool count = p.bump_evals != nullptr || p.bump_slots != nullptr;
-  void (*kern)(const TraceParams) =
-      bundle ? (five ? k_trace<MK, 0, 5, kBundle> : k_trace<MK, 0, kDefaultMinb, kBundle>)
-             : (five ? k_trace<MK, INTEG, 5, 1>
-                     : (count ? k_trace<MK, INTEG, kDefaultMinb, 1> : k_trace<MK, INTEG, kDefaultMinb, 1, MK != MK_GRAPH_SL>));
+  const bool inl = INTEG == 0 && (p.has_affine || p.has_quad);
+  void (*kern)(const TraceParams) = k_trace<MK, INTEG, kDefaultMinb, 1>;
+  if (bundle) {
+    kern = five ? k_trace<MK, 0, 5, kBundle> : k_trace<MK, 0, kDefaultMinb, kBundle>;
+  } else if (five) {
+    kern = k_trace<MK, INTEG, 5, 1>;
+  } else if constexpr (MK == MK_GRAPH_SL) {
+    if (inl) kern = count ? k_trace<MK, 0, kDefaultMinb, 1, true, false> : k_trace<MK, 0, kDefaultMinb, 1, false, false>;
+    else if (!count) kern = k_trace<MK, INTEG, kDefaultMinb, 1, false>;
+  } else if constexpr (MK == MK_GRAPH_ISO) {
+    if (inl) kern = k_trace<MK, 0, kDefaultMinb, 1, true, false>;
+  }
   if (x2) kern = k_trace_x2<INTEG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -2729,16 +2992,38 @@ cudaError_t launch_illuminate_t(const TraceParams &p, const LightParams &l, cuda
   return cudaGetLastError();
 }
 
+// The lockstep form: the warps' lists after the bump table and the spheres.
+template <int INTEG>
+cudaError_t launch_illuminate_sl(const TraceParams &p, const LightParams &l, cudaStream_t st) {
+  const size_t smem =
+      (size_t)(table_float4s(p.kind, p.K, 0) + (p.nodes ? 0 : p.S) + kWarpsPerBlock * lists_float4(true)) *
+      sizeof(float4);
+  if (smem > 227u * 1024u) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_illuminate_sl<INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned per_block = 4u * kIllumGroups;  // hits per 128-thread block
+  const unsigned blocks = (p.n_items + per_block - 1u) / per_block;
+  if (blocks == 0) return cudaSuccess;
+  k_illuminate_sl<INTEG><<<blocks, 128, smem, st>>>(p, l);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_illuminate(const TraceParams &p0, const LightParams &l, cudaStream_t st) {
   if (!p0.hit_nrm) return cudaErrorInvalidValue;
-  TraceParams p = p0;  // keeps the cull grid: the light geodesics sum per lane (accel_lane)
+  TraceParams p = p0;  // keeps the cull grid
   p.h = l.h;
   p.max_steps = l.max_steps;
   p.energy = 0;
-  p.step_lists = 0;  // the light geodesics keep per-lane lists (shoot), for l.list_steps steps
   p.list_steps = l.list_steps;
   const int mk = p.kind == 2 ? MK_LOCAL : (p.kind == 1 ? MK_TWIST : (p.aniso ? MK_GRAPH_ANISO : MK_GRAPH_ISO));
   const bool rk4 = p.integrator == 0;
+  // isotropic truncated bumps with lists that serve several steps: the warp's marches in lockstep
+  // over shared lists (k_illuminate_sl), unless the light asks for one list walk per lane
+  if (mk == MK_GRAPH_ISO && p.cull_masks && l.list_steps > 0 && p.K <= kStepListBumps && !l.per_lane) {
+    p.step_lists = 1;
+    return rk4 ? launch_illuminate_sl<0>(p, l, st) : launch_illuminate_sl<1>(p, l, st);
+  }
+  p.step_lists = 0;  // the light geodesics keep per-lane lists (shoot), for l.list_steps steps
   if (mk == MK_LOCAL) return rk4 ? launch_illuminate_t<MK_LOCAL, 0>(p, l, st) : launch_illuminate_t<MK_LOCAL, 1>(p, l, st);
   if (mk == MK_TWIST) return rk4 ? launch_illuminate_t<MK_TWIST, 0>(p, l, st) : launch_illuminate_t<MK_TWIST, 1>(p, l, st);
   if (mk == MK_GRAPH_ANISO)

@@ -92,13 +92,15 @@ class Camera:
 class Light:
     """A point light for Riemannian illumination and the parameters of the geodesic shooting
     toward it: step h and step budget of each light geodesic, at most ``iters`` Gauss-Newton
-    steps to a miss of at most ``tol`` scene units, forward-difference step ``delta``."""
+    steps to a miss of at most ``tol`` scene units, forward-difference step ``delta``;
+    ``schedule`` 1 has each lane march on its own instead of the warp's lockstep marches."""
     pos: tuple = (1.0, 6.0, -3.0)
     h: float = 0.005
     max_steps: int = 4000
     iters: int = 24
     tol: float = 1e-4
     delta: float = 1e-3
+    schedule: int = 0
 
 
 @dataclasses.dataclass

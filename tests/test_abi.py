@@ -159,7 +159,7 @@ def test_trace_lit_validation(rg):
     assert st == rg.RGEO_EINVAL and "light" in rg.rgeo_last_error()
     good = scenes.Light()
     bad = [dict(h=0.0), dict(h=float("nan")), dict(pos=(0.0, float("inf"), 0.0)), dict(max_steps=0),
-           dict(iters=-1), dict(tol=0.0), dict(delta=-1e-3)]
+           dict(iters=-1), dict(tol=0.0), dict(delta=-1e-3), dict(schedule=2), dict(schedule=-1)]
     for kw in bad:
         import dataclasses
         lt = rg.light_struct(dataclasses.replace(good, **kw))
