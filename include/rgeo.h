@@ -280,7 +280,7 @@ rgeo_status rgeo_trace_host(const rgeo_metric *metric, const rgeo_scene *scene,
  * out->bump_evals, when given, receives the bump terms of the view rays and of the light
  * geodesics together.
  * `lit` (DEVICE [W*H] int32, may be NULL) receives 1 for lit hits, else 0.
- * Allocates a work counter and a 12-byte-per-pixel normal buffer with
+ * Allocates work counters and a 16-byte-per-pixel buffer (normals, hit list) with
  * cudaMallocAsync on the stream.  Asynchronous on the stream.
  * Errors: those of rgeo_trace, and RGEO_EINVAL for a NULL light, a non-finite
  * light position, h or tol or delta not finite or <= 0, max_steps < 1, iters < 0,

@@ -641,7 +641,7 @@ rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, c
   p.fog = 0.f;
   const size_t N = (size_t)width * height;
   char *buf = nullptr;
-  RGEO_CUDA(cudaMallocAsync((void **)&buf, 16 + 12 * N, st), "rgeo_trace_lit: work counter and normals");
+  RGEO_CUDA(cudaMallocAsync((void **)&buf, 16 + 16 * N, st), "rgeo_trace_lit: work counters, normals, hit list");
   p.counter = (uint32_t *)buf;
   p.hit_nrm = (float *)(buf + 16);
   rgeo::LightParams l;
@@ -654,6 +654,9 @@ rgeo_status rgeo_trace_lit(const rgeo_metric *metric, const rgeo_scene *scene, c
   l.lit = lit;
   l.list_steps = p.cull_masks ? list_steps_for(metric->d, light->h) : 0;
   l.per_lane = light->schedule;
+  l.n_hits = (uint32_t *)buf + 1;
+  l.hit_next = (uint32_t *)buf + 2;
+  l.hits = (int32_t *)(buf + 16 + 12 * N);
   cudaError_t e = cudaMemsetAsync(buf, 0, 16, st);
   if (e == cudaSuccess) e = rgeo::launch_trace(p, st);
   if (e == cudaSuccess) e = rgeo::launch_illuminate(p, l, st);

@@ -215,6 +215,9 @@ struct LightParams {
   int32_t *lit;    // optional [N]
   int list_steps;  // steps a lane's culled-sum list serves at step h (0: a cell per right-hand side)
   int per_lane;    // 1: each lane walks its own cell's list (no lockstep marches)
+  int32_t *hits;       // [N] the hit list of the lockstep form (k_hit_list)
+  uint32_t *n_hits;    // its length
+  uint32_t *hit_next;  // the next unclaimed entry
 };
 
 // Instance table of a batch passed by value in the kernel's parameter space (CUDA

@@ -1811,6 +1811,23 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
   if (P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
 }
 
+// The hits of a finished trace, listed in queue-item order (the trace's 32-pixel tiles) one
+// warp's worth at a time: LP.hits[0 .. *LP.n_hits).  Pixels without a hit are marked unlit.
+__global__ void __launch_bounds__(128) k_hit_list(const TraceParams P, const LightParams LP) {
+  const unsigned item = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31u;
+  int p = 0;
+  bool hit = false;
+  if (item < P.n_items && item_pixel(P, item, p)) {
+    hit = P.id[p] >= 0;
+    if (!hit && LP.lit) LP.lit[p] = 0;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, hit);
+  unsigned first = 0;
+  if (lane == 0 && m) first = atomicAdd(LP.n_hits, (unsigned)__popc(m));
+  first = __shfl_sync(0xffffffffu, first, 0);
+  if (hit) LP.hits[first + (unsigned)__popc(m & ((1u << lane) - 1u))] = p;
+}
+
 // The same illumination with the warp's light geodesics marched in lockstep, for isotropic
 // truncated bumps with a cull grid: every iteration advances each lane's current march by one
 // step, and the warp sums the bumps of one list together (the union of the marching lanes' cull
@@ -1820,7 +1837,8 @@ __global__ void __launch_bounds__(128) k_illuminate(const TraceParams P, const L
 // k_illuminate and starts its next three marches, or ends its solve (lane 0 then marches the
 // shadow geodesic).  Each march takes the steps of shoot: the lists hold every bump that is
 // nonzero at a lane's stage points, in the order of the dense sums, so every pixel is the same
-// bit for bit as with k_illuminate.
+// bit for bit as with k_illuminate.  The grid is persistent: a warp takes the next ten hits of
+// the hit list (k_hit_list) once its ten solves have ended.
 template <int INTEG>
 __global__ void __launch_bounds__(128, 4) k_illuminate_sl(const TraceParams P, const LightParams LP) {
   extern __shared__ float4 smem[];
@@ -1831,196 +1849,203 @@ __global__ void __launch_bounds__(128, 4) k_illuminate_sl(const TraceParams P, c
   const float4 ghdr = __ldg(P.cull_hdr);
   const unsigned lane = threadIdx.x & 31u, grp = lane / 3u, role = lane - 3u * grp;
   const unsigned base = 3u * min(grp, kIllumGroups - 1u);  // the group's lane 0 (lanes 30, 31: none)
-  const unsigned item = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kIllumGroups + grp;
+  const unsigned n_hits = *LP.n_hits;
   const size_t N = (size_t)P.W * P.H;
-  int p = 0, id = -1;
-  if (grp < kIllumGroups && item < P.n_items && item_pixel(P, item, p)) {
-    id = P.id[p];
-    if (id < 0 && role == 0 && LP.lit) LP.lit[p] = 0;
-  }
-  constexpr int kMarch = 0, kWait = 1, kDone = 2;
-  int phase = id >= 0 ? kMarch : kDone;
-  const F3 L = f3(LP.L[0], LP.L[1], LP.L[2]);
-  F3 n = f3(0.f, 0.f, 1.f), q = f3(0.f, 0.f, 0.f), d0 = f3(0.f, 0.f, 1.f), b1 = d0, b2 = d0;
-  if (phase == kMarch) {
-    const F3 Ph = f3(P.hit[p], P.hit[N + p], P.hit[2 * N + p]);
-    n = f3(P.hit_nrm[p], P.hit_nrm[N + p], P.hit_nrm[2 * N + p]);
-    q = axpy(1e-3f, n, Ph);
-    d0 = normalize(L - q);
-    int ax = 0;  // e1 across the axis least aligned with d0 (lowest index on ties), e2 = d0 x e1
-    if (fabsf(d0.y) < fabsf(d0.x)) ax = 1;
-    if (fabsf(d0.z) < fabsf(ax == 0 ? d0.x : d0.y)) ax = 2;
-    b1 = normalize(cross(f3(ax == 0 ? 1.f : 0.f, ax == 1 ? 1.f : 0.f, ax == 2 ? 1.f : 0.f), d0));
-    b2 = cross(d0, b1);
-  }
-  float al = 0.f, be = 0.f;
-  int k = 0;
-  bool lit = false, shadow = false, ok = false, blocked = false, fresh = false;
-  F3 u = d0, ud = d0, e = f3(0.f, 0.f, 0.f);
-  Ray r;
-  ray_clear(r);
-  WorkCount evals, w;  // the lane's counts; those of its current march (counted if the solve uses it)
-  // starts this lane's march from q in the Euclidean direction d (shoot's first lines)
-  auto start = [&](F3 d) {
-    ud = rsqrtf(metric_dd<MK_GRAPH_SL>(P, sb, q, d)) * d;
-    for (int c = 0; c < 3; c++) {
-      r.xh[c] = comp(q, c);
-      r.xl[c] = 0.f;
-      r.vh[c] = comp(ud, c);
-      r.vl[c] = 0.f;
-    }
-    r.steps = 0;
-    blocked = false;
-    fresh = true;
-    phase = kMarch;
-  };
-  // the shaded colour of the hit (lane 0 of its group)
-  auto finish = [&](float cosg) {
-    const int obj = id < P.S ? id : P.S;
-    const float inten = lit ? fmaf(0.9f, cosg, 0.1f) : 0.1f;
-    P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
-                            to_u8(P.albedo[3 * obj + 2] * inten), 255);
-    if (LP.lit) LP.lit[p] = lit ? 1 : 0;
-    phase = kDone;
-  };
-  if (phase == kMarch) start(normalize(axpy(role == 2u ? LP.delta : 0.f, b2, axpy(role == 1u ? LP.delta : 0.f, b1, d0))));
-  float cosg = 0.f;
+  WorkCount evals;  // the lane's counts over all of its solves
   for (;;) {
-    // the decision of every group whose three marches have ended (k_illuminate's, in its order)
-    const unsigned waiting = __ballot_sync(0xffffffffu, phase == kWait);
-    const bool ready = phase == kWait && ((waiting >> base) & 7u) == 7u;
-    if (__any_sync(0xffffffffu, ready)) {
-      F3 eg[3];
-      bool okg[3];
-      for (unsigned j = 0; j < 3u; ++j) {
-        eg[j] = f3(__shfl_sync(0xffffffffu, e.x, base + j), __shfl_sync(0xffffffffu, e.y, base + j),
-                   __shfl_sync(0xffffffffu, e.z, base + j));
-        okg[j] = __shfl_sync(0xffffffffu, ok ? 1 : 0, base + j) != 0;
+    unsigned first = 0;
+    if (lane == 0) first = atomicAdd(LP.hit_next, kIllumGroups);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= n_hits) break;
+    int p = 0, id = -1;
+    if (grp < kIllumGroups && first + grp < n_hits) {
+      p = LP.hits[first + grp];
+      id = P.id[p];
+    }
+    constexpr int kMarch = 0, kWait = 1, kDone = 2;
+    int phase = id >= 0 ? kMarch : kDone;
+    const F3 L = f3(LP.L[0], LP.L[1], LP.L[2]);
+    F3 n = f3(0.f, 0.f, 1.f), q = f3(0.f, 0.f, 0.f), d0 = f3(0.f, 0.f, 1.f), b1 = d0, b2 = d0;
+    if (phase == kMarch) {
+      const F3 Ph = f3(P.hit[p], P.hit[N + p], P.hit[2 * N + p]);
+      n = f3(P.hit_nrm[p], P.hit_nrm[N + p], P.hit_nrm[2 * N + p]);
+      q = axpy(1e-3f, n, Ph);
+      d0 = normalize(L - q);
+      int ax = 0;  // e1 across the axis least aligned with d0 (lowest index on ties), e2 = d0 x e1
+      if (fabsf(d0.y) < fabsf(d0.x)) ax = 1;
+      if (fabsf(d0.z) < fabsf(ax == 0 ? d0.x : d0.y)) ax = 2;
+      b1 = normalize(cross(f3(ax == 0 ? 1.f : 0.f, ax == 1 ? 1.f : 0.f, ax == 2 ? 1.f : 0.f), d0));
+      b2 = cross(d0, b1);
+    }
+    float al = 0.f, be = 0.f;
+    int k = 0;
+    bool lit = false, shadow = false, ok = false, blocked = false, fresh = false;
+    F3 u = d0, ud = d0, e = f3(0.f, 0.f, 0.f);
+    Ray r;
+    ray_clear(r);
+    WorkCount w;  // the counts of the lane's current march (counted if the solve uses it)
+    // starts this lane's march from q in the Euclidean direction d (shoot's first lines)
+    auto start = [&](F3 d) {
+      ud = rsqrtf(metric_dd<MK_GRAPH_SL>(P, sb, q, d)) * d;
+      for (int c = 0; c < 3; c++) {
+        r.xh[c] = comp(q, c);
+        r.xl[c] = 0.f;
+        r.vh[c] = comp(ud, c);
+        r.vl[c] = 0.f;
       }
-      if (ready) {
-        const bool conv = okg[0] && sqrtf(dot(eg[0], eg[0])) <= LP.tol;
-        const bool more = okg[0] && !conv && k != LP.iters;
-        if (role == 0u || (more && (role == 1u || okg[1]))) {
-          evals.evals += w.evals;
-          evals.slots += w.slots;
+      r.steps = 0;
+      blocked = false;
+      fresh = true;
+      phase = kMarch;
+    };
+    // the shaded colour of the hit (lane 0 of its group)
+    auto finish = [&](float cosg) {
+      const int obj = id < P.S ? id : P.S;
+      const float inten = lit ? fmaf(0.9f, cosg, 0.1f) : 0.1f;
+      P.rgba[p] = make_uchar4(to_u8(P.albedo[3 * obj] * inten), to_u8(P.albedo[3 * obj + 1] * inten),
+                              to_u8(P.albedo[3 * obj + 2] * inten), 255);
+      if (LP.lit) LP.lit[p] = lit ? 1 : 0;
+      phase = kDone;
+    };
+    if (phase == kMarch) start(normalize(axpy(role == 2u ? LP.delta : 0.f, b2, axpy(role == 1u ? LP.delta : 0.f, b1, d0))));
+    float cosg = 0.f;
+    for (;;) {
+      // the decision of every group whose three marches have ended (k_illuminate's, in its order)
+      const unsigned waiting = __ballot_sync(0xffffffffu, phase == kWait);
+      const bool ready = phase == kWait && ((waiting >> base) & 7u) == 7u;
+      if (__any_sync(0xffffffffu, ready)) {
+        F3 eg[3];
+        bool okg[3];
+        for (unsigned j = 0; j < 3u; ++j) {
+          eg[j] = f3(__shfl_sync(0xffffffffu, e.x, base + j), __shfl_sync(0xffffffffu, e.y, base + j),
+                     __shfl_sync(0xffffffffu, e.z, base + j));
+          okg[j] = __shfl_sync(0xffffffffu, ok ? 1 : 0, base + j) != 0;
         }
-        w = WorkCount{};
-        bool next = false;
-        if (okg[0]) {
-          u = ud;
-          if (conv) {
-            lit = true;
-          } else if (more && okg[1] && okg[2]) {
-            const F3 J0 = (1.f / LP.delta) * (eg[1] - eg[0]);
-            const F3 J1 = (1.f / LP.delta) * (eg[2] - eg[0]);
-            const float A00 = dot(J0, J0), A01 = dot(J0, J1), A11 = dot(J1, J1);
-            const float r0 = -dot(J0, eg[0]), r1 = -dot(J1, eg[0]);
-            const float det = A00 * A11 - A01 * A01;
-            if (det > 1e-12f * (A00 * A11)) {
-              float s0 = (r0 * A11 - r1 * A01) / det, s1 = (A00 * r1 - A01 * r0) / det;
-              const float sn = sqrtf(s0 * s0 + s1 * s1);
-              if (sn > 0.25f) {
-                s0 *= 0.25f / sn;
-                s1 *= 0.25f / sn;
+        if (ready) {
+          const bool conv = okg[0] && sqrtf(dot(eg[0], eg[0])) <= LP.tol;
+          const bool more = okg[0] && !conv && k != LP.iters;
+          if (role == 0u || (more && (role == 1u || okg[1]))) {
+            evals.evals += w.evals;
+            evals.slots += w.slots;
+          }
+          w = WorkCount{};
+          bool next = false;
+          if (okg[0]) {
+            u = ud;
+            if (conv) {
+              lit = true;
+            } else if (more && okg[1] && okg[2]) {
+              const F3 J0 = (1.f / LP.delta) * (eg[1] - eg[0]);
+              const F3 J1 = (1.f / LP.delta) * (eg[2] - eg[0]);
+              const float A00 = dot(J0, J0), A01 = dot(J0, J1), A11 = dot(J1, J1);
+              const float r0 = -dot(J0, eg[0]), r1 = -dot(J1, eg[0]);
+              const float det = A00 * A11 - A01 * A01;
+              if (det > 1e-12f * (A00 * A11)) {
+                float s0 = (r0 * A11 - r1 * A01) / det, s1 = (A00 * r1 - A01 * r0) / det;
+                const float sn = sqrtf(s0 * s0 + s1 * s1);
+                if (sn > 0.25f) {
+                  s0 *= 0.25f / sn;
+                  s1 *= 0.25f / sn;
+                }
+                al += s0;
+                be += s1;
+                next = true;
               }
-              al += s0;
-              be += s1;
-              next = true;
+            }
+          }
+          if (next) {
+            ++k;
+            const float aa = role == 1u ? al + LP.delta : al, bb = role == 2u ? be + LP.delta : be;
+            start(normalize(axpy(bb, b2, axpy(aa, b1, d0))));
+          } else if (role != 0u) {
+            phase = kDone;
+          } else {
+            if (lit) {
+              cosg = dot(n, u) * rsqrtf(metric_inv_nn<MK_GRAPH_SL>(P, sb, q, n));
+              if (!(cosg > 0.f)) lit = false;
+            }
+            if (lit) {
+              shadow = true;
+              start(normalize(axpy(be, b2, axpy(al, b1, d0))));
+            } else {
+              finish(cosg);
             }
           }
         }
-        if (next) {
-          ++k;
-          const float aa = role == 1u ? al + LP.delta : al, bb = role == 2u ? be + LP.delta : be;
-          start(normalize(axpy(bb, b2, axpy(aa, b1, d0))));
-        } else if (role != 0u) {
-          phase = kDone;
-        } else {
-          if (lit) {
-            cosg = dot(n, u) * rsqrtf(metric_inv_nn<MK_GRAPH_SL>(P, sb, q, n));
-            if (!(cosg > 0.f)) lit = false;
-          }
-          if (lit) {
-            shadow = true;
-            start(normalize(axpy(be, b2, axpy(al, b1, d0))));
-          } else {
-            finish(cosg);
-          }
-        }
       }
-    }
-    if (__all_sync(0xffffffffu, phase == kDone)) break;
-    // one step of every lane's march, the warp's sums together
-    const bool marching = phase == kMarch;
-    WorkCount *wc = marching && !shadow ? &w : &evals;
-    step_list_refresh(P, sb, wl, ghdr, marching, fresh, xhi(r));
-    fresh = false;
-    bool inside = true;
-    F3 x = xhi(r);
-    const F3 v = vhi(r);
-    F3 a1 = accel<MK_GRAPH_SL, true>(P, sb, SumCtx{ghdr, &wl, marching, wc}, x, v, inside);
-    bool ended = false, moved = false;
-    if (marching && P.skippable && !inside) {
-      // straight line x + t v: closest approach to L at tL, next support ball at te
-      const float te = support_entry<MK_GRAPH_SL>(sb, P.K, x, v);
-      const F3 wv = L - x;
-      const float tL = fmaxf(dot(wv, v) / dot(v, v), 0.f);
-      const float tend = fminf(tL, te);
-      HitRec hr;
-      if (shadow && tend > 0.f && scene_hit(P, ss, x, v, tend, hr)) {
-        blocked = true;
-        ok = ended = true;
-      } else if (tL <= te) {
-        e = axpy(tL, v, x) - L;
-        ok = ended = true;
-      } else {
-        for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], te * comp(v, c));
-        x = xhi(r);
-        moved = true;
-      }
-    }
-    if (__any_sync(0xffffffffu, moved)) {
-      // the advance left the list's reach: list afresh at every marching lane's position
-      if (wl.np >= 0) step_list(P, sb, wl, ghdr, marching && !ended, x);
-      bool dummy;
-      const F3 am = accel<MK_GRAPH_SL, false>(P, sb, SumCtx{ghdr, &wl, moved, wc}, x, v, dummy);
-      if (moved) a1 = am;
-    }
-    if (marching && !ended && r.steps >= P.max_steps) {
-      ok = false;
-      ended = true;
-    }
-    const bool go = marching && !ended;
-    if (__any_sync(0xffffffffu, go)) {
-      F3 dx, dvel;
-      step_increments<MK_GRAPH_SL, INTEG>(P, sb, SumCtx{ghdr, &wl, go, wc}, x, v, a1, dx, dvel);
-      if (go) {
-        for (int c = 0; c < 3; c++) {
-          comp_add(r.xh[c], r.xl[c], comp(dx, c));
-          comp_add(r.vh[c], r.vl[c], comp(dvel, c));
-        }
-        ++r.steps;
-        const F3 D = xhi(r) - x;
-        const float t = dot(L - x, D) / dot(D, D);
+      if (__all_sync(0xffffffffu, phase == kDone)) break;
+      // one step of every lane's march, the warp's sums together
+      const bool marching = phase == kMarch;
+      WorkCount *wc = marching && !shadow ? &w : &evals;
+      step_list_refresh(P, sb, wl, ghdr, marching, fresh, xhi(r));
+      fresh = false;
+      bool inside = true;
+      F3 x = xhi(r);
+      const F3 v = vhi(r);
+      F3 a1 = accel<MK_GRAPH_SL, true>(P, sb, SumCtx{ghdr, &wl, marching, wc}, x, v, inside);
+      bool ended = false, moved = false;
+      if (marching && P.skippable && !inside) {
+        // straight line x + t v: closest approach to L at tL, next support ball at te
+        const float te = support_entry<MK_GRAPH_SL>(sb, P.K, x, v);
+        const F3 wv = L - x;
+        const float tL = fmaxf(dot(wv, v) / dot(v, v), 0.f);
+        const float tend = fminf(tL, te);
         HitRec hr;
-        if (t < 1.f) {  // the closest approach lies on this segment (or the distance grows)
-          const float tc = fmaxf(t, 0.f);
-          if (shadow && tc > 0.f && scene_hit(P, ss, x, D, tc, hr)) blocked = true;
-          else e = axpy(tc, D, x) - L;
-          ok = ended = true;
-        } else if (shadow && scene_hit(P, ss, x, D, 1.f, hr)) {
+        if (shadow && tend > 0.f && scene_hit(P, ss, x, v, tend, hr)) {
           blocked = true;
           ok = ended = true;
+        } else if (tL <= te) {
+          e = axpy(tL, v, x) - L;
+          ok = ended = true;
+        } else {
+          for (int c = 0; c < 3; c++) comp_add(r.xh[c], r.xl[c], te * comp(v, c));
+          x = xhi(r);
+          moved = true;
         }
       }
-    }
-    ++wl.age;
-    if (ended) {
-      if (shadow) {  // lane 0's shadow geodesic
-        if (blocked) lit = false;
-        finish(cosg);
-      } else {
-        phase = kWait;
+      if (__any_sync(0xffffffffu, moved)) {
+        // the advance left the list's reach: list afresh at every marching lane's position
+        if (wl.np >= 0) step_list(P, sb, wl, ghdr, marching && !ended, x);
+        bool dummy;
+        const F3 am = accel<MK_GRAPH_SL, false>(P, sb, SumCtx{ghdr, &wl, moved, wc}, x, v, dummy);
+        if (moved) a1 = am;
+      }
+      if (marching && !ended && r.steps >= P.max_steps) {
+        ok = false;
+        ended = true;
+      }
+      const bool go = marching && !ended;
+      if (__any_sync(0xffffffffu, go)) {
+        F3 dx, dvel;
+        step_increments<MK_GRAPH_SL, INTEG>(P, sb, SumCtx{ghdr, &wl, go, wc}, x, v, a1, dx, dvel);
+        if (go) {
+          for (int c = 0; c < 3; c++) {
+            comp_add(r.xh[c], r.xl[c], comp(dx, c));
+            comp_add(r.vh[c], r.vl[c], comp(dvel, c));
+          }
+          ++r.steps;
+          const F3 D = xhi(r) - x;
+          const float t = dot(L - x, D) / dot(D, D);
+          HitRec hr;
+          if (t < 1.f) {  // the closest approach lies on this segment (or the distance grows)
+            const float tc = fmaxf(t, 0.f);
+            if (shadow && tc > 0.f && scene_hit(P, ss, x, D, tc, hr)) blocked = true;
+            else e = axpy(tc, D, x) - L;
+            ok = ended = true;
+          } else if (shadow && scene_hit(P, ss, x, D, 1.f, hr)) {
+            blocked = true;
+            ok = ended = true;
+          }
+        }
+      }
+      ++wl.age;
+      if (ended) {
+        if (shadow) {  // lane 0's shadow geodesic
+          if (blocked) lit = false;
+          finish(cosg);
+        } else {
+          phase = kWait;
+        }
       }
     }
   }
@@ -2999,12 +3024,23 @@ cudaError_t launch_illuminate_sl(const TraceParams &p, const LightParams &l, cud
       (size_t)(table_float4s(p.kind, p.K, 0) + (p.nodes ? 0 : p.S) + kWarpsPerBlock * lists_float4(true)) *
       sizeof(float4);
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_illuminate_sl<INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (p.n_items == 0) return cudaSuccess;
+  k_hit_list<<<(p.n_items + 127u) / 128u, 128, 0, st>>>(p, l);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const unsigned per_block = 4u * kIllumGroups;  // hits per 128-thread block
-  const unsigned blocks = (p.n_items + per_block - 1u) / per_block;
-  if (blocks == 0) return cudaSuccess;
-  k_illuminate_sl<INTEG><<<blocks, 128, smem, st>>>(p, l);
+  e = cudaFuncSetAttribute(k_illuminate_sl<INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_illuminate_sl<INTEG>, 128, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // persistent: as many blocks as fit, at most one per 40 queue items
+  long long blocks = (long long)sms * per_sm;
+  const long long need = ((long long)p.n_items + 4 * kIllumGroups - 1) / (4 * kIllumGroups);
+  if (blocks > need) blocks = need;
+  k_illuminate_sl<INTEG><<<(unsigned)blocks, 128, smem, st>>>(p, l);
   return cudaGetLastError();
 }
 
