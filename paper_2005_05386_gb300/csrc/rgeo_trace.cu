@@ -1844,8 +1844,9 @@ __global__ void __launch_bounds__(128) k_hit_list(const TraceParams P, const Lig
 // shadow geodesic).  Each march takes the steps of shoot: the lists hold every bump that is
 // nonzero at a lane's stage points, in the order of the dense sums, so every pixel is the same
 // bit for bit as with k_illuminate.  The grid is persistent: a warp takes the next ten hits of
-// the hit list (k_hit_list) once its ten solves have ended.
-template <int INTEG>
+// the hit list (k_hit_list) once its ten solves have ended.  COUNT false (no work counters
+// asked for) leaves the counts unread, so the compiler drops them.
+template <int INTEG, bool COUNT = true>
 __global__ void __launch_bounds__(128, 4) k_illuminate_sl(const TraceParams P, const LightParams LP) {
   extern __shared__ float4 smem[];
   const int nb4 = stage_shared<MK_GRAPH_SL>(P, smem);
@@ -2055,8 +2056,8 @@ __global__ void __launch_bounds__(128, 4) k_illuminate_sl(const TraceParams P, c
       }
     }
   }
-  if (P.bump_evals) atomicAdd(P.bump_evals, evals.evals);
-  if (P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
+  if (COUNT && P.bump_evals) atomicAdd(P.bump_evals, evals.evals);
+  if (COUNT && P.bump_slots) atomicAdd(P.bump_slots, evals.slots);
 }
 
 #endif
@@ -3034,19 +3035,22 @@ cudaError_t launch_illuminate_sl(const TraceParams &p, const LightParams &l, cud
   k_hit_list<<<(p.n_items + 127u) / 128u, 128, 0, st>>>(p, l);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_illuminate_sl<INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // without work counters when the launch asks for none
+  void (*kern)(const TraceParams, const LightParams) =
+      p.bump_evals || p.bump_slots ? k_illuminate_sl<INTEG, true> : k_illuminate_sl<INTEG, false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_illuminate_sl<INTEG>, 128, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // persistent: as many blocks as fit, at most one per 40 queue items
   long long blocks = (long long)sms * per_sm;
   const long long need = ((long long)p.n_items + 4 * kIllumGroups - 1) / (4 * kIllumGroups);
   if (blocks > need) blocks = need;
-  k_illuminate_sl<INTEG><<<(unsigned)blocks, 128, smem, st>>>(p, l);
+  kern<<<(unsigned)blocks, 128, smem, st>>>(p, l);
   return cudaGetLastError();
 }
 
